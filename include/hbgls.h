@@ -1,0 +1,164 @@
+/*
+ * hbgls.h -- C ABI of the GB300 harmonic balance (HB) Galerkin/least-squares Navier-Stokes library.
+ *
+ * The library evaluates and solves the discrete HB-GLS equations of arXiv 2411.14315 (Sec. 2):
+ * incompressible Newtonian flow on P1 tetrahedra with equal-order velocity and pressure, the solution
+ * represented by its values at N = 2 n_h + 1 equally spaced instances of one period T (Eq. upghharm),
+ * coupled in time by H = E^-1 Omega E (Eq. NS-harm), stabilised by GLS with the per-instance tau of
+ * Eq. (tau), and solved by pseudo-time-stepped Newton-Krylov iterations (Eqs. NR, splitK; Sec. 2.3).
+ *
+ * Conventions (every entry point):
+ *  - Every function returns an hb_status; HB_OK is 0.  Nothing throws across the ABI.  On failure,
+ *    hb_last_error() returns a thread-local message describing the last error of this thread.
+ *  - The caller owns every array it passes.  Host arrays are read (or written) during the call only
+ *    and are never retained; the library copies what it keeps.  `_dev` entry points take device
+ *    pointers owned by the caller, valid for the duration of the work queued on the given stream.
+ *  - Instance layout ("instances"): double (or float) [n_nodes][4][N], fields u1, u2, u3, p, the N
+ *    instances t_n = n T / N contiguous.  Harmonic layout ("harmonics"): double
+ *    [n_nodes][4][2 n_h + 1], per field (a0, a1, b1, ..., a_nh, b_nh) of the real series
+ *    f(t) = a0 + sum_k a_k cos(k w t) + b_k sin(k w t), w = 2 pi / T.
+ *  - Waveform arguments `a`, `b` have n_h + 1 entries (b[0] ignored) in the same real series; they are
+ *    the truncated Fourier data of a boundary condition (Eq. upgh_def).
+ *  - Units are the caller's (the paper uses cgs).
+ *  - A problem is bound to one device and one stream; calls on one problem must not overlap in time
+ *    from several host threads.
+ */
+#ifndef HBGLS_H
+#define HBGLS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HB_OK = 0,
+    HB_ERR_INVALID_ARG = 1,   /* null pointer, size or tag out of range */
+    HB_ERR_MESH = 2,          /* degenerate tetrahedron, face not on the mesh, index out of range */
+    HB_ERR_CUDA = 3,          /* a CUDA runtime call failed (message carries the CUDA error string) */
+    HB_ERR_OOM = 4,           /* device allocation failed */
+    HB_ERR_NOT_CONVERGED = 5, /* solve stopped at its iteration limit; best state kept */
+    HB_ERR_NAN = 6,           /* residual became NaN/Inf; last finite state kept */
+    HB_ERR_TIMEOUT = 7,       /* reserved: a bounded device wait gave up */
+    HB_ERR_STATE = 8          /* call out of order (e.g. solve before any inflow is set) */
+} hb_status;
+
+typedef struct hb_problem hb_problem;    /* opaque; owned by the library, freed by hb_destroy */
+
+/* Mesh of linear tetrahedra (Sec. 2.3, P1 interpolation).  Boundary triangles carry a tag: tag 0 is a
+ * no-slip wall (u = 0, stationary walls as in Sec. 2.1); positive tags are caps whose condition is set
+ * by hb_set_inflow / hb_set_outlet_*; a cap with no condition is traction free (h = 0).
+ * The local vertex order of each tetrahedron is significant: tau's metric is that of the map to the
+ * parent tetrahedron with local vertex 0 at its origin (Eq. tau). */
+typedef struct {
+    int64_t n_nodes, n_tets, n_faces;
+    const double *xyz;        /* [n_nodes][3] */
+    const int32_t *tets;      /* [n_tets][4], 0-based node ids */
+    const int32_t *faces;     /* [n_faces][3] boundary triangles, any orientation */
+    const int32_t *face_tag;  /* [n_faces] */
+} hb_mesh;
+
+/* Create a problem (Eq. NS-time data): density rho > 0, dynamic viscosity mu > 0, period T > 0 and
+ * n_h >= 0 retained harmonics, N = 2 n_h + 1 <= 31 instances.  Builds the element patches, geometry
+ * and boundary data on `device`; `cuda_stream` (a cudaStream_t, may be NULL for a library-owned
+ * stream) orders all later device work of this problem.  Errors: INVALID_ARG, MESH, CUDA, OOM. */
+hb_status hb_create(const hb_mesh *mesh, double rho, double mu, double period_T, int n_h, int device,
+                    void *cuda_stream, hb_problem **out);
+hb_status hb_destroy(hb_problem *p);
+const char *hb_last_error(void);
+
+/* Dirichlet inflow on cap `tag` (Eq. NS-time, u = g on Gamma_g): g(x, t) = profile(x) q(t) with
+ * q the waveform (a, b).  profile: [n_nodes][3] (read at the cap's nodes only), or NULL for the
+ * parabolic profile at unit flow rate: (2 / (pi R^2)) max(0, 1 - r^2 / R^2) along the inward normal,
+ * R the largest in-plane distance of a cap node from the cap's area-weighted centroid.  Nodes shared
+ * with a wall keep u = 0; nodes shared by two inflow caps take the values of the cap set last (a
+ * repeated call for the same tag replaces it in place).  Errors: INVALID_ARG (tag 0 or unknown). */
+hb_status hb_set_inflow(hb_problem *p, int tag, const double *profile, const double *a, const double *b);
+/* Outlet at fixed pressure P(t) (Sec. 3 uses steady values): traction h = -P on cap `tag`. */
+hb_status hb_set_outlet_pressure(hb_problem *p, int tag, const double *a, const double *b);
+/* Resistance outlet -- an extension the paper leaves out of scope (Sec. 3 and Sec. 4):
+ * h_n = -(P_d(t_n) + R Q_n), Q_n the outflow rate through the cap at instance n. */
+hb_status hb_set_outlet_resistance(hb_problem *p, int tag, double R, const double *a, const double *b);
+/* Backflow stabilisation coefficient beta in [0, 1] on every Neumann face (Sec. 2.3; default 0.2). */
+hb_status hb_set_backflow(hb_problem *p, double beta);
+
+/* Initial state from harmonics ([n_nodes][4][2 n_h + 1]) or NULL for the default: Dirichlet values
+ * built in (Sec. 2.3), zero interior velocity, pressure at the mean outlet level.  Dirichlet values
+ * always overwrite the velocity of Dirichlet nodes. */
+hb_status hb_set_initial(hb_problem *p, const double *harmonics);
+/* Same, from instance values [n_nodes][4][N]. */
+hb_status hb_set_instances(hb_problem *p, const double *instances);
+
+typedef struct {
+    int precision;            /* 0: every kernel FP64 ("plain FP64"); 1: mixed -- FP32 Jv, FP64 residual,
+                                 Arnoldi, norms and update */
+    double rtol;              /* stop when ||r|| <= rtol ||r0|| and ||dy|| <= 10 rtol ||y||            */
+    double switch_rtol;       /* pseudo-time phase (paper tangent) until ||r|| / ||r0|| < switch_rtol
+                                 (Sec. 2.3 uses 1e-3 as its whole convergence criterion); then exact
+                                 Newton                                                               */
+    double gmres_rtol_pseudo; /* GMRES tolerance in the pseudo phase (paper: 0.03)                     */
+    double gmres_rtol_newton; /* GMRES tolerance in the Newton phase                                   */
+    int gmres_restart;        /* Krylov basis size m (<= 200)                                          */
+    int max_gmres;            /* GMRES iteration cap per linear solve                                  */
+    int max_steps;            /* outer (pseudo + Newton) step cap                                      */
+    double dt_pseudo;         /* pseudo time step; <= 0 selects the CFL rule of Sec. 2.3               */
+    double cfl;               /* CFL number of that rule (1)                                           */
+    int use_learned;          /* 1: start from the learned warm start if one is attached               */
+    int verbose;              /* print one line per outer step to stderr                               */
+} hb_solve_opts;
+
+typedef struct {
+    int steps, newton_steps, gmres_iters, jv_calls, residual_calls;
+    double res0, res_final, seconds, dt_pseudo;
+    int status;               /* hb_status of the solve */
+} hb_report;
+
+hb_status hb_default_opts(hb_solve_opts *o);
+/* Solve for the periodic state (Eq. NR with the split tangent of Eq. splitK and pseudo time stepping).
+ * The state of the problem is updated in place; NOT_CONVERGED / NAN keep the best finite state. */
+hb_status hb_solve(hb_problem *p, const hb_solve_opts *o, hb_report *rep);
+/* Harmonic coefficients of the current state (u* = E u, Eq. upghdft; reconstruction of Sec. 3.2). */
+hb_status hb_get_harmonics(hb_problem *p, double *out);
+/* Instance values of the current state [n_nodes][4][N]. */
+hb_status hb_get_instances(hb_problem *p, double *out);
+
+/* ---- hot-path entry points (host buffers; copies in and out are part of the call) ---------------- */
+
+/* Residual r(y) of Eq. (Rmc) at instance values y (Dirichlet values taken from y as given): momentum
+ * rows of Dirichlet nodes are 0.  precision 0 = FP64 kernels, 1 = FP32 kernels (inputs rounded). */
+hb_status hb_residual(hb_problem *p, const double *y, double *r, int precision);
+/* Jacobian-vector product at state y along v.  kind 0: the paper's tangent (P + C, Eqs. ptangent,
+ * K_mat, ctangent, F_mat) with U and tau frozen at y; kind 1: the exact derivative of hb_residual.
+ * shift adds shift * M v on the velocity rows (pseudo time term, Sec. 2.3: shift = c1 rho / dt).
+ * Dirichlet velocity rows return v (identity); v's Dirichlet velocity entries are treated as 0. */
+hb_status hb_jv(hb_problem *p, const double *y, const double *v, double *jv, int kind, int precision,
+                double shift);
+/* Jacobi diagonal: diag(P) + shift M_AA (Sec. 2.3); 1 on Dirichlet velocity rows. */
+hb_status hb_jacobi_diag(hb_problem *p, const double *y, double *d, int precision, double shift);
+
+/* ---- device-pointer twins: all arrays on the problem's device, of type double (precision 0) or float
+ * (precision 1), in instance layout; work is queued on `stream` (NULL: the problem's stream) and the
+ * call returns without synchronising.  Outputs must not alias inputs. */
+hb_status hb_residual_dev(hb_problem *p, const void *y, void *r, int precision, void *stream);
+hb_status hb_jv_dev(hb_problem *p, const void *y, const void *v, void *jv, int kind, int precision,
+                    double shift, void *stream);
+hb_status hb_jacobi_diag_dev(hb_problem *p, const void *y, void *d, int precision, double shift,
+                             void *stream);
+
+/* ---- introspection ------------------------------------------------------------------------------ */
+typedef struct {
+    int64_t n_nodes, n_tets, n_faces, n_dirichlet_nodes, n_neumann_faces;
+    int n_h, N, n_patches32, n_patches64, patch_nodes_max32, patch_elems_max32;
+    int64_t device_bytes;
+    double h_char;            /* edge of the regular tetrahedron of mean element volume (Sec. 2.3) */
+} hb_info;
+hb_status hb_get_info(hb_problem *p, hb_info *info);
+/* Number of kernel launches queued by this problem since creation (all entry points). */
+int64_t hb_launch_count(const hb_problem *p);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HBGLS_H */

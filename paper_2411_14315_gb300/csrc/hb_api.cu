@@ -1,0 +1,1206 @@
+// Host runtime and C ABI of libhbgls: problem set-up (face orientation, Morton-ordered element patches,
+// geometry), boundary data, operator dispatch and the pseudo-time Newton-GMRES solve
+// (arXiv 2411.14315, Sec. 2.3: Eq. NR, Eq. splitK, pseudo time stepping, Jacobi + GMRES).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "hb_internal.cuh"
+#include "hbgls.h"
+
+using namespace hb;
+
+namespace {
+
+thread_local std::string g_err;
+
+hb_status fail(hb_status st, const std::string &msg) {
+    g_err = msg;
+    return st;
+}
+
+#define HB_CUDA(expr)                                                                                   \
+    do {                                                                                                \
+        cudaError_t _e = (expr);                                                                        \
+        if (_e != cudaSuccess)                                                                          \
+            return fail(_e == cudaErrorMemoryAllocation ? HB_ERR_OOM : HB_ERR_CUDA,                     \
+                        std::string(#expr) + ": " + cudaGetErrorString(_e));                            \
+    } while (0)
+
+#define HB_TRY(expr)                                                                                    \
+    do {                                                                                                \
+        hb_status _s = (expr);                                                                          \
+        if (_s != HB_OK) return _s;                                                                     \
+    } while (0)
+
+#define HB_LAUNCHED(p, k)                                                                               \
+    do {                                                                                                \
+        (p)->launches += (k);                                                                           \
+        cudaError_t _e = cudaGetLastError();                                                            \
+        if (_e != cudaSuccess) return fail(HB_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(_e)); \
+    } while (0)
+
+constexpr double kC1 = 1.5;   // generalized-alpha with rho_inf = 0 (Sec. 2.3)
+
+template <typename T>
+struct DBuf {
+    T *p = nullptr;
+    size_t n = 0;
+    DBuf() = default;
+    DBuf(const DBuf &) = delete;
+    DBuf &operator=(const DBuf &) = delete;
+    ~DBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+};
+
+template <typename T>
+struct PatchSetDev {
+    int P = 0, nl_max = 0, ep_max = 0;
+    DBuf<int> eptr, nptr, nodes;
+    DBuf<uint32_t> lconn;
+    DBuf<T> geom;
+};
+
+struct Inflow {
+    int tag;
+    std::vector<double> profile;   // [n_nodes][3] or empty = parabolic
+    std::vector<double> coef;      // real series (a0, a1, b1, ...)
+};
+
+struct Outlet {
+    int tag;
+    double R;                      // 0 for a pressure outlet
+    std::vector<double> coef;
+};
+
+}  // namespace
+
+struct hb_problem {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int64_t n_nodes = 0, n_tets = 0, n_faces = 0;
+    int n_h = 0, N = 1;
+    double rho = 1, mu = 1, T = 1, omega = 1, beta = 0.2;
+    std::vector<double> xyz;
+    std::vector<int32_t> tets, faces, face_tag;
+    std::vector<double> fnormal, farea;
+    double vol_mean = 0, vol_min = 0;
+    PatchSetDev<float> ps32;
+    PatchSetDev<double> ps64;
+    DBuf<double> d_xyz;
+    DBuf<int> d_tets_ord;
+    DBuf<double> H64;
+    DBuf<float> H32;
+    // boundary data
+    std::vector<Inflow> inflows;
+    std::vector<Outlet> outlets;
+    bool bc_dirty = true;
+    int n_dir = 0, n_nf = 0, n_out = 0;
+    bool has_res = false;
+    double u_c = 0;
+    std::vector<double> level;       // mean outlet pressure per instance
+    DBuf<int> d_dir_nodes, d_dir_wave, d_nf_nodes, d_nf_out;
+    DBuf<uint8_t> d_flag;
+    DBuf<double> d_dir_prof, d_g, d_W, d_coef;
+    DBuf<double> d_nf_geo64, d_hbase64, d_R64, d_Q64;
+    DBuf<float> d_nf_geo32, d_hbase32, d_R32, d_Q32;
+    // state and work
+    DBuf<double> y;
+    bool y_set = false;
+    DBuf<double> w64a, w64b;
+    DBuf<float> w32a, w32b, w32c;
+    DBuf<double> scratch, small;
+    int64_t launches = 0;
+    int64_t dev_bytes = 0;
+    int sm_count = 148;
+    // Krylov storage (lazily sized)
+    int km = 0;
+    DBuf<double> kV, kz64, kdx, kdiag, kres, ktmp, kh;
+    DBuf<float> kz32, kw32, ky32, kdiag32;
+};
+
+namespace {
+
+template <typename T>
+hb_status dalloc(hb_problem *p, DBuf<T> &b, size_t n) {
+    if (b.n >= n && b.p) return HB_OK;
+    if (b.p) {
+        p->dev_bytes -= int64_t(b.n * sizeof(T));
+        b.release();
+    }
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMalloc(&b.p, n * sizeof(T));
+    if (e != cudaSuccess) {
+        b.p = nullptr;
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? HB_ERR_OOM : HB_ERR_CUDA,
+                    std::string("cudaMalloc(") + std::to_string(n * sizeof(T)) + "): " + cudaGetErrorString(e));
+    }
+    b.n = n;
+    p->dev_bytes += int64_t(n * sizeof(T));
+    return HB_OK;
+}
+
+// set-up copies are synchronous: the host vectors are usually temporaries
+template <typename T>
+hb_status upload(hb_problem *p, DBuf<T> &b, const std::vector<T> &h) {
+    HB_TRY(dalloc(p, b, h.size()));
+    if (!h.empty()) {
+        HB_CUDA(cudaMemcpyAsync(b.p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, p->stream));
+        HB_CUDA(cudaStreamSynchronize(p->stream));
+    }
+    return HB_OK;
+}
+
+inline uint64_t spread3(uint64_t x) {  // 21 bits -> every third bit
+    x &= 0x1fffff;
+    x = (x | x << 32) & 0x1f00000000ffffULL;
+    x = (x | x << 16) & 0x1f0000ff0000ffULL;
+    x = (x | x << 8) & 0x100f00f00f00f00fULL;
+    x = (x | x << 4) & 0x10c30c30c30c30c3ULL;
+    x = (x | x << 2) & 0x1249249249249249ULL;
+    return x;
+}
+
+// Greedy patches along the Morton order: close a patch when it would exceed NL nodes or EP elements.
+struct HostPatches {
+    std::vector<int> eptr, nptr, nodes;
+    std::vector<uint32_t> lconn;
+    int nl_max = 0, ep_max = 0;
+};
+
+HostPatches build_patches(const std::vector<int32_t> &tets_ord, int64_t n_tets, int64_t n_nodes, int NL, int EP) {
+    HostPatches hp;
+    std::vector<int> stamp(size_t(n_nodes), -1), local(size_t(n_nodes), 0);
+    hp.eptr.push_back(0);
+    hp.nptr.push_back(0);
+    hp.lconn.resize(size_t(n_tets));
+    int pid = 0, cur_nodes = 0, cur_elems = 0;
+    for (int64_t e = 0; e < n_tets; ++e) {
+        const int32_t *t = &tets_ord[size_t(4 * e)];
+        int fresh = 0;
+        for (int a = 0; a < 4; ++a) {
+            bool dup = false;
+            for (int b = 0; b < a; ++b) dup |= (t[b] == t[a]);
+            if (!dup && stamp[t[a]] != pid) ++fresh;
+        }
+        if (cur_elems > 0 && (cur_nodes + fresh > NL || cur_elems + 1 > EP)) {
+            hp.eptr.push_back(int(e));
+            hp.nptr.push_back(int(hp.nodes.size()));
+            hp.nl_max = std::max(hp.nl_max, cur_nodes);
+            hp.ep_max = std::max(hp.ep_max, cur_elems);
+            ++pid;
+            cur_nodes = 0;
+            cur_elems = 0;
+        }
+        uint32_t packed = 0;
+        for (int a = 0; a < 4; ++a) {
+            if (stamp[t[a]] != pid) {
+                stamp[t[a]] = pid;
+                local[t[a]] = cur_nodes++;
+                hp.nodes.push_back(t[a]);
+            }
+            packed |= uint32_t(local[t[a]]) << (8 * a);
+        }
+        hp.lconn[size_t(e)] = packed;
+        ++cur_elems;
+    }
+    hp.eptr.push_back(int(n_tets));
+    hp.nptr.push_back(int(hp.nodes.size()));
+    hp.nl_max = std::max(hp.nl_max, cur_nodes);
+    hp.ep_max = std::max(hp.ep_max, cur_elems);
+    return hp;
+}
+
+int choose_nl(int N, size_t ts, size_t budget) {
+    const size_t per_node = size_t(in_fields(MODE_JVE) + out_fields(MODE_JVE)) * N * ts + 4;
+    const size_t per_elem = kGeomStride * ts + 4;
+    const size_t fixed = size_t(N) * N * ts + 256;
+    long nl = long((budget - fixed) / (per_node + 3 * per_elem));
+    return int(std::max(8L, std::min(128L, nl)));
+}
+
+template <typename T>
+hb_status make_patchset(hb_problem *p, PatchSetDev<T> &ps, const std::vector<int32_t> &tets_ord, size_t budget) {
+    const int NL = choose_nl(p->N, sizeof(T), budget);
+    const int EP = 3 * NL;
+    HostPatches hp = build_patches(tets_ord, p->n_tets, p->n_nodes, NL, EP);
+    ps.P = int(hp.eptr.size()) - 1;
+    ps.nl_max = hp.nl_max;
+    ps.ep_max = hp.ep_max;
+    HB_TRY(upload(p, ps.eptr, hp.eptr));
+    HB_TRY(upload(p, ps.nptr, hp.nptr));
+    HB_TRY(upload(p, ps.nodes, hp.nodes));
+    HB_TRY(upload(p, ps.lconn, hp.lconn));
+    HB_TRY(dalloc(p, ps.geom, size_t(p->n_tets) * kGeomStride));
+    launch_geom<T>(p->d_xyz.p, p->d_tets_ord.p, int(p->n_tets), p->mu / p->rho, ps.geom.p, p->stream);
+    HB_LAUNCHED(p, 1);
+    HB_CUDA(cudaStreamSynchronize(p->stream));   // host vectors above are about to go out of scope
+    return HB_OK;
+}
+
+template <typename T>
+PatchSetDev<T> &patches(hb_problem *p);
+template <>
+PatchSetDev<float> &patches<float>(hb_problem *p) { return p->ps32; }
+template <>
+PatchSetDev<double> &patches<double>(hb_problem *p) { return p->ps64; }
+
+template <typename T>
+const T *Hmat(hb_problem *p);
+template <>
+const float *Hmat<float>(hb_problem *p) { return p->H32.p; }
+template <>
+const double *Hmat<double>(hb_problem *p) { return p->H64.p; }
+
+// ---------------------------------------------------------------------------------------------------
+// boundary data
+
+std::vector<double> real_series(const double *a, const double *b, int n_h) {
+    std::vector<double> c(size_t(2 * n_h + 1), 0.0);
+    c[0] = a[0];
+    for (int k = 1; k <= n_h; ++k) {
+        c[size_t(2 * k - 1)] = a[k];
+        c[size_t(2 * k)] = b[k];
+    }
+    return c;
+}
+
+// parabolic unit-flow profile on cap `tag` (definition in hbgls.h); returns per-node vectors
+void parabolic_profile(const hb_problem *p, int tag, std::vector<double> &prof) {
+    prof.assign(size_t(3 * p->n_nodes), 0.0);
+    double A = 0, c[3] = {0, 0, 0}, nrm[3] = {0, 0, 0};
+    std::vector<int> nodes;
+    for (int64_t f = 0; f < p->n_faces; ++f) {
+        if (p->face_tag[size_t(f)] != tag) continue;
+        const double S = p->farea[size_t(f)];
+        A += S;
+        for (int i = 0; i < 3; ++i) {
+            double m = 0;
+            for (int b = 0; b < 3; ++b) m += p->xyz[size_t(3 * p->faces[size_t(3 * f + b)] + i)] / 3.0;
+            c[i] += S * m;
+            nrm[i] += S * p->fnormal[size_t(3 * f + i)];
+        }
+        for (int b = 0; b < 3; ++b) nodes.push_back(p->faces[size_t(3 * f + b)]);
+    }
+    if (A <= 0) return;
+    double nn = std::sqrt(nrm[0] * nrm[0] + nrm[1] * nrm[1] + nrm[2] * nrm[2]);
+    for (int i = 0; i < 3; ++i) {
+        c[i] /= A;
+        nrm[i] /= nn;
+    }
+    std::sort(nodes.begin(), nodes.end());
+    nodes.erase(std::unique(nodes.begin(), nodes.end()), nodes.end());
+    std::vector<double> r2(nodes.size());
+    double R2 = 0;
+    for (size_t k = 0; k < nodes.size(); ++k) {
+        double d[3], dn = 0;
+        for (int i = 0; i < 3; ++i) {
+            d[i] = p->xyz[size_t(3 * nodes[k] + i)] - c[i];
+            dn += d[i] * nrm[i];
+        }
+        double s = 0;
+        for (int i = 0; i < 3; ++i) {
+            const double e = d[i] - dn * nrm[i];
+            s += e * e;
+        }
+        r2[k] = s;
+        R2 = std::max(R2, s);
+    }
+    const double scale = 2.0 / (M_PI * R2);
+    for (size_t k = 0; k < nodes.size(); ++k) {
+        const double v = scale * std::max(0.0, 1.0 - r2[k] / R2);
+        for (int i = 0; i < 3; ++i) prof[size_t(3 * nodes[k] + i)] = -v * nrm[i];
+    }
+}
+
+hb_status prepare_bc(hb_problem *p) {
+    if (!p->bc_dirty) return HB_OK;
+    const int N = p->N, M = 2 * p->n_h + 1;
+    const int64_t n = p->n_nodes;
+    std::vector<int> wave(size_t(n), -2);      // -2 free, -1 wall, >= 0 inflow index
+    std::vector<double> prof(size_t(3 * n), 0.0);
+    for (size_t k = 0; k < p->inflows.size(); ++k) {
+        const Inflow &in = p->inflows[k];
+        std::vector<double> pp;
+        const std::vector<double> *src = &in.profile;
+        if (in.profile.empty()) {
+            parabolic_profile(p, in.tag, pp);
+            src = &pp;
+        }
+        for (int64_t f = 0; f < p->n_faces; ++f) {
+            if (p->face_tag[size_t(f)] != in.tag) continue;
+            for (int b = 0; b < 3; ++b) {
+                const int nd = p->faces[size_t(3 * f + b)];   // the cap set last wins
+                wave[size_t(nd)] = int(k);
+                for (int i = 0; i < 3; ++i) prof[size_t(3 * nd + i)] = (*src)[size_t(3 * nd + i)];
+            }
+        }
+    }
+    for (int64_t f = 0; f < p->n_faces; ++f)
+        if (p->face_tag[size_t(f)] == 0)
+            for (int b = 0; b < 3; ++b) wave[size_t(p->faces[size_t(3 * f + b)])] = -1;
+    std::vector<int> dir_nodes, dir_wave;
+    std::vector<double> dir_prof;
+    std::vector<uint8_t> flag(size_t(n), 0);
+    for (int64_t a = 0; a < n; ++a) {
+        if (wave[size_t(a)] == -2) continue;
+        dir_nodes.push_back(int(a));
+        dir_wave.push_back(wave[size_t(a)] >= 0 ? wave[size_t(a)] : -1);
+        for (int i = 0; i < 3; ++i) dir_prof.push_back(wave[size_t(a)] >= 0 ? prof[size_t(3 * a + i)] : 0.0);
+        flag[size_t(a)] = 1;
+    }
+    // Neumann faces: every cap that is not an inflow (walls are Dirichlet)
+    std::vector<int> nf_nodes, nf_out;
+    std::vector<double> nf_geo;
+    for (int64_t f = 0; f < p->n_faces; ++f) {
+        const int tag = p->face_tag[size_t(f)];
+        if (tag == 0) continue;
+        bool is_in = false;
+        for (auto &in : p->inflows) is_in |= (in.tag == tag);
+        if (is_in) continue;
+        int o = -1;
+        for (size_t k = 0; k < p->outlets.size(); ++k)
+            if (p->outlets[k].tag == tag) o = int(k);
+        for (int b = 0; b < 3; ++b) nf_nodes.push_back(p->faces[size_t(3 * f + b)]);
+        nf_out.push_back(o);
+        for (int i = 0; i < 3; ++i) nf_geo.push_back(p->fnormal[size_t(3 * f + i)]);
+        nf_geo.push_back(p->farea[size_t(f)]);
+    }
+    p->n_dir = int(dir_nodes.size());
+    p->n_nf = int(nf_out.size());
+    p->n_out = int(p->outlets.size());
+    // waveforms: inflows first, then outlets
+    const int n_wave = int(p->inflows.size() + p->outlets.size());
+    std::vector<double> coef;
+    for (auto &in : p->inflows) coef.insert(coef.end(), in.coef.begin(), in.coef.end());
+    for (auto &o : p->outlets) coef.insert(coef.end(), o.coef.begin(), o.coef.end());
+    (void)M;
+    HB_TRY(upload(p, p->d_coef, coef));
+    HB_TRY(dalloc(p, p->d_W, size_t(std::max(1, n_wave * N))));
+    launch_sample_waveforms(p->d_coef.p, n_wave, p->n_h, N, p->T, p->d_W.p, p->stream);
+    HB_LAUNCHED(p, n_wave > 0 ? 1 : 0);
+    HB_TRY(upload(p, p->d_dir_nodes, dir_nodes));
+    HB_TRY(upload(p, p->d_dir_wave, dir_wave));
+    HB_TRY(upload(p, p->d_dir_prof, dir_prof));
+    HB_TRY(upload(p, p->d_flag, flag));
+    HB_TRY(dalloc(p, p->d_g, size_t(std::max(1, p->n_dir * 3 * N))));
+    launch_dirichlet_values(p->d_dir_nodes.p, p->d_dir_wave.p, p->d_dir_prof.p, p->n_dir, p->d_W.p, N, p->d_g.p,
+                            p->stream);
+    HB_LAUNCHED(p, p->n_dir > 0 ? 1 : 0);
+    HB_TRY(upload(p, p->d_nf_nodes, nf_nodes));
+    HB_TRY(upload(p, p->d_nf_out, nf_out));
+    HB_TRY(upload(p, p->d_nf_geo64, nf_geo));
+    std::vector<float> nf_geo32(nf_geo.begin(), nf_geo.end());
+    HB_TRY(upload(p, p->d_nf_geo32, nf_geo32));
+    std::vector<double> W(size_t(n_wave * N));
+    if (n_wave > 0) {
+        HB_CUDA(cudaMemcpyAsync(W.data(), p->d_W.p, W.size() * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+        HB_CUDA(cudaStreamSynchronize(p->stream));
+    }
+    const int n_in = int(p->inflows.size());
+    std::vector<double> hbase(size_t(std::max(1, p->n_out * N)), 0.0), R(size_t(std::max(1, p->n_out)), 0.0);
+    p->has_res = false;
+    p->level.assign(size_t(N), 0.0);
+    for (int o = 0; o < p->n_out; ++o) {
+        R[size_t(o)] = p->outlets[size_t(o)].R;
+        p->has_res |= (R[size_t(o)] != 0.0);
+        for (int t = 0; t < N; ++t) {
+            hbase[size_t(o * N + t)] = -W[size_t((n_in + o) * N + t)];
+            p->level[size_t(t)] += W[size_t((n_in + o) * N + t)] / p->n_out;
+        }
+    }
+    HB_TRY(upload(p, p->d_hbase64, hbase));
+    HB_TRY(upload(p, p->d_R64, R));
+    std::vector<float> hb32(hbase.begin(), hbase.end()), R32(R.begin(), R.end());
+    HB_TRY(upload(p, p->d_hbase32, hb32));
+    HB_TRY(upload(p, p->d_R32, R32));
+    HB_TRY(dalloc(p, p->d_Q64, size_t(std::max(1, p->n_out * N))));
+    HB_TRY(dalloc(p, p->d_Q32, size_t(std::max(1, p->n_out * N))));
+    // characteristic inlet velocity of the CFL rule: largest mean inflow speed over the instances
+    p->u_c = 0;
+    for (int k = 0; k < n_in; ++k) {
+        const Inflow &in = p->inflows[size_t(k)];
+        double A = 0, fl = 0;
+        for (int64_t f = 0; f < p->n_faces; ++f) {
+            if (p->face_tag[size_t(f)] != in.tag) continue;
+            const double S = p->farea[size_t(f)];
+            A += S;
+            for (int b = 0; b < 3; ++b) {
+                const int nd = p->faces[size_t(3 * f + b)];
+                if (wave[size_t(nd)] != k) continue;
+                double un = 0;
+                for (int i = 0; i < 3; ++i) un += prof[size_t(3 * nd + i)] * p->fnormal[size_t(3 * f + i)];
+                fl += S / 3.0 * std::fabs(un);
+            }
+        }
+        double qmax = 0;
+        for (int t = 0; t < N; ++t) qmax = std::max(qmax, std::fabs(W[size_t(k * N + t)]));
+        if (A > 0) p->u_c = std::max(p->u_c, fl * qmax / A);
+    }
+    HB_CUDA(cudaStreamSynchronize(p->stream));
+    p->bc_dirty = false;
+    return HB_OK;
+}
+
+// ---------------------------------------------------------------------------------------------------
+// operators
+
+template <typename T>
+hb_status apply_op(hb_problem *p, int mode, const T *y, const T *v, T *out, double shift, cudaStream_t s) {
+    HB_TRY(prepare_bc(p));
+    PatchSetDev<T> &ps = patches<T>(p);
+    const int N = p->N;
+    HB_CUDA(cudaMemsetAsync(out, 0, size_t(p->n_nodes) * 4 * N * sizeof(T), s));
+    ElemArgs<T> ea;
+    ea.pv = PatchView<T>{ps.P, ps.nl_max, ps.ep_max, ps.eptr.p, ps.nptr.p, ps.nodes.p, ps.lconn.p, ps.geom.p};
+    ea.y = y;
+    ea.v = v;
+    ea.out = out;
+    ea.H = Hmat<T>(p);
+    ea.flag = p->d_flag.p;
+    ea.N = N;
+    ea.rho = T(p->rho);
+    ea.mu = T(p->mu);
+    ea.shift = T(shift);
+    if (ps.P > 0) {
+        launch_elem<T>(mode, ea, ps.P, s);
+        HB_LAUNCHED(p, 1);
+    }
+    if (mode != MODE_DIAG && p->n_nf > 0) {
+        FaceArgs<T> fa;
+        fa.n_faces = p->n_nf;
+        fa.fnodes = p->d_nf_nodes.p;
+        fa.foutlet = p->d_nf_out.p;
+        fa.flag = p->d_flag.p;
+        fa.y = y;
+        fa.v = v;
+        fa.out = out;
+        fa.N = N;
+        fa.rho = T(p->rho);
+        fa.beta = T(p->beta);
+        if constexpr (sizeof(T) == 4) {
+            fa.fgeo = p->d_nf_geo32.p;
+            fa.hbase = p->d_hbase32.p;
+            fa.R = p->d_R32.p;
+            fa.Q = p->d_Q32.p;
+        } else {
+            fa.fgeo = p->d_nf_geo64.p;
+            fa.hbase = p->d_hbase64.p;
+            fa.R = p->d_R64.p;
+            fa.Q = p->d_Q64.p;
+        }
+        if (p->has_res) HB_CUDA(cudaMemsetAsync(fa.Q, 0, size_t(p->n_out) * N * sizeof(T), s));
+        launch_faces<T>(mode, fa, p->has_res, s);
+        HB_LAUNCHED(p, p->has_res ? 2 : 1);
+    }
+    if (p->n_dir > 0) {
+        launch_dirichlet_rows<T>(mode, p->d_dir_nodes.p, p->n_dir, v, out, N, s);
+        HB_LAUNCHED(p, 1);
+    }
+    return HB_OK;
+}
+
+hb_status check_precision(int precision) {
+    if (precision != 0 && precision != 1) return fail(HB_ERR_INVALID_ARG, "precision must be 0 (FP64) or 1 (FP32)");
+    return HB_OK;
+}
+
+// host-buffer wrapper: copies in, converts, applies, converts, copies out
+hb_status host_op(hb_problem *p, int mode, const double *y, const double *v, double *out, int precision,
+                  double shift) {
+    if (!p || !y || !out || ((mode == MODE_JVP || mode == MODE_JVE) && !v))
+        return fail(HB_ERR_INVALID_ARG, "null argument");
+    HB_TRY(check_precision(precision));
+    const size_t nd = size_t(p->n_nodes) * 4 * p->N;
+    HB_CUDA(cudaSetDevice(p->device));
+    HB_TRY(dalloc(p, p->w64a, nd));
+    HB_TRY(dalloc(p, p->w64b, nd));
+    HB_CUDA(cudaMemcpyAsync(p->w64a.p, y, nd * sizeof(double), cudaMemcpyHostToDevice, p->stream));
+    const bool jv = (mode == MODE_JVP || mode == MODE_JVE);
+    if (precision == 0) {
+        double *vd = nullptr;
+        if (jv) {
+            HB_TRY(dalloc(p, p->kres, nd));
+            HB_CUDA(cudaMemcpyAsync(p->kres.p, v, nd * sizeof(double), cudaMemcpyHostToDevice, p->stream));
+            vd = p->kres.p;
+        }
+        HB_TRY(apply_op<double>(p, mode, p->w64a.p, vd, p->w64b.p, shift, p->stream));
+    } else {
+        HB_TRY(dalloc(p, p->w32a, nd));
+        HB_TRY(dalloc(p, p->w32b, nd));
+        HB_TRY(dalloc(p, p->w32c, nd));
+        launch_convert<double, float>(p->w64a.p, p->w32a.p, int64_t(nd), p->stream);
+        HB_LAUNCHED(p, 1);
+        if (jv) {
+            HB_CUDA(cudaMemcpyAsync(p->w64b.p, v, nd * sizeof(double), cudaMemcpyHostToDevice, p->stream));
+            launch_convert<double, float>(p->w64b.p, p->w32c.p, int64_t(nd), p->stream);
+            HB_LAUNCHED(p, 1);
+        }
+        HB_TRY(apply_op<float>(p, mode, p->w32a.p, jv ? p->w32c.p : nullptr, p->w32b.p, shift, p->stream));
+        launch_convert<float, double>(p->w32b.p, p->w64b.p, int64_t(nd), p->stream);
+        HB_LAUNCHED(p, 1);
+    }
+    HB_CUDA(cudaMemcpyAsync(out, p->w64b.p, nd * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+    HB_CUDA(cudaStreamSynchronize(p->stream));
+    return HB_OK;
+}
+
+hb_status dev_op(hb_problem *p, int mode, const void *y, const void *v, void *out, int precision, double shift,
+                 void *stream) {
+    if (!p || !y || !out || ((mode == MODE_JVP || mode == MODE_JVE) && !v))
+        return fail(HB_ERR_INVALID_ARG, "null argument");
+    HB_TRY(check_precision(precision));
+    if (out == y || (v && out == v)) return fail(HB_ERR_INVALID_ARG, "output aliases an input");
+    HB_CUDA(cudaSetDevice(p->device));
+    cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : p->stream;
+    if (precision == 0)
+        return apply_op<double>(p, mode, static_cast<const double *>(y), static_cast<const double *>(v),
+                                static_cast<double *>(out), shift, s);
+    return apply_op<float>(p, mode, static_cast<const float *>(y), static_cast<const float *>(v),
+                           static_cast<float *>(out), shift, s);
+}
+
+// ---------------------------------------------------------------------------------------------------
+// reductions and the Krylov solver
+
+hb_status dev_norm(hb_problem *p, const double *x, int64_t n, double &out) {
+    HB_TRY(dalloc(p, p->small, 512));
+    launch_dot(x, x, n, p->scratch.p, p->small.p, p->stream);
+    HB_LAUNCHED(p, 2);
+    double v = 0;
+    HB_CUDA(cudaMemcpyAsync(&v, p->small.p, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+    HB_CUDA(cudaStreamSynchronize(p->stream));
+    out = std::sqrt(v);
+    return HB_OK;
+}
+
+struct OpCtx {
+    int mode;
+    double shift;
+    int precision;
+};
+
+// w(double) = A z, with z given in double (z64) and, for the mixed path, its float copy made here
+hb_status apply_A(hb_problem *p, const OpCtx &c, const double *z64, double *w) {
+    const int64_t nd = p->n_nodes * 4 * p->N;
+    if (c.precision == 0) return apply_op<double>(p, c.mode, p->y.p, z64, w, c.shift, p->stream);
+    launch_convert<double, float>(z64, p->kz32.p, nd, p->stream);
+    HB_LAUNCHED(p, 1);
+    HB_TRY(apply_op<float>(p, c.mode, p->ky32.p, p->kz32.p, p->kw32.p, c.shift, p->stream));
+    launch_convert<float, double>(p->kw32.p, w, nd, p->stream);
+    HB_LAUNCHED(p, 1);
+    return HB_OK;
+}
+
+// Right-preconditioned restarted GMRES with classical Gram-Schmidt (one re-orthogonalisation pass when
+// the norm drops by more than 1/sqrt(2)) and Givens rotations; Arnoldi vectors and scalars in FP64.
+hb_status gmres(hb_problem *p, const OpCtx &c, const double *b, double *x, double tol, int m, int maxit,
+                int &iters, int &jv_calls) {
+    const int64_t nd = p->n_nodes * 4 * p->N;
+    double *V = p->kV.p;
+    std::vector<double> Hh(size_t((m + 1) * m), 0.0), cs(size_t(m), 0.0), sn(size_t(m), 0.0), g(size_t(m + 1), 0.0);
+    std::vector<double> hv(size_t(m + 2), 0.0), h2(size_t(m + 2), 0.0);
+    HB_CUDA(cudaMemsetAsync(x, 0, size_t(nd) * sizeof(double), p->stream));
+    double bnorm = 0;
+    HB_TRY(dev_norm(p, b, nd, bnorm));
+    iters = 0;
+    if (bnorm == 0) return HB_OK;
+    // residual of x = 0
+    HB_CUDA(cudaMemcpyAsync(p->kres.p, b, size_t(nd) * sizeof(double), cudaMemcpyDeviceToDevice, p->stream));
+    double beta = bnorm;
+    while (true) {
+        launch_scale_copy(1.0 / beta, p->kres.p, V, nd, p->stream);
+        HB_LAUNCHED(p, 1);
+        std::fill(g.begin(), g.end(), 0.0);
+        g[0] = beta;
+        int k = 0;
+        bool done = false;
+        for (int j = 0; j < m; ++j) {
+            double *vj = V + int64_t(j) * nd;
+            double *w = V + int64_t(j + 1) * nd;
+            launch_precond<double>(vj, p->kdiag.p, p->kz64.p, nd, p->stream);
+            HB_LAUNCHED(p, 1);
+            HB_TRY(apply_A(p, c, p->kz64.p, w));
+            ++jv_calls;
+            // pass 1
+            launch_multidot(V, nd, j + 1, w, nd, p->scratch.p, p->kh.p, p->stream);
+            HB_LAUNCHED(p, 2);
+            launch_multiaxpy_norm(V, nd, j + 1, p->kh.p, w, nd, p->scratch.p, p->kh.p + (m + 2), p->stream);
+            HB_LAUNCHED(p, 2);
+            HB_CUDA(cudaMemcpyAsync(hv.data(), p->kh.p, size_t(j + 2) * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+            double after2 = 0;
+            HB_CUDA(cudaMemcpyAsync(&after2, p->kh.p + (m + 2), sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+            HB_CUDA(cudaStreamSynchronize(p->stream));
+            const double before2 = hv[size_t(j + 1)];
+            if (!std::isfinite(after2) || !std::isfinite(before2)) return fail(HB_ERR_NAN, "non-finite value in GMRES");
+            if (after2 < 0.5 * before2) {   // re-orthogonalise
+                launch_multidot(V, nd, j + 1, w, nd, p->scratch.p, p->kh.p, p->stream);
+                HB_LAUNCHED(p, 2);
+                launch_multiaxpy_norm(V, nd, j + 1, p->kh.p, w, nd, p->scratch.p, p->kh.p + (m + 2), p->stream);
+                HB_LAUNCHED(p, 2);
+                HB_CUDA(cudaMemcpyAsync(h2.data(), p->kh.p, size_t(j + 1) * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+                HB_CUDA(cudaMemcpyAsync(&after2, p->kh.p + (m + 2), sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+                HB_CUDA(cudaStreamSynchronize(p->stream));
+                for (int i = 0; i <= j; ++i) hv[size_t(i)] += h2[size_t(i)];
+            }
+            const double hn = std::sqrt(std::max(after2, 0.0));
+            for (int i = 0; i <= j; ++i) Hh[size_t(i * m + j)] = hv[size_t(i)];
+            Hh[size_t((j + 1) * m + j)] = hn;
+            if (hn > 0) {
+                launch_scale_copy(1.0 / hn, w, w, nd, p->stream);
+                HB_LAUNCHED(p, 1);
+            }
+            for (int i = 0; i < j; ++i) {
+                const double a0 = Hh[size_t(i * m + j)], a1 = Hh[size_t((i + 1) * m + j)];
+                Hh[size_t(i * m + j)] = cs[size_t(i)] * a0 + sn[size_t(i)] * a1;
+                Hh[size_t((i + 1) * m + j)] = -sn[size_t(i)] * a0 + cs[size_t(i)] * a1;
+            }
+            const double a0 = Hh[size_t(j * m + j)], a1 = Hh[size_t((j + 1) * m + j)];
+            const double den = std::hypot(a0, a1);
+            cs[size_t(j)] = den > 0 ? a0 / den : 1.0;
+            sn[size_t(j)] = den > 0 ? a1 / den : 0.0;
+            Hh[size_t(j * m + j)] = den;
+            Hh[size_t((j + 1) * m + j)] = 0.0;
+            g[size_t(j + 1)] = -sn[size_t(j)] * g[size_t(j)];
+            g[size_t(j)] = cs[size_t(j)] * g[size_t(j)];
+            ++iters;
+            k = j + 1;
+            if (std::fabs(g[size_t(j + 1)]) <= tol * bnorm || iters >= maxit || hn == 0) {
+                done = true;
+                break;
+            }
+        }
+        // back substitution, then x += M^-1 V_k y_k
+        std::vector<double> yk(size_t(k), 0.0);
+        for (int i = k - 1; i >= 0; --i) {
+            double s = g[size_t(i)];
+            for (int l = i + 1; l < k; ++l) s -= Hh[size_t(i * m + l)] * yk[size_t(l)];
+            yk[size_t(i)] = Hh[size_t(i * m + i)] != 0 ? s / Hh[size_t(i * m + i)] : 0.0;
+        }
+        HB_CUDA(cudaMemcpyAsync(p->kh.p, yk.data(), size_t(k) * sizeof(double), cudaMemcpyHostToDevice, p->stream));
+        launch_combine(V, nd, k, p->kh.p, p->ktmp.p, nd, p->stream);
+        launch_precond<double>(p->ktmp.p, p->kdiag.p, p->kz64.p, nd, p->stream);
+        launch_axpy(1.0, p->kz64.p, x, nd, p->stream);
+        HB_LAUNCHED(p, 3);
+        HB_CUDA(cudaStreamSynchronize(p->stream));   // yk (host) consumed
+        if (done && (std::fabs(g[size_t(k)]) <= tol * bnorm || iters >= maxit)) break;
+        if (iters >= maxit) break;
+        // true residual for the restart: res = b - A x
+        HB_TRY(apply_A(p, c, x, p->ktmp.p));
+        ++jv_calls;
+        launch_scale_copy(1.0, b, p->kres.p, nd, p->stream);
+        launch_axpy(-1.0, p->ktmp.p, p->kres.p, nd, p->stream);
+        HB_LAUNCHED(p, 2);
+        HB_TRY(dev_norm(p, p->kres.p, nd, beta));
+        if (beta <= tol * bnorm || beta == 0) break;
+    }
+    return HB_OK;
+}
+
+hb_status ensure_krylov(hb_problem *p, int m) {
+    const size_t nd = size_t(p->n_nodes) * 4 * p->N;
+    if (p->km < m) {
+        p->kV.release();
+        HB_TRY(dalloc(p, p->kV, nd * size_t(m + 1)));
+        p->km = m;
+    }
+    HB_TRY(dalloc(p, p->kz64, nd));
+    HB_TRY(dalloc(p, p->kdx, nd));
+    HB_TRY(dalloc(p, p->kdiag, nd));
+    HB_TRY(dalloc(p, p->kres, nd));
+    HB_TRY(dalloc(p, p->ktmp, nd));
+    HB_TRY(dalloc(p, p->kh, size_t(2 * (m + 2) + 8)));
+    HB_TRY(dalloc(p, p->kz32, nd));
+    HB_TRY(dalloc(p, p->kw32, nd));
+    HB_TRY(dalloc(p, p->ky32, nd));
+    HB_TRY(dalloc(p, p->kdiag32, nd));
+    HB_TRY(dalloc(p, p->w64a, nd));
+    HB_TRY(dalloc(p, p->w64b, nd));
+    return HB_OK;
+}
+
+hb_status default_initial(hb_problem *p) {
+    const int N = p->N;
+    std::vector<double> y(size_t(p->n_nodes) * 4 * N, 0.0);
+    for (int64_t a = 0; a < p->n_nodes; ++a)
+        for (int t = 0; t < N; ++t) y[size_t((a * 4 + 3) * N + t)] = p->level[size_t(t)];
+    HB_TRY(upload(p, p->y, y));
+    HB_CUDA(cudaStreamSynchronize(p->stream));
+    p->y_set = true;
+    return HB_OK;
+}
+
+hb_status apply_dirichlet_state(hb_problem *p) {
+    launch_apply_dirichlet(p->d_dir_nodes.p, p->n_dir, p->d_g.p, p->y.p, p->N, p->stream);
+    HB_LAUNCHED(p, p->n_dir > 0 ? 1 : 0);
+    return HB_OK;
+}
+
+double h_char(const hb_problem *p) { return std::cbrt(6.0 * std::sqrt(2.0) * p->vol_mean); }
+
+}  // namespace
+
+// =====================================================================================================
+// C ABI
+
+extern "C" {
+
+const char *hb_last_error(void) { return g_err.c_str(); }
+
+hb_status hb_create(const hb_mesh *mesh, double rho, double mu, double period_T, int n_h, int device,
+                    void *cuda_stream, hb_problem **out) {
+    if (!mesh || !out || !mesh->xyz || !mesh->tets || (mesh->n_faces > 0 && (!mesh->faces || !mesh->face_tag)))
+        return fail(HB_ERR_INVALID_ARG, "null mesh array");
+    *out = nullptr;
+    if (mesh->n_nodes <= 0 || mesh->n_tets <= 0 || mesh->n_faces < 0)
+        return fail(HB_ERR_INVALID_ARG, "empty mesh");
+    if (mesh->n_nodes >= (int64_t(1) << 21) || mesh->n_tets >= (int64_t(1) << 31) / 4)
+        return fail(HB_ERR_INVALID_ARG, "mesh too large (n_nodes must be < 2^21)");
+    if (!(rho > 0) || !(mu > 0) || !(period_T > 0)) return fail(HB_ERR_INVALID_ARG, "rho, mu and T must be > 0");
+    if (n_h < 0 || 2 * n_h + 1 > kMaxN) return fail(HB_ERR_INVALID_ARG, "n_h must be in [0, 15]");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return fail(HB_ERR_CUDA, "no such CUDA device");
+    }
+    hb_problem *p = new hb_problem();
+    auto bail = [&](hb_status st) {
+        delete p;
+        return st;
+    };
+    p->device = device;
+    if (cudaSetDevice(device) != cudaSuccess) return bail(fail(HB_ERR_CUDA, "cudaSetDevice failed"));
+    cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (cuda_stream) {
+        p->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking) != cudaSuccess)
+            return bail(fail(HB_ERR_CUDA, "cudaStreamCreate failed"));
+        p->own_stream = true;
+    }
+    p->n_nodes = mesh->n_nodes;
+    p->n_tets = mesh->n_tets;
+    p->n_faces = mesh->n_faces;
+    p->n_h = n_h;
+    p->N = 2 * n_h + 1;
+    p->rho = rho;
+    p->mu = mu;
+    p->T = period_T;
+    p->omega = 2.0 * M_PI / period_T;
+    p->xyz.assign(mesh->xyz, mesh->xyz + 3 * mesh->n_nodes);
+    p->tets.assign(mesh->tets, mesh->tets + 4 * mesh->n_tets);
+    if (mesh->n_faces > 0) {
+        p->faces.assign(mesh->faces, mesh->faces + 3 * mesh->n_faces);
+        p->face_tag.assign(mesh->face_tag, mesh->face_tag + mesh->n_faces);
+    }
+    for (int32_t v : p->tets)
+        if (v < 0 || v >= mesh->n_nodes) return bail(fail(HB_ERR_MESH, "tetrahedron node index out of range"));
+    for (int32_t v : p->faces)
+        if (v < 0 || v >= mesh->n_nodes) return bail(fail(HB_ERR_MESH, "face node index out of range"));
+    for (int32_t t : p->face_tag)
+        if (t < 0) return bail(fail(HB_ERR_MESH, "negative face tag"));
+    // volumes and Morton keys of the centroids
+    const int64_t E = p->n_tets;
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int64_t a = 0; a < p->n_nodes; ++a)
+        for (int i = 0; i < 3; ++i) {
+            lo[i] = std::min(lo[i], p->xyz[size_t(3 * a + i)]);
+            hi[i] = std::max(hi[i], p->xyz[size_t(3 * a + i)]);
+        }
+    std::vector<std::pair<uint64_t, int>> keys(static_cast<size_t>(E));
+    double vsum = 0, vmin = 1e300;
+    for (int64_t e = 0; e < E; ++e) {
+        const int32_t *t = &p->tets[size_t(4 * e)];
+        double x[4][3], c[3] = {0, 0, 0};
+        for (int a = 0; a < 4; ++a)
+            for (int i = 0; i < 3; ++i) {
+                x[a][i] = p->xyz[size_t(3 * t[a] + i)];
+                c[i] += 0.25 * x[a][i];
+            }
+        double u[3], v[3], w[3];
+        for (int i = 0; i < 3; ++i) {
+            u[i] = x[1][i] - x[0][i];
+            v[i] = x[2][i] - x[0][i];
+            w[i] = x[3][i] - x[0][i];
+        }
+        const double det = u[0] * (v[1] * w[2] - v[2] * w[1]) - u[1] * (v[0] * w[2] - v[2] * w[0]) +
+                           u[2] * (v[0] * w[1] - v[1] * w[0]);
+        const double vol = std::fabs(det) / 6.0;
+        vsum += vol;
+        vmin = std::min(vmin, vol);
+        uint64_t code = 0;
+        for (int i = 0; i < 3; ++i) {
+            const double span = hi[i] - lo[i] > 0 ? hi[i] - lo[i] : 1.0;
+            const uint64_t q = uint64_t(std::min(2097151.0, std::max(0.0, (c[i] - lo[i]) / span * 2097151.0)));
+            code |= spread3(q) << i;
+        }
+        keys[size_t(e)] = {code, int(e)};
+    }
+    p->vol_mean = vsum / double(E);
+    p->vol_min = vmin;
+    if (!(vmin > 1e-14 * p->vol_mean))
+        return bail(fail(HB_ERR_MESH, "degenerate tetrahedron (zero volume)"));
+    std::sort(keys.begin(), keys.end());
+    std::vector<int32_t> tets_ord(size_t(4 * E));
+    for (int64_t e = 0; e < E; ++e)
+        for (int a = 0; a < 4; ++a) tets_ord[size_t(4 * e + a)] = p->tets[size_t(4 * keys[size_t(e)].second + a)];
+    // boundary faces: outward normal away from the owning tetrahedron's opposite vertex, and area
+    {
+        static const int loc[4][3] = {{1, 2, 3}, {0, 2, 3}, {0, 1, 3}, {0, 1, 2}};
+        std::vector<std::pair<uint64_t, int64_t>> tf(static_cast<size_t>(4 * E));
+        for (int64_t e = 0; e < E; ++e)
+            for (int l = 0; l < 4; ++l) {
+                uint64_t s[3];
+                for (int b = 0; b < 3; ++b) s[b] = uint64_t(p->tets[size_t(4 * e + loc[l][b])]);
+                std::sort(s, s + 3);
+                tf[size_t(4 * e + l)] = {(s[0] << 42) | (s[1] << 21) | s[2], 4 * e + l};
+            }
+        std::sort(tf.begin(), tf.end());
+        p->fnormal.assign(size_t(3 * p->n_faces), 0.0);
+        p->farea.assign(size_t(p->n_faces), 0.0);
+        for (int64_t f = 0; f < p->n_faces; ++f) {
+            uint64_t s[3];
+            for (int b = 0; b < 3; ++b) s[b] = uint64_t(p->faces[size_t(3 * f + b)]);
+            std::sort(s, s + 3);
+            const uint64_t key = (s[0] << 42) | (s[1] << 21) | s[2];
+            auto it = std::lower_bound(tf.begin(), tf.end(), std::make_pair(key, int64_t(-1)));
+            if (it == tf.end() || it->first != key) return bail(fail(HB_ERR_MESH, "boundary face is not a tetrahedron face"));
+            const int64_t e = it->second / 4, l = it->second % 4;
+            const int opp = p->tets[size_t(4 * e + l)];
+            const int32_t *fn = &p->faces[size_t(3 * f)];
+            double a[3], b[3], cr[3], away = 0;
+            for (int i = 0; i < 3; ++i) {
+                a[i] = p->xyz[size_t(3 * fn[1] + i)] - p->xyz[size_t(3 * fn[0] + i)];
+                b[i] = p->xyz[size_t(3 * fn[2] + i)] - p->xyz[size_t(3 * fn[0] + i)];
+            }
+            cr[0] = a[1] * b[2] - a[2] * b[1];
+            cr[1] = a[2] * b[0] - a[0] * b[2];
+            cr[2] = a[0] * b[1] - a[1] * b[0];
+            const double nn = std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+            if (!(nn > 0)) return bail(fail(HB_ERR_MESH, "degenerate boundary face"));
+            for (int i = 0; i < 3; ++i) {
+                const double m = (p->xyz[size_t(3 * fn[0] + i)] + p->xyz[size_t(3 * fn[1] + i)] +
+                                  p->xyz[size_t(3 * fn[2] + i)]) / 3.0;
+                away += cr[i] * (m - p->xyz[size_t(3 * opp + i)]);
+            }
+            const double sgn = away >= 0 ? 1.0 : -1.0;
+            for (int i = 0; i < 3; ++i) p->fnormal[size_t(3 * f + i)] = sgn * cr[i] / nn;
+            p->farea[size_t(f)] = 0.5 * nn;
+        }
+    }
+    hb_status st;
+    if ((st = upload(p, p->d_xyz, p->xyz)) != HB_OK) return bail(st);
+    if ((st = upload(p, p->d_tets_ord, std::vector<int>(tets_ord.begin(), tets_ord.end()))) != HB_OK) return bail(st);
+    if ((st = make_patchset<float>(p, p->ps32, tets_ord, 110 * 1024)) != HB_OK) return bail(st);
+    if ((st = make_patchset<double>(p, p->ps64, tets_ord, 200 * 1024)) != HB_OK) return bail(st);
+    // H = E^-1 Omega E in real closed form: (w/2) (-1)^(j-k) / sin(pi (j-k) / N), zero diagonal
+    {
+        const int N = p->N;
+        std::vector<double> H(size_t(N * N), 0.0);
+        for (int j = 0; j < N; ++j)
+            for (int k = 0; k < N; ++k)
+                if (j != k) {
+                    const int d = j - k;
+                    H[size_t(j * N + k)] = 0.5 * p->omega * ((d % 2 == 0) ? 1.0 : -1.0) / std::sin(M_PI * double(d) / N);
+                }
+        if ((st = upload(p, p->H64, H)) != HB_OK) return bail(st);
+        if ((st = upload(p, p->H32, std::vector<float>(H.begin(), H.end()))) != HB_OK) return bail(st);
+    }
+    if ((st = dalloc(p, p->scratch, 300000)) != HB_OK) return bail(st);
+    if ((st = dalloc(p, p->small, 512)) != HB_OK) return bail(st);
+    if ((st = dalloc(p, p->y, size_t(p->n_nodes) * 4 * p->N)) != HB_OK) return bail(st);
+    if (cudaStreamSynchronize(p->stream) != cudaSuccess) return bail(fail(HB_ERR_CUDA, "set-up failed"));
+    *out = p;
+    return HB_OK;
+}
+
+hb_status hb_destroy(hb_problem *p) {
+    if (!p) return HB_OK;
+    cudaSetDevice(p->device);
+    if (p->stream) cudaStreamSynchronize(p->stream);
+    const bool own = p->own_stream;
+    cudaStream_t s = p->stream;
+    delete p;
+    if (own) cudaStreamDestroy(s);
+    return HB_OK;
+}
+
+static hb_status check_tag(hb_problem *p, int tag) {
+    if (!p) return fail(HB_ERR_INVALID_ARG, "null problem");
+    if (tag <= 0) return fail(HB_ERR_INVALID_ARG, "tag must be > 0 (tag 0 is the wall)");
+    for (int32_t t : p->face_tag)
+        if (t == tag) return HB_OK;
+    return fail(HB_ERR_INVALID_ARG, "no boundary face carries tag " + std::to_string(tag));
+}
+
+hb_status hb_set_inflow(hb_problem *p, int tag, const double *profile, const double *a, const double *b) {
+    HB_TRY(check_tag(p, tag));
+    if (!a || !b) return fail(HB_ERR_INVALID_ARG, "null waveform");
+    Inflow in;
+    in.tag = tag;
+    if (profile) in.profile.assign(profile, profile + 3 * p->n_nodes);
+    in.coef = real_series(a, b, p->n_h);
+    for (auto &o : p->outlets)
+        if (o.tag == tag) return fail(HB_ERR_INVALID_ARG, "tag already set as an outlet");
+    for (auto &x : p->inflows)
+        if (x.tag == tag) {
+            x = in;
+            p->bc_dirty = true;
+            return HB_OK;
+        }
+    p->inflows.push_back(in);
+    p->bc_dirty = true;
+    return HB_OK;
+}
+
+static hb_status set_outlet(hb_problem *p, int tag, double R, const double *a, const double *b) {
+    HB_TRY(check_tag(p, tag));
+    if (!a || !b) return fail(HB_ERR_INVALID_ARG, "null waveform");
+    if (!(R >= 0) || !std::isfinite(R)) return fail(HB_ERR_INVALID_ARG, "resistance must be finite and >= 0");
+    for (auto &in : p->inflows)
+        if (in.tag == tag) return fail(HB_ERR_INVALID_ARG, "tag already set as an inflow");
+    Outlet o{tag, R, real_series(a, b, p->n_h)};
+    for (auto &x : p->outlets)
+        if (x.tag == tag) {
+            x = o;
+            p->bc_dirty = true;
+            return HB_OK;
+        }
+    p->outlets.push_back(o);
+    p->bc_dirty = true;
+    return HB_OK;
+}
+
+hb_status hb_set_outlet_pressure(hb_problem *p, int tag, const double *a, const double *b) {
+    return set_outlet(p, tag, 0.0, a, b);
+}
+
+hb_status hb_set_outlet_resistance(hb_problem *p, int tag, double R, const double *a, const double *b) {
+    return set_outlet(p, tag, R, a, b);
+}
+
+hb_status hb_set_backflow(hb_problem *p, double beta) {
+    if (!p) return fail(HB_ERR_INVALID_ARG, "null problem");
+    if (!(beta >= 0 && beta <= 1)) return fail(HB_ERR_INVALID_ARG, "beta must be in [0, 1]");
+    p->beta = beta;
+    return HB_OK;
+}
+
+hb_status hb_set_instances(hb_problem *p, const double *y) {
+    if (!p) return fail(HB_ERR_INVALID_ARG, "null problem");
+    HB_CUDA(cudaSetDevice(p->device));
+    HB_TRY(prepare_bc(p));
+    if (!y) {
+        HB_TRY(default_initial(p));
+    } else {
+        const size_t nd = size_t(p->n_nodes) * 4 * p->N;
+        HB_CUDA(cudaMemcpyAsync(p->y.p, y, nd * sizeof(double), cudaMemcpyHostToDevice, p->stream));
+        p->y_set = true;
+    }
+    HB_TRY(apply_dirichlet_state(p));
+    HB_CUDA(cudaStreamSynchronize(p->stream));
+    return HB_OK;
+}
+
+hb_status hb_set_initial(hb_problem *p, const double *harm) {
+    if (!p) return fail(HB_ERR_INVALID_ARG, "null problem");
+    if (!harm) return hb_set_instances(p, nullptr);
+    HB_CUDA(cudaSetDevice(p->device));
+    HB_TRY(prepare_bc(p));
+    const int M = 2 * p->n_h + 1;
+    const size_t nc = size_t(p->n_nodes) * 4 * M;
+    HB_TRY(dalloc(p, p->w64a, std::max(nc, size_t(p->n_nodes) * 4 * p->N)));
+    HB_CUDA(cudaMemcpyAsync(p->w64a.p, harm, nc * sizeof(double), cudaMemcpyHostToDevice, p->stream));
+    launch_harmonics(p->w64a.p, p->y.p, p->n_nodes * 4, p->N, p->n_h, 1, p->T, p->stream);
+    HB_LAUNCHED(p, 1);
+    p->y_set = true;
+    HB_TRY(apply_dirichlet_state(p));
+    HB_CUDA(cudaStreamSynchronize(p->stream));
+    return HB_OK;
+}
+
+hb_status hb_get_instances(hb_problem *p, double *out) {
+    if (!p || !out) return fail(HB_ERR_INVALID_ARG, "null argument");
+    if (!p->y_set) return fail(HB_ERR_STATE, "no state yet (set an initial state or solve first)");
+    HB_CUDA(cudaSetDevice(p->device));
+    const size_t nd = size_t(p->n_nodes) * 4 * p->N;
+    HB_CUDA(cudaMemcpyAsync(out, p->y.p, nd * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+    HB_CUDA(cudaStreamSynchronize(p->stream));
+    return HB_OK;
+}
+
+hb_status hb_get_harmonics(hb_problem *p, double *out) {
+    if (!p || !out) return fail(HB_ERR_INVALID_ARG, "null argument");
+    if (!p->y_set) return fail(HB_ERR_STATE, "no state yet (set an initial state or solve first)");
+    HB_CUDA(cudaSetDevice(p->device));
+    const int M = 2 * p->n_h + 1;
+    const size_t nc = size_t(p->n_nodes) * 4 * M;
+    HB_TRY(dalloc(p, p->w64b, std::max(nc, size_t(p->n_nodes) * 4 * p->N)));
+    launch_harmonics(p->y.p, p->w64b.p, p->n_nodes * 4, p->N, p->n_h, 0, p->T, p->stream);
+    HB_LAUNCHED(p, 1);
+    HB_CUDA(cudaMemcpyAsync(out, p->w64b.p, nc * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+    HB_CUDA(cudaStreamSynchronize(p->stream));
+    return HB_OK;
+}
+
+hb_status hb_residual(hb_problem *p, const double *y, double *r, int precision) {
+    return host_op(p, MODE_RES, y, nullptr, r, precision, 0.0);
+}
+
+hb_status hb_jv(hb_problem *p, const double *y, const double *v, double *jv, int kind, int precision, double shift) {
+    if (kind != 0 && kind != 1) return fail(HB_ERR_INVALID_ARG, "kind must be 0 (paper tangent) or 1 (exact)");
+    return host_op(p, kind == 0 ? MODE_JVP : MODE_JVE, y, v, jv, precision, shift);
+}
+
+hb_status hb_jacobi_diag(hb_problem *p, const double *y, double *d, int precision, double shift) {
+    return host_op(p, MODE_DIAG, y, nullptr, d, precision, shift);
+}
+
+hb_status hb_residual_dev(hb_problem *p, const void *y, void *r, int precision, void *stream) {
+    return dev_op(p, MODE_RES, y, nullptr, r, precision, 0.0, stream);
+}
+
+hb_status hb_jv_dev(hb_problem *p, const void *y, const void *v, void *jv, int kind, int precision, double shift,
+                    void *stream) {
+    if (kind != 0 && kind != 1) return fail(HB_ERR_INVALID_ARG, "kind must be 0 (paper tangent) or 1 (exact)");
+    return dev_op(p, kind == 0 ? MODE_JVP : MODE_JVE, y, v, jv, precision, shift, stream);
+}
+
+hb_status hb_jacobi_diag_dev(hb_problem *p, const void *y, void *d, int precision, double shift, void *stream) {
+    return dev_op(p, MODE_DIAG, y, nullptr, d, precision, shift, stream);
+}
+
+hb_status hb_default_opts(hb_solve_opts *o) {
+    if (!o) return fail(HB_ERR_INVALID_ARG, "null options");
+    o->precision = 1;
+    o->rtol = 1e-11;
+    o->switch_rtol = 1e-3;
+    o->gmres_rtol_pseudo = 0.03;
+    o->gmres_rtol_newton = 1e-3;
+    o->gmres_restart = 60;
+    o->max_gmres = 3000;
+    o->max_steps = 400;
+    o->dt_pseudo = 0.0;
+    o->cfl = 1.0;
+    o->use_learned = 0;
+    o->verbose = 0;
+    return HB_OK;
+}
+
+hb_status hb_solve(hb_problem *p, const hb_solve_opts *opts, hb_report *rep) {
+    if (!p) return fail(HB_ERR_INVALID_ARG, "null problem");
+    hb_solve_opts o;
+    hb_default_opts(&o);
+    if (opts) o = *opts;
+    HB_TRY(check_precision(o.precision));
+    if (o.gmres_restart < 1 || o.gmres_restart > 200) return fail(HB_ERR_INVALID_ARG, "gmres_restart must be in [1, 200]");
+    HB_CUDA(cudaSetDevice(p->device));
+    const auto t0 = std::chrono::steady_clock::now();
+    HB_TRY(prepare_bc(p));
+    if (p->inflows.empty()) return fail(HB_ERR_STATE, "no inflow set");
+    if (!p->y_set) HB_TRY(default_initial(p));
+    HB_TRY(apply_dirichlet_state(p));
+    const int64_t nd = p->n_nodes * 4 * p->N;
+    HB_TRY(ensure_krylov(p, o.gmres_restart));
+    hb_report R;
+    std::memset(&R, 0, sizeof(R));
+    const double dt = o.dt_pseudo > 0 ? o.dt_pseudo : (p->u_c > 0 ? o.cfl * h_char(p) / p->u_c : INFINITY);
+    R.dt_pseudo = dt;
+    const double shift = std::isfinite(dt) ? kC1 * p->rho / dt : 0.0;
+    double *r = p->w64a.p;
+    double *b = p->w64b.p;
+    HB_TRY(apply_op<double>(p, MODE_RES, p->y.p, nullptr, r, 0.0, p->stream));
+    R.residual_calls++;
+    double rn = 0;
+    HB_TRY(dev_norm(p, r, nd, rn));
+    R.res0 = rn;
+    double r0 = rn;
+    bool newton = false;
+    hb_status result = HB_ERR_NOT_CONVERGED;
+    double dxn = INFINITY;
+    for (int step = 0; step < o.max_steps; ++step) {
+        if (!std::isfinite(rn)) {
+            result = fail(HB_ERR_NAN, "residual is not finite");
+            break;
+        }
+        if (r0 == 0 || (rn <= o.rtol * r0 && step > 0)) {
+            result = HB_OK;
+            break;
+        }
+        if (rn < o.switch_rtol * r0) newton = true;
+        OpCtx c{newton ? MODE_JVE : MODE_JVP, newton ? 0.0 : shift, o.precision};
+        // Jacobi diagonal of P (+ pseudo mass) and the frozen state in the kernels' precision
+        if (o.precision == 1) {
+            launch_convert<double, float>(p->y.p, p->ky32.p, nd, p->stream);
+            HB_LAUNCHED(p, 1);
+            HB_TRY(apply_op<float>(p, MODE_DIAG, p->ky32.p, nullptr, p->kdiag32.p, c.shift, p->stream));
+            launch_convert<float, double>(p->kdiag32.p, p->kdiag.p, nd, p->stream);
+            HB_LAUNCHED(p, 1);
+        } else {
+            HB_TRY(apply_op<double>(p, MODE_DIAG, p->y.p, nullptr, p->kdiag.p, c.shift, p->stream));
+        }
+        launch_scale_copy(-1.0, r, b, nd, p->stream);
+        HB_LAUNCHED(p, 1);
+        int its = 0, jvc = 0;
+        const double tol = newton ? o.gmres_rtol_newton : o.gmres_rtol_pseudo;
+        HB_TRY(gmres(p, c, b, p->kdx.p, tol, o.gmres_restart, o.max_gmres, its, jvc));
+        R.gmres_iters += its;
+        R.jv_calls += jvc;
+        launch_axpy(1.0, p->kdx.p, p->y.p, nd, p->stream);
+        HB_LAUNCHED(p, 1);
+        HB_TRY(apply_op<double>(p, MODE_RES, p->y.p, nullptr, r, 0.0, p->stream));
+        R.residual_calls++;
+        double yn = 0;
+        HB_TRY(dev_norm(p, p->kdx.p, nd, dxn));
+        HB_TRY(dev_norm(p, p->y.p, nd, yn));
+        HB_TRY(dev_norm(p, r, nd, rn));
+        R.steps++;
+        if (newton) R.newton_steps++;
+        if (o.verbose)
+            std::fprintf(stderr, "hb_solve step %d %s gmres %d |r|/|r0| %.3e |dy|/|y| %.3e\n", step,
+                         newton ? "newton" : "pseudo", its, rn / r0, yn > 0 ? dxn / yn : 0.0);
+        if (newton && rn <= o.rtol * r0 && dxn <= 10 * o.rtol * yn) {
+            result = HB_OK;
+            break;
+        }
+    }
+    R.res_final = rn;
+    R.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    R.status = result;
+    if (rep) *rep = R;
+    if (result == HB_ERR_NOT_CONVERGED) g_err = "solve reached max_steps";
+    return result;
+}
+
+hb_status hb_get_info(hb_problem *p, hb_info *info) {
+    if (!p || !info) return fail(HB_ERR_INVALID_ARG, "null argument");
+    HB_TRY(prepare_bc(p));
+    info->n_nodes = p->n_nodes;
+    info->n_tets = p->n_tets;
+    info->n_faces = p->n_faces;
+    info->n_dirichlet_nodes = p->n_dir;
+    info->n_neumann_faces = p->n_nf;
+    info->n_h = p->n_h;
+    info->N = p->N;
+    info->n_patches32 = p->ps32.P;
+    info->n_patches64 = p->ps64.P;
+    info->patch_nodes_max32 = p->ps32.nl_max;
+    info->patch_elems_max32 = p->ps32.ep_max;
+    info->device_bytes = p->dev_bytes;
+    info->h_char = h_char(p);
+    return HB_OK;
+}
+
+int64_t hb_launch_count(const hb_problem *p) { return p ? p->launches : 0; }
+
+}  // extern "C"

@@ -1,0 +1,790 @@
+// Fused element kernels of the HB-GLS residual and its Jacobian-vector products (arXiv 2411.14315,
+// Sec. 2.2-2.3), plus the per-element geometry precompute.
+//
+// One CTA processes one element patch at a time: it stages the patch's node rows (all N instances of
+// every field) in shared memory, applies the time-coupling H = E^-1 Omega E (Eq. NS-harm) to them
+// there, runs one thread per (element, instance) over the patch, accumulates element contributions
+// per local node with shared-memory atomics, and flushes each local node once to global memory.  The
+// H terms of the residual, -H N_A (least-squares) and rho N_A H u (Galerkin), are applied to the
+// patch-assembled T = rho M u - int N_A tau L at flush time: H is linear and acts on the instance
+// index only, so applying it per patch and summing equals applying it after global assembly.
+#include "hb_internal.cuh"
+
+namespace hb {
+
+namespace {
+
+struct Layout {
+    size_t H, geom, Y, V, HY, HV, Q, T, node, conn, total;
+};
+
+__host__ __device__ inline size_t pad16(size_t b) { return (b + 15) & ~size_t(15); }
+
+__host__ __device__ inline Layout make_layout(int mode, int N, int nl, int ep, size_t ts) {
+    Layout L;
+    size_t o = 0;
+    const size_t row4 = size_t(nl) * 4 * N * ts, row3 = size_t(nl) * 3 * N * ts;
+    L.H = o;    o += pad16(size_t(N) * N * ts);
+    L.geom = o; o += pad16(size_t(ep) * kGeomStride * ts);
+    L.Y = o;    o += pad16(row4);
+    L.V = o;    if (mode == MODE_JVP || mode == MODE_JVE) o += pad16(row4);
+    L.HY = o;   if (mode == MODE_RES || mode == MODE_JVE) o += pad16(row3);
+    L.HV = o;   if (mode == MODE_JVE) o += pad16(row3);
+    L.Q = o;    o += pad16(row4);
+    L.T = o;    if (mode != MODE_DIAG) o += pad16(row3);
+    L.node = o; o += pad16(size_t(nl) * 4);
+    L.conn = o; o += pad16(size_t(ep) * 4);
+    L.total = o;
+    return L;
+}
+
+// ---------------------------------------------------------------------------------------------------
+// per (element, instance) arithmetic
+
+template <typename T>
+__device__ __forceinline__ T rsqrt_t(T x);
+template <>
+__device__ __forceinline__ float rsqrt_t<float>(float x) { return rsqrtf(x); }
+template <>
+__device__ __forceinline__ double rsqrt_t<double>(double x) { return rsqrt(x); }
+
+template <typename T, int MODE>
+__device__ __forceinline__ void element_instance(int e, int n, int N, T rho, T mu, T shift,
+                                                 const T *__restrict__ sGeom,
+                                                 const uint32_t *__restrict__ sConn,
+                                                 const T *__restrict__ sY, const T *__restrict__ sV,
+                                                 const T *__restrict__ sHY, const T *__restrict__ sHV,
+                                                 T *sQ, T *sT) {
+    const int N4 = 4 * N, N3 = 3 * N;
+    const uint32_t c = sConn[e];
+    const int lo[4] = {int(c & 255u), int((c >> 8) & 255u), int((c >> 16) & 255u), int(c >> 24)};
+    const T *g = sGeom + e * kGeomStride;
+    T gN[4][3];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) gN[a][j] = g[a * 3 + j];
+    const T V = g[12], g2 = g[13];
+    const T w = V * T(0.25);
+    const T qb = T(kQB), qd = T(kQA - kQB);
+    const T m20 = V * T(0.05);   // int N_a N_b = V (1 + delta_ab) / 20
+
+    // frozen / current velocity at the 4 nodes
+    T u[4][3];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) u[a][i] = sY[lo[a] * N4 + i * N + n];
+    T usum[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) usum[i] = u[0][i] + u[1][i] + u[2][i] + u[3][i];
+
+    if constexpr (MODE == MODE_DIAG) {
+        T dvel[4] = {0, 0, 0, 0}, udNs[4] = {0, 0, 0, 0};
+        T taus = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            T uq[3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) uq[i] = qb * usum[i] + qd * u[q][i];
+            T udN[4];
+#pragma unroll
+            for (int a = 1; a < 4; ++a) udN[a] = uq[0] * gN[a][0] + uq[1] * gN[a][1] + uq[2] * gN[a][2];
+            udN[0] = -(udN[1] + udN[2] + udN[3]);
+            const T tau = rsqrt_t<T>(udN[1] * udN[1] + udN[2] * udN[2] + udN[3] * udN[3] + g2);
+            taus += tau;
+            dvel[q] += w * rho * qd * udN[q];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                udNs[a] += udN[a];
+                dvel[a] += w * rho * tau * udN[a] * udN[a];
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const T gg = gN[a][0] * gN[a][0] + gN[a][1] * gN[a][1] + gN[a][2] * gN[a][2];
+            const T dv = dvel[a] + w * rho * qb * udNs[a] + mu * V * gg + shift * V * T(0.1);
+            const T dp = (w / rho) * taus * gg;
+            atomicAdd(sQ + lo[a] * N4 + n, dv);
+            atomicAdd(sQ + lo[a] * N4 + 3 * N + n, dp);
+        }
+        return;
+    } else if constexpr (MODE == MODE_RES) {
+        T p[4], hu[4][3];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            p[a] = sY[lo[a] * N4 + 3 * N + n];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) hu[a][i] = sHY[lo[a] * N3 + i * N + n];
+        }
+        T gU[3][3], gP[3], husum[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            husum[i] = hu[0][i] + hu[1][i] + hu[2][i] + hu[3][i];
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                gU[i][j] = u[0][i] * gN[0][j] + u[1][i] * gN[1][j] + u[2][i] * gN[2][j] + u[3][i] * gN[3][j];
+        }
+#pragma unroll
+        for (int j = 0; j < 3; ++j) gP[j] = p[0] * gN[0][j] + p[1] * gN[1][j] + p[2] * gN[2][j] + p[3] * gN[3][j];
+        T qm[4][3], tt[4][3];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) qm[a][i] = tt[a][i] = T(0);
+        T S[3] = {0, 0, 0}, convs[3] = {0, 0, 0};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            T uq[3], huq[3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                uq[i] = qb * usum[i] + qd * u[q][i];
+                huq[i] = qb * husum[i] + qd * hu[q][i];
+            }
+            T udN[4];
+#pragma unroll
+            for (int a = 1; a < 4; ++a) udN[a] = uq[0] * gN[a][0] + uq[1] * gN[a][1] + uq[2] * gN[a][2];
+            udN[0] = -(udN[1] + udN[2] + udN[3]);
+            const T tau = rsqrt_t<T>(udN[1] * udN[1] + udN[2] * udN[2] + udN[3] * udN[3] + g2);
+            T tL[3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const T conv = uq[0] * gU[i][0] + uq[1] * gU[i][1] + uq[2] * gU[i][2];
+                tL[i] = tau * (rho * (huq[i] + conv) + gP[i]);
+                convs[i] += conv;
+                S[i] += tL[i];
+                qm[q][i] += w * rho * qd * conv;
+                tt[q][i] -= w * qd * tL[i];
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int i = 0; i < 3; ++i) qm[a][i] += w * udN[a] * tL[i];
+        }
+        const T pbar = T(0.25) * (p[0] + p[1] + p[2] + p[3]);
+        const T div = gU[0][0] + gU[1][1] + gU[2][2];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const T visc = gN[a][0] * gU[i][0] + gN[a][1] * gU[i][1] + gN[a][2] * gU[i][2];
+                const T vq = qm[a][i] + w * rho * qb * convs[i] + mu * V * visc - V * gN[a][i] * pbar;
+                const T vt = tt[a][i] + rho * m20 * (usum[i] + u[a][i]) - w * qb * S[i];
+                atomicAdd(sQ + lo[a] * N4 + i * N + n, vq);
+                atomicAdd(sT + lo[a] * N3 + i * N + n, vt);
+            }
+            const T qc = w * div + (w / rho) * (gN[a][0] * S[0] + gN[a][1] * S[1] + gN[a][2] * S[2]);
+            atomicAdd(sQ + lo[a] * N4 + 3 * N + n, qc);
+        }
+        return;
+    } else if constexpr (MODE == MODE_JVP) {
+        T dv[4][3], dvp[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            dvp[a] = sV[lo[a] * N4 + 3 * N + n];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) dv[a][i] = sV[lo[a] * N4 + i * N + n];
+        }
+        T gV[3][3], gVp[3], dvsum[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            dvsum[i] = dv[0][i] + dv[1][i] + dv[2][i] + dv[3][i];
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                gV[i][j] = dv[0][i] * gN[0][j] + dv[1][i] * gN[1][j] + dv[2][i] * gN[2][j] + dv[3][i] * gN[3][j];
+        }
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            gVp[j] = dvp[0] * gN[0][j] + dvp[1] * gN[1][j] + dvp[2] * gN[2][j] + dvp[3] * gN[3][j];
+        T qm[4][3];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) qm[a][i] = T(0);
+        T S[3] = {0, 0, 0}, ugvs[3] = {0, 0, 0};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            T uq[3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) uq[i] = qb * usum[i] + qd * u[q][i];
+            T udN[4];
+#pragma unroll
+            for (int a = 1; a < 4; ++a) udN[a] = uq[0] * gN[a][0] + uq[1] * gN[a][1] + uq[2] * gN[a][2];
+            udN[0] = -(udN[1] + udN[2] + udN[3]);
+            const T tau = rsqrt_t<T>(udN[1] * udN[1] + udN[2] * udN[2] + udN[3] * udN[3] + g2);
+            T X[3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const T ugv = uq[0] * gV[i][0] + uq[1] * gV[i][1] + uq[2] * gV[i][2];
+                X[i] = tau * (rho * ugv + gVp[i]);
+                ugvs[i] += ugv;
+                S[i] += X[i];
+                qm[q][i] += w * rho * qd * ugv;
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int i = 0; i < 3; ++i) qm[a][i] += w * udN[a] * X[i];
+        }
+        const T pbar = T(0.25) * (dvp[0] + dvp[1] + dvp[2] + dvp[3]);
+        const T div = gV[0][0] + gV[1][1] + gV[2][2];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const T visc = gN[a][0] * gV[i][0] + gN[a][1] * gV[i][1] + gN[a][2] * gV[i][2];
+                const T mv = m20 * (dvsum[i] + dv[a][i]);
+                const T vq = qm[a][i] + w * rho * qb * ugvs[i] + mu * V * visc - V * gN[a][i] * pbar + shift * mv;
+                atomicAdd(sQ + lo[a] * N4 + i * N + n, vq);
+                atomicAdd(sT + lo[a] * N3 + i * N + n, rho * mv);
+            }
+            const T qc = w * div + (w / rho) * (gN[a][0] * S[0] + gN[a][1] * S[1] + gN[a][2] * S[2]);
+            atomicAdd(sQ + lo[a] * N4 + 3 * N + n, qc);
+        }
+        return;
+    } else {  // MODE_JVE
+        T p[4], hu[4][3], dv[4][3], dvp[4], hdv[4][3];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            p[a] = sY[lo[a] * N4 + 3 * N + n];
+            dvp[a] = sV[lo[a] * N4 + 3 * N + n];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                hu[a][i] = sHY[lo[a] * N3 + i * N + n];
+                dv[a][i] = sV[lo[a] * N4 + i * N + n];
+                hdv[a][i] = sHV[lo[a] * N3 + i * N + n];
+            }
+        }
+        T gU[3][3], gP[3], gV[3][3], gVp[3], husum[3], dvsum[3], hdvsum[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            husum[i] = hu[0][i] + hu[1][i] + hu[2][i] + hu[3][i];
+            dvsum[i] = dv[0][i] + dv[1][i] + dv[2][i] + dv[3][i];
+            hdvsum[i] = hdv[0][i] + hdv[1][i] + hdv[2][i] + hdv[3][i];
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                gU[i][j] = u[0][i] * gN[0][j] + u[1][i] * gN[1][j] + u[2][i] * gN[2][j] + u[3][i] * gN[3][j];
+                gV[i][j] = dv[0][i] * gN[0][j] + dv[1][i] * gN[1][j] + dv[2][i] * gN[2][j] + dv[3][i] * gN[3][j];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            gP[j] = p[0] * gN[0][j] + p[1] * gN[1][j] + p[2] * gN[2][j] + p[3] * gN[3][j];
+            gVp[j] = dvp[0] * gN[0][j] + dvp[1] * gN[1][j] + dvp[2] * gN[2][j] + dvp[3] * gN[3][j];
+        }
+        T qm[4][3], tt[4][3];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) qm[a][i] = tt[a][i] = T(0);
+        T S[3] = {0, 0, 0}, dconvs[3] = {0, 0, 0};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            T uq[3], huq[3], duq[3], hduq[3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                uq[i] = qb * usum[i] + qd * u[q][i];
+                huq[i] = qb * husum[i] + qd * hu[q][i];
+                duq[i] = qb * dvsum[i] + qd * dv[q][i];
+                hduq[i] = qb * hdvsum[i] + qd * hdv[q][i];
+            }
+            T udN[4], dudN[4];
+#pragma unroll
+            for (int a = 1; a < 4; ++a) {
+                udN[a] = uq[0] * gN[a][0] + uq[1] * gN[a][1] + uq[2] * gN[a][2];
+                dudN[a] = duq[0] * gN[a][0] + duq[1] * gN[a][1] + duq[2] * gN[a][2];
+            }
+            udN[0] = -(udN[1] + udN[2] + udN[3]);
+            dudN[0] = -(dudN[1] + dudN[2] + dudN[3]);
+            const T tau = rsqrt_t<T>(udN[1] * udN[1] + udN[2] * udN[2] + udN[3] * udN[3] + g2);
+            const T dtau = -tau * tau * tau * (udN[1] * dudN[1] + udN[2] * dudN[2] + udN[3] * dudN[3]);
+            T tL[3], dtL[3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const T conv = uq[0] * gU[i][0] + uq[1] * gU[i][1] + uq[2] * gU[i][2];
+                const T dconv = duq[0] * gU[i][0] + duq[1] * gU[i][1] + duq[2] * gU[i][2]
+                              + uq[0] * gV[i][0] + uq[1] * gV[i][1] + uq[2] * gV[i][2];
+                const T L = rho * (huq[i] + conv) + gP[i];
+                const T dL = rho * (hduq[i] + dconv) + gVp[i];
+                tL[i] = tau * L;
+                dtL[i] = dtau * L + tau * dL;
+                dconvs[i] += dconv;
+                S[i] += dtL[i];
+                qm[q][i] += w * rho * qd * dconv;
+                tt[q][i] -= w * qd * dtL[i];
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int i = 0; i < 3; ++i) qm[a][i] += w * (dudN[a] * tL[i] + udN[a] * dtL[i]);
+        }
+        const T pbar = T(0.25) * (dvp[0] + dvp[1] + dvp[2] + dvp[3]);
+        const T div = gV[0][0] + gV[1][1] + gV[2][2];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const T visc = gN[a][0] * gV[i][0] + gN[a][1] * gV[i][1] + gN[a][2] * gV[i][2];
+                const T mv = m20 * (dvsum[i] + dv[a][i]);
+                const T vq = qm[a][i] + w * rho * qb * dconvs[i] + mu * V * visc - V * gN[a][i] * pbar + shift * mv;
+                const T vt = tt[a][i] + rho * mv - w * qb * S[i];
+                atomicAdd(sQ + lo[a] * N4 + i * N + n, vq);
+                atomicAdd(sT + lo[a] * N3 + i * N + n, vt);
+            }
+            const T qc = w * div + (w / rho) * (gN[a][0] * S[0] + gN[a][1] * S[1] + gN[a][2] * S[2]);
+            atomicAdd(sQ + lo[a] * N4 + 3 * N + n, qc);
+        }
+        return;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------------
+// the patch kernel
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 2 : 1)) elem_kernel(ElemArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int N = a.N, N4 = 4 * N, N3 = 3 * N;
+    const Layout L = make_layout(MODE, N, a.pv.nl_max, a.pv.ep_max, sizeof(T));
+    T *sH = reinterpret_cast<T *>(smem + L.H);
+    T *sGeom = reinterpret_cast<T *>(smem + L.geom);
+    T *sY = reinterpret_cast<T *>(smem + L.Y);
+    T *sV = reinterpret_cast<T *>(smem + L.V);
+    T *sHY = reinterpret_cast<T *>(smem + L.HY);
+    T *sHV = reinterpret_cast<T *>(smem + L.HV);
+    T *sQ = reinterpret_cast<T *>(smem + L.Q);
+    T *sT = reinterpret_cast<T *>(smem + L.T);
+    int *sNode = reinterpret_cast<int *>(smem + L.node);
+    uint32_t *sConn = reinterpret_cast<uint32_t *>(smem + L.conn);
+    const int tid = threadIdx.x, nt = blockDim.x;
+
+    for (int i = tid; i < N * N; i += nt) sH[i] = a.H[i];
+
+    for (int p = blockIdx.x; p < a.pv.n_patches; p += gridDim.x) {
+        const int e0 = a.pv.eptr[p], ne = a.pv.eptr[p + 1] - e0;
+        const int q0 = a.pv.nptr[p], nl = a.pv.nptr[p + 1] - q0;
+        for (int i = tid; i < nl; i += nt) sNode[i] = a.pv.nodes[q0 + i];
+        for (int i = tid; i < ne; i += nt) sConn[i] = a.pv.lconn[e0 + i];
+        {
+            const uint4 *src = reinterpret_cast<const uint4 *>(a.pv.geom + size_t(e0) * kGeomStride);
+            uint4 *dst = reinterpret_cast<uint4 *>(sGeom);
+            const int nvec = int(ne * kGeomStride * sizeof(T) / 16);
+            for (int i = tid; i < nvec; i += nt) dst[i] = src[i];
+        }
+        for (int i = tid; i < nl * N4; i += nt) sQ[i] = T(0);
+        if constexpr (MODE != MODE_DIAG)
+            for (int i = tid; i < nl * N3; i += nt) sT[i] = T(0);
+        __syncthreads();
+
+        // gather the patch's node rows: 4 N values per node, 16-byte chunks
+        const int cpr = int(N4 * sizeof(T) / 16);
+        for (int i = tid; i < nl * cpr; i += nt) {
+            const int l = i / cpr, c = i - l * cpr;
+            const size_t gidx = size_t(sNode[l]) * cpr + c;
+            reinterpret_cast<uint4 *>(sY)[i] = reinterpret_cast<const uint4 *>(a.y)[gidx];
+            if constexpr (MODE == MODE_JVP || MODE == MODE_JVE)
+                reinterpret_cast<uint4 *>(sV)[i] = reinterpret_cast<const uint4 *>(a.v)[gidx];
+        }
+        __syncthreads();
+        if constexpr (MODE == MODE_JVP || MODE == MODE_JVE) {
+            // Dirichlet velocity entries of the direction are not unknowns: treat them as 0
+            for (int i = tid; i < nl * N3; i += nt) {
+                const int l = i / N3, r = i - l * N3;
+                if (a.flag[sNode[l]] & 1) sV[l * N4 + r] = T(0);
+            }
+            __syncthreads();
+        }
+        if constexpr (MODE == MODE_RES || MODE == MODE_JVE) {
+            // time coupling of the staged velocities: (H u)[l][i][n] = sum_k H[n][k] u[l][i][k]
+            for (int i = tid; i < nl * N3; i += nt) {
+                const int l = i / N3, r = i - l * N3, f = r / N, n = r - f * N;
+                const T *h = sH + n * N;
+                const T *x = sY + l * N4 + f * N;
+                T acc = 0;
+                for (int k = 0; k < N; ++k) acc += h[k] * x[k];
+                sHY[i] = acc;
+                if constexpr (MODE == MODE_JVE) {
+                    const T *xv = sV + l * N4 + f * N;
+                    T acc2 = 0;
+                    for (int k = 0; k < N; ++k) acc2 += h[k] * xv[k];
+                    sHV[i] = acc2;
+                }
+            }
+            __syncthreads();
+        }
+
+        for (int i = tid; i < ne * N; i += nt) {
+            const int e = i / N, n = i - e * N;
+            element_instance<T, MODE>(e, n, N, a.rho, a.mu, a.shift, sGeom, sConn, sY, sV, sHY, sHV, sQ, sT);
+        }
+        __syncthreads();
+
+        // flush: out += Q + H T (velocity rows), once per local node
+        for (int i = tid; i < nl * N4; i += nt) {
+            const int l = i / N4, r = i - l * N4, f = r / N, n = r - f * N;
+            T val;
+            if constexpr (MODE == MODE_DIAG) {
+                val = (f == 1 || f == 2) ? sQ[l * N4 + n] : sQ[i];
+            } else {
+                val = sQ[i];
+                if (f < 3) {
+                    const T *h = sH + n * N;
+                    const T *t = sT + l * N3 + f * N;
+                    T acc = 0;
+                    for (int k = 0; k < N; ++k) acc += h[k] * t[k];
+                    val += acc;
+                }
+            }
+            atomicAdd(a.out + size_t(sNode[l]) * N4 + r, val);
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------------------------------
+// geometry precompute: grad N_a, V, C_I nu^2 G:G with G = J^-T J^-1 (metric of the parent map)
+
+template <typename T>
+__global__ void geom_kernel(const double *__restrict__ xyz, const int *__restrict__ tets, int n_tets,
+                            double nu, T *__restrict__ geom) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_tets) return;
+    double x[4][3];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int nd = tets[4 * e + a];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) x[a][i] = xyz[3 * nd + i];
+    }
+    double J[3][3];   // J[i][k] = (x_{k+1} - x_0)_i
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) J[i][k] = x[k + 1][i] - x[0][i];
+    const double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+    const double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+    const double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+    const double det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+    const double id = 1.0 / det;
+    double Ji[3][3];  // inverse: Ji[k][i] = d xi_k / d x_i
+    Ji[0][0] = c00 * id;
+    Ji[1][0] = c01 * id;
+    Ji[2][0] = c02 * id;
+    Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * id;
+    Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * id;
+    Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * id;
+    Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * id;
+    Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * id;
+    Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * id;
+    T *g = geom + size_t(e) * kGeomStride;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        g[i] = T(-(Ji[0][i] + Ji[1][i] + Ji[2][i]));
+#pragma unroll
+        for (int k = 0; k < 3; ++k) g[3 * (k + 1) + i] = T(Ji[k][i]);
+    }
+    double GG = 0.0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const double Gij = Ji[0][i] * Ji[0][j] + Ji[1][i] * Ji[1][j] + Ji[2][i] * Ji[2][j];
+            GG += Gij * Gij;
+        }
+    g[12] = T(fabs(det) / 6.0);
+    g[13] = T(kCI * nu * nu * GG);
+    g[14] = T(0);
+    g[15] = T(0);
+}
+
+// ---------------------------------------------------------------------------------------------------
+// Neumann faces: -int N_A h n_i and backflow -int N_A (rho/2) beta |u.n|_- u_i (3 edge midpoints)
+
+template <typename T, int MODE>
+__global__ void outlet_flux_kernel(FaceArgs<T> a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n_faces * a.N) return;
+    const int f = i / a.N, n = i - f * a.N;
+    const int o = a.foutlet[f];
+    if (o < 0) return;
+    const int N4 = 4 * a.N;
+    const T *x = (MODE == MODE_RES) ? a.y : a.v;
+    const T nx = a.fgeo[4 * f], ny = a.fgeo[4 * f + 1], nz = a.fgeo[4 * f + 2], S = a.fgeo[4 * f + 3];
+    T s = 0;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        const int nd = a.fnodes[3 * f + b];
+        if (MODE != MODE_RES && (a.flag[nd] & 1)) continue;
+        const T *r = x + size_t(nd) * N4 + n;
+        s += r[0] * nx + r[a.N] * ny + r[2 * a.N] * nz;
+    }
+    atomicAdd(a.Q + o * a.N + n, s * S / T(3));
+}
+
+template <typename T, int MODE>
+__global__ void face_kernel(FaceArgs<T> a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n_faces * a.N) return;
+    const int N = a.N, N4 = 4 * N;
+    const int f = i / N, n = i - f * N;
+    const T nrm[3] = {a.fgeo[4 * f], a.fgeo[4 * f + 1], a.fgeo[4 * f + 2]};
+    const T S3 = a.fgeo[4 * f + 3] / T(3);
+    int nd[3];
+    T u[3][3], v[3][3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        nd[b] = a.fnodes[3 * f + b];
+        const T *r = a.y + size_t(nd[b]) * N4 + n;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) u[b][k] = r[k * N];
+        if (MODE != MODE_RES) {
+            const bool dir = a.flag[nd[b]] & 1;
+            const T *rv = a.v + size_t(nd[b]) * N4 + n;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) v[b][k] = dir ? T(0) : rv[k * N];
+        }
+    }
+    const int o = a.foutlet[f];
+    T h = 0;
+    if (o >= 0) {
+        if (MODE == MODE_RES) h = a.hbase[o * N + n] - a.R[o] * a.Q[o * N + n];
+        else h = -a.R[o] * a.Q[o * N + n];
+    }
+    T c[3][3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) c[b][k] = -S3 * h * nrm[k];
+    const T cb = -S3 * T(0.5) * (T(0.5) * a.rho * a.beta);
+    const int e0[3] = {0, 1, 0}, e1[3] = {1, 2, 2};
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        T um[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) um[k] = T(0.5) * (u[e0[m]][k] + u[e1[m]][k]);
+        const T s = um[0] * nrm[0] + um[1] * nrm[1] + um[2] * nrm[2];
+        const T sm = s < T(0) ? s : T(0);
+        T term[3];
+        if (MODE == MODE_RES) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) term[k] = sm * um[k];
+        } else {
+            T vm[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) vm[k] = T(0.5) * (v[e0[m]][k] + v[e1[m]][k]);
+            const T vn = (MODE == MODE_JVE && s < T(0)) ? vm[0] * nrm[0] + vm[1] * nrm[1] + vm[2] * nrm[2] : T(0);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) term[k] = sm * vm[k] + vn * um[k];
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            c[e0[m]][k] += cb * term[k];
+            c[e1[m]][k] += cb * term[k];
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) atomicAdd(a.out + size_t(nd[b]) * N4 + k * N + n, c[b][k]);
+}
+
+template <typename T, int MODE>
+__global__ void dirichlet_rows_kernel(const int *__restrict__ dir_nodes, int n_dir, const T *__restrict__ v,
+                                      T *__restrict__ out, int N) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_dir * 3 * N) return;
+    const int d = i / (3 * N), r = i - d * 3 * N;
+    const size_t idx = size_t(dir_nodes[d]) * 4 * N + r;
+    if (MODE == MODE_RES) out[idx] = T(0);
+    else if (MODE == MODE_DIAG) out[idx] = T(1);
+    else out[idx] = v[idx];
+}
+
+// ---------------------------------------------------------------------------------------------------
+// boundary-condition sampling and harmonic transforms (Eqs. upgh_def, upghdft)
+
+// angle 2 pi k n / N reduced exactly to [0, 2 pi) through (k n mod N)
+__device__ __forceinline__ void cos_sin_kn(int k, int n, int N, double &c, double &s) {
+    const int r = int((long long)k * n % N);
+    sincospi(2.0 * double(r) / double(N), &s, &c);
+}
+
+__global__ void sample_waveforms_kernel(const double *__restrict__ coef, int n_wave, int n_h, int N,
+                                        double *__restrict__ W) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_wave * N) return;
+    const int w = i / N, n = i - w * N;
+    const double *c = coef + size_t(w) * (2 * n_h + 1);
+    double q = c[0];
+    for (int k = 1; k <= n_h; ++k) {
+        double cs, sn;
+        cos_sin_kn(k, n, N, cs, sn);
+        q += c[2 * k - 1] * cs + c[2 * k] * sn;
+    }
+    W[i] = q;
+}
+
+__global__ void dirichlet_values_kernel(const int *__restrict__ dir_nodes, const int *__restrict__ dir_wave,
+                                        const double *__restrict__ prof, int n_dir,
+                                        const double *__restrict__ W, int N, double *__restrict__ g) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_dir * 3 * N) return;
+    const int d = i / (3 * N), r = i - d * 3 * N, k = r / N, n = r - k * N;
+    const int wv = dir_wave[d];
+    g[i] = wv < 0 ? 0.0 : prof[3 * d + k] * W[wv * N + n];
+    (void)dir_nodes;
+}
+
+__global__ void apply_dirichlet_kernel(const int *__restrict__ dir_nodes, int n_dir,
+                                       const double *__restrict__ g, double *__restrict__ y, int N) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_dir * 3 * N) return;
+    const int d = i / (3 * N), r = i - d * 3 * N;
+    y[size_t(dir_nodes[d]) * 4 * N + r] = g[i];
+}
+
+// inverse = 0: coef[row][m] from y[row][n] (a0, a_k = 2/N sum y cos, b_k = 2/N sum y sin)
+// inverse = 1: y[row][n] from coef[row][m]
+__global__ void harmonics_kernel(const double *__restrict__ in, double *__restrict__ out, int64_t rows,
+                                 int N, int n_h) {
+    const int M = 2 * n_h + 1;
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= rows * M) return;
+    const int64_t row = i / M;
+    const int m = int(i - row * M);
+    const double *y = in + row * N;
+    double acc = 0.0;
+    if (m == 0) {
+        for (int n = 0; n < N; ++n) acc += y[n];
+        acc /= double(N);
+    } else {
+        const int k = (m + 1) / 2;
+        const bool is_sin = (m % 2) == 0;
+        for (int n = 0; n < N; ++n) {
+            double cs, sn;
+            cos_sin_kn(k, n, N, cs, sn);
+            acc += y[n] * (is_sin ? sn : cs);
+        }
+        acc *= 2.0 / double(N);
+    }
+    out[i] = acc;
+}
+
+__global__ void synthesis_kernel(const double *__restrict__ coef, double *__restrict__ y, int64_t rows,
+                                 int N, int n_h) {
+    const int M = 2 * n_h + 1;
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= rows * N) return;
+    const int64_t row = i / N;
+    const int n = int(i - row * N);
+    const double *c = coef + row * M;
+    double acc = c[0];
+    for (int k = 1; k <= n_h; ++k) {
+        double cs, sn;
+        cos_sin_kn(k, n, N, cs, sn);
+        acc += c[2 * k - 1] * cs + c[2 * k] * sn;
+    }
+    y[i] = acc;
+}
+
+inline int nblk(int64_t n, int b) { return int((n + b - 1) / b); }
+
+}  // namespace
+
+size_t elem_smem_bytes(int mode, int N, int nl_max, int ep_max, size_t tsize) {
+    return make_layout(mode, N, nl_max, ep_max, tsize).total;
+}
+
+template <typename T, int MODE>
+static void launch_elem_mode(const ElemArgs<T> &a, int grid, cudaStream_t s) {
+    const size_t smem = elem_smem_bytes(MODE, a.N, a.pv.nl_max, a.pv.ep_max, sizeof(T));
+    static size_t configured = 0;
+    if (smem > 48 * 1024 && smem > configured) {
+        cudaFuncSetAttribute(elem_kernel<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        configured = smem;
+    }
+    elem_kernel<T, MODE><<<grid, kBlock, smem, s>>>(a);
+}
+
+template <typename T>
+void launch_elem(int mode, const ElemArgs<T> &a, int grid, cudaStream_t s) {
+    switch (mode) {
+        case MODE_RES: launch_elem_mode<T, MODE_RES>(a, grid, s); break;
+        case MODE_JVP: launch_elem_mode<T, MODE_JVP>(a, grid, s); break;
+        case MODE_JVE: launch_elem_mode<T, MODE_JVE>(a, grid, s); break;
+        default: launch_elem_mode<T, MODE_DIAG>(a, grid, s); break;
+    }
+}
+
+template <typename T>
+void launch_geom(const double *xyz, const int *tets, int n_tets, double nu, T *geom, cudaStream_t s) {
+    if (n_tets > 0) geom_kernel<T><<<nblk(n_tets, 128), 128, 0, s>>>(xyz, tets, n_tets, nu, geom);
+}
+
+template <typename T>
+void launch_faces(int mode, const FaceArgs<T> &a, bool has_resistance, cudaStream_t s) {
+    const int64_t n = int64_t(a.n_faces) * a.N;
+    if (n == 0 || mode == MODE_DIAG) return;
+    const int g = nblk(n, 128);
+    if (mode == MODE_RES) {
+        if (has_resistance) outlet_flux_kernel<T, MODE_RES><<<g, 128, 0, s>>>(a);
+        face_kernel<T, MODE_RES><<<g, 128, 0, s>>>(a);
+    } else if (mode == MODE_JVP) {
+        if (has_resistance) outlet_flux_kernel<T, MODE_JVP><<<g, 128, 0, s>>>(a);
+        face_kernel<T, MODE_JVP><<<g, 128, 0, s>>>(a);
+    } else {
+        if (has_resistance) outlet_flux_kernel<T, MODE_JVE><<<g, 128, 0, s>>>(a);
+        face_kernel<T, MODE_JVE><<<g, 128, 0, s>>>(a);
+    }
+}
+
+template <typename T>
+void launch_dirichlet_rows(int mode, const int *dir_nodes, int n_dir, const T *v, T *out, int N,
+                           cudaStream_t s) {
+    const int64_t n = int64_t(n_dir) * 3 * N;
+    if (n == 0) return;
+    const int g = nblk(n, 256);
+    if (mode == MODE_RES) dirichlet_rows_kernel<T, MODE_RES><<<g, 256, 0, s>>>(dir_nodes, n_dir, v, out, N);
+    else if (mode == MODE_DIAG) dirichlet_rows_kernel<T, MODE_DIAG><<<g, 256, 0, s>>>(dir_nodes, n_dir, v, out, N);
+    else dirichlet_rows_kernel<T, MODE_JVP><<<g, 256, 0, s>>>(dir_nodes, n_dir, v, out, N);
+}
+
+void launch_sample_waveforms(const double *coef, int n_wave, int n_h, int N, double T, double *W,
+                             cudaStream_t s) {
+    (void)T;
+    if (n_wave > 0) sample_waveforms_kernel<<<nblk(int64_t(n_wave) * N, 128), 128, 0, s>>>(coef, n_wave, n_h, N, W);
+}
+
+void launch_dirichlet_values(const int *dir_nodes, const int *dir_wave, const double *dir_profile,
+                             int n_dir, const double *W, int N, double *g, cudaStream_t s) {
+    if (n_dir > 0)
+        dirichlet_values_kernel<<<nblk(int64_t(n_dir) * 3 * N, 256), 256, 0, s>>>(dir_nodes, dir_wave, dir_profile,
+                                                                                n_dir, W, N, g);
+}
+
+void launch_apply_dirichlet(const int *dir_nodes, int n_dir, const double *g, double *y, int N,
+                            cudaStream_t s) {
+    if (n_dir > 0)
+        apply_dirichlet_kernel<<<nblk(int64_t(n_dir) * 3 * N, 256), 256, 0, s>>>(dir_nodes, n_dir, g, y, N);
+}
+
+void launch_harmonics(const double *in, double *out, int64_t rows, int N, int n_h, int inverse, double T,
+                      cudaStream_t s) {
+    (void)T;
+    if (rows == 0) return;
+    if (!inverse)
+        harmonics_kernel<<<nblk(rows * (2 * n_h + 1), 256), 256, 0, s>>>(in, out, rows, N, n_h);
+    else
+        synthesis_kernel<<<nblk(rows * N, 256), 256, 0, s>>>(in, out, rows, N, n_h);
+}
+
+template void launch_elem<float>(int, const ElemArgs<float> &, int, cudaStream_t);
+template void launch_elem<double>(int, const ElemArgs<double> &, int, cudaStream_t);
+template void launch_geom<float>(const double *, const int *, int, double, float *, cudaStream_t);
+template void launch_geom<double>(const double *, const int *, int, double, double *, cudaStream_t);
+template void launch_faces<float>(int, const FaceArgs<float> &, bool, cudaStream_t);
+template void launch_faces<double>(int, const FaceArgs<double> &, bool, cudaStream_t);
+template void launch_dirichlet_rows<float>(int, const int *, int, const float *, float *, int, cudaStream_t);
+template void launch_dirichlet_rows<double>(int, const int *, int, const double *, double *, int, cudaStream_t);
+
+}  // namespace hb

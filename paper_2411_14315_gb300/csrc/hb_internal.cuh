@@ -1,0 +1,120 @@
+// Internal declarations shared by the CUDA translation units of libhbgls (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+namespace hb {
+
+// Kernel variants of the fused element pass.
+enum Mode : int {
+    MODE_RES = 0,    // residual, Eq. (Rmc)
+    MODE_JVP = 1,    // paper tangent (P + C) v, Eqs. (ptangent), (K_mat), (ctangent), (F_mat)
+    MODE_JVE = 2,    // exact Jacobian-vector product
+    MODE_DIAG = 3    // Jacobi diagonal of P (+ pseudo mass), Sec. 2.3
+};
+
+constexpr int kGeomStride = 16;       // per element: grad N_a (4 x 3), V, C_I nu^2 G:G, 2 pad
+constexpr int kBlock = 256;           // threads per CTA of the element kernel
+constexpr int kMaxN = 31;             // largest number of time instances supported
+constexpr double kCI = 3.0;           // Eq. (tau)
+// 4-point degree-2 Gauss rule on a tetrahedron (barycentric coordinates of the points)
+constexpr double kQA = 0.5854101966249685;
+constexpr double kQB = 0.1381966011250105;
+
+// Fields per local node staged in shared memory, by mode.
+__host__ __device__ constexpr int in_fields(int mode) {
+    return mode == MODE_RES ? 7 : mode == MODE_JVP ? 8 : mode == MODE_JVE ? 14 : 4;
+}
+__host__ __device__ constexpr int out_fields(int mode) { return mode == MODE_DIAG ? 4 : 7; }
+
+// Element patches: elements renumbered so each patch's elements are contiguous; each patch lists its
+// distinct nodes; each element stores its 4 nodes as local indices (uint8) into that list.
+template <typename T>
+struct PatchView {
+    int n_patches;
+    int nl_max;                    // largest node count of a patch
+    int ep_max;                    // largest element count of a patch
+    const int *eptr;               // [P+1]
+    const int *nptr;               // [P+1]
+    const int *nodes;              // [nptr[P]]
+    const uint32_t *lconn;         // [E]
+    const T *geom;                 // [E][kGeomStride]
+};
+
+template <typename T>
+struct ElemArgs {
+    PatchView<T> pv;
+    const T *y;                    // state, instance layout [n][4][N]
+    const T *v;                    // direction (JVP, JVE)
+    T *out;                        // accumulated output, instance layout (zeroed by the caller)
+    const T *H;                    // [N][N]
+    const uint8_t *flag;           // per node, bit 0: Dirichlet velocity
+    int N;
+    T rho, mu, shift;
+};
+
+// Boundary (Neumann) faces.
+template <typename T>
+struct FaceArgs {
+    int n_faces;                   // Neumann faces
+    const int *fnodes;             // [F][3]
+    const T *fgeo;                 // [F][4]: outward unit normal, area
+    const int *foutlet;            // [F] outlet index or -1 (traction free)
+    const T *hbase;                // [n_out][N]: -P_d(t_n)
+    const T *R;                    // [n_out] resistance (0 for pressure outlets)
+    T *Q;                          // [n_out][N] outlet flux scratch (zeroed by caller)
+    const uint8_t *flag;
+    const T *y;
+    const T *v;
+    T *out;
+    int N;
+    T rho, beta;
+};
+
+size_t elem_smem_bytes(int mode, int N, int nl_max, int ep_max, size_t tsize);
+
+template <typename T>
+void launch_elem(int mode, const ElemArgs<T> &a, int grid, cudaStream_t s);
+template <typename T>
+void launch_geom(const double *xyz, const int *tets_patch_order, int n_tets, double nu, T *geom,
+                 cudaStream_t s);
+template <typename T>
+void launch_faces(int mode, const FaceArgs<T> &a, bool has_resistance, cudaStream_t s);
+template <typename T>
+void launch_dirichlet_rows(int mode, const int *dir_nodes, int n_dir, const T *v, T *out, int N,
+                           cudaStream_t s);
+
+// sampling of boundary waveforms (Eq. upgh_def at the instances of Eq. upghharm)
+void launch_sample_waveforms(const double *coef, int n_wave, int n_h, int N, double T, double *W,
+                             cudaStream_t s);
+void launch_dirichlet_values(const int *dir_nodes, const int *dir_wave, const double *dir_profile,
+                             int n_dir, const double *W, int N, double *g, cudaStream_t s);
+void launch_apply_dirichlet(const int *dir_nodes, int n_dir, const double *g, double *y, int N,
+                            cudaStream_t s);
+void launch_harmonics(const double *y, double *coef, int64_t rows, int N, int n_h, int inverse,
+                      double T, cudaStream_t s);
+
+// vector kernels
+template <typename A, typename B>
+void launch_convert(const A *x, B *y, int64_t n, cudaStream_t s);
+void launch_axpy(double a, const double *x, double *y, int64_t n, cudaStream_t s);
+void launch_scale_copy(double a, const double *x, double *y, int64_t n, cudaStream_t s);
+template <typename T>
+void launch_precond(const double *x, const double *d, T *z, int64_t n, cudaStream_t s);
+// partials[nb * (k + 1)]; result[k + 1] = (V_j . w for j < k, w . w)
+int multidot_blocks(int64_t n);
+void launch_multidot(const double *V, int64_t ld, int k, const double *w, int64_t n, double *partials,
+                     double *result, cudaStream_t s);
+// w -= sum_j h[j] V_j; result[0] = ||w||^2 after the update (partials scratch as above)
+void launch_multiaxpy_norm(const double *V, int64_t ld, int k, const double *h, double *w, int64_t n,
+                           double *partials, double *result, cudaStream_t s);
+// y = sum_j c[j] V_j (c on device)
+void launch_combine(const double *V, int64_t ld, int k, const double *c, double *y, int64_t n,
+                    cudaStream_t s);
+void launch_dot(const double *x, const double *y, int64_t n, double *partials, double *result,
+                cudaStream_t s);
+
+}  // namespace hb

@@ -1,0 +1,274 @@
+"""Thin Python binding of libhbgls (the C ABI declared in include/hbgls.h).
+
+Argument marshalling only: every step of the method runs in the library's CUDA kernels.  Importing
+this module does not load the library; the first call does, and raises if libhbgls.so has not been
+built (there is no fallback).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libhbgls.so")
+
+HB_OK = 0
+STATUS = {0: "HB_OK", 1: "HB_ERR_INVALID_ARG", 2: "HB_ERR_MESH", 3: "HB_ERR_CUDA", 4: "HB_ERR_OOM",
+          5: "HB_ERR_NOT_CONVERGED", 6: "HB_ERR_NAN", 7: "HB_ERR_TIMEOUT", 8: "HB_ERR_STATE"}
+
+PAPER, EXACT = 0, 1
+FP64, FP32 = 0, 1
+
+
+class HBError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class hb_mesh(C.Structure):
+    _fields_ = [("n_nodes", C.c_int64), ("n_tets", C.c_int64), ("n_faces", C.c_int64),
+                ("xyz", C.POINTER(C.c_double)), ("tets", C.POINTER(C.c_int32)),
+                ("faces", C.POINTER(C.c_int32)), ("face_tag", C.POINTER(C.c_int32))]
+
+
+class hb_solve_opts(C.Structure):
+    _fields_ = [("precision", C.c_int), ("rtol", C.c_double), ("switch_rtol", C.c_double),
+                ("gmres_rtol_pseudo", C.c_double), ("gmres_rtol_newton", C.c_double),
+                ("gmres_restart", C.c_int), ("max_gmres", C.c_int), ("max_steps", C.c_int),
+                ("dt_pseudo", C.c_double), ("cfl", C.c_double), ("use_learned", C.c_int),
+                ("verbose", C.c_int)]
+
+
+class hb_report(C.Structure):
+    _fields_ = [("steps", C.c_int), ("newton_steps", C.c_int), ("gmres_iters", C.c_int),
+                ("jv_calls", C.c_int), ("residual_calls", C.c_int), ("res0", C.c_double),
+                ("res_final", C.c_double), ("seconds", C.c_double), ("dt_pseudo", C.c_double),
+                ("status", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class hb_info(C.Structure):
+    _fields_ = [("n_nodes", C.c_int64), ("n_tets", C.c_int64), ("n_faces", C.c_int64),
+                ("n_dirichlet_nodes", C.c_int64), ("n_neumann_faces", C.c_int64), ("n_h", C.c_int),
+                ("N", C.c_int), ("n_patches32", C.c_int), ("n_patches64", C.c_int),
+                ("patch_nodes_max32", C.c_int), ("patch_elems_max32", C.c_int),
+                ("device_bytes", C.c_int64), ("h_char", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_DP = C.POINTER(C.c_double)
+_VP = C.c_void_p
+_P = C.c_void_p
+# name -> (argtypes, restype); every entry point declared in include/hbgls.h
+SIGNATURES = {
+    "hb_create": ([C.POINTER(hb_mesh), C.c_double, C.c_double, C.c_double, C.c_int, C.c_int, _VP,
+                   C.POINTER(_P)], C.c_int),
+    "hb_destroy": ([_P], C.c_int),
+    "hb_last_error": ([], C.c_char_p),
+    "hb_set_inflow": ([_P, C.c_int, _DP, _DP, _DP], C.c_int),
+    "hb_set_outlet_pressure": ([_P, C.c_int, _DP, _DP], C.c_int),
+    "hb_set_outlet_resistance": ([_P, C.c_int, C.c_double, _DP, _DP], C.c_int),
+    "hb_set_backflow": ([_P, C.c_double], C.c_int),
+    "hb_set_initial": ([_P, _DP], C.c_int),
+    "hb_set_instances": ([_P, _DP], C.c_int),
+    "hb_default_opts": ([C.POINTER(hb_solve_opts)], C.c_int),
+    "hb_solve": ([_P, C.POINTER(hb_solve_opts), C.POINTER(hb_report)], C.c_int),
+    "hb_get_harmonics": ([_P, _DP], C.c_int),
+    "hb_get_instances": ([_P, _DP], C.c_int),
+    "hb_residual": ([_P, _DP, _DP, C.c_int], C.c_int),
+    "hb_jv": ([_P, _DP, _DP, _DP, C.c_int, C.c_int, C.c_double], C.c_int),
+    "hb_jacobi_diag": ([_P, _DP, _DP, C.c_int, C.c_double], C.c_int),
+    "hb_residual_dev": ([_P, _VP, _VP, C.c_int, _VP], C.c_int),
+    "hb_jv_dev": ([_P, _VP, _VP, _VP, C.c_int, C.c_int, C.c_double, _VP], C.c_int),
+    "hb_jacobi_diag_dev": ([_P, _VP, _VP, C.c_int, C.c_double, _VP], C.c_int),
+    "hb_get_info": ([_P, C.POINTER(hb_info)], C.c_int),
+    "hb_launch_count": ([_P], C.c_int64),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libhbgls.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libhbgls.so not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, (args, res) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(st: int):
+    if st != HB_OK:
+        raise HBError(st, lib().hb_last_error().decode())
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(_DP)
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None and a.shape != tuple(shape):
+        a = a.reshape(shape)
+    return a
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    return C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+
+
+class Problem:
+    """One HB problem on one device (hb_create .. hb_destroy)."""
+
+    def __init__(self, xyz, tets, faces, face_tag, rho: float, mu: float, T: float, n_h: int,
+                 device: int = 0, stream=None):
+        self._xyz = _f64(xyz)
+        self._tets = np.ascontiguousarray(tets, dtype=np.int32)
+        self._faces = np.ascontiguousarray(faces, dtype=np.int32)
+        self._tag = np.ascontiguousarray(face_tag, dtype=np.int32)
+        m = hb_mesh(self._xyz.shape[0], self._tets.shape[0], self._faces.shape[0], _dptr(self._xyz),
+                    self._tets.ctypes.data_as(C.POINTER(C.c_int32)),
+                    self._faces.ctypes.data_as(C.POINTER(C.c_int32)),
+                    self._tag.ctypes.data_as(C.POINTER(C.c_int32)))
+        h = _P()
+        _check(lib().hb_create(C.byref(m), rho, mu, T, n_h, device, _stream_handle(stream), C.byref(h)))
+        self._h = h
+        self.n_nodes = int(self._xyz.shape[0])
+        self.n_h = int(n_h)
+        self.N = 2 * self.n_h + 1
+        self.shape = (self.n_nodes, 4, self.N)
+
+    @classmethod
+    def from_mesh(cls, mesh, rho, mu, T, n_h, **kw):
+        return cls(mesh.xyz, mesh.tets, mesh.faces, mesh.face_tag, rho, mu, T, n_h, **kw)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().hb_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # boundary conditions -------------------------------------------------------------------------
+    def _wave(self, a, b):
+        a = _f64(a)
+        b = _f64(b)
+        if a.shape != (self.n_h + 1,) or b.shape != (self.n_h + 1,):
+            raise ValueError("waveform arrays need n_h + 1 entries")
+        return a, b
+
+    def set_inflow(self, tag: int, profile, a, b):
+        a, b = self._wave(a, b)
+        prof = None if profile is None else _f64(profile, (self.n_nodes, 3))
+        _check(lib().hb_set_inflow(self._h, tag, None if prof is None else _dptr(prof), _dptr(a), _dptr(b)))
+
+    def set_outlet_pressure(self, tag: int, a, b):
+        a, b = self._wave(a, b)
+        _check(lib().hb_set_outlet_pressure(self._h, tag, _dptr(a), _dptr(b)))
+
+    def set_outlet_resistance(self, tag: int, R: float, a, b):
+        a, b = self._wave(a, b)
+        _check(lib().hb_set_outlet_resistance(self._h, tag, R, _dptr(a), _dptr(b)))
+
+    def set_backflow(self, beta: float):
+        _check(lib().hb_set_backflow(self._h, beta))
+
+    def set_initial(self, harmonics=None):
+        hm = None if harmonics is None else _f64(harmonics, (self.n_nodes, 4, 2 * self.n_h + 1))
+        _check(lib().hb_set_initial(self._h, None if hm is None else _dptr(hm)))
+
+    def set_instances(self, y=None):
+        yy = None if y is None else _f64(y, self.shape)
+        _check(lib().hb_set_instances(self._h, None if yy is None else _dptr(yy)))
+
+    # hot path, host buffers ------------------------------------------------------------------------
+    def residual(self, y, precision: int = FP64):
+        y = _f64(y, self.shape)
+        r = np.empty(self.shape)
+        _check(lib().hb_residual(self._h, _dptr(y), _dptr(r), precision))
+        return r
+
+    def jv(self, y, v, kind: int = PAPER, precision: int = FP64, shift: float = 0.0, out=None):
+        y = _f64(y, self.shape)
+        v = _f64(v, self.shape)
+        r = np.empty(self.shape) if out is None else out
+        _check(lib().hb_jv(self._h, _dptr(y), _dptr(v), _dptr(r), kind, precision, shift))
+        return r
+
+    def jacobi_diag(self, y, precision: int = FP64, shift: float = 0.0):
+        y = _f64(y, self.shape)
+        d = np.empty(self.shape)
+        _check(lib().hb_jacobi_diag(self._h, _dptr(y), _dptr(d), precision, shift))
+        return d
+
+    # hot path, device buffers (torch tensors of float64 / float32, instance layout) --------------
+    def residual_dev(self, y, r, precision: int, stream=None):
+        _check(lib().hb_residual_dev(self._h, y.data_ptr(), r.data_ptr(), precision, _stream_handle(stream)))
+
+    def jv_dev(self, y, v, out, kind: int, precision: int, shift: float = 0.0, stream=None):
+        _check(lib().hb_jv_dev(self._h, y.data_ptr(), v.data_ptr(), out.data_ptr(), kind, precision, shift,
+                               _stream_handle(stream)))
+
+    def jacobi_diag_dev(self, y, d, precision: int, shift: float = 0.0, stream=None):
+        _check(lib().hb_jacobi_diag_dev(self._h, y.data_ptr(), d.data_ptr(), precision, shift,
+                                        _stream_handle(stream)))
+
+    # solve -----------------------------------------------------------------------------------------
+    @staticmethod
+    def default_opts(**kw) -> hb_solve_opts:
+        o = hb_solve_opts()
+        _check(lib().hb_default_opts(C.byref(o)))
+        for k, v in kw.items():
+            setattr(o, k, v)
+        return o
+
+    def solve(self, opts: hb_solve_opts | None = None, check: bool = True, **kw):
+        o = opts if opts is not None else self.default_opts(**kw)
+        rep = hb_report()
+        st = lib().hb_solve(self._h, C.byref(o), C.byref(rep))
+        if check:
+            _check(st)
+        return rep.as_dict()
+
+    def harmonics(self):
+        out = np.empty((self.n_nodes, 4, 2 * self.n_h + 1))
+        _check(lib().hb_get_harmonics(self._h, _dptr(out)))
+        return out
+
+    def instances(self):
+        out = np.empty(self.shape)
+        _check(lib().hb_get_instances(self._h, _dptr(out)))
+        return out
+
+    def info(self):
+        i = hb_info()
+        _check(lib().hb_get_info(self._h, C.byref(i)))
+        return i.as_dict()
+
+    def launch_count(self) -> int:
+        return int(lib().hb_launch_count(self._h))
