@@ -1,0 +1,420 @@
+#!/usr/bin/env python3
+"""Benchmark of the harmonic balance GLS hot path on GB300.
+
+Metric: HB Jv element-instances/s -- n_tets x N per application of the paper's tangent (Eqs. ptangent,
+K_mat, ctangent, F_mat; arXiv 2411.14315 Sec. 2.3) in FP32, including the in-patch spectral coupling,
+boundary terms and Dirichlet rows, on the Glenn-like T-junction stand-in (~1.0M tetrahedra, N = 21
+instances, resistance outlets).  A step is one Jv application with inputs resident in HBM; L2 is
+flushed (256 MiB write) between steps.  `e2e` is the same metric through the C ABI with host buffers
+(host-to-device copies of y and v and the device-to-host copy of Jv inside each step).
+
+Extra keys: residual and exact-Jv rates, time to solve the Womersley pipe in mixed precision and in
+plain FP64 (both to 1e-8 of a tight FP64 solution), and the CPU oracle's rate on a bounded sample.
+
+`--impl reference` times the CPU oracle (the plain FP64 statement of the method) on a bounded sample
+of the same workload, as the comparison arm.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "HB Jv element-instances/s"
+UNIT = "element-instances/s"
+FLOPS_PER_UNIT_JVP = 800.0        # algorithmic FP32 flops per element-instance, paper-tangent Jv
+BYTES_PER_UNIT_JVP = 11.0         # algorithmic HBM bytes per element-instance at N = 21
+SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12   # 80.5
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "elem_jvp_fp32_glenn_like.md")
+KERNEL_SOURCE = os.path.join(ROOT, "paper_2411_14315_gb300", "csrc", "hb_element.cu")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--tets", type=int, default=1_000_000)
+    ap.add_argument("--n-h", type=int, default=10)
+    ap.add_argument("--skip-solve", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--extra", action="store_true", help="also time residual / exact Jv / FP64 rates")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------------------------------
+# distributed plumbing (replicas only: no data-path collective)
+
+
+class Dist:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+
+    def init(self, backend):
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.init_process_group(backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def done(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------------------------------
+# clocks during the timed region
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(self.device)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        mhz, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                mhz.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": mx, "samples": len(mhz),
+                "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------------------------------
+# CPU oracle on a bounded sample
+
+
+def oracle_sample(spec, n_elems: int):
+    """Oracle problem on the first n_elems tetrahedra of the workload mesh (no boundary faces)."""
+    from oracle import hb_oracle as O
+    m = spec.mesh
+    sub = m.tets[:n_elems]
+    used, inv = np.unique(sub, return_inverse=True)
+    pr = O.HBProblem(m.xyz[used], inv.reshape(-1, 4), np.zeros((0, 3), dtype=np.int64), np.zeros(0, dtype=np.int64),
+                     spec.rho, spec.mu, spec.T, spec.n_h)
+    return pr, len(used)
+
+
+def time_oracle_jv(spec, n_elems: int, reps: int):
+    from oracle import hb_oracle as O
+    from paper_2411_14315_gb300 import inputs as I
+    pr, nn = oracle_sample(spec, n_elems)
+    y = I.random_state(nn, spec.N, 71)
+    v = I.random_state(nn, spec.N, 72)
+    ts = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        O.jv_paper(pr, y, v)
+        ts.append(time.perf_counter() - t0)
+    return n_elems * spec.N / statistics.median(ts), ts
+
+
+def cpu_baseline(spec, target_s: float = 12.0):
+    n0 = 4000
+    rate0, _ = time_oracle_jv(spec, n0, 1)
+    n_el = int(min(spec.mesh.n_tets, max(n0, rate0 * target_s / 3 / spec.N)))
+    rate, ts = time_oracle_jv(spec, n_el, 3)
+    return {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"oracle jv_paper (FP64 numpy) on the first {n_el} of {spec.mesh.n_tets} tetrahedra of the "
+                      f"workload mesh at N={spec.N}, median of 3 applications ({sum(ts):.1f} s)"}
+
+
+def run_reference(args, dist: Dist, spec, config):
+    if dist.rank != 0:
+        return
+    K, W = args.steps, args.warmup
+    budget = 150.0
+    rate0, _ = time_oracle_jv(spec, 3000, 1)
+    per_step = budget / max(1, K + W)
+    n_el = int(min(spec.mesh.n_tets, max(200, rate0 * per_step / spec.N)))
+    from oracle import hb_oracle as O
+    from paper_2411_14315_gb300 import inputs as I
+    pr, nn = oracle_sample(spec, n_el)
+    y = I.random_state(nn, spec.N, 71)
+    v = I.random_state(nn, spec.N, 72)
+    for _ in range(W):
+        O.jv_paper(pr, y, v)
+    t0 = time.perf_counter()
+    for _ in range(K):
+        O.jv_paper(pr, y, v)
+    dt = time.perf_counter() - t0
+    value = n_el * spec.N * K / dt
+    sample = (f"oracle jv_paper (FP64 numpy, 1 thread) on the first {n_el} of {spec.mesh.n_tets} tetrahedra of "
+              f"the workload mesh at N={spec.N}, per step")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": K, "warmup": W, "ms_per_step": 1e3 * dt / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------------------------------
+# GPU arm
+
+
+def traffic_from_profile():
+    """DRAM bytes per launch of the element kernel from the committed ncu summary, if it was taken on
+    the current kernel source (same SHA-256), else None."""
+    try:
+        text = open(PROFILE_SUMMARY).read()
+        sha = hashlib.sha256(open(KERNEL_SOURCE, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        if ":" in line and line.strip().startswith("-"):
+            k, v = line.strip()[1:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_sha256") != sha:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch_full_size"])
+    except (KeyError, ValueError):
+        return None
+
+
+def time_solves():
+    """Time to solve the Womersley pipe (~3,000 tets, N = 9) to 1e-8 of a tight FP64 solution."""
+    from paper_2411_14315_gb300 import hbgls
+    from paper_2411_14315_gb300 import workloads as W
+    spec = W.womersley_spec()
+    out = {"workload": "womersley pipe ~3,000 tets N=9"}
+    ref = hbgls.Problem.from_spec(spec)
+    rep = ref.solve(precision=0, rtol=1e-13, check=False)
+    yref = ref.instances()
+    out["reference"] = {"status": rep["status"], "res_rel": rep["res_final"] / max(rep["res0"], 1e-300)}
+    for name, prec in (("mixed", 1), ("fp64", 0)):
+        p = hbgls.Problem.from_spec(spec)
+        rep = p.solve(precision=prec, rtol=1e-10, check=False)
+        y = p.instances()
+        err = float(np.linalg.norm(y - yref) / np.linalg.norm(yref))
+        out[name] = {"seconds": rep["seconds"], "rel_err_vs_fp64_ref": err, "status": rep["status"],
+                     "steps": rep["steps"], "gmres_iters": rep["gmres_iters"], "jv_calls": rep["jv_calls"]}
+        p.close()
+    ref.close()
+    return out
+
+
+def run_ours(args, dist: Dist, spec, config):
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2411_14315_gb300 import hbgls
+    from paper_2411_14315_gb300 import inputs as I
+
+    dev = dist.local if torch.cuda.device_count() > dist.local else 0
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream()          # one explicit stream: the library's kernels, the L2 flush
+    torch.cuda.set_stream(stream)         # and the timing events are all ordered on it
+    prob = hbgls.Problem.from_spec(spec, device=dev, stream=stream)
+    info = prob.info()
+    n, N = spec.mesh.n_nodes, spec.N
+    units = spec.mesh.n_tets * N
+    y = I.random_state(n, N, 81)
+    v = I.random_state(n, N, 82)
+    y32 = torch.tensor(y, dtype=torch.float32, device="cuda")
+    v32 = torch.tensor(v, dtype=torch.float32, device="cuda")
+    out32 = torch.empty_like(y32)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MiB > 129 MB L2
+    shift = 1.5 * spec.rho / 0.005
+
+    def jv():
+        prob.jv_dev(y32, v32, out32, hbgls.PAPER, hbgls.FP32, shift, stream=stream)
+
+    K, W = args.steps, args.warmup
+    for i in range(W):
+        flush.fill_(float(i))
+        jv()
+    torch.cuda.synchronize()
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    clocks = ClockSampler(dev)
+    dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.25)
+    prob.profile_read()
+    prob.profile_elem(True)
+    l0 = prob.launch_count()
+    for i in range(K):
+        flush.fill_(float(i))
+        ev0[i].record(stream)
+        jv()
+        ev1[i].record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    launches = prob.launch_count() - l0
+    prob.profile_elem(False)
+    elem_ms, elem_n = prob.profile_read()
+    clk = clocks.stop()
+    step_ms = [ev0[i].elapsed_time(ev1[i]) for i in range(K)]
+    ms = dist.max(statistics.mean(step_ms))
+    value = dist.world * units / (ms / 1e3)
+    elem_avg_ms = elem_ms / max(1, elem_n)
+    achieved = FLOPS_PER_UNIT_JVP * units / (elem_avg_ms / 1e3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+            "kernel": "elem_kernel<float, MODE_JVP>", "kernel_ms": elem_avg_ms,
+            "flops_per_unit": FLOPS_PER_UNIT_JVP, "units_per_launch": units,
+            "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (derived, not measured)"}
+    tr = traffic_from_profile()
+    if tr is not None:
+        roof["traffic"] = tr
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    hbm = {"algorithmic_bytes_per_unit": BYTES_PER_UNIT_JVP,
+           "achieved_gbs": BYTES_PER_UNIT_JVP * units / (elem_avg_ms / 1e3) / 1e9,
+           "peak_gbs": hbm_peak, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+    hbm["frac"] = hbm["achieved_gbs"] / hbm_peak
+
+    result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": K, "warmup": W,
+              "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+              "dtype": "f32", "data": "synthetic", "config": dict(config, n_patches=info["n_patches32"],
+                                                                  patch_nodes_max=info["patch_nodes_max32"]),
+              "roofline": roof, "hbm_view": hbm, "clocks": clk, "gpu_launches": int(launches)}
+
+    # end to end through the C ABI with pinned host buffers
+    if not args.skip_e2e:
+        hy = torch.empty((n, 4, N), dtype=torch.float64, pin_memory=True).numpy()
+        hv = torch.empty((n, 4, N), dtype=torch.float64, pin_memory=True).numpy()
+        ho = torch.empty((n, 4, N), dtype=torch.float64, pin_memory=True).numpy()
+        hy[...] = y
+        hv[...] = v
+        for _ in range(2):
+            prob.jv(hy, hv, kind=hbgls.PAPER, precision=hbgls.FP32, shift=shift, out=ho)
+        ke = max(3, min(20, K // 10))
+        dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            prob.jv(hy, hv, kind=hbgls.PAPER, precision=hbgls.FP32, shift=shift, out=ho)
+        te = dist.max((time.perf_counter() - t0) / ke)
+        nb = n * 4 * N * 8
+        result["e2e"] = {"value": dist.world * units / te, "unit": UNIT, "h2d_bytes_per_step": 2 * nb,
+                         "d2h_bytes_per_step": nb, "ms_per_step": 1e3 * te,
+                         "path": "hb_jv (host float64 buffers, FP32 kernels)"}
+
+    if args.extra:
+        rates = {}
+        y64 = y32.double()
+        v64 = v32.double()
+        o64 = torch.empty_like(y64)
+        cases = [("residual_fp32", lambda: prob.residual_dev(y32, out32, hbgls.FP32, stream=stream)),
+                 ("jv_exact_fp32", lambda: prob.jv_dev(y32, v32, out32, hbgls.EXACT, hbgls.FP32, 0.0, stream=stream)),
+                 ("residual_fp64", lambda: prob.residual_dev(y64, o64, hbgls.FP64, stream=stream)),
+                 ("jv_paper_fp64", lambda: prob.jv_dev(y64, v64, o64, hbgls.PAPER, hbgls.FP64, shift, stream=stream))]
+        for name, fn in cases:
+            fn()
+            torch.cuda.synchronize()
+            reps = 20 if "fp32" in name else 5
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            tot = 0.0
+            for i in range(reps):
+                flush.fill_(float(i))
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                tot += e0.elapsed_time(e1)
+            rates[name] = units / (tot / reps / 1e3)
+        result["other_rates"] = rates
+
+    if dist.rank == 0 and dist.world == 1:
+        if not args.skip_solve:
+            try:
+                result["time_to_solve"] = time_solves()
+            except Exception as e:  # reported, not hidden
+                result["time_to_solve"] = {"error": repr(e)}
+        if not args.skip_cpu:
+            result["cpu_baseline"] = cpu_baseline(spec)
+    prob.close()
+    if dist.rank == 0:
+        print(json.dumps(result), flush=True)
+
+
+def main():
+    args = parse()
+    dist = Dist()
+    from paper_2411_14315_gb300 import workloads as W
+    spec = W.glenn_spec(n_tets=args.tets, n_h=args.n_h)
+    config = {"workload": f"glenn_like_tjunction_{spec.mesh.n_tets}_tets_N{spec.N}",
+              "n_tets": spec.mesh.n_tets, "n_nodes": spec.mesh.n_nodes, "N": spec.N,
+              "step": "one paper-tangent Jv (FP32) incl. spectral coupling, boundary terms, Dirichlet rows",
+              "l2": "flushed between steps (256 MiB write)", "parallelism": "replicas"}
+    if args.impl == "reference":
+        run_reference(args, dist, spec, config)
+        return
+    import torch
+    dist.init("nccl" if torch.cuda.is_available() else "gloo")
+    try:
+        run_ours(args, dist, spec, config)
+    finally:
+        dist.done()
+
+
+if __name__ == "__main__":
+    main()

@@ -157,6 +157,11 @@ typedef struct {
 hb_status hb_get_info(hb_problem *p, hb_info *info);
 /* Number of kernel launches queued by this problem since creation (all entry points). */
 int64_t hb_launch_count(const hb_problem *p);
+/* Element-kernel timing: when enabled, every launch of the fused element kernel is bracketed by CUDA
+ * events on the stream it is launched on.  hb_profile_read synchronises with those events, returns the
+ * summed device time in milliseconds and the number of launches since the last read, and resets. */
+hb_status hb_profile_elem(hb_problem *p, int enable);
+hb_status hb_profile_read(hb_problem *p, double *ms, int64_t *launches);
 
 #ifdef __cplusplus
 }

@@ -126,6 +126,10 @@ struct hb_problem {
     int km = 0;
     DBuf<double> kV, kz64, kdx, kdiag, kres, ktmp, kh;
     DBuf<float> kz32, kw32, ky32, kdiag32;
+    // element-kernel timing
+    bool prof_on = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev;
+    size_t prof_used = 0;
 };
 
 namespace {
@@ -473,8 +477,21 @@ hb_status apply_op(hb_problem *p, int mode, const T *y, const T *v, T *out, doub
     ea.mu = T(p->mu);
     ea.shift = T(shift);
     if (ps.P > 0) {
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (p->prof_on) {
+            if (p->prof_used == p->prof_ev.size()) {
+                HB_CUDA(cudaEventCreate(&e0));
+                HB_CUDA(cudaEventCreate(&e1));
+                p->prof_ev.push_back({e0, e1});
+            }
+            e0 = p->prof_ev[p->prof_used].first;
+            e1 = p->prof_ev[p->prof_used].second;
+            ++p->prof_used;
+            HB_CUDA(cudaEventRecord(e0, s));
+        }
         launch_elem<T>(mode, ea, ps.P, s);
         HB_LAUNCHED(p, 1);
+        if (p->prof_on) HB_CUDA(cudaEventRecord(e1, s));
     }
     if (mode != MODE_DIAG && p->n_nf > 0) {
         FaceArgs<T> fa;
@@ -930,6 +947,10 @@ hb_status hb_destroy(hb_problem *p) {
     if (p->stream) cudaStreamSynchronize(p->stream);
     const bool own = p->own_stream;
     cudaStream_t s = p->stream;
+    for (auto &ev : p->prof_ev) {
+        cudaEventDestroy(ev.first);
+        cudaEventDestroy(ev.second);
+    }
     delete p;
     if (own) cudaStreamDestroy(s);
     return HB_OK;
@@ -1202,5 +1223,27 @@ hb_status hb_get_info(hb_problem *p, hb_info *info) {
 }
 
 int64_t hb_launch_count(const hb_problem *p) { return p ? p->launches : 0; }
+
+hb_status hb_profile_elem(hb_problem *p, int enable) {
+    if (!p) return fail(HB_ERR_INVALID_ARG, "null problem");
+    p->prof_on = enable != 0;
+    return HB_OK;
+}
+
+hb_status hb_profile_read(hb_problem *p, double *ms, int64_t *launches) {
+    if (!p || !ms || !launches) return fail(HB_ERR_INVALID_ARG, "null argument");
+    HB_CUDA(cudaSetDevice(p->device));
+    double total = 0;
+    for (size_t i = 0; i < p->prof_used; ++i) {
+        HB_CUDA(cudaEventSynchronize(p->prof_ev[i].second));
+        float t = 0;
+        HB_CUDA(cudaEventElapsedTime(&t, p->prof_ev[i].first, p->prof_ev[i].second));
+        total += t;
+    }
+    *ms = total;
+    *launches = int64_t(p->prof_used);
+    p->prof_used = 0;
+    return HB_OK;
+}
 
 }  // extern "C"

@@ -90,6 +90,8 @@ SIGNATURES = {
     "hb_jacobi_diag_dev": ([_P, _VP, _VP, C.c_int, C.c_double, _VP], C.c_int),
     "hb_get_info": ([_P, C.POINTER(hb_info)], C.c_int),
     "hb_launch_count": ([_P], C.c_int64),
+    "hb_profile_elem": ([_P, C.c_int], C.c_int),
+    "hb_profile_read": ([_P, C.POINTER(C.c_double), C.POINTER(C.c_int64)], C.c_int),
 }
 
 _lib = None
@@ -126,10 +128,20 @@ def _f64(a, shape=None):
     return a
 
 
+_CUDA_STREAM_LEGACY = 1     # cudaStreamLegacy: the legacy default stream
+
+
 def _stream_handle(stream):
+    """cudaStream_t of a torch stream (or a raw handle).  A torch stream whose handle is 0 is the legacy
+    default stream and is passed as cudaStreamLegacy, because a NULL handle means "the problem's own
+    stream" in the C ABI."""
     if stream is None:
         return None
-    return C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+    if hasattr(stream, "cuda_stream"):
+        h = int(stream.cuda_stream)
+        return C.c_void_p(h if h != 0 else _CUDA_STREAM_LEGACY)
+    h = int(stream)
+    return C.c_void_p(h) if h != 0 else None
 
 
 class Problem:
@@ -156,6 +168,20 @@ class Problem:
     @classmethod
     def from_mesh(cls, mesh, rho, mu, T, n_h, **kw):
         return cls(mesh.xyz, mesh.tets, mesh.faces, mesh.face_tag, rho, mu, T, n_h, **kw)
+
+    @classmethod
+    def from_spec(cls, spec, **kw):
+        """Create a problem from a workload spec (paper_2411_14315_gb300.workloads.Spec)."""
+        m = spec.mesh
+        p = cls(m.xyz, m.tets, m.faces, spec.face_tag, spec.rho, spec.mu, spec.T, spec.n_h, **kw)
+        p.set_backflow(spec.beta)
+        for tag, prof, a, b in spec.inflows:
+            p.set_inflow(tag, prof, a, b)
+        for tag, a, b in spec.outlets_p:
+            p.set_outlet_pressure(tag, a, b)
+        for tag, R, a, b in spec.outlets_r:
+            p.set_outlet_resistance(tag, R, a, b)
+        return p
 
     def close(self):
         if getattr(self, "_h", None):
@@ -272,3 +298,13 @@ class Problem:
 
     def launch_count(self) -> int:
         return int(lib().hb_launch_count(self._h))
+
+    def profile_elem(self, enable: bool):
+        _check(lib().hb_profile_elem(self._h, int(bool(enable))))
+
+    def profile_read(self):
+        """(total milliseconds, launches) of the element kernel since profiling was enabled / read."""
+        ms = C.c_double()
+        n = C.c_int64()
+        _check(lib().hb_profile_read(self._h, C.byref(ms), C.byref(n)))
+        return ms.value, n.value

@@ -1,38 +1,9 @@
-"""Test problems: one boundary-condition spec applied identically to the CPU oracle and to the library.
-
-A spec is plain data (mesh from the seeded input generators, fluid constants, waveform harmonics), so
-both sides receive the same inputs and compute everything else on their own.
-"""
+"""Test adapters: apply one workload spec identically to the CPU oracle and to the library."""
 from __future__ import annotations
 
-import dataclasses
-import math
-
-import numpy as np
-
 from paper_2411_14315_gb300 import inputs as I
-
-
-@dataclasses.dataclass
-class Spec:
-    mesh: I.Mesh
-    rho: float
-    mu: float
-    T: float
-    n_h: int
-    beta: float = 0.2
-    inflows: list = dataclasses.field(default_factory=list)      # (tag, profile or None, a, b)
-    outlets_p: list = dataclasses.field(default_factory=list)    # (tag, a, b)
-    outlets_r: list = dataclasses.field(default_factory=list)    # (tag, R, a, b)
-    tags: np.ndarray | None = None                               # face tags override
-
-    @property
-    def N(self):
-        return 2 * self.n_h + 1
-
-    @property
-    def face_tag(self):
-        return self.mesh.face_tag if self.tags is None else self.tags
+from paper_2411_14315_gb300.workloads import (Spec, box_spec, dirichlet_nodes, glenn_spec,  # noqa: F401
+                                              womersley_spec)
 
 
 def oracle_problem(spec: Spec, convection: bool = True):
@@ -53,72 +24,4 @@ def oracle_problem(spec: Spec, convection: bool = True):
 
 def gpu_problem(spec: Spec, **kw):
     from paper_2411_14315_gb300 import hbgls
-    m = spec.mesh
-    p = hbgls.Problem(m.xyz, m.tets, m.faces, spec.face_tag, spec.rho, spec.mu, spec.T, spec.n_h, **kw)
-    p.set_backflow(spec.beta)
-    for tag, prof, a, b in spec.inflows:
-        p.set_inflow(tag, prof, a, b)
-    for tag, a, b in spec.outlets_p:
-        p.set_outlet_pressure(tag, a, b)
-    for tag, R, a, b in spec.outlets_r:
-        p.set_outlet_resistance(tag, R, a, b)
-    return p
-
-
-def dirichlet_nodes(spec: Spec) -> np.ndarray:
-    m = spec.mesh
-    tags = spec.face_tag
-    dtags = [0] + [t for t, *_ in spec.inflows]
-    return np.unique(m.faces[np.isin(tags, dtags)].ravel())
-
-
-# ------------------------------------------------------------------------------------------------
-# specs
-
-
-def box_spec(seed=11, n_h=2, n=(6, 4, 4), resistance=True, beta=0.2, jitter=0.2) -> Spec:
-    """Box with an inlet (x-min, uniform profile), no-slip walls (y faces), a pressure outlet (x-max)
-    and a resistance outlet (z faces)."""
-    m = I.box_mesh(*n, lx=1.5, jitter=jitter, seed=seed)
-    tag = m.face_tag.copy()
-    tag[(tag == 3) | (tag == 4)] = 0
-    a, b = I.waveform_harmonics(n_h, 1.0, seed)
-    pa, pb = I.waveform_harmonics(n_h, 0.5, seed + 1)
-    s = Spec(m, 1.1, 0.07, 1.7, n_h, beta=beta, tags=tag)
-    s.inflows.append((1, I.uniform_profile(m, [1], [1.0, 0.2, 0.0]), a, b))
-    s.outlets_p.append((2, pa, pb))
-    if resistance:
-        s.outlets_r.append((5, 0.8, pa * 0.3, pb * 0.3))
-    return s
-
-
-def womersley_spec(level: int = 1, n_h: int = 4, seed: int = 1001, parabolic_none: bool = True) -> Spec:
-    """Straight pipe R = 1, L = 5, rho = 1, mu = 0.04, Womersley number 4 (omega = 16 nu), mean
-    Reynolds number 100 (mean velocity 2), parabolic inflow scaled by seeded harmonics, traction-free
-    outlet."""
-    m = I.womersley_mesh(level)
-    nu = 0.04
-    omega = 16.0 * nu
-    T = 2.0 * math.pi / omega
-    a, b = I.waveform_harmonics(n_h, 2.0 * math.pi, seed)
-    s = Spec(m, 1.0, 0.04, T, n_h)
-    s.inflows.append((1, None if parabolic_none else I.parabolic_profile(m, 1), a, b))
-    return s
-
-
-def glenn_spec(n_tets=1_000_000, n_h=10, seed=2000) -> Spec:
-    """Glenn-like T-junction in cgs units: rho 1.06, mu 0.04, T 0.6979 s, parabolic inflow on both
-    inflow tubes (10 seeded harmonics), resistance outlets at a mean level of 7.5 mmHg."""
-    m = I.glenn_like(n_tets, seed)
-    mmHg = 1333.22
-    s = Spec(m, 1.06, 0.04, 0.6979, n_h)
-    for k, tag in enumerate(m.inlet_tags):
-        q_mean = 0.5 * math.pi * 0.36 * 30.0           # mean velocity 15 cm/s
-        a, b = I.waveform_harmonics(n_h, q_mean, seed + 10 + k)
-        s.inflows.append((tag, None, a, b))
-    for k, tag in enumerate(m.outlet_tags):
-        pa = np.zeros(n_h + 1)
-        pb = np.zeros(n_h + 1)
-        pa[0] = 7.0 * mmHg
-        s.outlets_r.append((tag, 30.0, pa, pb))
-    return s
+    return hbgls.Problem.from_spec(spec, **kw)
