@@ -147,6 +147,26 @@ hb_status hb_jv_dev(hb_problem *p, const void *y, const void *v, void *jv, int k
 hb_status hb_jacobi_diag_dev(hb_problem *p, const void *y, void *d, int precision, double shift,
                              void *stream);
 
+/* Jacobian-vector product that allocates no device memory (the paper has no counterpart: this is a
+ * library-integration entry point).  For callers that must not have the library allocate: an
+ * application whose device memory is entirely owned by its own allocator (for example a framework's
+ * caching pool, which can leave cudaMalloc failing while the pool still holds free memory), or a
+ * latency-critical loop in which a cudaMalloc / cudaFree would stall it by synchronising the device.
+ * Same arguments, layouts and result as hb_jv_dev.  Differences:
+ *  - it performs no cudaMalloc, cudaFree or other allocating call; its only scratch (the per-outlet
+ *    flow rates of resistance outlets) is a file-scope device array of 4096 doubles that every GPU
+ *    which loads the library holds until the process exits;
+ *  - outlets x instances above 4096 is rejected with HB_ERR_INVALID_ARG;
+ *  - the boundary data must already be prepared: after the last hb_set_* call, call hb_get_info (or any
+ *    other entry point) once; otherwise HB_ERR_STATE;
+ *  - the first call on a device looks up the scratch array's device address (cudaGetSymbolAddress, with
+ *    that device current); make that first call before any stream capture;
+ *  - all calls in the process share the one scratch array per device and it keeps the last call's
+ *    contents (the call clears the part it uses before use): calls that overlap in time on the GPU,
+ *    from any problem or stream, race on it and must be serialised by the caller. */
+hb_status hb_jv_dev_noalloc(hb_problem *p, const void *y, const void *v, void *jv, int kind, int precision,
+                            double shift, void *stream);
+
 /* ---- introspection ------------------------------------------------------------------------------ */
 typedef struct {
     int64_t n_nodes, n_tets, n_faces, n_dirichlet_nodes, n_neumann_faces;

@@ -767,6 +767,88 @@ double h_char(const hb_problem *p) { return std::cbrt(6.0 * std::sqrt(2.0) * p->
 
 }  // namespace
 
+// ---------------------------------------------------------------------------------------------------
+// Jacobian-vector product without any device allocation (hb_jv_dev_noalloc)
+//
+// The only scratch of the Jv pass is the per-outlet flux Q [n_out][N] of the resistance outlets.  Here
+// it lives in this file-scope array, which every GPU that loads the library holds until the process
+// exits.  Host code may not use the array's name as a device address (on the host it is a stand-in
+// symbol), so its device address is looked up once per device with cudaGetSymbolAddress.
+
+constexpr int kNoAllocScratch = 4096;   // doubles: n_out x N must not exceed this
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratch];
+constexpr int kMaxDevices = 64;
+static void *g_noalloc_ptr[kMaxDevices] = {nullptr};
+
+hb_status noalloc_scratch(int device, void **ptr) {
+    if (device < 0 || device >= kMaxDevices) return fail(HB_ERR_INVALID_ARG, "device index too large for the no-alloc scratch table");
+    if (!g_noalloc_ptr[device]) {   // first call on this device, which is current here
+        void *q = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&q, g_noalloc_scratch);
+        if (e != cudaSuccess || !q) {
+            cudaGetLastError();
+            return fail(HB_ERR_CUDA, std::string("cudaGetSymbolAddress(no-alloc scratch): ") + cudaGetErrorString(e));
+        }
+        g_noalloc_ptr[device] = q;
+    }
+    *ptr = g_noalloc_ptr[device];
+    return HB_OK;
+}
+
+template <typename T>
+hb_status apply_jv_noalloc(hb_problem *p, int mode, const T *y, const T *v, T *out, double shift, cudaStream_t s,
+                           T *qscratch) {
+    PatchSetDev<T> &ps = patches<T>(p);
+    const int N = p->N;
+    HB_CUDA(cudaMemsetAsync(out, 0, size_t(p->n_nodes) * 4 * N * sizeof(T), s));
+    ElemArgs<T> ea;
+    ea.pv = PatchView<T>{ps.P, ps.nl_max, ps.ep_max, ps.eptr.p, ps.nptr.p, ps.nodes.p, ps.lconn.p, ps.geom.p};
+    ea.y = y;
+    ea.v = v;
+    ea.out = out;
+    ea.H = Hmat<T>(p);
+    ea.flag = p->d_flag.p;
+    ea.N = N;
+    ea.rho = T(p->rho);
+    ea.mu = T(p->mu);
+    ea.shift = T(shift);
+    if (ps.P > 0) {
+        launch_elem<T>(mode, ea, ps.P, s);
+        HB_LAUNCHED(p, 1);
+    }
+    if (p->n_nf > 0) {
+        FaceArgs<T> fa;
+        fa.n_faces = p->n_nf;
+        fa.fnodes = p->d_nf_nodes.p;
+        fa.foutlet = p->d_nf_out.p;
+        fa.flag = p->d_flag.p;
+        fa.y = y;
+        fa.v = v;
+        fa.out = out;
+        fa.N = N;
+        fa.rho = T(p->rho);
+        fa.beta = T(p->beta);
+        if constexpr (sizeof(T) == 4) {
+            fa.fgeo = p->d_nf_geo32.p;
+            fa.hbase = p->d_hbase32.p;
+            fa.R = p->d_R32.p;
+        } else {
+            fa.fgeo = p->d_nf_geo64.p;
+            fa.hbase = p->d_hbase64.p;
+            fa.R = p->d_R64.p;
+        }
+        fa.Q = qscratch;   // the shared array keeps the last call's values: clear it first
+        if (p->has_res) HB_CUDA(cudaMemsetAsync(qscratch, 0, size_t(p->n_out) * N * sizeof(T), s));
+        launch_faces<T>(mode, fa, p->has_res, s);
+        HB_LAUNCHED(p, p->has_res ? 2 : 1);
+    }
+    if (p->n_dir > 0) {
+        launch_dirichlet_rows<T>(mode, p->d_dir_nodes.p, p->n_dir, v, out, N, s);
+        HB_LAUNCHED(p, 1);
+    }
+    return HB_OK;
+}
+
 // =====================================================================================================
 // C ABI
 
@@ -1201,6 +1283,31 @@ hb_status hb_solve(hb_problem *p, const hb_solve_opts *opts, hb_report *rep) {
     if (rep) *rep = R;
     if (result == HB_ERR_NOT_CONVERGED) g_err = "solve reached max_steps";
     return result;
+}
+
+hb_status hb_jv_dev_noalloc(hb_problem *p, const void *y, const void *v, void *jv, int kind, int precision,
+                            double shift, void *stream) {
+    if (!p || !y || !v || !jv) return fail(HB_ERR_INVALID_ARG, "null argument");
+    if (kind != 0 && kind != 1) return fail(HB_ERR_INVALID_ARG, "kind must be 0 (paper tangent) or 1 (exact)");
+    HB_TRY(check_precision(precision));
+    if (jv == y || jv == v) return fail(HB_ERR_INVALID_ARG, "output aliases an input");
+    if (p->bc_dirty)
+        return fail(HB_ERR_STATE, "boundary data not prepared: after the last hb_set_* call, call hb_get_info "
+                                  "(or any other entry point) once before hb_jv_dev_noalloc");
+    if (int64_t(p->n_out) * p->N > kNoAllocScratch)
+        return fail(HB_ERR_INVALID_ARG, "outlets x instances (" + std::to_string(int64_t(p->n_out) * p->N) +
+                                            ") exceeds the no-alloc scratch limit of " +
+                                            std::to_string(kNoAllocScratch) + " values");
+    HB_CUDA(cudaSetDevice(p->device));
+    void *q = nullptr;
+    HB_TRY(noalloc_scratch(p->device, &q));
+    cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : p->stream;
+    const int mode = kind == 0 ? MODE_JVP : MODE_JVE;
+    if (precision == 0)
+        return apply_jv_noalloc<double>(p, mode, static_cast<const double *>(y), static_cast<const double *>(v),
+                                        static_cast<double *>(jv), shift, s, static_cast<double *>(q));
+    return apply_jv_noalloc<float>(p, mode, static_cast<const float *>(y), static_cast<const float *>(v),
+                                   static_cast<float *>(jv), shift, s, static_cast<float *>(q));
 }
 
 hb_status hb_get_info(hb_problem *p, hb_info *info) {

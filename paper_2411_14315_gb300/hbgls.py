@@ -92,6 +92,7 @@ SIGNATURES = {
     "hb_launch_count": ([_P], C.c_int64),
     "hb_profile_elem": ([_P, C.c_int], C.c_int),
     "hb_profile_read": ([_P, C.POINTER(C.c_double), C.POINTER(C.c_int64)], C.c_int),
+    "hb_jv_dev_noalloc": ([_P, _VP, _VP, _VP, C.c_int, C.c_int, C.c_double, _VP], C.c_int),
 }
 
 _lib = None
@@ -259,6 +260,11 @@ class Problem:
     def jv_dev(self, y, v, out, kind: int, precision: int, shift: float = 0.0, stream=None):
         _check(lib().hb_jv_dev(self._h, y.data_ptr(), v.data_ptr(), out.data_ptr(), kind, precision, shift,
                                _stream_handle(stream)))
+
+    def jv_dev_noalloc(self, y, v, out, kind: int, precision: int, shift: float = 0.0, stream=None):
+        """hb_jv_dev without any device allocation (see include/hbgls.h for the conditions)."""
+        _check(lib().hb_jv_dev_noalloc(self._h, y.data_ptr(), v.data_ptr(), out.data_ptr(), kind, precision,
+                                       shift, _stream_handle(stream)))
 
     def jacobi_diag_dev(self, y, d, precision: int, shift: float = 0.0, stream=None):
         _check(lib().hb_jacobi_diag_dev(self._h, y.data_ptr(), d.data_ptr(), precision, shift,
