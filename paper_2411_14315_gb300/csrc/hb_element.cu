@@ -48,23 +48,48 @@ __device__ __forceinline__ float rsqrt_t<float>(float x) { return rsqrtf(x); }
 template <>
 __device__ __forceinline__ double rsqrt_t<double>(double x) { return rsqrt(x); }
 
-template <typename T, int MODE>
-__device__ __forceinline__ void element_instance(int e, int n, int N, T rho, T mu, T shift,
+__device__ __forceinline__ void load_geom(const float *g, float gN[4][3], float &V, float &g2) {
+    const float4 *g4 = reinterpret_cast<const float4 *>(g);
+    const float4 a0 = g4[0], a1 = g4[1], a2 = g4[2], a3 = g4[3];
+    gN[0][0] = a0.x; gN[0][1] = a0.y; gN[0][2] = a0.z;
+    gN[1][0] = a0.w; gN[1][1] = a1.x; gN[1][2] = a1.y;
+    gN[2][0] = a1.z; gN[2][1] = a1.w; gN[2][2] = a2.x;
+    gN[3][0] = a2.y; gN[3][1] = a2.z; gN[3][2] = a2.w;
+    V = a3.x;
+    g2 = a3.y;
+}
+
+__device__ __forceinline__ void load_geom(const double *g, double gN[4][3], double &V, double &g2) {
+    const double2 *g2v = reinterpret_cast<const double2 *>(g);
+    double v[14];
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+        const double2 t = g2v[k];
+        v[2 * k] = t.x;
+        v[2 * k + 1] = t.y;
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) gN[a][j] = v[3 * a + j];
+    V = v[12];
+    g2 = v[13];
+}
+
+// NT > 0: the number of instances is the compile-time constant NT; NT = 0: runtime N
+template <typename T, int MODE, int NT>
+__device__ __forceinline__ void element_instance(int e, int n, int Nrt, T rho, T mu, T shift,
                                                  const T *__restrict__ sGeom,
                                                  const uint32_t *__restrict__ sConn,
                                                  const T *__restrict__ sY, const T *__restrict__ sV,
                                                  const T *__restrict__ sHY, const T *__restrict__ sHV,
                                                  T *sQ, T *sT) {
+    const int N = NT > 0 ? NT : Nrt;
     const int N4 = 4 * N, N3 = 3 * N;
     const uint32_t c = sConn[e];
     const int lo[4] = {int(c & 255u), int((c >> 8) & 255u), int((c >> 16) & 255u), int(c >> 24)};
-    const T *g = sGeom + e * kGeomStride;
-    T gN[4][3];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) gN[a][j] = g[a * 3 + j];
-    const T V = g[12], g2 = g[13];
+    T gN[4][3], V, g2;
+    load_geom(sGeom + e * kGeomStride, gN, V, g2);
     const T w = V * T(0.25);
     const T qb = T(kQB), qd = T(kQA - kQB);
     const T m20 = V * T(0.05);   // int N_a N_b = V (1 + delta_ab) / 20
@@ -341,12 +366,31 @@ __device__ __forceinline__ void element_instance(int e, int n, int N, T rho, T m
 // ---------------------------------------------------------------------------------------------------
 // the patch kernel
 
-template <typename T, int MODE>
+// H is circulant: H[j][k] = h[(j - k) mod N] with h its first column (h[0] = 0).  For a fixed N one row
+// of N values is multiplied with the kernel held in registers; x_in may equal x_out (read fully first).
+template <typename T, int NT>
+__device__ __forceinline__ void circulant_row(const T *__restrict__ hcol, const T *x_in, T *x_out) {
+    T x[NT], h[NT];
+#pragma unroll
+    for (int k = 0; k < NT; ++k) x[k] = x_in[k];
+#pragma unroll
+    for (int d = 0; d < NT; ++d) h[d] = hcol[d];
+#pragma unroll
+    for (int m = 0; m < NT; ++m) {
+        T acc = T(0);
+#pragma unroll
+        for (int k = 0; k < NT; ++k)
+            if (k != m) acc += h[(m - k + NT) % NT] * x[k];
+        x_out[m] = acc;
+    }
+}
+
+template <typename T, int MODE, int NT>
 __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 2 : 1)) elem_kernel(ElemArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int N = a.N, N4 = 4 * N, N3 = 3 * N;
+    const int N = NT > 0 ? NT : a.N, N4 = 4 * N, N3 = 3 * N;
     const Layout L = make_layout(MODE, N, a.pv.nl_max, a.pv.ep_max, sizeof(T));
-    T *sH = reinterpret_cast<T *>(smem + L.H);
+    T *sH = reinterpret_cast<T *>(smem + L.H);       // full H (runtime N) or its first column (fixed N)
     T *sGeom = reinterpret_cast<T *>(smem + L.geom);
     T *sY = reinterpret_cast<T *>(smem + L.Y);
     T *sV = reinterpret_cast<T *>(smem + L.V);
@@ -358,7 +402,11 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 2 : 1)) elem_kernel(
     uint32_t *sConn = reinterpret_cast<uint32_t *>(smem + L.conn);
     const int tid = threadIdx.x, nt = blockDim.x;
 
-    for (int i = tid; i < N * N; i += nt) sH[i] = a.H[i];
+    if constexpr (NT > 0) {
+        for (int i = tid; i < N; i += nt) sH[i] = a.H[i * N];
+    } else {
+        for (int i = tid; i < N * N; i += nt) sH[i] = a.H[i];
+    }
 
     for (int p = blockIdx.x; p < a.pv.n_patches; p += gridDim.x) {
         const int e0 = a.pv.eptr[p], ne = a.pv.eptr[p + 1] - e0;
@@ -396,18 +444,28 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 2 : 1)) elem_kernel(
         }
         if constexpr (MODE == MODE_RES || MODE == MODE_JVE) {
             // time coupling of the staged velocities: (H u)[l][i][n] = sum_k H[n][k] u[l][i][k]
-            for (int i = tid; i < nl * N3; i += nt) {
-                const int l = i / N3, r = i - l * N3, f = r / N, n = r - f * N;
-                const T *h = sH + n * N;
-                const T *x = sY + l * N4 + f * N;
-                T acc = 0;
-                for (int k = 0; k < N; ++k) acc += h[k] * x[k];
-                sHY[i] = acc;
-                if constexpr (MODE == MODE_JVE) {
-                    const T *xv = sV + l * N4 + f * N;
-                    T acc2 = 0;
-                    for (int k = 0; k < N; ++k) acc2 += h[k] * xv[k];
-                    sHV[i] = acc2;
+            if constexpr (NT > 0) {
+                const int rows = nl * 3;
+                for (int r = tid; r < (MODE == MODE_JVE ? 2 : 1) * rows; r += nt) {
+                    const int which = r >= rows, rr = r - which * rows, l = rr / 3, f = rr - 3 * l;
+                    const T *src = (which ? sV : sY) + l * N4 + f * N;
+                    T *dst = (which ? sHV : sHY) + l * N3 + f * N;
+                    circulant_row<T, NT>(sH, src, dst);
+                }
+            } else {
+                for (int i = tid; i < nl * N3; i += nt) {
+                    const int l = i / N3, r = i - l * N3, f = r / N, n = r - f * N;
+                    const T *h = sH + n * N;
+                    const T *x = sY + l * N4 + f * N;
+                    T acc = 0;
+                    for (int k = 0; k < N; ++k) acc += h[k] * x[k];
+                    sHY[i] = acc;
+                    if constexpr (MODE == MODE_JVE) {
+                        const T *xv = sV + l * N4 + f * N;
+                        T acc2 = 0;
+                        for (int k = 0; k < N; ++k) acc2 += h[k] * xv[k];
+                        sHV[i] = acc2;
+                    }
                 }
             }
             __syncthreads();
@@ -415,9 +473,18 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 2 : 1)) elem_kernel(
 
         for (int i = tid; i < ne * N; i += nt) {
             const int e = i / N, n = i - e * N;
-            element_instance<T, MODE>(e, n, N, a.rho, a.mu, a.shift, sGeom, sConn, sY, sV, sHY, sHV, sQ, sT);
+            element_instance<T, MODE, NT>(e, n, N, a.rho, a.mu, a.shift, sGeom, sConn, sY, sV, sHY, sHV, sQ, sT);
         }
         __syncthreads();
+
+        // H T on the patch-assembled T rows (fixed N: in place, one row per thread)
+        if constexpr (MODE != MODE_DIAG && NT > 0) {
+            for (int r = tid; r < nl * 3; r += nt) {
+                T *row = sT + (r / 3) * N3 + (r % 3) * N;
+                circulant_row<T, NT>(sH, row, row);
+            }
+            __syncthreads();
+        }
 
         // flush: out += Q + H T (velocity rows), once per local node
         for (int i = tid; i < nl * N4; i += nt) {
@@ -428,11 +495,15 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 2 : 1)) elem_kernel(
             } else {
                 val = sQ[i];
                 if (f < 3) {
-                    const T *h = sH + n * N;
-                    const T *t = sT + l * N3 + f * N;
-                    T acc = 0;
-                    for (int k = 0; k < N; ++k) acc += h[k] * t[k];
-                    val += acc;
+                    if constexpr (NT > 0) {
+                        val += sT[l * N3 + f * N + n];
+                    } else {
+                        const T *h = sH + n * N;
+                        const T *t = sT + l * N3 + f * N;
+                        T acc = 0;
+                        for (int k = 0; k < N; ++k) acc += h[k] * t[k];
+                        val += acc;
+                    }
                 }
             }
             atomicAdd(a.out + size_t(sNode[l]) * N4 + r, val);
@@ -695,15 +766,26 @@ size_t elem_smem_bytes(int mode, int N, int nl_max, int ep_max, size_t tsize) {
     return make_layout(mode, N, nl_max, ep_max, tsize).total;
 }
 
-template <typename T, int MODE>
-static void launch_elem_mode(const ElemArgs<T> &a, int grid, cudaStream_t s) {
+template <typename T, int MODE, int NT>
+static void launch_elem_n(const ElemArgs<T> &a, int grid, cudaStream_t s) {
     const size_t smem = elem_smem_bytes(MODE, a.N, a.pv.nl_max, a.pv.ep_max, sizeof(T));
     static size_t configured = 0;
     if (smem > 48 * 1024 && smem > configured) {
-        cudaFuncSetAttribute(elem_kernel<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        cudaFuncSetAttribute(elem_kernel<T, MODE, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         configured = smem;
     }
-    elem_kernel<T, MODE><<<grid, kBlock, smem, s>>>(a);
+    elem_kernel<T, MODE, NT><<<grid, kBlock, smem, s>>>(a);
+}
+
+// fixed-N instantiations for the instance counts of the workloads; any other N runs the generic kernel
+template <typename T, int MODE>
+static void launch_elem_mode(const ElemArgs<T> &a, int grid, cudaStream_t s) {
+    switch (a.N) {
+        case 9: launch_elem_n<T, MODE, 9>(a, grid, s); break;
+        case 13: launch_elem_n<T, MODE, 13>(a, grid, s); break;
+        case 21: launch_elem_n<T, MODE, 21>(a, grid, s); break;
+        default: launch_elem_n<T, MODE, 0>(a, grid, s); break;
+    }
 }
 
 template <typename T>
