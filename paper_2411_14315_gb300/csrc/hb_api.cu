@@ -176,18 +176,23 @@ inline uint64_t spread3(uint64_t x) {  // 21 bits -> every third bit
 }
 
 // Greedy patches along the Morton order: close a patch when it would exceed NL nodes or EP elements.
+// Inside a patch the elements are then re-sequenced so that an element shares no node with the `window`
+// elements before it where possible: threads of one warp that handle the same instance of elements a
+// short distance apart then add into different shared-memory addresses.
 struct HostPatches {
     std::vector<int> eptr, nptr, nodes;
     std::vector<uint32_t> lconn;
+    std::vector<int> perm;          // element k of the patch order is element perm[k] of the input order
     int nl_max = 0, ep_max = 0;
 };
 
-HostPatches build_patches(const std::vector<int32_t> &tets_ord, int64_t n_tets, int64_t n_nodes, int NL, int EP) {
+HostPatches build_patches(const std::vector<int32_t> &tets_ord, int64_t n_tets, int64_t n_nodes, int NL, int EP,
+                          int window) {
     HostPatches hp;
     std::vector<int> stamp(size_t(n_nodes), -1), local(size_t(n_nodes), 0);
+    std::vector<uint32_t> lc(static_cast<size_t>(n_tets));
     hp.eptr.push_back(0);
     hp.nptr.push_back(0);
-    hp.lconn.resize(size_t(n_tets));
     int pid = 0, cur_nodes = 0, cur_elems = 0;
     for (int64_t e = 0; e < n_tets; ++e) {
         const int32_t *t = &tets_ord[size_t(4 * e)];
@@ -215,13 +220,47 @@ HostPatches build_patches(const std::vector<int32_t> &tets_ord, int64_t n_tets, 
             }
             packed |= uint32_t(local[t[a]]) << (8 * a);
         }
-        hp.lconn[size_t(e)] = packed;
+        lc[size_t(e)] = packed;
         ++cur_elems;
     }
     hp.eptr.push_back(int(n_tets));
     hp.nptr.push_back(int(hp.nodes.size()));
     hp.nl_max = std::max(hp.nl_max, cur_nodes);
     hp.ep_max = std::max(hp.ep_max, cur_elems);
+    // re-sequence inside each patch
+    hp.perm.resize(size_t(n_tets));
+    hp.lconn.resize(size_t(n_tets));
+    std::vector<int> cnt(256, 0), rem, placed;
+    const int P = int(hp.eptr.size()) - 1;
+    for (int q = 0; q < P; ++q) {
+        const int e0 = hp.eptr[size_t(q)], e1 = hp.eptr[size_t(q + 1)];
+        rem.clear();
+        placed.clear();
+        for (int e = e0; e < e1; ++e) rem.push_back(e);
+        std::fill(cnt.begin(), cnt.end(), 0);
+        for (int k = e0; k < e1; ++k) {
+            size_t pick = 0;
+            for (size_t j = 0; j < rem.size(); ++j) {
+                const uint32_t c = lc[size_t(rem[j])];
+                bool clash = false;
+                for (int a = 0; a < 4; ++a) clash |= cnt[(c >> (8 * a)) & 255u] > 0;
+                if (!clash) {
+                    pick = j;
+                    break;
+                }
+            }
+            const int e = rem[pick];
+            rem.erase(rem.begin() + long(pick));
+            hp.perm[size_t(k)] = e;
+            hp.lconn[size_t(k)] = lc[size_t(e)];
+            placed.push_back(e);
+            for (int a = 0; a < 4; ++a) ++cnt[(lc[size_t(e)] >> (8 * a)) & 255u];
+            if (int(placed.size()) > window) {
+                const uint32_t old = lc[size_t(placed[placed.size() - 1 - size_t(window)])];
+                for (int a = 0; a < 4; ++a) --cnt[(old >> (8 * a)) & 255u];
+            }
+        }
+    }
     return hp;
 }
 
@@ -237,7 +276,7 @@ template <typename T>
 hb_status make_patchset(hb_problem *p, PatchSetDev<T> &ps, const std::vector<int32_t> &tets_ord, size_t budget) {
     const int NL = choose_nl(p->N, sizeof(T), budget);
     const int EP = 3 * NL;
-    HostPatches hp = build_patches(tets_ord, p->n_tets, p->n_nodes, NL, EP);
+    HostPatches hp = build_patches(tets_ord, p->n_tets, p->n_nodes, NL, EP, std::max(1, 31 / p->N));
     ps.P = int(hp.eptr.size()) - 1;
     ps.nl_max = hp.nl_max;
     ps.ep_max = hp.ep_max;
@@ -245,6 +284,10 @@ hb_status make_patchset(hb_problem *p, PatchSetDev<T> &ps, const std::vector<int
     HB_TRY(upload(p, ps.nptr, hp.nptr));
     HB_TRY(upload(p, ps.nodes, hp.nodes));
     HB_TRY(upload(p, ps.lconn, hp.lconn));
+    std::vector<int> tets_p(size_t(4 * p->n_tets));
+    for (int64_t k = 0; k < p->n_tets; ++k)
+        for (int a = 0; a < 4; ++a) tets_p[size_t(4 * k + a)] = tets_ord[size_t(4 * hp.perm[size_t(k)] + a)];
+    HB_TRY(upload(p, p->d_tets_ord, tets_p));
     HB_TRY(dalloc(p, ps.geom, size_t(p->n_tets) * kGeomStride));
     launch_geom<T>(p->d_xyz.p, p->d_tets_ord.p, int(p->n_tets), p->mu / p->rho, ps.geom.p, p->stream);
     HB_LAUNCHED(p, 1);
@@ -999,7 +1042,6 @@ hb_status hb_create(const hb_mesh *mesh, double rho, double mu, double period_T,
     }
     hb_status st;
     if ((st = upload(p, p->d_xyz, p->xyz)) != HB_OK) return bail(st);
-    if ((st = upload(p, p->d_tets_ord, std::vector<int>(tets_ord.begin(), tets_ord.end()))) != HB_OK) return bail(st);
     if ((st = make_patchset<float>(p, p->ps32, tets_ord, 110 * 1024)) != HB_OK) return bail(st);
     if ((st = make_patchset<double>(p, p->ps64, tets_ord, 200 * 1024)) != HB_OK) return bail(st);
     // H = E^-1 Omega E in real closed form: (w/2) (-1)^(j-k) / sin(pi (j-k) / N), zero diagonal

@@ -29,9 +29,9 @@ __host__ __device__ inline Layout make_layout(int mode, int N, int nl, int ep, s
     L.Y = o;    o += pad16(row4);
     L.V = o;    if (mode == MODE_JVP || mode == MODE_JVE) o += pad16(row4);
     L.HY = o;   if (mode == MODE_RES || mode == MODE_JVE) o += pad16(row3);
-    L.HV = o;   if (mode == MODE_JVE) o += pad16(row3);
+    L.HV = o;   if (mode == MODE_JVE || mode == MODE_JVP) o += pad16(row3);
     L.Q = o;    o += pad16(row4);
-    L.T = o;    if (mode != MODE_DIAG) o += pad16(row3);
+    L.T = o;    if (mode == MODE_RES || mode == MODE_JVE) o += pad16(row3);
     L.node = o; o += pad16(size_t(nl) * 4);
     L.conn = o; o += pad16(size_t(ep) * 4);
     L.total = o;
@@ -203,17 +203,21 @@ __device__ __forceinline__ void element_instance(int e, int n, int Nrt, T rho, T
         }
         return;
     } else if constexpr (MODE == MODE_JVP) {
-        T dv[4][3], dvp[4];
+        T dv[4][3], dvp[4], hdv[4][3];
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
             dvp[a] = sV[lo[a] * N4 + 3 * N + n];
 #pragma unroll
-            for (int i = 0; i < 3; ++i) dv[a][i] = sV[lo[a] * N4 + i * N + n];
+            for (int i = 0; i < 3; ++i) {
+                dv[a][i] = sV[lo[a] * N4 + i * N + n];
+                hdv[a][i] = sHV[lo[a] * N3 + i * N + n];
+            }
         }
-        T gV[3][3], gVp[3], dvsum[3];
+        T gV[3][3], gVp[3], dvsum[3], hdvsum[3];
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             dvsum[i] = dv[0][i] + dv[1][i] + dv[2][i] + dv[3][i];
+            hdvsum[i] = hdv[0][i] + hdv[1][i] + hdv[2][i] + hdv[3][i];
 #pragma unroll
             for (int j = 0; j < 3; ++j)
                 gV[i][j] = dv[0][i] * gN[0][j] + dv[1][i] * gN[1][j] + dv[2][i] * gN[2][j] + dv[3][i] * gN[3][j];
@@ -259,9 +263,10 @@ __device__ __forceinline__ void element_instance(int e, int n, int Nrt, T rho, T
             for (int i = 0; i < 3; ++i) {
                 const T visc = gN[a][0] * gV[i][0] + gN[a][1] * gV[i][1] + gN[a][2] * gV[i][2];
                 const T mv = m20 * (dvsum[i] + dv[a][i]);
-                const T vq = qm[a][i] + w * rho * qb * ugvs[i] + mu * V * visc - V * gN[a][i] * pbar + shift * mv;
+                const T mhv = m20 * (hdvsum[i] + hdv[a][i]);     // F block: H (rho M v) = rho M (H v)
+                const T vq = qm[a][i] + w * rho * qb * ugvs[i] + mu * V * visc - V * gN[a][i] * pbar
+                           + shift * mv + rho * mhv;
                 atomicAdd(sQ + lo[a] * N4 + i * N + n, vq);
-                atomicAdd(sT + lo[a] * N3 + i * N + n, rho * mv);
             }
             const T qc = w * div + (w / rho) * (gN[a][0] * S[0] + gN[a][1] * S[1] + gN[a][2] * S[2]);
             atomicAdd(sQ + lo[a] * N4 + 3 * N + n, qc);
@@ -366,6 +371,13 @@ __device__ __forceinline__ void element_instance(int e, int n, int Nrt, T rho, T
 // ---------------------------------------------------------------------------------------------------
 // the patch kernel
 
+// 16-byte global -> shared copy that does not block the issuing thread (completion: cp_async_wait_all)
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src) {
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // H is circulant: H[j][k] = h[(j - k) mod N] with h its first column (h[0] = 0).  For a fixed N one row
 // of N values is multiplied with the kernel held in registers; x_in may equal x_out (read fully first).
 template <typename T, int NT>
@@ -420,19 +432,21 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 2 : 1)) elem_kernel(
             for (int i = tid; i < nvec; i += nt) dst[i] = src[i];
         }
         for (int i = tid; i < nl * N4; i += nt) sQ[i] = T(0);
-        if constexpr (MODE != MODE_DIAG)
+        if constexpr (MODE == MODE_RES || MODE == MODE_JVE)
             for (int i = tid; i < nl * N3; i += nt) sT[i] = T(0);
         __syncthreads();
 
-        // gather the patch's node rows: 4 N values per node, 16-byte chunks
+        // gather the patch's node rows (4 N values per node) with asynchronous 16-byte copies, so every
+        // thread keeps all of its loads in flight
         const int cpr = int(N4 * sizeof(T) / 16);
         for (int i = tid; i < nl * cpr; i += nt) {
             const int l = i / cpr, c = i - l * cpr;
             const size_t gidx = size_t(sNode[l]) * cpr + c;
-            reinterpret_cast<uint4 *>(sY)[i] = reinterpret_cast<const uint4 *>(a.y)[gidx];
+            cp_async16(reinterpret_cast<uint4 *>(sY) + i, reinterpret_cast<const uint4 *>(a.y) + gidx);
             if constexpr (MODE == MODE_JVP || MODE == MODE_JVE)
-                reinterpret_cast<uint4 *>(sV)[i] = reinterpret_cast<const uint4 *>(a.v)[gidx];
+                cp_async16(reinterpret_cast<uint4 *>(sV) + i, reinterpret_cast<const uint4 *>(a.v) + gidx);
         }
+        cp_async_wait_all();
         __syncthreads();
         if constexpr (MODE == MODE_JVP || MODE == MODE_JVE) {
             // Dirichlet velocity entries of the direction are not unknowns: treat them as 0
@@ -442,12 +456,16 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 2 : 1)) elem_kernel(
             }
             __syncthreads();
         }
-        if constexpr (MODE == MODE_RES || MODE == MODE_JVE) {
-            // time coupling of the staged velocities: (H u)[l][i][n] = sum_k H[n][k] u[l][i][k]
+        if constexpr (MODE != MODE_DIAG) {
+            // time coupling of the staged velocities: (H x)[l][i][n] = sum_k H[n][k] x[l][i][k] for
+            // x = u (RES, JVE) and x = v (JVP, JVE)
+            constexpr bool hy = (MODE == MODE_RES || MODE == MODE_JVE);
+            constexpr bool hv = (MODE == MODE_JVP || MODE == MODE_JVE);
+            constexpr int nsrc = (hy ? 1 : 0) + (hv ? 1 : 0);
             if constexpr (NT > 0) {
                 const int rows = nl * 3;
-                for (int r = tid; r < (MODE == MODE_JVE ? 2 : 1) * rows; r += nt) {
-                    const int which = r >= rows, rr = r - which * rows, l = rr / 3, f = rr - 3 * l;
+                for (int r = tid; r < nsrc * rows; r += nt) {
+                    const int which = hy ? (r >= rows) : 1, rr = r - (r >= rows) * rows, l = rr / 3, f = rr - 3 * l;
                     const T *src = (which ? sV : sY) + l * N4 + f * N;
                     T *dst = (which ? sHV : sHY) + l * N3 + f * N;
                     circulant_row<T, NT>(sH, src, dst);
@@ -456,11 +474,13 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 2 : 1)) elem_kernel(
                 for (int i = tid; i < nl * N3; i += nt) {
                     const int l = i / N3, r = i - l * N3, f = r / N, n = r - f * N;
                     const T *h = sH + n * N;
-                    const T *x = sY + l * N4 + f * N;
-                    T acc = 0;
-                    for (int k = 0; k < N; ++k) acc += h[k] * x[k];
-                    sHY[i] = acc;
-                    if constexpr (MODE == MODE_JVE) {
+                    if constexpr (hy) {
+                        const T *x = sY + l * N4 + f * N;
+                        T acc = 0;
+                        for (int k = 0; k < N; ++k) acc += h[k] * x[k];
+                        sHY[i] = acc;
+                    }
+                    if constexpr (hv) {
                         const T *xv = sV + l * N4 + f * N;
                         T acc2 = 0;
                         for (int k = 0; k < N; ++k) acc2 += h[k] * xv[k];
@@ -478,7 +498,7 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 2 : 1)) elem_kernel(
         __syncthreads();
 
         // H T on the patch-assembled T rows (fixed N: in place, one row per thread)
-        if constexpr (MODE != MODE_DIAG && NT > 0) {
+        if constexpr ((MODE == MODE_RES || MODE == MODE_JVE) && NT > 0) {
             for (int r = tid; r < nl * 3; r += nt) {
                 T *row = sT + (r / 3) * N3 + (r % 3) * N;
                 circulant_row<T, NT>(sH, row, row);
@@ -492,6 +512,8 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 2 : 1)) elem_kernel(
             T val;
             if constexpr (MODE == MODE_DIAG) {
                 val = (f == 1 || f == 2) ? sQ[l * N4 + n] : sQ[i];
+            } else if constexpr (MODE == MODE_JVP) {
+                val = sQ[i];
             } else {
                 val = sQ[i];
                 if (f < 3) {

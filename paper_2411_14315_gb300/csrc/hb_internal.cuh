@@ -25,10 +25,14 @@ constexpr double kQA = 0.5854101966249685;
 constexpr double kQB = 0.1381966011250105;
 
 // Fields per local node staged in shared memory, by mode.
+// JVP stages y, v and H v (the F block is applied as rho M (H v): M and H commute); RES stages y and
+// H u; JVE stages y, H u, v, H v.  RES and JVE accumulate Q (4 fields) and T (3 fields).
 __host__ __device__ constexpr int in_fields(int mode) {
-    return mode == MODE_RES ? 7 : mode == MODE_JVP ? 8 : mode == MODE_JVE ? 14 : 4;
+    return mode == MODE_RES ? 7 : mode == MODE_JVP ? 11 : mode == MODE_JVE ? 14 : 4;
 }
-__host__ __device__ constexpr int out_fields(int mode) { return mode == MODE_DIAG ? 4 : 7; }
+__host__ __device__ constexpr int out_fields(int mode) {
+    return (mode == MODE_DIAG || mode == MODE_JVP) ? 4 : 7;
+}
 
 // Element patches: elements renumbered so each patch's elements are contiguous; each patch lists its
 // distinct nodes; each element stores its 4 nodes as local indices (uint8) into that list.
