@@ -64,9 +64,14 @@ struct DBuf {
 template <typename T>
 struct PatchSetDev {
     int P = 0, nl_max = 0, ep_max = 0;
-    DBuf<int> eptr, nptr, nodes;
+    DBuf<int> eptr, nptr, nodes, dptr;
     DBuf<uint32_t> lconn;
+    DBuf<uint8_t> dloc;
     DBuf<T> geom;
+    std::vector<int> h_nptr, h_nodes;   // host copies, to rebuild the Dirichlet lists
+    PatchView<T> view() const {
+        return PatchView<T>{P, nl_max, ep_max, eptr.p, nptr.p, nodes.p, lconn.p, geom.p, dptr.p, dloc.p};
+    }
 };
 
 struct Inflow {
@@ -284,6 +289,10 @@ hb_status make_patchset(hb_problem *p, PatchSetDev<T> &ps, const std::vector<int
     HB_TRY(upload(p, ps.nptr, hp.nptr));
     HB_TRY(upload(p, ps.nodes, hp.nodes));
     HB_TRY(upload(p, ps.lconn, hp.lconn));
+    ps.h_nptr = hp.nptr;
+    ps.h_nodes = hp.nodes;
+    HB_TRY(upload(p, ps.dptr, std::vector<int>(size_t(ps.P + 1), 0)));   // no Dirichlet nodes until set
+    HB_TRY(dalloc(p, ps.dloc, 1));
     std::vector<int> tets_p(size_t(4 * p->n_tets));
     for (int64_t k = 0; k < p->n_tets; ++k)
         for (int a = 0; a < 4; ++a) tets_p[size_t(4 * k + a)] = tets_ord[size_t(4 * hp.perm[size_t(k)] + a)];
@@ -370,6 +379,21 @@ void parabolic_profile(const hb_problem *p, int tag, std::vector<double> &prof) 
     }
 }
 
+template <typename T>
+hb_status dirichlet_lists(hb_problem *p, PatchSetDev<T> &ps, const std::vector<uint8_t> &flag) {
+    std::vector<int> dptr(size_t(ps.P + 1), 0);
+    std::vector<uint8_t> dloc;
+    for (int q = 0; q < ps.P; ++q) {
+        for (int k = ps.h_nptr[size_t(q)]; k < ps.h_nptr[size_t(q + 1)]; ++k)
+            if (flag[size_t(ps.h_nodes[size_t(k)])] & 1) dloc.push_back(uint8_t(k - ps.h_nptr[size_t(q)]));
+        dptr[size_t(q + 1)] = int(dloc.size());
+    }
+    if (dloc.empty()) dloc.push_back(0);
+    HB_TRY(upload(p, ps.dptr, dptr));
+    HB_TRY(upload(p, ps.dloc, dloc));
+    return HB_OK;
+}
+
 hb_status prepare_bc(hb_problem *p) {
     if (!p->bc_dirty) return HB_OK;
     const int N = p->N, M = 2 * p->n_h + 1;
@@ -440,6 +464,8 @@ hb_status prepare_bc(hb_problem *p) {
     HB_TRY(upload(p, p->d_dir_wave, dir_wave));
     HB_TRY(upload(p, p->d_dir_prof, dir_prof));
     HB_TRY(upload(p, p->d_flag, flag));
+    HB_TRY(dirichlet_lists(p, p->ps32, flag));
+    HB_TRY(dirichlet_lists(p, p->ps64, flag));
     HB_TRY(dalloc(p, p->d_g, size_t(std::max(1, p->n_dir * 3 * N))));
     launch_dirichlet_values(p->d_dir_nodes.p, p->d_dir_wave.p, p->d_dir_prof.p, p->n_dir, p->d_W.p, N, p->d_g.p,
                             p->stream);
@@ -509,7 +535,7 @@ hb_status apply_op(hb_problem *p, int mode, const T *y, const T *v, T *out, doub
     const int N = p->N;
     HB_CUDA(cudaMemsetAsync(out, 0, size_t(p->n_nodes) * 4 * N * sizeof(T), s));
     ElemArgs<T> ea;
-    ea.pv = PatchView<T>{ps.P, ps.nl_max, ps.ep_max, ps.eptr.p, ps.nptr.p, ps.nodes.p, ps.lconn.p, ps.geom.p};
+    ea.pv = ps.view();
     ea.y = y;
     ea.v = v;
     ea.out = out;
@@ -845,7 +871,7 @@ hb_status apply_jv_noalloc(hb_problem *p, int mode, const T *y, const T *v, T *o
     const int N = p->N;
     HB_CUDA(cudaMemsetAsync(out, 0, size_t(p->n_nodes) * 4 * N * sizeof(T), s));
     ElemArgs<T> ea;
-    ea.pv = PatchView<T>{ps.P, ps.nl_max, ps.ep_max, ps.eptr.p, ps.nptr.p, ps.nodes.p, ps.lconn.p, ps.geom.p};
+    ea.pv = ps.view();
     ea.y = y;
     ea.v = v;
     ea.out = out;

@@ -15,7 +15,7 @@ namespace hb {
 namespace {
 
 struct Layout {
-    size_t H, geom, Y, V, HY, HV, Q, T, node, conn, total;
+    size_t H, geom, Y, V, HY, HV, T, node, conn, total;
 };
 
 __host__ __device__ inline size_t pad16(size_t b) { return (b + 15) & ~size_t(15); }
@@ -30,7 +30,6 @@ __host__ __device__ inline Layout make_layout(int mode, int N, int nl, int ep, s
     L.V = o;    if (mode == MODE_JVP || mode == MODE_JVE) o += pad16(row4);
     L.HY = o;   if (mode == MODE_RES || mode == MODE_JVE) o += pad16(row3);
     L.HV = o;   if (mode == MODE_JVE || mode == MODE_JVP) o += pad16(row3);
-    L.Q = o;    o += pad16(row4);
     L.T = o;    if (mode == MODE_RES || mode == MODE_JVE) o += pad16(row3);
     L.node = o; o += pad16(size_t(nl) * 4);
     L.conn = o; o += pad16(size_t(ep) * 4);
@@ -83,11 +82,17 @@ __device__ __forceinline__ void element_instance(int e, int n, int Nrt, T rho, T
                                                  const uint32_t *__restrict__ sConn,
                                                  const T *__restrict__ sY, const T *__restrict__ sV,
                                                  const T *__restrict__ sHY, const T *__restrict__ sHV,
-                                                 T *sQ, T *sT) {
+                                                 const int *__restrict__ sNode, T *__restrict__ gout,
+                                                 T *sT) {
     const int N = NT > 0 ? NT : Nrt;
     const int N4 = 4 * N, N3 = 3 * N;
     const uint32_t c = sConn[e];
     const int lo[4] = {int(c & 255u), int((c >> 8) & 255u), int((c >> 16) & 255u), int(c >> 24)};
+    // global rows of the 4 nodes at this instance: contributions without instance coupling are added
+    // there directly (native global reductions)
+    T *go[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) go[a] = gout + size_t(sNode[lo[a]]) * N4 + n;
     T gN[4][3], V, g2;
     load_geom(sGeom + e * kGeomStride, gN, V, g2);
     const T w = V * T(0.25);
@@ -130,8 +135,10 @@ __device__ __forceinline__ void element_instance(int e, int n, int Nrt, T rho, T
             const T gg = gN[a][0] * gN[a][0] + gN[a][1] * gN[a][1] + gN[a][2] * gN[a][2];
             const T dv = dvel[a] + w * rho * qb * udNs[a] + mu * V * gg + shift * V * T(0.1);
             const T dp = (w / rho) * taus * gg;
-            atomicAdd(sQ + lo[a] * N4 + n, dv);
-            atomicAdd(sQ + lo[a] * N4 + 3 * N + n, dp);
+            atomicAdd(go[a], dv);
+            atomicAdd(go[a] + N, dv);
+            atomicAdd(go[a] + 2 * N, dv);
+            atomicAdd(go[a] + 3 * N, dp);
         }
         return;
     } else if constexpr (MODE == MODE_RES) {
@@ -195,11 +202,11 @@ __device__ __forceinline__ void element_instance(int e, int n, int Nrt, T rho, T
                 const T visc = gN[a][0] * gU[i][0] + gN[a][1] * gU[i][1] + gN[a][2] * gU[i][2];
                 const T vq = qm[a][i] + w * rho * qb * convs[i] + mu * V * visc - V * gN[a][i] * pbar;
                 const T vt = tt[a][i] + rho * m20 * (usum[i] + u[a][i]) - w * qb * S[i];
-                atomicAdd(sQ + lo[a] * N4 + i * N + n, vq);
+                atomicAdd(go[a] + i * N, vq);
                 atomicAdd(sT + lo[a] * N3 + i * N + n, vt);
             }
             const T qc = w * div + (w / rho) * (gN[a][0] * S[0] + gN[a][1] * S[1] + gN[a][2] * S[2]);
-            atomicAdd(sQ + lo[a] * N4 + 3 * N + n, qc);
+            atomicAdd(go[a] + 3 * N, qc);
         }
         return;
     } else if constexpr (MODE == MODE_JVP) {
@@ -266,10 +273,10 @@ __device__ __forceinline__ void element_instance(int e, int n, int Nrt, T rho, T
                 const T mhv = m20 * (hdvsum[i] + hdv[a][i]);     // F block: H (rho M v) = rho M (H v)
                 const T vq = qm[a][i] + w * rho * qb * ugvs[i] + mu * V * visc - V * gN[a][i] * pbar
                            + shift * mv + rho * mhv;
-                atomicAdd(sQ + lo[a] * N4 + i * N + n, vq);
+                atomicAdd(go[a] + i * N, vq);
             }
             const T qc = w * div + (w / rho) * (gN[a][0] * S[0] + gN[a][1] * S[1] + gN[a][2] * S[2]);
-            atomicAdd(sQ + lo[a] * N4 + 3 * N + n, qc);
+            atomicAdd(go[a] + 3 * N, qc);
         }
         return;
     } else {  // MODE_JVE
@@ -358,11 +365,11 @@ __device__ __forceinline__ void element_instance(int e, int n, int Nrt, T rho, T
                 const T mv = m20 * (dvsum[i] + dv[a][i]);
                 const T vq = qm[a][i] + w * rho * qb * dconvs[i] + mu * V * visc - V * gN[a][i] * pbar + shift * mv;
                 const T vt = tt[a][i] + rho * mv - w * qb * S[i];
-                atomicAdd(sQ + lo[a] * N4 + i * N + n, vq);
+                atomicAdd(go[a] + i * N, vq);
                 atomicAdd(sT + lo[a] * N3 + i * N + n, vt);
             }
             const T qc = w * div + (w / rho) * (gN[a][0] * S[0] + gN[a][1] * S[1] + gN[a][2] * S[2]);
-            atomicAdd(sQ + lo[a] * N4 + 3 * N + n, qc);
+            atomicAdd(go[a] + 3 * N, qc);
         }
         return;
     }
@@ -408,7 +415,6 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 2 : 1)) elem_kernel(
     T *sV = reinterpret_cast<T *>(smem + L.V);
     T *sHY = reinterpret_cast<T *>(smem + L.HY);
     T *sHV = reinterpret_cast<T *>(smem + L.HV);
-    T *sQ = reinterpret_cast<T *>(smem + L.Q);
     T *sT = reinterpret_cast<T *>(smem + L.T);
     int *sNode = reinterpret_cast<int *>(smem + L.node);
     uint32_t *sConn = reinterpret_cast<uint32_t *>(smem + L.conn);
@@ -431,7 +437,6 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 2 : 1)) elem_kernel(
             const int nvec = int(ne * kGeomStride * sizeof(T) / 16);
             for (int i = tid; i < nvec; i += nt) dst[i] = src[i];
         }
-        for (int i = tid; i < nl * N4; i += nt) sQ[i] = T(0);
         if constexpr (MODE == MODE_RES || MODE == MODE_JVE)
             for (int i = tid; i < nl * N3; i += nt) sT[i] = T(0);
         __syncthreads();
@@ -449,12 +454,16 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 2 : 1)) elem_kernel(
         cp_async_wait_all();
         __syncthreads();
         if constexpr (MODE == MODE_JVP || MODE == MODE_JVE) {
-            // Dirichlet velocity entries of the direction are not unknowns: treat them as 0
-            for (int i = tid; i < nl * N3; i += nt) {
-                const int l = i / N3, r = i - l * N3;
-                if (a.flag[sNode[l]] & 1) sV[l * N4 + r] = T(0);
+            // Dirichlet velocity entries of the direction are not unknowns: treat them as 0 (only the
+            // patches touching a Dirichlet boundary have any)
+            const int d0 = a.pv.dptr[p], nd = a.pv.dptr[p + 1] - d0;
+            if (nd > 0) {
+                for (int i = tid; i < nd * N3; i += nt) {
+                    const int k = i / N3, r = i - k * N3;
+                    sV[int(a.pv.dloc[d0 + k]) * N4 + r] = T(0);
+                }
+                __syncthreads();
             }
-            __syncthreads();
         }
         if constexpr (MODE != MODE_DIAG) {
             // time coupling of the staged velocities: (H x)[l][i][n] = sum_k H[n][k] x[l][i][k] for
@@ -493,7 +502,8 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 2 : 1)) elem_kernel(
 
         for (int i = tid; i < ne * N; i += nt) {
             const int e = i / N, n = i - e * N;
-            element_instance<T, MODE, NT>(e, n, N, a.rho, a.mu, a.shift, sGeom, sConn, sY, sV, sHY, sHV, sQ, sT);
+            element_instance<T, MODE, NT>(e, n, N, a.rho, a.mu, a.shift, sGeom, sConn, sY, sV, sHY, sHV, sNode,
+                                          a.out, sT);
         }
         __syncthreads();
 
@@ -506,29 +516,22 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 2 : 1)) elem_kernel(
             __syncthreads();
         }
 
-        // flush: out += Q + H T (velocity rows), once per local node
-        for (int i = tid; i < nl * N4; i += nt) {
-            const int l = i / N4, r = i - l * N4, f = r / N, n = r - f * N;
-            T val;
-            if constexpr (MODE == MODE_DIAG) {
-                val = (f == 1 || f == 2) ? sQ[l * N4 + n] : sQ[i];
-            } else if constexpr (MODE == MODE_JVP) {
-                val = sQ[i];
-            } else {
-                val = sQ[i];
-                if (f < 3) {
-                    if constexpr (NT > 0) {
-                        val += sT[l * N3 + f * N + n];
-                    } else {
-                        const T *h = sH + n * N;
-                        const T *t = sT + l * N3 + f * N;
-                        T acc = 0;
-                        for (int k = 0; k < N; ++k) acc += h[k] * t[k];
-                        val += acc;
-                    }
+        // flush: out += H T on the velocity rows, once per local node
+        if constexpr (MODE == MODE_RES || MODE == MODE_JVE) {
+            for (int i = tid; i < nl * N3; i += nt) {
+                const int l = i / N3, r = i - l * N3;
+                T val;
+                if constexpr (NT > 0) {
+                    val = sT[i];
+                } else {
+                    const int f = r / N, n = r - f * N;
+                    const T *h = sH + n * N;
+                    const T *t = sT + l * N3 + f * N;
+                    val = T(0);
+                    for (int k = 0; k < N; ++k) val += h[k] * t[k];
                 }
+                atomicAdd(a.out + size_t(sNode[l]) * N4 + r, val);
             }
-            atomicAdd(a.out + size_t(sNode[l]) * N4 + r, val);
         }
         __syncthreads();
     }

@@ -26,12 +26,13 @@ constexpr double kQB = 0.1381966011250105;
 
 // Fields per local node staged in shared memory, by mode.
 // JVP stages y, v and H v (the F block is applied as rho M (H v): M and H commute); RES stages y and
-// H u; JVE stages y, H u, v, H v.  RES and JVE accumulate Q (4 fields) and T (3 fields).
+// H u; JVE stages y, H u, v, H v.  Element contributions that need no instance coupling go straight to
+// global memory; RES and JVE accumulate T (3 fields) per patch node in shared memory for H T.
 __host__ __device__ constexpr int in_fields(int mode) {
     return mode == MODE_RES ? 7 : mode == MODE_JVP ? 11 : mode == MODE_JVE ? 14 : 4;
 }
 __host__ __device__ constexpr int out_fields(int mode) {
-    return (mode == MODE_DIAG || mode == MODE_JVP) ? 4 : 7;
+    return (mode == MODE_DIAG || mode == MODE_JVP) ? 0 : 3;
 }
 
 // Element patches: elements renumbered so each patch's elements are contiguous; each patch lists its
@@ -46,6 +47,8 @@ struct PatchView {
     const int *nodes;              // [nptr[P]]
     const uint32_t *lconn;         // [E]
     const T *geom;                 // [E][kGeomStride]
+    const int *dptr;               // [P+1] range of each patch's Dirichlet local nodes in dloc
+    const uint8_t *dloc;           // local indices of the patch nodes with Dirichlet velocity
 };
 
 template <typename T>
