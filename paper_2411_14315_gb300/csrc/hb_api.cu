@@ -131,6 +131,15 @@ struct hb_problem {
     int km = 0;
     DBuf<double> kV, kz64, kdx, kdiag, kres, ktmp, kh;
     DBuf<float> kz32, kw32, ky32, kdiag32;
+    // graph-captured GMRES restart cycles, one per operator (paper tangent / exact)
+    struct CycleGraph {
+        cudaGraphExec_t exec = nullptr;
+        int m = 0, precision = -1;
+        double shift = 0;
+        int64_t launches = 0;
+    } cycle[2];
+    DBuf<double> gm;
+    DBuf<int> gate;
     // element-kernel timing
     bool prof_on = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev;
@@ -688,107 +697,157 @@ hb_status apply_A(hb_problem *p, const OpCtx &c, const double *z64, double *w) {
     return HB_OK;
 }
 
-// Right-preconditioned restarted GMRES with classical Gram-Schmidt (one re-orthogonalisation pass when
-// the norm drops by more than 1/sqrt(2)) and Givens rotations; Arnoldi vectors and scalars in FP64.
+// Device-side GMRES bookkeeping layout (doubles): pass-1 and pass-2 Gram-Schmidt coefficients, ||w||^2,
+// the rotated Hessenberg matrix R [(m+1) x m], Givens cosines and sines, rotated right-hand side g,
+// residual estimates, and three scalars.
+struct GmLayout {
+    size_t h1, h2, nrm2, R, cs, sn, g, resid, invnorm, invbeta, beta2, total;
+};
+
+GmLayout gm_layout(int m) {
+    GmLayout L;
+    size_t o = 0;
+    L.h1 = o; o += size_t(m + 2);
+    L.h2 = o; o += size_t(m + 2);
+    L.nrm2 = o; o += 1;
+    L.R = o; o += size_t(m + 1) * size_t(m);
+    L.cs = o; o += size_t(m);
+    L.sn = o; o += size_t(m);
+    L.g = o; o += size_t(m + 1);
+    L.resid = o; o += size_t(m);
+    L.invnorm = o; o += 1;
+    L.invbeta = o; o += 1;
+    L.beta2 = o; o += 1;
+    L.total = o;
+    return L;
+}
+
+// Enqueue the m Arnoldi iterations of one restart cycle (V_0 already normalised): right Jacobi
+// preconditioning, A z, classical Gram-Schmidt with a second pass when more than half of ||w||^2 was
+// removed, then the Hessenberg / Givens update on the device.  No host synchronisation.
+hb_status record_cycle(hb_problem *p, const OpCtx &c, int m) {
+    const int64_t nd = p->n_nodes * 4 * p->N;
+    const GmLayout L = gm_layout(m);
+    double *G = p->gm.p;
+    double *V = p->kV.p;
+    cudaStream_t s = p->stream;
+    for (int j = 0; j < m; ++j) {
+        double *vj = V + int64_t(j) * nd;
+        double *w = V + int64_t(j + 1) * nd;
+        launch_precond<double>(vj, p->kdiag.p, p->kz64.p, nd, s);
+        HB_LAUNCHED(p, 1);
+        HB_TRY(apply_A(p, c, p->kz64.p, w));
+        launch_multidot(V, nd, j + 1, w, nd, p->scratch.p, G + L.h1, s);
+        launch_multiaxpy_norm(V, nd, j + 1, G + L.h1, w, nd, p->scratch.p, G + L.nrm2, s);
+        launch_reorth_gate(G + L.h1 + (j + 1), G + L.nrm2, p->gate.p, s);
+        launch_multidot(V, nd, j + 1, w, nd, p->scratch.p, G + L.h2, s, p->gate.p);
+        launch_multiaxpy_norm(V, nd, j + 1, G + L.h2, w, nd, p->scratch.p, G + L.nrm2, s, p->gate.p);
+        launch_arnoldi_update(j, m, G + L.h1, G + L.h2, G + L.nrm2, G + L.R, G + L.cs, G + L.sn, G + L.g,
+                              G + L.resid, G + L.invnorm, s);
+        launch_scale_dev(w, G + L.invnorm, w, nd, s);
+        HB_LAUNCHED(p, 11);
+    }
+    return HB_OK;
+}
+
+hb_status cycle_graph(hb_problem *p, const OpCtx &c, int m, hb_problem::CycleGraph *&out) {
+    hb_problem::CycleGraph &gc = p->cycle[c.mode == MODE_JVE ? 1 : 0];
+    out = &gc;
+    if (gc.exec && gc.m == m && gc.precision == c.precision && gc.shift == c.shift) return HB_OK;
+    if (gc.exec) {
+        cudaGraphExecDestroy(gc.exec);
+        gc.exec = nullptr;
+    }
+    const int64_t l0 = p->launches;
+    HB_CUDA(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeRelaxed));
+    hb_status st = record_cycle(p, c, m);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(p->stream, &graph);
+    if (st != HB_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e != cudaSuccess) return fail(HB_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&gc.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        gc.exec = nullptr;
+        return fail(HB_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    gc.m = m;
+    gc.precision = c.precision;
+    gc.shift = c.shift;
+    gc.launches = p->launches - l0;
+    p->launches = l0;
+    return HB_OK;
+}
+
+// Right-preconditioned restarted GMRES(m): FP64 Arnoldi vectors and scalars, operator in the
+// precision of c.  Each restart cycle is one CUDA-graph launch of m iterations followed by one host
+// synchronisation; the host then picks the first iteration that met the tolerance and forms the update.
 hb_status gmres(hb_problem *p, const OpCtx &c, const double *b, double *x, double tol, int m, int maxit,
                 int &iters, int &jv_calls) {
     const int64_t nd = p->n_nodes * 4 * p->N;
+    cudaStream_t s = p->stream;
+    const GmLayout L = gm_layout(m);
+    HB_TRY(dalloc(p, p->gm, L.total));
+    HB_TRY(dalloc(p, p->gate, 1));
+    double *G = p->gm.p;
     double *V = p->kV.p;
-    std::vector<double> Hh(size_t((m + 1) * m), 0.0), cs(size_t(m), 0.0), sn(size_t(m), 0.0), g(size_t(m + 1), 0.0);
-    std::vector<double> hv(size_t(m + 2), 0.0), h2(size_t(m + 2), 0.0);
-    HB_CUDA(cudaMemsetAsync(x, 0, size_t(nd) * sizeof(double), p->stream));
+    HB_CUDA(cudaMemsetAsync(x, 0, size_t(nd) * sizeof(double), s));
     double bnorm = 0;
     HB_TRY(dev_norm(p, b, nd, bnorm));
     iters = 0;
     if (bnorm == 0) return HB_OK;
-    // residual of x = 0
-    HB_CUDA(cudaMemcpyAsync(p->kres.p, b, size_t(nd) * sizeof(double), cudaMemcpyDeviceToDevice, p->stream));
-    double beta = bnorm;
+    hb_problem::CycleGraph *gc = nullptr;
+    HB_TRY(cycle_graph(p, c, m, gc));
+    std::vector<double> resid(static_cast<size_t>(m)), g(static_cast<size_t>(m + 1)), R(static_cast<size_t>((m + 1) * m)), yk(static_cast<size_t>(m));
+    bool first = true;
     while (true) {
-        launch_scale_copy(1.0 / beta, p->kres.p, V, nd, p->stream);
-        HB_LAUNCHED(p, 1);
-        std::fill(g.begin(), g.end(), 0.0);
-        g[0] = beta;
-        int k = 0;
-        bool done = false;
-        for (int j = 0; j < m; ++j) {
-            double *vj = V + int64_t(j) * nd;
-            double *w = V + int64_t(j + 1) * nd;
-            launch_precond<double>(vj, p->kdiag.p, p->kz64.p, nd, p->stream);
-            HB_LAUNCHED(p, 1);
-            HB_TRY(apply_A(p, c, p->kz64.p, w));
+        if (first) {
+            HB_CUDA(cudaMemcpyAsync(p->kres.p, b, size_t(nd) * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        } else {
+            HB_TRY(apply_A(p, c, x, p->ktmp.p));
             ++jv_calls;
-            // pass 1
-            launch_multidot(V, nd, j + 1, w, nd, p->scratch.p, p->kh.p, p->stream);
+            launch_scale_copy(1.0, b, p->kres.p, nd, s);
+            launch_axpy(-1.0, p->ktmp.p, p->kres.p, nd, s);
             HB_LAUNCHED(p, 2);
-            launch_multiaxpy_norm(V, nd, j + 1, p->kh.p, w, nd, p->scratch.p, p->kh.p + (m + 2), p->stream);
-            HB_LAUNCHED(p, 2);
-            HB_CUDA(cudaMemcpyAsync(hv.data(), p->kh.p, size_t(j + 2) * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
-            double after2 = 0;
-            HB_CUDA(cudaMemcpyAsync(&after2, p->kh.p + (m + 2), sizeof(double), cudaMemcpyDeviceToHost, p->stream));
-            HB_CUDA(cudaStreamSynchronize(p->stream));
-            const double before2 = hv[size_t(j + 1)];
-            if (!std::isfinite(after2) || !std::isfinite(before2)) return fail(HB_ERR_NAN, "non-finite value in GMRES");
-            if (after2 < 0.5 * before2) {   // re-orthogonalise
-                launch_multidot(V, nd, j + 1, w, nd, p->scratch.p, p->kh.p, p->stream);
-                HB_LAUNCHED(p, 2);
-                launch_multiaxpy_norm(V, nd, j + 1, p->kh.p, w, nd, p->scratch.p, p->kh.p + (m + 2), p->stream);
-                HB_LAUNCHED(p, 2);
-                HB_CUDA(cudaMemcpyAsync(h2.data(), p->kh.p, size_t(j + 1) * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
-                HB_CUDA(cudaMemcpyAsync(&after2, p->kh.p + (m + 2), sizeof(double), cudaMemcpyDeviceToHost, p->stream));
-                HB_CUDA(cudaStreamSynchronize(p->stream));
-                for (int i = 0; i <= j; ++i) hv[size_t(i)] += h2[size_t(i)];
-            }
-            const double hn = std::sqrt(std::max(after2, 0.0));
-            for (int i = 0; i <= j; ++i) Hh[size_t(i * m + j)] = hv[size_t(i)];
-            Hh[size_t((j + 1) * m + j)] = hn;
-            if (hn > 0) {
-                launch_scale_copy(1.0 / hn, w, w, nd, p->stream);
-                HB_LAUNCHED(p, 1);
-            }
-            for (int i = 0; i < j; ++i) {
-                const double a0 = Hh[size_t(i * m + j)], a1 = Hh[size_t((i + 1) * m + j)];
-                Hh[size_t(i * m + j)] = cs[size_t(i)] * a0 + sn[size_t(i)] * a1;
-                Hh[size_t((i + 1) * m + j)] = -sn[size_t(i)] * a0 + cs[size_t(i)] * a1;
-            }
-            const double a0 = Hh[size_t(j * m + j)], a1 = Hh[size_t((j + 1) * m + j)];
-            const double den = std::hypot(a0, a1);
-            cs[size_t(j)] = den > 0 ? a0 / den : 1.0;
-            sn[size_t(j)] = den > 0 ? a1 / den : 0.0;
-            Hh[size_t(j * m + j)] = den;
-            Hh[size_t((j + 1) * m + j)] = 0.0;
-            g[size_t(j + 1)] = -sn[size_t(j)] * g[size_t(j)];
-            g[size_t(j)] = cs[size_t(j)] * g[size_t(j)];
-            ++iters;
-            k = j + 1;
-            if (std::fabs(g[size_t(j + 1)]) <= tol * bnorm || iters >= maxit || hn == 0) {
-                done = true;
+        }
+        launch_dot(p->kres.p, p->kres.p, nd, p->scratch.p, G + L.beta2, s);
+        launch_cycle_init(G + L.beta2, m, G + L.g, G + L.invbeta, s);
+        launch_scale_dev(p->kres.p, G + L.invbeta, V, nd, s);
+        HB_LAUNCHED(p, 4);
+        HB_CUDA(cudaGraphLaunch(gc->exec, s));
+        p->launches += gc->launches;
+        jv_calls += m;
+        HB_CUDA(cudaMemcpyAsync(resid.data(), G + L.resid, size_t(m) * sizeof(double), cudaMemcpyDeviceToHost, s));
+        HB_CUDA(cudaMemcpyAsync(g.data(), G + L.g, size_t(m + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
+        HB_CUDA(cudaMemcpyAsync(R.data(), G + L.R, R.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+        HB_CUDA(cudaStreamSynchronize(s));
+        int k = m;
+        for (int j = 0; j < m; ++j) {
+            if (!std::isfinite(resid[size_t(j)])) return fail(HB_ERR_NAN, "non-finite value in GMRES");
+            if (resid[size_t(j)] <= tol * bnorm) {
+                k = j + 1;
                 break;
             }
         }
-        // back substitution, then x += M^-1 V_k y_k
-        std::vector<double> yk(size_t(k), 0.0);
+        k = std::max(1, std::min(k, maxit - iters));
         for (int i = k - 1; i >= 0; --i) {
-            double s = g[size_t(i)];
-            for (int l = i + 1; l < k; ++l) s -= Hh[size_t(i * m + l)] * yk[size_t(l)];
-            yk[size_t(i)] = Hh[size_t(i * m + i)] != 0 ? s / Hh[size_t(i * m + i)] : 0.0;
+            double acc = g[size_t(i)];
+            for (int l = i + 1; l < k; ++l) acc -= R[size_t(i) * m + l] * yk[size_t(l)];
+            const double d = R[size_t(i) * m + i];
+            yk[size_t(i)] = d != 0 ? acc / d : 0.0;
         }
-        HB_CUDA(cudaMemcpyAsync(p->kh.p, yk.data(), size_t(k) * sizeof(double), cudaMemcpyHostToDevice, p->stream));
-        launch_combine(V, nd, k, p->kh.p, p->ktmp.p, nd, p->stream);
-        launch_precond<double>(p->ktmp.p, p->kdiag.p, p->kz64.p, nd, p->stream);
-        launch_axpy(1.0, p->kz64.p, x, nd, p->stream);
+        HB_CUDA(cudaMemcpyAsync(p->kh.p, yk.data(), size_t(k) * sizeof(double), cudaMemcpyHostToDevice, s));
+        launch_combine(V, nd, k, p->kh.p, p->ktmp.p, nd, s);
+        launch_precond<double>(p->ktmp.p, p->kdiag.p, p->kz64.p, nd, s);
+        launch_axpy(1.0, p->kz64.p, x, nd, s);
         HB_LAUNCHED(p, 3);
-        HB_CUDA(cudaStreamSynchronize(p->stream));   // yk (host) consumed
-        if (done && (std::fabs(g[size_t(k)]) <= tol * bnorm || iters >= maxit)) break;
-        if (iters >= maxit) break;
-        // true residual for the restart: res = b - A x
-        HB_TRY(apply_A(p, c, x, p->ktmp.p));
-        ++jv_calls;
-        launch_scale_copy(1.0, b, p->kres.p, nd, p->stream);
-        launch_axpy(-1.0, p->ktmp.p, p->kres.p, nd, p->stream);
-        HB_LAUNCHED(p, 2);
-        HB_TRY(dev_norm(p, p->kres.p, nd, beta));
-        if (beta <= tol * bnorm || beta == 0) break;
+        HB_CUDA(cudaStreamSynchronize(s));   // yk consumed
+        iters += k;
+        if (resid[size_t(k - 1)] <= tol * bnorm || iters >= maxit) break;
+        first = false;
     }
     return HB_OK;
 }
@@ -805,7 +864,7 @@ hb_status ensure_krylov(hb_problem *p, int m) {
     HB_TRY(dalloc(p, p->kdiag, nd));
     HB_TRY(dalloc(p, p->kres, nd));
     HB_TRY(dalloc(p, p->ktmp, nd));
-    HB_TRY(dalloc(p, p->kh, size_t(2 * (m + 2) + 8)));
+    HB_TRY(dalloc(p, p->kh, size_t(2 * (m + 2) + 8)));   // combination coefficients
     HB_TRY(dalloc(p, p->kz32, nd));
     HB_TRY(dalloc(p, p->kw32, nd));
     HB_TRY(dalloc(p, p->ky32, nd));
@@ -1101,6 +1160,8 @@ hb_status hb_destroy(hb_problem *p) {
         cudaEventDestroy(ev.first);
         cudaEventDestroy(ev.second);
     }
+    for (auto &gc : p->cycle)
+        if (gc.exec) cudaGraphExecDestroy(gc.exec);
     delete p;
     if (own) cudaStreamDestroy(s);
     return HB_OK;
@@ -1268,6 +1329,8 @@ hb_status hb_default_opts(hb_solve_opts *o) {
     return HB_OK;
 }
 
+static hb_status solve_impl(hb_problem *p, const hb_solve_opts &o, hb_report *rep);
+
 hb_status hb_solve(hb_problem *p, const hb_solve_opts *opts, hb_report *rep) {
     if (!p) return fail(HB_ERR_INVALID_ARG, "null problem");
     hb_solve_opts o;
@@ -1276,6 +1339,28 @@ hb_status hb_solve(hb_problem *p, const hb_solve_opts *opts, hb_report *rep) {
     HB_TRY(check_precision(o.precision));
     if (o.gmres_restart < 1 || o.gmres_restart > 200) return fail(HB_ERR_INVALID_ARG, "gmres_restart must be in [1, 200]");
     HB_CUDA(cudaSetDevice(p->device));
+    if (p->own_stream) return solve_impl(p, o, rep);
+    // the GMRES cycles are captured as CUDA graphs, which needs a stream of our own: order it after the
+    // caller's stream, solve on it, and synchronise before handing the caller's stream back
+    cudaStream_t user = p->stream, own = nullptr;
+    cudaEvent_t ev = nullptr;
+    HB_CUDA(cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking));
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaStreamDestroy(own);
+        return fail(HB_ERR_CUDA, "cudaEventCreate failed");
+    }
+    cudaEventRecord(ev, user);
+    cudaStreamWaitEvent(own, ev, 0);
+    p->stream = own;
+    hb_status st = solve_impl(p, o, rep);
+    cudaStreamSynchronize(own);
+    p->stream = user;
+    cudaEventDestroy(ev);
+    cudaStreamDestroy(own);
+    return st;
+}
+
+static hb_status solve_impl(hb_problem *p, const hb_solve_opts &o, hb_report *rep) {
     const auto t0 = std::chrono::steady_clock::now();
     HB_TRY(prepare_bc(p));
     if (p->inflows.empty()) return fail(HB_ERR_STATE, "no inflow set");
@@ -1299,6 +1384,7 @@ hb_status hb_solve(hb_problem *p, const hb_solve_opts *opts, hb_report *rep) {
     bool newton = false;
     hb_status result = HB_ERR_NOT_CONVERGED;
     double dxn = INFINITY;
+    double eta = 0.1, rn_prev = rn;   // Eisenstat-Walker forcing term of the Newton phase
     for (int step = 0; step < o.max_steps; ++step) {
         if (!std::isfinite(rn)) {
             result = fail(HB_ERR_NAN, "residual is not finite");
@@ -1323,7 +1409,18 @@ hb_status hb_solve(hb_problem *p, const hb_solve_opts *opts, hb_report *rep) {
         launch_scale_copy(-1.0, r, b, nd, p->stream);
         HB_LAUNCHED(p, 1);
         int its = 0, jvc = 0;
-        const double tol = newton ? o.gmres_rtol_newton : o.gmres_rtol_pseudo;
+        double tol = o.gmres_rtol_pseudo;
+        if (newton) {
+            if (R.newton_steps > 0) {
+                double e = 0.9 * (rn / rn_prev) * (rn / rn_prev);
+                const double safe = 0.9 * eta * eta;
+                if (safe > 0.1) e = std::max(e, safe);
+                eta = e;
+            }
+            eta = std::min(0.1, std::max(o.gmres_rtol_newton, eta));
+            tol = eta;
+        }
+        rn_prev = rn;
         HB_TRY(gmres(p, c, b, p->kdx.p, tol, o.gmres_restart, o.max_gmres, its, jvc));
         R.gmres_iters += its;
         R.jv_calls += jvc;

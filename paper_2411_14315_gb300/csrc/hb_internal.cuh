@@ -112,12 +112,20 @@ void launch_scale_copy(double a, const double *x, double *y, int64_t n, cudaStre
 template <typename T>
 void launch_precond(const double *x, const double *d, T *z, int64_t n, cudaStream_t s);
 // partials[nb * (k + 1)]; result[k + 1] = (V_j . w for j < k, w . w)
+// With a non-null gate that holds 0 at run time, launch_multidot writes zeros and launch_multiaxpy_norm
+// leaves w and result unchanged (the second, conditional pass of classical Gram-Schmidt).
 int multidot_blocks(int64_t n);
 void launch_multidot(const double *V, int64_t ld, int k, const double *w, int64_t n, double *partials,
-                     double *result, cudaStream_t s);
+                     double *result, cudaStream_t s, const int *gate = nullptr);
 // w -= sum_j h[j] V_j; result[0] = ||w||^2 after the update (partials scratch as above)
 void launch_multiaxpy_norm(const double *V, int64_t ld, int k, const double *h, double *w, int64_t n,
-                           double *partials, double *result, cudaStream_t s);
+                           double *partials, double *result, cudaStream_t s, const int *gate = nullptr);
+void launch_reorth_gate(const double *before2, const double *after2, int *gate, cudaStream_t s);
+// device-side GMRES bookkeeping (Hessenberg column, Givens rotations, residual estimate)
+void launch_arnoldi_update(int j, int m, const double *h1, const double *h2, const double *nrm2, double *R,
+                           double *cs, double *sn, double *g, double *resid, double *invnorm, cudaStream_t s);
+void launch_cycle_init(const double *beta2, int m, double *g, double *invbeta, cudaStream_t s);
+void launch_scale_dev(const double *x, const double *sp, double *y, int64_t n, cudaStream_t s);
 // y = sum_j c[j] V_j (c on device)
 void launch_combine(const double *V, int64_t ld, int k, const double *c, double *y, int64_t n,
                     cudaStream_t s);

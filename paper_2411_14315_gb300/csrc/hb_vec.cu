@@ -57,7 +57,8 @@ __device__ __forceinline__ double warp_sum(double v) {
 // partials[b * (k+1) + j] = sum over this block's chunks of V_j . w (j < k) and w . w (j = k)
 __global__ void __launch_bounds__(kVB) multidot_kernel(const double *__restrict__ V, int64_t ld, int k,
                                                        const double *__restrict__ w, int64_t n,
-                                                       double *__restrict__ partials) {
+                                                       double *__restrict__ partials, const int *gate) {
+    if (gate && *gate == 0) return;
     __shared__ double sw[kChunk];
     __shared__ double sp[kVB / 32][kMaxK + 1];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -96,11 +97,16 @@ __global__ void __launch_bounds__(kVB) multidot_kernel(const double *__restrict_
     }
 }
 
-// result[j] = sum_b partials[b * stride + j] for j < cnt
+// result[j] = sum_b partials[b * stride + j] for j < cnt.  With a gate that is 0: zero_if_closed writes
+// zeros, otherwise the result is left unchanged.
 __global__ void finish_kernel(const double *__restrict__ partials, int nb, int stride, int cnt,
-                              double *__restrict__ result) {
+                              double *__restrict__ result, const int *gate = nullptr, int zero_if_closed = 0) {
     const int j = blockIdx.x;
     if (j >= cnt) return;
+    if (gate && *gate == 0) {
+        if (zero_if_closed && threadIdx.x == 0) result[j] = 0.0;
+        return;
+    }
     double s = 0.0;
     for (int b = threadIdx.x; b < nb; b += blockDim.x) s += partials[int64_t(b) * stride + j];
     __shared__ double red[32];
@@ -117,7 +123,9 @@ __global__ void finish_kernel(const double *__restrict__ partials, int nb, int s
 // w -= sum_j h[j] V_j, then partials[b] = this block's share of ||w||^2
 __global__ void __launch_bounds__(kVB) multiaxpy_norm_kernel(const double *__restrict__ V, int64_t ld, int k,
                                                              const double *__restrict__ h, double *__restrict__ w,
-                                                             int64_t n, double *__restrict__ partials) {
+                                                             int64_t n, double *__restrict__ partials,
+                                                             const int *gate) {
+    if (gate && *gate == 0) return;
     __shared__ double sh[kMaxK];
     __shared__ double red[kVB / 32];
     for (int j = threadIdx.x; j < k; j += kVB) sh[j] = h[j];
@@ -166,6 +174,54 @@ __global__ void __launch_bounds__(kVB) dot_kernel(const double *__restrict__ x, 
     }
 }
 
+// gate = 1 when classical Gram-Schmidt lost more than half of ||w||^2 (a second pass is needed)
+__global__ void reorth_gate_kernel(const double *before2, const double *after2, int *gate) {
+    *gate = (*after2 < 0.5 * *before2) ? 1 : 0;
+}
+
+// One Arnoldi column: h = h1 + h2 and ||w|| give column j of the Hessenberg matrix; apply the previous
+// Givens rotations, form rotation j, update the rotated right-hand side g, record |g[j+1]| (the GMRES
+// residual estimate) and 1 / ||w|| for the normalisation of the next basis vector.
+__global__ void arnoldi_update_kernel(int j, int m, const double *__restrict__ h1, const double *__restrict__ h2,
+                                      const double *__restrict__ nrm2, double *__restrict__ R,
+                                      double *__restrict__ cs, double *__restrict__ sn, double *__restrict__ g,
+                                      double *__restrict__ resid, double *__restrict__ invnorm) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double col[kMaxK + 1];
+    for (int i = 0; i <= j; ++i) col[i] = h1[i] + h2[i];
+    const double hn = sqrt(fmax(*nrm2, 0.0));
+    col[j + 1] = hn;
+    for (int i = 0; i < j; ++i) {
+        const double a0 = col[i], a1 = col[i + 1];
+        col[i] = cs[i] * a0 + sn[i] * a1;
+        col[i + 1] = -sn[i] * a0 + cs[i] * a1;
+    }
+    const double den = hypot(col[j], col[j + 1]);
+    cs[j] = den > 0 ? col[j] / den : 1.0;
+    sn[j] = den > 0 ? col[j + 1] / den : 0.0;
+    col[j] = den;
+    g[j + 1] = -sn[j] * g[j];
+    g[j] = cs[j] * g[j];
+    for (int i = 0; i <= j; ++i) R[i * m + j] = col[i];
+    resid[j] = fabs(g[j + 1]);
+    *invnorm = hn > 0 ? 1.0 / hn : 0.0;
+}
+
+// start of a restart cycle: beta = sqrt(beta2), g = (beta, 0, ...), invbeta = 1 / beta
+__global__ void cycle_init_kernel(const double *beta2, int m, double *g, double *invbeta) {
+    const int i = threadIdx.x;
+    const double beta = sqrt(fmax(*beta2, 0.0));
+    for (int k = i; k <= m; k += blockDim.x) g[k] = (k == 0) ? beta : 0.0;
+    if (i == 0) *invbeta = beta > 0 ? 1.0 / beta : 0.0;
+}
+
+__global__ void scale_dev_kernel(const double *__restrict__ x, const double *__restrict__ sp, double *__restrict__ y,
+                                 int64_t n) {
+    const double a = *sp;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        y[i] = a * x[i];
+}
+
 int stream_grid(int64_t n) {
     const int cap = sm_count() * 8;
     const int need = nblk(n, kVB);
@@ -199,17 +255,34 @@ void launch_precond(const double *x, const double *d, T *z, int64_t n, cudaStrea
 }
 
 void launch_multidot(const double *V, int64_t ld, int k, const double *w, int64_t n, double *partials,
-                     double *result, cudaStream_t s) {
+                     double *result, cudaStream_t s, const int *gate) {
     const int nb = multidot_blocks(n);
-    multidot_kernel<<<nb, kVB, 0, s>>>(V, ld, k, w, n, partials);
-    finish_kernel<<<k + 1, 256, 0, s>>>(partials, nb, k + 1, k + 1, result);
+    multidot_kernel<<<nb, kVB, 0, s>>>(V, ld, k, w, n, partials, gate);
+    finish_kernel<<<k + 1, 256, 0, s>>>(partials, nb, k + 1, k + 1, result, gate, 1);
 }
 
 void launch_multiaxpy_norm(const double *V, int64_t ld, int k, const double *h, double *w, int64_t n,
-                           double *partials, double *result, cudaStream_t s) {
+                           double *partials, double *result, cudaStream_t s, const int *gate) {
     const int nb = stream_grid(n);
-    multiaxpy_norm_kernel<<<nb, kVB, 0, s>>>(V, ld, k, h, w, n, partials);
-    finish_kernel<<<1, 256, 0, s>>>(partials, nb, 1, 1, result);
+    multiaxpy_norm_kernel<<<nb, kVB, 0, s>>>(V, ld, k, h, w, n, partials, gate);
+    finish_kernel<<<1, 256, 0, s>>>(partials, nb, 1, 1, result, gate, 0);
+}
+
+void launch_reorth_gate(const double *before2, const double *after2, int *gate, cudaStream_t s) {
+    reorth_gate_kernel<<<1, 1, 0, s>>>(before2, after2, gate);
+}
+
+void launch_arnoldi_update(int j, int m, const double *h1, const double *h2, const double *nrm2, double *R,
+                           double *cs, double *sn, double *g, double *resid, double *invnorm, cudaStream_t s) {
+    arnoldi_update_kernel<<<1, 32, 0, s>>>(j, m, h1, h2, nrm2, R, cs, sn, g, resid, invnorm);
+}
+
+void launch_cycle_init(const double *beta2, int m, double *g, double *invbeta, cudaStream_t s) {
+    cycle_init_kernel<<<1, 256, 0, s>>>(beta2, m, g, invbeta);
+}
+
+void launch_scale_dev(const double *x, const double *sp, double *y, int64_t n, cudaStream_t s) {
+    if (n > 0) scale_dev_kernel<<<stream_grid(n), kVB, 0, s>>>(x, sp, y, n);
 }
 
 void launch_combine(const double *V, int64_t ld, int k, const double *c, double *y, int64_t n,

@@ -91,3 +91,24 @@ def glenn_spec(n_tets=1_000_000, n_h=10, seed=2000) -> Spec:
         pa[0] = 7.0 * mmHg
         s.outlets_r.append((tag, 30.0, pa, pb))
     return s
+
+
+def coronary_spec(n_tets=300_000, n_h=10, seed=4000, reynolds=100.0) -> Spec:
+    """Stenosed coronary-like tube (radius U(0.15, 0.25) cm, 30-70 % diameter reduction) in cgs units:
+    rho 1.06, mu 0.04, T 0.8 s, parabolic inflow with 10 seeded harmonics at a mean Reynolds number of
+    `reynolds`, outlet at a steady 70 mmHg (Sec. 3.3 stand-in)."""
+    m = I.stenosed_tube(n_tets, seed)
+    rng = np.random.default_rng(seed + 7)
+    R = float(np.max(np.linalg.norm(m.xyz[:, :2], axis=1)))
+    nu = 0.04 / 1.06
+    u_mean = reynolds * nu / (2.0 * R)
+    a, b = I.waveform_harmonics(n_h, u_mean * math.pi * R * R, seed + 11, amp_lo=0.3, amp_hi=0.8)
+    mmHg = 1333.22
+    pa = np.zeros(n_h + 1)
+    pb = np.zeros(n_h + 1)
+    pa[0] = 70.0 * mmHg
+    s = Spec(m, 1.06, 0.04, 0.8, n_h, name=f"coronary_s{seed}")
+    s.inflows.append((1, None, a, b))
+    s.outlets_p.append((2, pa, pb))
+    del rng
+    return s
