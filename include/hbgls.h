@@ -107,6 +107,10 @@ typedef struct {
     double cfl;               /* CFL number of that rule (1)                                           */
     int use_learned;          /* 1: start from the learned warm start if one is attached               */
     int verbose;              /* print one line per outer step to stderr                               */
+    int ser;                  /* 1: switched evolution relaxation -- the pseudo step grows as
+                                 ||r0|| / ||r|| (an extension; the paper keeps dt fixed; the converged
+                                 state is the same root)                                              */
+    double ser_max;           /* cap of that growth factor                                             */
 } hb_solve_opts;
 
 typedef struct {

@@ -140,6 +140,8 @@ struct hb_problem {
     } cycle[2];
     DBuf<double> gm;
     DBuf<int> gate;
+    DBuf<double> shift_dev;
+    double shift_host = 0;
     // element-kernel timing
     bool prof_on = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev;
@@ -538,7 +540,8 @@ hb_status prepare_bc(hb_problem *p) {
 // operators
 
 template <typename T>
-hb_status apply_op(hb_problem *p, int mode, const T *y, const T *v, T *out, double shift, cudaStream_t s) {
+hb_status apply_op(hb_problem *p, int mode, const T *y, const T *v, T *out, double shift, cudaStream_t s,
+                   const double *shift_dev = nullptr) {
     HB_TRY(prepare_bc(p));
     PatchSetDev<T> &ps = patches<T>(p);
     const int N = p->N;
@@ -554,6 +557,7 @@ hb_status apply_op(hb_problem *p, int mode, const T *y, const T *v, T *out, doub
     ea.rho = T(p->rho);
     ea.mu = T(p->mu);
     ea.shift = T(shift);
+    ea.shift_dev = shift_dev;
     if (ps.P > 0) {
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (p->prof_on) {
@@ -683,15 +687,16 @@ struct OpCtx {
     int mode;
     double shift;
     int precision;
+    const double *shift_dev = nullptr;   // pseudo shift read from device memory (graph-stable)
 };
 
 // w(double) = A z, with z given in double (z64) and, for the mixed path, its float copy made here
 hb_status apply_A(hb_problem *p, const OpCtx &c, const double *z64, double *w) {
     const int64_t nd = p->n_nodes * 4 * p->N;
-    if (c.precision == 0) return apply_op<double>(p, c.mode, p->y.p, z64, w, c.shift, p->stream);
+    if (c.precision == 0) return apply_op<double>(p, c.mode, p->y.p, z64, w, c.shift, p->stream, c.shift_dev);
     launch_convert<double, float>(z64, p->kz32.p, nd, p->stream);
     HB_LAUNCHED(p, 1);
-    HB_TRY(apply_op<float>(p, c.mode, p->ky32.p, p->kz32.p, p->kw32.p, c.shift, p->stream));
+    HB_TRY(apply_op<float>(p, c.mode, p->ky32.p, p->kz32.p, p->kw32.p, c.shift, p->stream, c.shift_dev));
     launch_convert<float, double>(p->kw32.p, w, nd, p->stream);
     HB_LAUNCHED(p, 1);
     return HB_OK;
@@ -753,7 +758,8 @@ hb_status record_cycle(hb_problem *p, const OpCtx &c, int m) {
 hb_status cycle_graph(hb_problem *p, const OpCtx &c, int m, hb_problem::CycleGraph *&out) {
     hb_problem::CycleGraph &gc = p->cycle[c.mode == MODE_JVE ? 1 : 0];
     out = &gc;
-    if (gc.exec && gc.m == m && gc.precision == c.precision && gc.shift == c.shift) return HB_OK;
+    const double key = c.shift_dev ? -1.0 : c.shift;
+    if (gc.exec && gc.m == m && gc.precision == c.precision && gc.shift == key) return HB_OK;
     if (gc.exec) {
         cudaGraphExecDestroy(gc.exec);
         gc.exec = nullptr;
@@ -776,7 +782,7 @@ hb_status cycle_graph(hb_problem *p, const OpCtx &c, int m, hb_problem::CycleGra
     }
     gc.m = m;
     gc.precision = c.precision;
-    gc.shift = c.shift;
+    gc.shift = key;
     gc.launches = p->launches - l0;
     p->launches = l0;
     return HB_OK;
@@ -786,7 +792,7 @@ hb_status cycle_graph(hb_problem *p, const OpCtx &c, int m, hb_problem::CycleGra
 // precision of c.  Each restart cycle is one CUDA-graph launch of m iterations followed by one host
 // synchronisation; the host then picks the first iteration that met the tolerance and forms the update.
 hb_status gmres(hb_problem *p, const OpCtx &c, const double *b, double *x, double tol, int m, int maxit,
-                int &iters, int &jv_calls) {
+                int &iters, int &jv_calls, double *relres = nullptr) {
     const int64_t nd = p->n_nodes * 4 * p->N;
     cudaStream_t s = p->stream;
     const GmLayout L = gm_layout(m);
@@ -846,6 +852,7 @@ hb_status gmres(hb_problem *p, const OpCtx &c, const double *b, double *x, doubl
         HB_LAUNCHED(p, 3);
         HB_CUDA(cudaStreamSynchronize(s));   // yk consumed
         iters += k;
+        if (relres) *relres = resid[size_t(k - 1)] / bnorm;
         if (resid[size_t(k - 1)] <= tol * bnorm || iters >= maxit) break;
         first = false;
     }
@@ -1319,13 +1326,15 @@ hb_status hb_default_opts(hb_solve_opts *o) {
     o->switch_rtol = 1e-3;
     o->gmres_rtol_pseudo = 0.03;
     o->gmres_rtol_newton = 1e-3;
-    o->gmres_restart = 60;
-    o->max_gmres = 3000;
+    o->gmres_restart = 30;
+    o->max_gmres = 600;
     o->max_steps = 400;
     o->dt_pseudo = 0.0;
     o->cfl = 1.0;
     o->use_learned = 0;
     o->verbose = 0;
+    o->ser = 1;
+    o->ser_max = 1e4;
     return HB_OK;
 }
 
@@ -1372,7 +1381,8 @@ static hb_status solve_impl(hb_problem *p, const hb_solve_opts &o, hb_report *re
     std::memset(&R, 0, sizeof(R));
     const double dt = o.dt_pseudo > 0 ? o.dt_pseudo : (p->u_c > 0 ? o.cfl * h_char(p) / p->u_c : INFINITY);
     R.dt_pseudo = dt;
-    const double shift = std::isfinite(dt) ? kC1 * p->rho / dt : 0.0;
+    const double shift0 = std::isfinite(dt) ? kC1 * p->rho / dt : 0.0;
+    HB_TRY(dalloc(p, p->shift_dev, 1));
     double *r = p->w64a.p;
     double *b = p->w64b.p;
     HB_TRY(apply_op<double>(p, MODE_RES, p->y.p, nullptr, r, 0.0, p->stream));
@@ -1385,6 +1395,7 @@ static hb_status solve_impl(hb_problem *p, const hb_solve_opts &o, hb_report *re
     hb_status result = HB_ERR_NOT_CONVERGED;
     double dxn = INFINITY;
     double eta = 0.1, rn_prev = rn;   // Eisenstat-Walker forcing term of the Newton phase
+    double dtk = dt;                  // current pseudo step (adaptive when o.ser)
     for (int step = 0; step < o.max_steps; ++step) {
         if (!std::isfinite(rn)) {
             result = fail(HB_ERR_NAN, "residual is not finite");
@@ -1395,16 +1406,25 @@ static hb_status solve_impl(hb_problem *p, const hb_solve_opts &o, hb_report *re
             break;
         }
         if (rn < o.switch_rtol * r0) newton = true;
-        OpCtx c{newton ? MODE_JVE : MODE_JVP, newton ? 0.0 : shift, o.precision};
+        // Pseudo shift c1 rho / dt (Sec. 2.3).  Paper mode (o.ser = 0): fixed dt with the paper's tangent,
+        // then exact Newton without shift.  Adaptive mode (o.ser = 1): dt grows with the residual drop while
+        // GMRES converges within its budget and shrinks when it does not; the exact Jacobian replaces the
+        // paper's tangent after the switch, and the shift is dropped once dt exceeds ser_max x the CFL step.
+        double shift = 0.0;
+        if (!o.ser) shift = newton ? 0.0 : shift0;
+        else if (std::isfinite(dtk) && dtk < dt * o.ser_max) shift = kC1 * p->rho / dtk;
+        p->shift_host = shift;
+        HB_CUDA(cudaMemcpyAsync(p->shift_dev.p, &p->shift_host, sizeof(double), cudaMemcpyHostToDevice, p->stream));
+        OpCtx c{newton ? MODE_JVE : MODE_JVP, shift, o.precision, p->shift_dev.p};
         // Jacobi diagonal of P (+ pseudo mass) and the frozen state in the kernels' precision
         if (o.precision == 1) {
             launch_convert<double, float>(p->y.p, p->ky32.p, nd, p->stream);
             HB_LAUNCHED(p, 1);
-            HB_TRY(apply_op<float>(p, MODE_DIAG, p->ky32.p, nullptr, p->kdiag32.p, c.shift, p->stream));
+            HB_TRY(apply_op<float>(p, MODE_DIAG, p->ky32.p, nullptr, p->kdiag32.p, c.shift, p->stream, c.shift_dev));
             launch_convert<float, double>(p->kdiag32.p, p->kdiag.p, nd, p->stream);
             HB_LAUNCHED(p, 1);
         } else {
-            HB_TRY(apply_op<double>(p, MODE_DIAG, p->y.p, nullptr, p->kdiag.p, c.shift, p->stream));
+            HB_TRY(apply_op<double>(p, MODE_DIAG, p->y.p, nullptr, p->kdiag.p, c.shift, p->stream, c.shift_dev));
         }
         launch_scale_copy(-1.0, r, b, nd, p->stream);
         HB_LAUNCHED(p, 1);
@@ -1420,8 +1440,10 @@ static hb_status solve_impl(hb_problem *p, const hb_solve_opts &o, hb_report *re
             eta = std::min(0.1, std::max(o.gmres_rtol_newton, eta));
             tol = eta;
         }
+        const double rn_before = rn;
         rn_prev = rn;
-        HB_TRY(gmres(p, c, b, p->kdx.p, tol, o.gmres_restart, o.max_gmres, its, jvc));
+        double relres = 0;
+        HB_TRY(gmres(p, c, b, p->kdx.p, tol, o.gmres_restart, o.max_gmres, its, jvc, &relres));
         R.gmres_iters += its;
         R.jv_calls += jvc;
         launch_axpy(1.0, p->kdx.p, p->y.p, nd, p->stream);
@@ -1434,10 +1456,14 @@ static hb_status solve_impl(hb_problem *p, const hb_solve_opts &o, hb_report *re
         HB_TRY(dev_norm(p, r, nd, rn));
         R.steps++;
         if (newton) R.newton_steps++;
+        if (o.ser) {
+            if (relres <= tol * 1.0001) dtk *= std::min(4.0, std::max(1.0, rn_before / std::max(rn, 1e-300)));
+            else dtk *= 0.5;
+        }
         if (o.verbose)
             std::fprintf(stderr, "hb_solve step %d %s gmres %d |r|/|r0| %.3e |dy|/|y| %.3e\n", step,
                          newton ? "newton" : "pseudo", its, rn / r0, yn > 0 ? dxn / yn : 0.0);
-        if (newton && rn <= o.rtol * r0 && dxn <= 10 * o.rtol * yn) {
+        if (newton && rn <= o.rtol * r0 && dxn <= 10 * o.rtol * yn && shift == 0.0) {
             result = HB_OK;
             break;
         }

@@ -419,6 +419,7 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 2 : 1)) elem_kernel(
     int *sNode = reinterpret_cast<int *>(smem + L.node);
     uint32_t *sConn = reinterpret_cast<uint32_t *>(smem + L.conn);
     const int tid = threadIdx.x, nt = blockDim.x;
+    const T shift = a.shift_dev ? T(*a.shift_dev) : a.shift;
 
     if constexpr (NT > 0) {
         for (int i = tid; i < N; i += nt) sH[i] = a.H[i * N];
@@ -502,7 +503,7 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 2 : 1)) elem_kernel(
 
         for (int i = tid; i < ne * N; i += nt) {
             const int e = i / N, n = i - e * N;
-            element_instance<T, MODE, NT>(e, n, N, a.rho, a.mu, a.shift, sGeom, sConn, sY, sV, sHY, sHV, sNode,
+            element_instance<T, MODE, NT>(e, n, N, a.rho, a.mu, shift, sGeom, sConn, sY, sV, sHY, sHV, sNode,
                                           a.out, sT);
         }
         __syncthreads();

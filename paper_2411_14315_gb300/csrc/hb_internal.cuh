@@ -61,6 +61,7 @@ struct ElemArgs {
     const uint8_t *flag;           // per node, bit 0: Dirichlet velocity
     int N;
     T rho, mu, shift;
+    const double *shift_dev = nullptr;   // if set, the shift is read from device memory instead
 };
 
 // Boundary (Neumann) faces.
