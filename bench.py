@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--skip-solve", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-batch", action="store_true")
     ap.add_argument("--extra", action="store_true", help="also time residual / exact Jv / FP64 rates")
     return ap.parse_args()
 
@@ -255,6 +256,55 @@ def time_solves():
     return out
 
 
+def time_batch(reps: int = 20):
+    """64 vessels of uneven size and N (20k-400k tets, N in {9, 13, 21}): one captured graph with one
+    persistent element launch for the whole batch, against 64 per-problem Jv calls."""
+    import torch
+
+    from paper_2411_14315_gb300 import hbgls
+    from paper_2411_14315_gb300 import inputs as I
+    from paper_2411_14315_gb300 import workloads as W
+    t0 = time.perf_counter()
+    specs = W.batch_specs()
+    stream = torch.cuda.current_stream()
+    probs = [hbgls.Problem.from_spec(s, stream=stream) for s in specs]
+    setup_s = time.perf_counter() - t0
+    ys = [torch.tensor(I.random_state(s.mesh.n_nodes, s.N, 200 + k), dtype=torch.float32, device="cuda")
+          for k, s in enumerate(specs)]
+    vs = [torch.tensor(I.random_state(s.mesh.n_nodes, s.N, 300 + k), dtype=torch.float32, device="cuda")
+          for k, s in enumerate(specs)]
+    outs = [torch.empty_like(y) for y in ys]
+    units = sum(s.mesh.n_tets * s.N for s in specs)
+    b = hbgls.Batch(probs, hbgls.FP32)
+
+    def batched():
+        b.jv_dev(ys, vs, outs, hbgls.PAPER, 300.0, stream=stream)
+
+    def sequential():
+        for p, y, v, o in zip(probs, ys, vs, outs):
+            p.jv_dev(y, v, o, hbgls.PAPER, hbgls.FP32, 300.0, stream=stream)
+
+    res = {"workload": f"{len(specs)} vessels, {sum(s.mesh.n_tets for s in specs)} tets, N in "
+                       f"{sorted(set(s.N for s in specs))}", "units_per_jv": units, "setup_s": setup_s}
+    for name, fn in (("batched", batched), ("sequential", sequential)):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        res[name] = {"ms_per_jv": ms, "element_instances_per_s": units / (ms / 1e3)}
+    res["graph_launches_per_batched_jv"] = 1
+    b.close()
+    for p in probs:
+        p.close()
+    return res
+
+
 def run_ours(args, dist: Dist, spec, config):
     import torch
 
@@ -384,6 +434,11 @@ def run_ours(args, dist: Dist, spec, config):
         result["other_rates"] = rates
 
     if dist.rank == 0 and dist.world == 1:
+        if not args.skip_batch:
+            try:
+                result["batch"] = time_batch()
+            except Exception as e:  # reported, not hidden
+                result["batch"] = {"error": repr(e)}
         if not args.skip_solve:
             try:
                 result["time_to_solve"] = time_solves()

@@ -111,6 +111,8 @@ typedef struct {
                                  ||r0|| / ||r|| (an extension; the paper keeps dt fixed; the converged
                                  state is the same root)                                              */
     double ser_max;           /* cap of that growth factor                                             */
+    double r_ref;             /* > 0: residual scale of rtol and switch_rtol instead of ||r0|| (lets a
+                                 warm-started solve stop at the same absolute residual as a cold one)  */
 } hb_solve_opts;
 
 typedef struct {
@@ -171,12 +173,78 @@ hb_status hb_jacobi_diag_dev(hb_problem *p, const void *y, void *d, int precisio
 hb_status hb_jv_dev_noalloc(hb_problem *p, const void *y, const void *v, void *jv, int kind, int precision,
                             double shift, void *stream);
 
+/* ---- learned warm start (not the paper's method: Sec. 4 only suggests harmonic balance solutions as
+ * machine-learning data) ---------------------------------------------------------------------------
+ * A message-passing network over the mesh graph predicts the harmonic coefficients of the solution from
+ * node positions, boundary flags, the inflow profile and the inflow waveform.  Weights are stored in
+ * BF16, arithmetic is FP32.  Architecture, with mlp(X) = relu(X W1 + b1) W2 + b2:
+ *   h = enc(x); for each layer: m_e = msg([h_src, h_dst, e_e]), a_i = sum_{e->i} m_e, h += upd([h, a]);
+ *   out = dec(h), out = [n][4][2 n_h + 1] normalised harmonics (velocity / U, pressure relative to the
+ *   mean outlet level / (p_scale rho U^2), U the largest mean inlet speed).
+ * Parameters, flat FP32 (hb_mpnn_get_params): per MLP in the order enc, (msg_l, upd_l) for each layer,
+ * dec: W1 [in][hidden], b1 [hidden], W2 [hidden][out], b2 [out], row-major. */
+typedef struct hb_mpnn hb_mpnn;
+typedef struct {
+    int hidden;               /* 32 .. 64 */
+    int layers;               /* message-passing layers, 1 .. 8 */
+    int n_h;                  /* harmonics predicted; must equal the problems' n_h (<= 11) */
+    int seed;                 /* initialisation seed */
+    double p_scale;           /* pressure normalisation: (p - mean outlet level) / (p_scale rho U^2); <= 0
+                                 means 1 */
+} hb_mpnn_config;
+hb_status hb_mpnn_create(const hb_mpnn_config *cfg, int device, hb_mpnn **out);
+hb_status hb_mpnn_destroy(hb_mpnn *net);
+int64_t hb_mpnn_num_params(const hb_mpnn *net);
+hb_status hb_mpnn_get_params(hb_mpnn *net, float *params);          /* host [num_params] */
+hb_status hb_mpnn_set_params(hb_mpnn *net, const float *params);    /* also resets the optimiser */
+/* Mean squared error of the prediction against target harmonics (host, [n][4][2 n_h + 1], physical
+ * units) and, if grad is non-NULL, its gradient with respect to the FP32 parameters (host). */
+hb_status hb_mpnn_loss_grad(hb_mpnn *net, hb_problem *p, const double *target, float *loss, float *grad);
+/* One Adam step (beta 0.9 / 0.999) on one problem's target harmonics; loss before the step. */
+hb_status hb_mpnn_train_step(hb_mpnn *net, hb_problem *p, const double *target, float lr, float *loss);
+/* Predicted harmonics [n][4][2 n_h + 1] in physical units (host). */
+hb_status hb_mpnn_predict(hb_mpnn *net, hb_problem *p, double *harmonics);
+/* The graph the network sees for a problem: node features x [n][32] (normalised position, wall /
+ * inflow / outlet flags, inflow profile / its largest magnitude, inflow waveform series / |a0|, zero
+ * padded), directed edges (both directions of every tetrahedron edge) and edge features e [n_edges][4]
+ * (normalised offset, length).  Any output pointer may be NULL; *n_edges is always written. */
+hb_status hb_mpnn_graph(hb_mpnn *net, hb_problem *p, float *x, int32_t *src, int32_t *dst, float *e,
+                        int64_t *n_edges);
+/* Set the problem's state to the prediction (Dirichlet values imposed on top). */
+hb_status hb_mpnn_warm_start(hb_mpnn *net, hb_problem *p);
+/* Attach a network (not owned) so that hb_solve with use_learned = 1 starts from its prediction. */
+hb_status hb_attach_learned(hb_problem *p, hb_mpnn *net);
+
+/* ---- batches of problems (many vessels of uneven size and N in one launch) --------------------------
+ * A batch applies the operator of every member problem in one captured CUDA graph: the output
+ * clearing, one persistent element pass whose work items (problem, patch) are taken from a global
+ * counter (so large and small problems share the SMs) and dispatched on each problem's N, then the
+ * boundary terms and Dirichlet rows of each problem.  All problems must live on one device; their
+ * boundary data are prepared at creation.  The graph is captured on first use and again whenever the
+ * operands, kind or shift change.  Work is ordered after `stream` (NULL: the first problem's stream) and
+ * `stream` waits for it. */
+typedef struct hb_batch hb_batch;
+hb_status hb_batch_create(hb_problem *const *problems, int count, int precision, hb_batch **out);
+hb_status hb_batch_destroy(hb_batch *b);
+/* y[q], v[q], jv[q]: device arrays of problem q (double for precision 0, float for 1), instance
+ * layout; same semantics as hb_jv_dev for each problem. */
+hb_status hb_batch_jv_dev(hb_batch *b, const void *const *y, const void *const *v, void *const *jv, int kind,
+                          double shift, void *stream);
+int64_t hb_batch_launch_count(const hb_batch *b);
+/* Patch-size autotuning: rebuild the problem's element patches (precision 0 or 1) with each candidate
+ * node cap, time `reps` paper-tangent Jv element passes with CUDA events, and keep the fastest.  Returns
+ * the chosen cap and its time per pass (ms). */
+hb_status hb_tune_patches(hb_problem *p, int precision, const int *candidates, int n_cand, int reps,
+                          int *best_nl, double *best_ms);
+
 /* ---- introspection ------------------------------------------------------------------------------ */
 typedef struct {
     int64_t n_nodes, n_tets, n_faces, n_dirichlet_nodes, n_neumann_faces;
     int n_h, N, n_patches32, n_patches64, patch_nodes_max32, patch_elems_max32;
     int64_t device_bytes;
     double h_char;            /* edge of the regular tetrahedron of mean element volume (Sec. 2.3) */
+    double u_ref;             /* largest mean inlet speed over the instances (CFL rule of Sec. 2.3)  */
+    double p_ref;             /* mean outlet pressure level over outlets and instances              */
 } hb_info;
 hb_status hb_get_info(hb_problem *p, hb_info *info);
 /* Number of kernel launches queued by this problem since creation (all entry points). */

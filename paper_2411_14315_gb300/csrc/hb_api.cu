@@ -2,6 +2,7 @@
 // geometry), boundary data, operator dispatch and the pseudo-time Newton-GMRES solve
 // (arXiv 2411.14315, Sec. 2.3: Eq. NR, Eq. splitK, pseudo time stepping, Jacobi + GMRES).
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -89,6 +90,11 @@ struct Outlet {
 }  // namespace
 
 struct hb_problem {
+    uint64_t uid = 0;                // unique per problem in this process
+    std::vector<int32_t> tets_morton; // elements in Morton order of their centroids (patch input)
+    hb_mpnn *learned = nullptr;      // attached warm-start network (not owned)
+    std::vector<double> h_prof;      // per-node Dirichlet profile (after prepare_bc)
+    std::vector<int> h_wave;         // per-node: -2 free, -1 wall, >= 0 inflow index
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -289,8 +295,9 @@ int choose_nl(int N, size_t ts, size_t budget) {
 }
 
 template <typename T>
-hb_status make_patchset(hb_problem *p, PatchSetDev<T> &ps, const std::vector<int32_t> &tets_ord, size_t budget) {
-    const int NL = choose_nl(p->N, sizeof(T), budget);
+hb_status make_patchset(hb_problem *p, PatchSetDev<T> &ps, const std::vector<int32_t> &tets_ord, size_t budget,
+                        int nl_override = 0) {
+    const int NL = nl_override > 0 ? std::min(nl_override, 255) : choose_nl(p->N, sizeof(T), budget);
     const int EP = 3 * NL;
     HostPatches hp = build_patches(tets_ord, p->n_tets, p->n_nodes, NL, EP, std::max(1, 31 / p->N));
     ps.P = int(hp.eptr.size()) - 1;
@@ -431,6 +438,8 @@ hb_status prepare_bc(hb_problem *p) {
     for (int64_t f = 0; f < p->n_faces; ++f)
         if (p->face_tag[size_t(f)] == 0)
             for (int b = 0; b < 3; ++b) wave[size_t(p->faces[size_t(3 * f + b)])] = -1;
+    p->h_prof = prof;
+    p->h_wave = wave;
     std::vector<int> dir_nodes, dir_wave;
     std::vector<double> dir_prof;
     std::vector<uint8_t> flag(size_t(n), 0);
@@ -984,6 +993,54 @@ hb_status apply_jv_noalloc(hb_problem *p, int mode, const T *y, const T *v, T *o
     return HB_OK;
 }
 
+namespace hb {
+
+hb_status set_error(hb_status st, const std::string &msg) { return fail(st, msg); }
+
+uint64_t problem_uid(const hb_problem *p) { return p ? p->uid : 0; }
+
+hb_status learned_inputs(hb_problem *p, LearnedInputs &in) {
+    if (!p) return fail(HB_ERR_INVALID_ARG, "null problem");
+    HB_CUDA(cudaSetDevice(p->device));
+    HB_TRY(prepare_bc(p));
+    if (p->inflows.empty()) return fail(HB_ERR_STATE, "the learned warm start needs an inflow");
+    in.n_nodes = p->n_nodes;
+    in.n_tets = p->n_tets;
+    in.n_h = p->n_h;
+    in.xyz = p->xyz;
+    in.tets = p->tets;
+    in.flags.assign(size_t(p->n_nodes), 0);
+    for (int64_t a = 0; a < p->n_nodes; ++a) {
+        const int w = p->h_wave[size_t(a)];
+        if (w == -1) in.flags[size_t(a)] |= 1;
+        if (w >= 0) in.flags[size_t(a)] |= 2;
+    }
+    for (int64_t f = 0; f < p->n_faces; ++f) {
+        const int tag = p->face_tag[size_t(f)];
+        bool is_in = false;
+        for (auto &x : p->inflows) is_in |= (x.tag == tag);
+        if (tag != 0 && !is_in)
+            for (int b = 0; b < 3; ++b) in.flags[size_t(p->faces[size_t(3 * f + b)])] |= 4;
+    }
+    in.profile.assign(size_t(3 * p->n_nodes), 0.0);   // the inflow profile on inflow (non-wall) nodes
+    for (int64_t a = 0; a < p->n_nodes; ++a)
+        if (p->h_wave[size_t(a)] >= 0)
+            for (int i = 0; i < 3; ++i) in.profile[size_t(3 * a + i)] = p->h_prof[size_t(3 * a + i)];
+    in.wave = p->inflows[0].coef;
+    in.u_ref = p->u_c > 0 ? p->u_c : 1.0;
+    double pr = 0;
+    for (double v : p->level) pr += v / double(p->level.size());
+    in.p_ref = pr;
+    in.rho = p->rho;
+    return HB_OK;
+}
+
+hb_status learned_set_initial(hb_problem *p, const double *harmonics_host) {
+    return hb_set_initial(p, harmonics_host);
+}
+
+}  // namespace hb
+
 // =====================================================================================================
 // C ABI
 
@@ -1008,6 +1065,8 @@ hb_status hb_create(const hb_mesh *mesh, double rho, double mu, double period_T,
         return fail(HB_ERR_CUDA, "no such CUDA device");
     }
     hb_problem *p = new hb_problem();
+    static std::atomic<uint64_t> next_uid{1};
+    p->uid = next_uid++;
     auto bail = [&](hb_status st) {
         delete p;
         return st;
@@ -1085,7 +1144,8 @@ hb_status hb_create(const hb_mesh *mesh, double rho, double mu, double period_T,
     if (!(vmin > 1e-14 * p->vol_mean))
         return bail(fail(HB_ERR_MESH, "degenerate tetrahedron (zero volume)"));
     std::sort(keys.begin(), keys.end());
-    std::vector<int32_t> tets_ord(size_t(4 * E));
+    std::vector<int32_t> &tets_ord = p->tets_morton;
+    tets_ord.assign(size_t(4 * E), 0);
     for (int64_t e = 0; e < E; ++e)
         for (int a = 0; a < 4; ++a) tets_ord[size_t(4 * e + a)] = p->tets[size_t(4 * keys[size_t(e)].second + a)];
     // boundary faces: outward normal away from the owning tetrahedron's opposite vertex, and area
@@ -1335,10 +1395,17 @@ hb_status hb_default_opts(hb_solve_opts *o) {
     o->verbose = 0;
     o->ser = 1;
     o->ser_max = 1e4;
+    o->r_ref = 0.0;
     return HB_OK;
 }
 
 static hb_status solve_impl(hb_problem *p, const hb_solve_opts &o, hb_report *rep);
+
+hb_status hb_attach_learned(hb_problem *p, hb_mpnn *net) {
+    if (!p) return fail(HB_ERR_INVALID_ARG, "null problem");
+    p->learned = net;
+    return HB_OK;
+}
 
 hb_status hb_solve(hb_problem *p, const hb_solve_opts *opts, hb_report *rep) {
     if (!p) return fail(HB_ERR_INVALID_ARG, "null problem");
@@ -1348,6 +1415,10 @@ hb_status hb_solve(hb_problem *p, const hb_solve_opts *opts, hb_report *rep) {
     HB_TRY(check_precision(o.precision));
     if (o.gmres_restart < 1 || o.gmres_restart > 200) return fail(HB_ERR_INVALID_ARG, "gmres_restart must be in [1, 200]");
     HB_CUDA(cudaSetDevice(p->device));
+    if (o.use_learned) {
+        if (!p->learned) return fail(HB_ERR_STATE, "use_learned set but no network attached (hb_attach_learned)");
+        HB_TRY(hb_mpnn_warm_start(p->learned, p));
+    }
     if (p->own_stream) return solve_impl(p, o, rep);
     // the GMRES cycles are captured as CUDA graphs, which needs a stream of our own: order it after the
     // caller's stream, solve on it, and synchronise before handing the caller's stream back
@@ -1390,7 +1461,7 @@ static hb_status solve_impl(hb_problem *p, const hb_solve_opts &o, hb_report *re
     double rn = 0;
     HB_TRY(dev_norm(p, r, nd, rn));
     R.res0 = rn;
-    double r0 = rn;
+    const double r0 = o.r_ref > 0 ? o.r_ref : rn;
     bool newton = false;
     hb_status result = HB_ERR_NOT_CONVERGED;
     double dxn = INFINITY;
@@ -1501,6 +1572,286 @@ hb_status hb_jv_dev_noalloc(hb_problem *p, const void *y, const void *v, void *j
                                    static_cast<float *>(jv), shift, s, static_cast<float *>(q));
 }
 
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------------------
+// batches: one captured graph applies the operator of many problems, their element work in one
+// persistent launch
+
+struct hb_batch {
+    std::vector<hb_problem *> probs;
+    int precision = 1, device = 0;
+    cudaStream_t stream = nullptr;
+    DBuf<ElemArgs<float>> args32;
+    DBuf<ElemArgs<double>> args64;
+    DBuf<int> first_item, counter;
+    int n_items = 0, grid = 0;
+    size_t smem = 0;
+    cudaGraphExec_t exec = nullptr;
+    int mode = -1;
+    double shift = 0;
+    std::vector<const void *> y, v;
+    std::vector<void *> out;
+    int64_t launches_per_replay = 0, launches = 0;
+};
+
+namespace {
+
+template <typename T>
+hb_status batch_record(hb_batch *b) {
+    cudaStream_t s = b->stream;
+    hb_problem *p0 = b->probs[0];
+    std::vector<ElemArgs<T>> args(b->probs.size());
+    size_t smem = 0;
+    for (size_t q = 0; q < b->probs.size(); ++q) {
+        hb_problem *p = b->probs[q];
+        PatchSetDev<T> &ps = patches<T>(p);
+        ElemArgs<T> &ea = args[q];
+        ea.pv = ps.view();
+        ea.y = static_cast<const T *>(b->y[q]);
+        ea.v = static_cast<const T *>(b->v[q]);
+        ea.out = static_cast<T *>(b->out[q]);
+        ea.H = Hmat<T>(p);
+        ea.flag = p->d_flag.p;
+        ea.N = p->N;
+        ea.rho = T(p->rho);
+        ea.mu = T(p->mu);
+        ea.shift = T(b->shift);
+        ea.shift_dev = nullptr;
+        smem = std::max(smem, elem_smem_bytes(b->mode, p->N, ps.nl_max, ps.ep_max, sizeof(T)));
+    }
+    DBuf<ElemArgs<T>> &dargs = [&]() -> DBuf<ElemArgs<T>> & {
+        if constexpr (sizeof(T) == 4) return b->args32;
+        else return b->args64;
+    }();
+    HB_TRY(dalloc(p0, dargs, args.size()));
+    HB_CUDA(cudaMemcpy(dargs.p, args.data(), args.size() * sizeof(ElemArgs<T>), cudaMemcpyHostToDevice));
+    int max_blocks = 1;
+    if (smem <= 113 * 1024 && sizeof(T) == 4) max_blocks = 2;
+    b->grid = p0->sm_count * max_blocks;
+    b->smem = smem;
+    const int64_t l0 = p0->launches;
+    HB_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+    hb_status st = HB_OK;
+    for (size_t q = 0; q < b->probs.size() && st == HB_OK; ++q) {
+        hb_problem *p = b->probs[q];
+        if (cudaMemsetAsync(b->out[q], 0, size_t(p->n_nodes) * 4 * p->N * sizeof(T), s) != cudaSuccess)
+            st = fail(HB_ERR_CUDA, "memset in batch capture");
+    }
+    if (st == HB_OK && cudaMemsetAsync(b->counter.p, 0, sizeof(int), s) != cudaSuccess)
+        st = fail(HB_ERR_CUDA, "memset in batch capture");
+    if (st == HB_OK) {
+        launch_batch_elem<T>(b->mode, dargs.p, b->first_item.p, int(b->probs.size()), b->n_items, b->counter.p,
+                             smem, b->grid, s);
+        p0->launches += 1;
+    }
+    for (size_t q = 0; q < b->probs.size() && st == HB_OK; ++q) {
+        hb_problem *p = b->probs[q];
+        const T *y = static_cast<const T *>(b->y[q]);
+        const T *v = static_cast<const T *>(b->v[q]);
+        T *out = static_cast<T *>(b->out[q]);
+        if (b->mode != MODE_DIAG && p->n_nf > 0) {
+            FaceArgs<T> fa;
+            fa.n_faces = p->n_nf;
+            fa.fnodes = p->d_nf_nodes.p;
+            fa.foutlet = p->d_nf_out.p;
+            fa.flag = p->d_flag.p;
+            fa.y = y;
+            fa.v = v;
+            fa.out = out;
+            fa.N = p->N;
+            fa.rho = T(p->rho);
+            fa.beta = T(p->beta);
+            if constexpr (sizeof(T) == 4) {
+                fa.fgeo = p->d_nf_geo32.p;
+                fa.hbase = p->d_hbase32.p;
+                fa.R = p->d_R32.p;
+                fa.Q = p->d_Q32.p;
+            } else {
+                fa.fgeo = p->d_nf_geo64.p;
+                fa.hbase = p->d_hbase64.p;
+                fa.R = p->d_R64.p;
+                fa.Q = p->d_Q64.p;
+            }
+            if (p->has_res && cudaMemsetAsync(fa.Q, 0, size_t(p->n_out) * p->N * sizeof(T), s) != cudaSuccess)
+                st = fail(HB_ERR_CUDA, "memset in batch capture");
+            launch_faces<T>(b->mode, fa, p->has_res, s);
+            p0->launches += p->has_res ? 2 : 1;
+        }
+        if (p->n_dir > 0) {
+            launch_dirichlet_rows<T>(b->mode, p->d_dir_nodes.p, p->n_dir, v, out, p->N, s);
+            p0->launches += 1;
+        }
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s, &graph);
+    if (st != HB_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e != cudaSuccess) return fail(HB_ERR_CUDA, std::string("batch capture: ") + cudaGetErrorString(e));
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+    e = cudaGraphInstantiate(&b->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(HB_ERR_CUDA, std::string("batch graph instantiate: ") + cudaGetErrorString(e));
+    b->launches_per_replay = p0->launches - l0;
+    p0->launches = l0;
+    return HB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+hb_status hb_batch_create(hb_problem *const *problems, int count, int precision, hb_batch **out) {
+    if (!problems || count <= 0 || !out) return fail(HB_ERR_INVALID_ARG, "empty batch");
+    HB_TRY(check_precision(precision));
+    *out = nullptr;
+    const int dev = problems[0]->device;
+    for (int q = 0; q < count; ++q) {
+        if (!problems[q]) return fail(HB_ERR_INVALID_ARG, "null problem in batch");
+        if (problems[q]->device != dev) return fail(HB_ERR_INVALID_ARG, "batch problems must share one device");
+    }
+    HB_CUDA(cudaSetDevice(dev));
+    hb_batch *b = new hb_batch();
+    b->probs.assign(problems, problems + count);
+    b->precision = precision;
+    b->device = dev;
+    std::vector<int> first(size_t(count) + 1, 0);
+    for (int q = 0; q < count; ++q) {
+        hb_status st = prepare_bc(problems[q]);
+        if (st != HB_OK) {
+            delete b;
+            return st;
+        }
+        const int P = precision == 0 ? problems[q]->ps64.P : problems[q]->ps32.P;
+        first[size_t(q) + 1] = first[size_t(q)] + P;
+    }
+    b->n_items = first[size_t(count)];
+    hb_problem *p0 = problems[0];
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete b;
+        return fail(HB_ERR_CUDA, "cudaStreamCreate failed");
+    }
+    hb_status st = upload(p0, b->first_item, first);
+    if (st == HB_OK) st = dalloc(p0, b->counter, 1);
+    if (st != HB_OK) {
+        cudaStreamDestroy(b->stream);
+        delete b;
+        return st;
+    }
+    *out = b;
+    return HB_OK;
+}
+
+hb_status hb_batch_destroy(hb_batch *b) {
+    if (!b) return HB_OK;
+    cudaSetDevice(b->device);
+    cudaStreamSynchronize(b->stream);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    cudaStream_t s = b->stream;
+    delete b;
+    cudaStreamDestroy(s);
+    return HB_OK;
+}
+
+hb_status hb_batch_jv_dev(hb_batch *b, const void *const *y, const void *const *v, void *const *jv, int kind,
+                          double shift, void *stream) {
+    if (!b || !y || !v || !jv) return fail(HB_ERR_INVALID_ARG, "null argument");
+    if (kind != 0 && kind != 1) return fail(HB_ERR_INVALID_ARG, "kind must be 0 (paper tangent) or 1 (exact)");
+    HB_CUDA(cudaSetDevice(b->device));
+    const size_t n = b->probs.size();
+    const int mode = kind == 0 ? MODE_JVP : MODE_JVE;
+    bool same = b->exec && b->mode == mode && b->shift == shift && b->y.size() == n;
+    for (size_t q = 0; same && q < n; ++q) same = (b->y[q] == y[q] && b->v[q] == v[q] && b->out[q] == jv[q]);
+    for (size_t q = 0; q < n; ++q)
+        if (!y[q] || !v[q] || !jv[q] || jv[q] == y[q] || jv[q] == v[q])
+            return fail(HB_ERR_INVALID_ARG, "null or aliased operand in batch");
+    if (!same) {
+        b->mode = mode;
+        b->shift = shift;
+        b->y.assign(y, y + n);
+        b->v.assign(v, v + n);
+        b->out.assign(jv, jv + n);
+        if (b->precision == 0) HB_TRY(batch_record<double>(b));
+        else HB_TRY(batch_record<float>(b));
+    }
+    cudaStream_t user = stream ? static_cast<cudaStream_t>(stream) : b->probs[0]->stream;
+    cudaEvent_t ev;
+    HB_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    cudaEventRecord(ev, user);
+    cudaStreamWaitEvent(b->stream, ev, 0);
+    cudaError_t e = cudaGraphLaunch(b->exec, b->stream);
+    cudaEventRecord(ev, b->stream);
+    cudaStreamWaitEvent(user, ev, 0);
+    cudaEventDestroy(ev);
+    if (e != cudaSuccess) return fail(HB_ERR_CUDA, std::string("batch graph launch: ") + cudaGetErrorString(e));
+    b->launches += b->launches_per_replay;
+    return HB_OK;
+}
+
+int64_t hb_batch_launch_count(const hb_batch *b) { return b ? b->launches : 0; }
+
+// Autotuning of the patch node cap: rebuild the patches with each candidate, time `reps` paper-tangent
+// Jv applications (CUDA events around the element pass), keep the fastest.
+hb_status hb_tune_patches(hb_problem *p, int precision, const int *candidates, int n_cand, int reps, int *best_nl,
+                          double *best_ms) {
+    if (!p || !candidates || n_cand <= 0 || reps <= 0) return fail(HB_ERR_INVALID_ARG, "bad tuning arguments");
+    HB_TRY(check_precision(precision));
+    HB_CUDA(cudaSetDevice(p->device));
+    HB_TRY(prepare_bc(p));
+    const size_t nd = size_t(p->n_nodes) * 4 * p->N;
+    double best = INFINITY;
+    int bnl = 0;
+    const size_t ts = precision == 0 ? sizeof(double) : sizeof(float);
+    const size_t budget = precision == 0 ? 200 * 1024 : 110 * 1024;
+    HB_TRY(dalloc(p, p->w64a, nd));
+    HB_TRY(dalloc(p, p->w64b, nd));
+    HB_TRY(dalloc(p, p->w32a, nd));
+    HB_TRY(dalloc(p, p->w32b, nd));
+    HB_TRY(dalloc(p, p->w32c, nd));
+    HB_TRY(dalloc(p, p->kres, nd));
+    HB_CUDA(cudaMemsetAsync(p->w64a.p, 0, nd * sizeof(double), p->stream));
+    HB_CUDA(cudaMemsetAsync(p->w32a.p, 0, nd * sizeof(float), p->stream));
+    HB_CUDA(cudaMemsetAsync(p->w64b.p, 0, nd * sizeof(double), p->stream));
+    HB_CUDA(cudaMemsetAsync(p->w32c.p, 0, nd * sizeof(float), p->stream));
+    auto rebuild = [&](int nl) -> hb_status {
+        if (precision == 0) HB_TRY(make_patchset<double>(p, p->ps64, p->tets_morton, budget, nl));
+        else HB_TRY(make_patchset<float>(p, p->ps32, p->tets_morton, budget, nl));
+        p->bc_dirty = true;                       // Dirichlet lists follow the new patches
+        return prepare_bc(p);
+    };
+    for (int c = 0; c < n_cand; ++c) {
+        const int nl = candidates[c];
+        if (nl < 8 || size_t(nl) * 21 * p->N * ts > budget) continue;
+        HB_TRY(rebuild(nl));
+        double ms = 0;
+        const bool was = p->prof_on;
+        p->prof_on = true;
+        double tmp = 0;
+        int64_t cnt = 0;
+        HB_TRY(hb_profile_read(p, &tmp, &cnt));
+        for (int r = 0; r < reps + 1; ++r) {
+            if (precision == 0) HB_TRY(apply_op<double>(p, MODE_JVP, p->w64a.p, p->w64b.p, p->kres.p, 0.0, p->stream));
+            else HB_TRY(apply_op<float>(p, MODE_JVP, p->w32a.p, p->w32c.p, p->w32b.p, 0.0, p->stream));
+            if (r == 0) HB_TRY(hb_profile_read(p, &tmp, &cnt));   // drop the first (cold) launch
+        }
+        HB_TRY(hb_profile_read(p, &ms, &cnt));
+        p->prof_on = was;
+        ms /= double(std::max<int64_t>(1, cnt));
+        if (ms < best) {
+            best = ms;
+            bnl = nl;
+        }
+    }
+    if (bnl == 0) return fail(HB_ERR_INVALID_ARG, "no candidate fits the shared-memory budget");
+    HB_TRY(rebuild(bnl));
+    if (best_nl) *best_nl = bnl;
+    if (best_ms) *best_ms = best;
+    return HB_OK;
+}
+
 hb_status hb_get_info(hb_problem *p, hb_info *info) {
     if (!p || !info) return fail(HB_ERR_INVALID_ARG, "null argument");
     HB_TRY(prepare_bc(p));
@@ -1517,6 +1868,10 @@ hb_status hb_get_info(hb_problem *p, hb_info *info) {
     info->patch_elems_max32 = p->ps32.ep_max;
     info->device_bytes = p->dev_bytes;
     info->h_char = h_char(p);
+    info->u_ref = p->u_c;
+    double pr = 0;
+    for (double v : p->level) pr += v / double(std::max<size_t>(1, p->level.size()));
+    info->p_ref = pr;
     return HB_OK;
 }
 

@@ -404,137 +404,220 @@ __device__ __forceinline__ void circulant_row(const T *__restrict__ hcol, const 
     }
 }
 
+// Shared-memory pointers of one patch pass.
+template <typename T>
+struct PatchSmem {
+    T *H, *geom, *Y, *V, *HY, *HV, *T_;
+    int *node;
+    uint32_t *conn;
+};
+
+template <typename T, int MODE>
+__device__ __forceinline__ PatchSmem<T> patch_smem(unsigned char *smem, int N, int nl_max, int ep_max) {
+    const Layout L = make_layout(MODE, N, nl_max, ep_max, sizeof(T));
+    PatchSmem<T> m;
+    m.H = reinterpret_cast<T *>(smem + L.H);
+    m.geom = reinterpret_cast<T *>(smem + L.geom);
+    m.Y = reinterpret_cast<T *>(smem + L.Y);
+    m.V = reinterpret_cast<T *>(smem + L.V);
+    m.HY = reinterpret_cast<T *>(smem + L.HY);
+    m.HV = reinterpret_cast<T *>(smem + L.HV);
+    m.T_ = reinterpret_cast<T *>(smem + L.T);
+    m.node = reinterpret_cast<int *>(smem + L.node);
+    m.conn = reinterpret_cast<uint32_t *>(smem + L.conn);
+    return m;
+}
+
+// Stage H (fixed N: its first column; runtime N: the full matrix).
+template <typename T, int NT>
+__device__ __forceinline__ void stage_H(const ElemArgs<T> &a, T *sH, int N) {
+    if constexpr (NT > 0) {
+        for (int i = threadIdx.x; i < N; i += blockDim.x) sH[i] = a.H[i * N];
+    } else {
+        for (int i = threadIdx.x; i < N * N; i += blockDim.x) sH[i] = a.H[i];
+    }
+}
+
+// One patch: gather, Dirichlet masking, in-patch H products, element-instance work, H T flush.
+// Ends with a block barrier, so shared memory can be reused by the next patch.
+template <typename T, int MODE, int NT>
+__device__ __forceinline__ void patch_pass(const ElemArgs<T> &a, int p, const PatchSmem<T> &sm, T shift) {
+    const int N = NT > 0 ? NT : a.N, N4 = 4 * N, N3 = 3 * N;
+    T *sH = sm.H, *sGeom = sm.geom, *sY = sm.Y, *sV = sm.V, *sHY = sm.HY, *sHV = sm.HV, *sT = sm.T_;
+    int *sNode = sm.node;
+    uint32_t *sConn = sm.conn;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int e0 = a.pv.eptr[p], ne = a.pv.eptr[p + 1] - e0;
+    const int q0 = a.pv.nptr[p], nl = a.pv.nptr[p + 1] - q0;
+    for (int i = tid; i < nl; i += nt) sNode[i] = a.pv.nodes[q0 + i];
+    for (int i = tid; i < ne; i += nt) sConn[i] = a.pv.lconn[e0 + i];
+    {
+        const uint4 *src = reinterpret_cast<const uint4 *>(a.pv.geom + size_t(e0) * kGeomStride);
+        uint4 *dst = reinterpret_cast<uint4 *>(sGeom);
+        const int nvec = int(ne * kGeomStride * sizeof(T) / 16);
+        for (int i = tid; i < nvec; i += nt) dst[i] = src[i];
+    }
+    if constexpr (MODE == MODE_RES || MODE == MODE_JVE)
+        for (int i = tid; i < nl * N3; i += nt) sT[i] = T(0);
+    __syncthreads();
+
+    // gather the patch's node rows (4 N values per node) with asynchronous 16-byte copies, so every
+    // thread keeps all of its loads in flight
+    const int cpr = int(N4 * sizeof(T) / 16);
+    for (int i = tid; i < nl * cpr; i += nt) {
+        const int l = i / cpr, c = i - l * cpr;
+        const size_t gidx = size_t(sNode[l]) * cpr + c;
+        cp_async16(reinterpret_cast<uint4 *>(sY) + i, reinterpret_cast<const uint4 *>(a.y) + gidx);
+        if constexpr (MODE == MODE_JVP || MODE == MODE_JVE)
+            cp_async16(reinterpret_cast<uint4 *>(sV) + i, reinterpret_cast<const uint4 *>(a.v) + gidx);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    if constexpr (MODE == MODE_JVP || MODE == MODE_JVE) {
+        // Dirichlet velocity entries of the direction are not unknowns: treat them as 0 (only the
+        // patches touching a Dirichlet boundary have any)
+        const int d0 = a.pv.dptr[p], nd = a.pv.dptr[p + 1] - d0;
+        if (nd > 0) {
+            for (int i = tid; i < nd * N3; i += nt) {
+                const int k = i / N3, r = i - k * N3;
+                sV[int(a.pv.dloc[d0 + k]) * N4 + r] = T(0);
+            }
+            __syncthreads();
+        }
+    }
+    if constexpr (MODE != MODE_DIAG) {
+        // time coupling of the staged velocities: (H x)[l][i][n] = sum_k H[n][k] x[l][i][k] for
+        // x = u (RES, JVE) and x = v (JVP, JVE)
+        constexpr bool hy = (MODE == MODE_RES || MODE == MODE_JVE);
+        constexpr bool hv = (MODE == MODE_JVP || MODE == MODE_JVE);
+        constexpr int nsrc = (hy ? 1 : 0) + (hv ? 1 : 0);
+        if constexpr (NT > 0) {
+            const int rows = nl * 3;
+            for (int r = tid; r < nsrc * rows; r += nt) {
+                const int which = hy ? (r >= rows) : 1, rr = r - (r >= rows) * rows, l = rr / 3, f = rr - 3 * l;
+                const T *src = (which ? sV : sY) + l * N4 + f * N;
+                T *dst = (which ? sHV : sHY) + l * N3 + f * N;
+                circulant_row<T, NT>(sH, src, dst);
+            }
+        } else {
+            for (int i = tid; i < nl * N3; i += nt) {
+                const int l = i / N3, r = i - l * N3, f = r / N, n = r - f * N;
+                const T *h = sH + n * N;
+                if constexpr (hy) {
+                    const T *x = sY + l * N4 + f * N;
+                    T acc = 0;
+                    for (int k = 0; k < N; ++k) acc += h[k] * x[k];
+                    sHY[i] = acc;
+                }
+                if constexpr (hv) {
+                    const T *xv = sV + l * N4 + f * N;
+                    T acc2 = 0;
+                    for (int k = 0; k < N; ++k) acc2 += h[k] * xv[k];
+                    sHV[i] = acc2;
+                }
+            }
+        }
+        __syncthreads();
+    }
+
+    for (int i = tid; i < ne * N; i += nt) {
+        const int e = i / N, n = i - e * N;
+        element_instance<T, MODE, NT>(e, n, N, a.rho, a.mu, shift, sGeom, sConn, sY, sV, sHY, sHV, sNode,
+                                      a.out, sT);
+    }
+    __syncthreads();
+
+    // H T on the patch-assembled T rows (fixed N: in place, one row per thread)
+    if constexpr ((MODE == MODE_RES || MODE == MODE_JVE) && NT > 0) {
+        for (int r = tid; r < nl * 3; r += nt) {
+            T *row = sT + (r / 3) * N3 + (r % 3) * N;
+            circulant_row<T, NT>(sH, row, row);
+        }
+        __syncthreads();
+    }
+
+    // flush: out += H T on the velocity rows, once per local node
+    if constexpr (MODE == MODE_RES || MODE == MODE_JVE) {
+        for (int i = tid; i < nl * N3; i += nt) {
+            const int l = i / N3, r = i - l * N3;
+            T val;
+            if constexpr (NT > 0) {
+                val = sT[i];
+            } else {
+                const int f = r / N, n = r - f * N;
+                const T *h = sH + n * N;
+                const T *t = sT + l * N3 + f * N;
+                val = T(0);
+                for (int k = 0; k < N; ++k) val += h[k] * t[k];
+            }
+            atomicAdd(a.out + size_t(sNode[l]) * N4 + r, val);
+        }
+    }
+    __syncthreads();
+}
+
 template <typename T, int MODE, int NT>
 __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 2 : 1)) elem_kernel(ElemArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int N = NT > 0 ? NT : a.N, N4 = 4 * N, N3 = 3 * N;
-    const Layout L = make_layout(MODE, N, a.pv.nl_max, a.pv.ep_max, sizeof(T));
-    T *sH = reinterpret_cast<T *>(smem + L.H);       // full H (runtime N) or its first column (fixed N)
-    T *sGeom = reinterpret_cast<T *>(smem + L.geom);
-    T *sY = reinterpret_cast<T *>(smem + L.Y);
-    T *sV = reinterpret_cast<T *>(smem + L.V);
-    T *sHY = reinterpret_cast<T *>(smem + L.HY);
-    T *sHV = reinterpret_cast<T *>(smem + L.HV);
-    T *sT = reinterpret_cast<T *>(smem + L.T);
-    int *sNode = reinterpret_cast<int *>(smem + L.node);
-    uint32_t *sConn = reinterpret_cast<uint32_t *>(smem + L.conn);
-    const int tid = threadIdx.x, nt = blockDim.x;
+    const int N = NT > 0 ? NT : a.N;
+    const PatchSmem<T> sm = patch_smem<T, MODE>(smem, N, a.pv.nl_max, a.pv.ep_max);
     const T shift = a.shift_dev ? T(*a.shift_dev) : a.shift;
+    stage_H<T, NT>(a, sm.H, N);
+    for (int p = blockIdx.x; p < a.pv.n_patches; p += gridDim.x) patch_pass<T, MODE, NT>(a, p, sm, shift);
+}
 
-    if constexpr (NT > 0) {
-        for (int i = tid; i < N; i += nt) sH[i] = a.H[i * N];
-    } else {
-        for (int i = tid; i < N * N; i += nt) sH[i] = a.H[i];
-    }
-
-    for (int p = blockIdx.x; p < a.pv.n_patches; p += gridDim.x) {
-        const int e0 = a.pv.eptr[p], ne = a.pv.eptr[p + 1] - e0;
-        const int q0 = a.pv.nptr[p], nl = a.pv.nptr[p + 1] - q0;
-        for (int i = tid; i < nl; i += nt) sNode[i] = a.pv.nodes[q0 + i];
-        for (int i = tid; i < ne; i += nt) sConn[i] = a.pv.lconn[e0 + i];
-        {
-            const uint4 *src = reinterpret_cast<const uint4 *>(a.pv.geom + size_t(e0) * kGeomStride);
-            uint4 *dst = reinterpret_cast<uint4 *>(sGeom);
-            const int nvec = int(ne * kGeomStride * sizeof(T) / 16);
-            for (int i = tid; i < nvec; i += nt) dst[i] = src[i];
-        }
-        if constexpr (MODE == MODE_RES || MODE == MODE_JVE)
-            for (int i = tid; i < nl * N3; i += nt) sT[i] = T(0);
+// Persistent kernel over the patches of many problems: work items (problem, patch) are taken from a
+// global counter, so problems of uneven size share the SMs; each item runs the fixed-N pass of its
+// problem's instance count (9, 13, 21) or the generic one.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 2 : 1)) batch_elem_kernel(const ElemArgs<T> *__restrict__ args,
+                                                               const int *__restrict__ first_item, int n_prob,
+                                                               int n_items, int *counter) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_item;
+    int last = -1;
+    while (true) {
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
         __syncthreads();
-
-        // gather the patch's node rows (4 N values per node) with asynchronous 16-byte copies, so every
-        // thread keeps all of its loads in flight
-        const int cpr = int(N4 * sizeof(T) / 16);
-        for (int i = tid; i < nl * cpr; i += nt) {
-            const int l = i / cpr, c = i - l * cpr;
-            const size_t gidx = size_t(sNode[l]) * cpr + c;
-            cp_async16(reinterpret_cast<uint4 *>(sY) + i, reinterpret_cast<const uint4 *>(a.y) + gidx);
-            if constexpr (MODE == MODE_JVP || MODE == MODE_JVE)
-                cp_async16(reinterpret_cast<uint4 *>(sV) + i, reinterpret_cast<const uint4 *>(a.v) + gidx);
-        }
-        cp_async_wait_all();
+        const int item = s_item;
         __syncthreads();
-        if constexpr (MODE == MODE_JVP || MODE == MODE_JVE) {
-            // Dirichlet velocity entries of the direction are not unknowns: treat them as 0 (only the
-            // patches touching a Dirichlet boundary have any)
-            const int d0 = a.pv.dptr[p], nd = a.pv.dptr[p + 1] - d0;
-            if (nd > 0) {
-                for (int i = tid; i < nd * N3; i += nt) {
-                    const int k = i / N3, r = i - k * N3;
-                    sV[int(a.pv.dloc[d0 + k]) * N4 + r] = T(0);
-                }
-                __syncthreads();
+        if (item >= n_items) break;
+        int lo = 0, hi = n_prob - 1;               // problem owning this item: first_item[q] <= item
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (first_item[mid] <= item) lo = mid;
+            else hi = mid - 1;
+        }
+        const ElemArgs<T> &a = args[lo];
+        const int patch = item - first_item[lo];
+        const T shift = a.shift_dev ? T(*a.shift_dev) : a.shift;
+        switch (a.N) {
+            case 9: {
+                const PatchSmem<T> sm = patch_smem<T, MODE>(smem, 9, a.pv.nl_max, a.pv.ep_max);
+                if (lo != last) { stage_H<T, 9>(a, sm.H, 9); __syncthreads(); }
+                patch_pass<T, MODE, 9>(a, patch, sm, shift);
+                break;
+            }
+            case 13: {
+                const PatchSmem<T> sm = patch_smem<T, MODE>(smem, 13, a.pv.nl_max, a.pv.ep_max);
+                if (lo != last) { stage_H<T, 13>(a, sm.H, 13); __syncthreads(); }
+                patch_pass<T, MODE, 13>(a, patch, sm, shift);
+                break;
+            }
+            case 21: {
+                const PatchSmem<T> sm = patch_smem<T, MODE>(smem, 21, a.pv.nl_max, a.pv.ep_max);
+                if (lo != last) { stage_H<T, 21>(a, sm.H, 21); __syncthreads(); }
+                patch_pass<T, MODE, 21>(a, patch, sm, shift);
+                break;
+            }
+            default: {
+                const PatchSmem<T> sm = patch_smem<T, MODE>(smem, a.N, a.pv.nl_max, a.pv.ep_max);
+                if (lo != last) { stage_H<T, 0>(a, sm.H, a.N); __syncthreads(); }
+                patch_pass<T, MODE, 0>(a, patch, sm, shift);
+                break;
             }
         }
-        if constexpr (MODE != MODE_DIAG) {
-            // time coupling of the staged velocities: (H x)[l][i][n] = sum_k H[n][k] x[l][i][k] for
-            // x = u (RES, JVE) and x = v (JVP, JVE)
-            constexpr bool hy = (MODE == MODE_RES || MODE == MODE_JVE);
-            constexpr bool hv = (MODE == MODE_JVP || MODE == MODE_JVE);
-            constexpr int nsrc = (hy ? 1 : 0) + (hv ? 1 : 0);
-            if constexpr (NT > 0) {
-                const int rows = nl * 3;
-                for (int r = tid; r < nsrc * rows; r += nt) {
-                    const int which = hy ? (r >= rows) : 1, rr = r - (r >= rows) * rows, l = rr / 3, f = rr - 3 * l;
-                    const T *src = (which ? sV : sY) + l * N4 + f * N;
-                    T *dst = (which ? sHV : sHY) + l * N3 + f * N;
-                    circulant_row<T, NT>(sH, src, dst);
-                }
-            } else {
-                for (int i = tid; i < nl * N3; i += nt) {
-                    const int l = i / N3, r = i - l * N3, f = r / N, n = r - f * N;
-                    const T *h = sH + n * N;
-                    if constexpr (hy) {
-                        const T *x = sY + l * N4 + f * N;
-                        T acc = 0;
-                        for (int k = 0; k < N; ++k) acc += h[k] * x[k];
-                        sHY[i] = acc;
-                    }
-                    if constexpr (hv) {
-                        const T *xv = sV + l * N4 + f * N;
-                        T acc2 = 0;
-                        for (int k = 0; k < N; ++k) acc2 += h[k] * xv[k];
-                        sHV[i] = acc2;
-                    }
-                }
-            }
-            __syncthreads();
-        }
-
-        for (int i = tid; i < ne * N; i += nt) {
-            const int e = i / N, n = i - e * N;
-            element_instance<T, MODE, NT>(e, n, N, a.rho, a.mu, shift, sGeom, sConn, sY, sV, sHY, sHV, sNode,
-                                          a.out, sT);
-        }
-        __syncthreads();
-
-        // H T on the patch-assembled T rows (fixed N: in place, one row per thread)
-        if constexpr ((MODE == MODE_RES || MODE == MODE_JVE) && NT > 0) {
-            for (int r = tid; r < nl * 3; r += nt) {
-                T *row = sT + (r / 3) * N3 + (r % 3) * N;
-                circulant_row<T, NT>(sH, row, row);
-            }
-            __syncthreads();
-        }
-
-        // flush: out += H T on the velocity rows, once per local node
-        if constexpr (MODE == MODE_RES || MODE == MODE_JVE) {
-            for (int i = tid; i < nl * N3; i += nt) {
-                const int l = i / N3, r = i - l * N3;
-                T val;
-                if constexpr (NT > 0) {
-                    val = sT[i];
-                } else {
-                    const int f = r / N, n = r - f * N;
-                    const T *h = sH + n * N;
-                    const T *t = sT + l * N3 + f * N;
-                    val = T(0);
-                    for (int k = 0; k < N; ++k) val += h[k] * t[k];
-                }
-                atomicAdd(a.out + size_t(sNode[l]) * N4 + r, val);
-            }
-        }
-        __syncthreads();
+        last = lo;
     }
 }
 
@@ -825,6 +908,21 @@ void launch_elem(int mode, const ElemArgs<T> &a, int grid, cudaStream_t s) {
 }
 
 template <typename T>
+void launch_batch_elem(int mode, const ElemArgs<T> *args, const int *first_item, int n_prob, int n_items,
+                       int *counter, size_t smem, int grid, cudaStream_t s) {
+    auto go = [&](auto kern) {
+        if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        kern<<<grid, kBlock, smem, s>>>(args, first_item, n_prob, n_items, counter);
+    };
+    switch (mode) {
+        case MODE_RES: go(batch_elem_kernel<T, MODE_RES>); break;
+        case MODE_JVP: go(batch_elem_kernel<T, MODE_JVP>); break;
+        case MODE_JVE: go(batch_elem_kernel<T, MODE_JVE>); break;
+        default: go(batch_elem_kernel<T, MODE_DIAG>); break;
+    }
+}
+
+template <typename T>
 void launch_geom(const double *xyz, const int *tets, int n_tets, double nu, T *geom, cudaStream_t s) {
     if (n_tets > 0) geom_kernel<T><<<nblk(n_tets, 128), 128, 0, s>>>(xyz, tets, n_tets, nu, geom);
 }
@@ -888,6 +986,10 @@ void launch_harmonics(const double *in, double *out, int64_t rows, int N, int n_
 
 template void launch_elem<float>(int, const ElemArgs<float> &, int, cudaStream_t);
 template void launch_elem<double>(int, const ElemArgs<double> &, int, cudaStream_t);
+template void launch_batch_elem<float>(int, const ElemArgs<float> *, const int *, int, int, int *, size_t, int,
+                                       cudaStream_t);
+template void launch_batch_elem<double>(int, const ElemArgs<double> *, const int *, int, int, int *, size_t, int,
+                                        cudaStream_t);
 template void launch_geom<float>(const double *, const int *, int, double, float *, cudaStream_t);
 template void launch_geom<double>(const double *, const int *, int, double, double *, cudaStream_t);
 template void launch_faces<float>(int, const FaceArgs<float> &, bool, cudaStream_t);

@@ -5,6 +5,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 
 namespace hb {
 
@@ -89,6 +90,11 @@ void launch_elem(int mode, const ElemArgs<T> &a, int grid, cudaStream_t s);
 template <typename T>
 void launch_geom(const double *xyz, const int *tets_patch_order, int n_tets, double nu, T *geom,
                  cudaStream_t s);
+// persistent element pass over the patches of several problems (args on the device; first_item[q] is the
+// first work item of problem q; *counter must be 0 at launch)
+template <typename T>
+void launch_batch_elem(int mode, const ElemArgs<T> *args, const int *first_item, int n_prob, int n_items,
+                       int *counter, size_t smem, int grid, cudaStream_t s);
 template <typename T>
 void launch_faces(int mode, const FaceArgs<T> &a, bool has_resistance, cudaStream_t s);
 template <typename T>
@@ -132,5 +138,18 @@ void launch_combine(const double *V, int64_t ld, int k, const double *c, double 
                     cudaStream_t s);
 void launch_dot(const double *x, const double *y, int64_t n, double *partials, double *result,
                 cudaStream_t s);
+
+// Inputs of the learned warm start taken from a problem (host copies).
+constexpr int kLearnedFeatures = 32;  // per-node input features of the network
+struct LearnedInputs {
+    int64_t n_nodes = 0, n_tets = 0;
+    int n_h = 0;
+    std::vector<double> xyz;          // [n][3]
+    std::vector<int32_t> tets;        // [E][4]
+    std::vector<uint8_t> flags;       // bit 0 wall, bit 1 inflow, bit 2 outlet / traction cap
+    std::vector<double> profile;      // [n][3] inflow profile (0 off the inflow caps)
+    std::vector<double> wave;         // real series of the first inflow waveform [2 n_h + 1]
+    double u_ref = 1, p_ref = 0, rho = 1;
+};
 
 }  // namespace hb

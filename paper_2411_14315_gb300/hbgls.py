@@ -39,7 +39,7 @@ class hb_solve_opts(C.Structure):
                 ("gmres_rtol_pseudo", C.c_double), ("gmres_rtol_newton", C.c_double),
                 ("gmres_restart", C.c_int), ("max_gmres", C.c_int), ("max_steps", C.c_int),
                 ("dt_pseudo", C.c_double), ("cfl", C.c_double), ("use_learned", C.c_int),
-                ("verbose", C.c_int), ("ser", C.c_int), ("ser_max", C.c_double)]
+                ("verbose", C.c_int), ("ser", C.c_int), ("ser_max", C.c_double), ("r_ref", C.c_double)]
 
 
 class hb_report(C.Structure):
@@ -57,7 +57,8 @@ class hb_info(C.Structure):
                 ("n_dirichlet_nodes", C.c_int64), ("n_neumann_faces", C.c_int64), ("n_h", C.c_int),
                 ("N", C.c_int), ("n_patches32", C.c_int), ("n_patches64", C.c_int),
                 ("patch_nodes_max32", C.c_int), ("patch_elems_max32", C.c_int),
-                ("device_bytes", C.c_int64), ("h_char", C.c_double)]
+                ("device_bytes", C.c_int64), ("h_char", C.c_double), ("u_ref", C.c_double),
+                ("p_ref", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -93,7 +94,30 @@ SIGNATURES = {
     "hb_profile_elem": ([_P, C.c_int], C.c_int),
     "hb_profile_read": ([_P, C.POINTER(C.c_double), C.POINTER(C.c_int64)], C.c_int),
     "hb_jv_dev_noalloc": ([_P, _VP, _VP, _VP, C.c_int, C.c_int, C.c_double, _VP], C.c_int),
+    "hb_mpnn_create": ([C.c_void_p, C.c_int, C.POINTER(_P)], C.c_int),
+    "hb_mpnn_destroy": ([_P], C.c_int),
+    "hb_mpnn_num_params": ([_P], C.c_int64),
+    "hb_mpnn_get_params": ([_P, C.POINTER(C.c_float)], C.c_int),
+    "hb_mpnn_set_params": ([_P, C.POINTER(C.c_float)], C.c_int),
+    "hb_mpnn_loss_grad": ([_P, _P, _DP, C.POINTER(C.c_float), C.POINTER(C.c_float)], C.c_int),
+    "hb_mpnn_train_step": ([_P, _P, _DP, C.c_float, C.POINTER(C.c_float)], C.c_int),
+    "hb_mpnn_predict": ([_P, _P, _DP], C.c_int),
+    "hb_mpnn_graph": ([_P, _P, C.POINTER(C.c_float), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                       C.POINTER(C.c_float), C.POINTER(C.c_int64)], C.c_int),
+    "hb_mpnn_warm_start": ([_P, _P], C.c_int),
+    "hb_attach_learned": ([_P, _P], C.c_int),
+    "hb_batch_create": ([C.POINTER(_P), C.c_int, C.c_int, C.POINTER(_P)], C.c_int),
+    "hb_batch_destroy": ([_P], C.c_int),
+    "hb_batch_jv_dev": ([_P, C.POINTER(_VP), C.POINTER(_VP), C.POINTER(_VP), C.c_int, C.c_double, _VP], C.c_int),
+    "hb_batch_launch_count": ([_P], C.c_int64),
+    "hb_tune_patches": ([_P, C.c_int, C.POINTER(C.c_int), C.c_int, C.c_int, C.POINTER(C.c_int),
+                         C.POINTER(C.c_double)], C.c_int),
 }
+
+
+class hb_mpnn_config(C.Structure):
+    _fields_ = [("hidden", C.c_int), ("layers", C.c_int), ("n_h", C.c_int), ("seed", C.c_int),
+                ("p_scale", C.c_double)]
 
 _lib = None
 
@@ -161,6 +185,7 @@ class Problem:
         h = _P()
         _check(lib().hb_create(C.byref(m), rho, mu, T, n_h, device, _stream_handle(stream), C.byref(h)))
         self._h = h
+        self.rho, self.mu, self.T = float(rho), float(mu), float(T)
         self.n_nodes = int(self._xyz.shape[0])
         self.n_h = int(n_h)
         self.N = 2 * self.n_h + 1
@@ -305,6 +330,14 @@ class Problem:
     def launch_count(self) -> int:
         return int(lib().hb_launch_count(self._h))
 
+    def tune_patches(self, precision: int, candidates, reps: int = 5):
+        """Autotune the element patch node cap; returns (best cap, ms per element pass)."""
+        c = (C.c_int * len(candidates))(*[int(x) for x in candidates])
+        best = C.c_int()
+        ms = C.c_double()
+        _check(lib().hb_tune_patches(self._h, precision, c, len(candidates), reps, C.byref(best), C.byref(ms)))
+        return best.value, ms.value
+
     def profile_elem(self, enable: bool):
         _check(lib().hb_profile_elem(self._h, int(bool(enable))))
 
@@ -314,3 +347,111 @@ class Problem:
         n = C.c_int64()
         _check(lib().hb_profile_read(self._h, C.byref(ms), C.byref(n)))
         return ms.value, n.value
+
+
+class MPNN:
+    """Learned warm-start network (hb_mpnn_*): message passing over the mesh graph, BF16 weights."""
+
+    F_IN, F_E = 32, 4
+
+    def __init__(self, n_h: int, hidden: int = 64, layers: int = 3, seed: int = 0, device: int = 0,
+                 p_scale: float = 1.0):
+        cfg = hb_mpnn_config(hidden, layers, n_h, seed, p_scale)
+        h = _P()
+        _check(lib().hb_mpnn_create(C.cast(C.pointer(cfg), C.c_void_p), device, C.byref(h)))
+        self._h = h
+        self.n_h, self.hidden, self.layers = n_h, hidden, layers
+        self.f_out = 4 * (2 * n_h + 1)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().hb_mpnn_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def num_params(self) -> int:
+        return int(lib().hb_mpnn_num_params(self._h))
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.num_params, dtype=np.float32)
+        _check(lib().hb_mpnn_get_params(self._h, out.ctypes.data_as(C.POINTER(C.c_float))))
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _check(lib().hb_mpnn_set_params(self._h, p.ctypes.data_as(C.POINTER(C.c_float))))
+
+    def loss_grad(self, problem: "Problem", target, want_grad: bool = True):
+        t = _f64(target)
+        loss = C.c_float()
+        g = np.empty(self.num_params, dtype=np.float32) if want_grad else None
+        _check(lib().hb_mpnn_loss_grad(self._h, problem._h, _dptr(t), C.byref(loss),
+                                       g.ctypes.data_as(C.POINTER(C.c_float)) if want_grad else None))
+        return loss.value, g
+
+    def train_step(self, problem: "Problem", target, lr: float) -> float:
+        t = _f64(target)
+        loss = C.c_float()
+        _check(lib().hb_mpnn_train_step(self._h, problem._h, _dptr(t), lr, C.byref(loss)))
+        return loss.value
+
+    def predict(self, problem: "Problem") -> np.ndarray:
+        out = np.empty((problem.n_nodes, 4, 2 * self.n_h + 1))
+        _check(lib().hb_mpnn_predict(self._h, problem._h, _dptr(out)))
+        return out
+
+    def graph(self, problem: "Problem"):
+        ne = C.c_int64()
+        _check(lib().hb_mpnn_graph(self._h, problem._h, None, None, None, None, C.byref(ne)))
+        n = problem.n_nodes
+        x = np.empty((n, self.F_IN), dtype=np.float32)
+        src = np.empty(ne.value, dtype=np.int32)
+        dst = np.empty(ne.value, dtype=np.int32)
+        e = np.empty((ne.value, self.F_E), dtype=np.float32)
+        fp = C.POINTER(C.c_float)
+        ip = C.POINTER(C.c_int32)
+        _check(lib().hb_mpnn_graph(self._h, problem._h, x.ctypes.data_as(fp), src.ctypes.data_as(ip),
+                                   dst.ctypes.data_as(ip), e.ctypes.data_as(fp), C.byref(ne)))
+        return x, src, dst, e
+
+    def warm_start(self, problem: "Problem"):
+        _check(lib().hb_mpnn_warm_start(self._h, problem._h))
+
+    def attach(self, problem: "Problem"):
+        _check(lib().hb_attach_learned(problem._h, self._h))
+
+
+class Batch:
+    """Many problems whose operator is applied in one captured graph (hb_batch_*)."""
+
+    def __init__(self, problems, precision: int = FP32):
+        self.problems = list(problems)
+        arr = (_P * len(self.problems))(*[p._h for p in self.problems])
+        h = _P()
+        _check(lib().hb_batch_create(arr, len(self.problems), precision, C.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().hb_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def jv_dev(self, ys, vs, outs, kind: int, shift: float = 0.0, stream=None):
+        n = len(self.problems)
+        mk = lambda ts: (_VP * n)(*[t.data_ptr() for t in ts])  # noqa: E731
+        _check(lib().hb_batch_jv_dev(self._h, mk(ys), mk(vs), mk(outs), kind, shift, _stream_handle(stream)))
+
+    def launch_count(self) -> int:
+        return int(lib().hb_batch_launch_count(self._h))

@@ -227,12 +227,12 @@ def womersley_mesh(level: int = 1) -> Mesh:
     return pipe_mesh(1.0, 5.0, 5 * f, 3 * f, 6 * f, name=f"womersley_l{level}")
 
 
-def stenosed_tube(n_tets_target: int, seed: int) -> Mesh:
-    """Coronary-like tube: radius U(0.15, 0.25), length 12 radii, one cosine stenosis with a 30-70 %
-    diameter reduction."""
+def stenosed_tube(n_tets_target: int, seed: int, severity=(0.3, 0.7)) -> Mesh:
+    """Coronary-like tube: radius U(0.15, 0.25), length 12 radii, one cosine stenosis with a diameter
+    reduction drawn from U(severity) (default 30-70 %)."""
     rng = np.random.default_rng(seed)
     R = rng.uniform(0.15, 0.25)
-    sev = rng.uniform(0.3, 0.7)
+    sev = rng.uniform(*severity)
     L = 12.0 * R
     zc = L * rng.uniform(0.35, 0.6)
     ls = 2.0 * R * rng.uniform(1.0, 2.0)

@@ -93,11 +93,11 @@ def glenn_spec(n_tets=1_000_000, n_h=10, seed=2000) -> Spec:
     return s
 
 
-def coronary_spec(n_tets=300_000, n_h=10, seed=4000, reynolds=100.0) -> Spec:
+def coronary_spec(n_tets=300_000, n_h=10, seed=4000, reynolds=100.0, severity=(0.3, 0.7)) -> Spec:
     """Stenosed coronary-like tube (radius U(0.15, 0.25) cm, 30-70 % diameter reduction) in cgs units:
     rho 1.06, mu 0.04, T 0.8 s, parabolic inflow with 10 seeded harmonics at a mean Reynolds number of
     `reynolds`, outlet at a steady 70 mmHg (Sec. 3.3 stand-in)."""
-    m = I.stenosed_tube(n_tets, seed)
+    m = I.stenosed_tube(n_tets, seed, severity)
     rng = np.random.default_rng(seed + 7)
     R = float(np.max(np.linalg.norm(m.xyz[:, :2], axis=1)))
     nu = 0.04 / 1.06
@@ -112,3 +112,57 @@ def coronary_spec(n_tets=300_000, n_h=10, seed=4000, reynolds=100.0) -> Spec:
     s.outlets_p.append((2, pa, pb))
     del rng
     return s
+
+
+def vessel_spec(seed: int, n_h: int = 4, n_core: int = 5, n_rim: int = 3, n_axial: int = 6) -> Spec:
+    """Seeded vessel-like pipe (the learned warm start's training family): radius U(0.8, 1.2), length
+    U(4, 6) radii, a cosine narrowing of U(0, 25) % of the diameter, rho 1, mu 0.04, Womersley number
+    U(3, 5), mean Reynolds number U(50, 100), parabolic inflow times seeded harmonics, traction-free
+    outlet."""
+    rng = np.random.default_rng(seed)
+    R = rng.uniform(0.8, 1.2)
+    L = R * rng.uniform(4.0, 6.0)
+    sev = rng.uniform(0.0, 0.25)
+    zc = L * rng.uniform(0.35, 0.65)
+    ls = R * rng.uniform(0.8, 1.5)
+
+    def rfun(z):
+        if abs(z - zc) < ls:
+            return R * (1.0 - 0.5 * sev * (1.0 + math.cos(math.pi * (z - zc) / ls)))
+        return R
+
+    m = I.pipe_mesh(R, L, n_core, n_rim, n_axial, radius_fn=rfun, name=f"vessel_s{seed}")
+    nu = 0.04
+    alpha = rng.uniform(3.0, 5.0)
+    omega = alpha * alpha * nu / (R * R)
+    re = rng.uniform(50.0, 100.0)
+    u_mean = re * nu / (2.0 * R)
+    a, b = I.waveform_harmonics(n_h, u_mean * math.pi * R * R, seed + 1)
+    s = Spec(m, 1.0, 0.04, 2.0 * math.pi / omega, n_h, name=f"vessel_s{seed}")
+    s.inflows.append((1, None, a, b))
+    return s
+
+
+def batch_specs(n: int = 64, seed: int = 5000, lo: int = 20_000, hi: int = 400_000):
+    """Batch of vessels of uneven size and N: sizes log-uniform in [lo, hi] tetrahedra, families drawn
+    from {pipe (oscillatory pipe flow), T-junction (Glenn-like), stenosed tube (coronary-like)}, n_h drawn
+    from {4, 6, 10}."""
+    rng = np.random.default_rng(seed)
+    specs = []
+    for k in range(n):
+        size = int(math.exp(rng.uniform(math.log(lo), math.log(hi))))
+        fam = int(rng.integers(3))
+        n_h = int(rng.choice([4, 6, 10]))
+        s = seed + 100 + k
+        if fam == 0:
+            m = I.pipe_by_size(size, s)
+            nu = 0.04
+            a, b = I.waveform_harmonics(n_h, 2.0 * math.pi, s)
+            sp = Spec(m, 1.0, 0.04, 2.0 * math.pi / (16 * nu), n_h, name=f"pipe_{k}")
+            sp.inflows.append((1, None, a, b))
+        elif fam == 1:
+            sp = glenn_spec(n_tets=size, n_h=n_h, seed=s)
+        else:
+            sp = coronary_spec(n_tets=size, n_h=n_h, seed=s)
+        specs.append(sp)
+    return specs

@@ -1,0 +1,53 @@
+"""Batched operator application (one captured graph, one persistent element launch over many problems of
+different N) against per-problem calls, and patch autotuning."""
+import numpy as np
+import pytest
+
+from paper_2411_14315_gb300 import inputs as I
+from tests import problems as P
+
+pytestmark = pytest.mark.gpu
+
+
+def _problems():
+    specs = [P.box_spec(seed=71, n_h=4, n=(6, 4, 4)), P.box_spec(seed=72, n_h=6, n=(5, 4, 3)),
+             P.box_spec(seed=73, n_h=10, n=(7, 5, 4)), P.box_spec(seed=74, n_h=2, n=(4, 4, 4)),
+             P.womersley_spec()]
+    return specs, [P.gpu_problem(s) for s in specs]
+
+
+@pytest.mark.parametrize("precision,kind", [(1, 0), (1, 1), (0, 0)])
+def test_batch_matches_individual_calls(precision, kind):
+    torch = pytest.importorskip("torch")
+    from paper_2411_14315_gb300 import hbgls
+    specs, probs = _problems()
+    dt = torch.float64 if precision == 0 else torch.float32
+    ys = [torch.tensor(I.random_state(s.mesh.n_nodes, s.N, 80 + k), dtype=dt, device="cuda") for k, s in enumerate(specs)]
+    vs = [torch.tensor(I.random_state(s.mesh.n_nodes, s.N, 90 + k), dtype=dt, device="cuda") for k, s in enumerate(specs)]
+    outs = [torch.empty_like(y) for y in ys]
+    refs = [torch.empty_like(y) for y in ys]
+    s = torch.cuda.current_stream()
+    for p, y, v, r in zip(probs, ys, vs, refs):
+        p.jv_dev(y, v, r, kind, precision, 0.6, stream=s)
+    b = hbgls.Batch(probs, precision)
+    for _ in range(2):                      # second call replays the captured graph
+        b.jv_dev(ys, vs, outs, kind, 0.6, stream=s)
+    s.synchronize()
+    tol = 1e-12 if precision == 0 else 2e-6
+    for o, r in zip(outs, refs):
+        o, r = o.double().cpu().numpy(), r.double().cpu().numpy()
+        assert np.linalg.norm(o - r) <= tol * np.linalg.norm(r)
+    assert b.launch_count() > 0
+    b.close()
+
+
+def test_patch_autotuning_keeps_results():
+    spec = P.womersley_spec()
+    gp = P.gpu_problem(spec)
+    y = I.random_state(spec.mesh.n_nodes, spec.N, 5)
+    v = I.random_state(spec.mesh.n_nodes, spec.N, 6)
+    before = gp.jv(y, v, 1, 1, 0.2)
+    best, ms = gp.tune_patches(1, [16, 32, 48, 64, 96], reps=3)
+    assert best in (16, 32, 48, 64, 96) and ms > 0
+    after = gp.jv(y, v, 1, 1, 0.2)
+    assert np.linalg.norm(after - before) <= 2e-6 * np.linalg.norm(before)
