@@ -105,7 +105,8 @@ struct hb_problem {
     std::vector<int32_t> tets, faces, face_tag;
     std::vector<double> fnormal, farea;
     double vol_mean = 0, vol_min = 0;
-    PatchSetDev<float> ps32;
+    PatchSetDev<float> ps32;         // FP32 passes except the exact Jacobian's
+    PatchSetDev<float> ps32e;        // FP32 exact-Jacobian pass (smaller patches: more staged fields)
     PatchSetDev<double> ps64;
     DBuf<double> d_xyz;
     DBuf<int> d_tets_ord;
@@ -286,18 +287,27 @@ HostPatches build_patches(const std::vector<int32_t> &tets_ord, int64_t n_tets, 
     return hp;
 }
 
-int choose_nl(int N, size_t ts, size_t budget) {
-    const size_t per_node = size_t(in_fields(MODE_JVE) + out_fields(MODE_JVE)) * N * ts + 4;
-    const size_t per_elem = kGeomStride * ts + 4;
-    const size_t fixed = size_t(N) * N * ts + 256;
-    long nl = long((budget - fixed) / (per_node + 3 * per_elem));
-    return int(std::max(8L, std::min(128L, nl)));
+// Largest patch node cap whose shared-memory layout for `mode` fits `budget` bytes (3 elements per
+// node), and whose layout for every mode fits the per-block hardware limit.
+int choose_nl(int N, size_t ts, size_t budget, int mode) {
+    const size_t hw = 227 * 1024;
+    int nl = 8;
+    for (int c = 8; c <= 160; ++c) {
+        if (elem_smem_bytes(mode, N, c, 3 * c, ts) > budget) break;
+        bool ok = true;
+        for (int m = 0; m < 4; ++m) ok &= elem_smem_bytes(m, N, c, 3 * c, ts) <= hw;
+        if (!ok) break;
+        nl = c;
+    }
+    return nl;
 }
 
+// Patches sized so that `size_mode`'s shared-memory layout fits `budget` (two blocks per SM for FP32,
+// one for FP64), unless nl_override gives the node cap.
 template <typename T>
 hb_status make_patchset(hb_problem *p, PatchSetDev<T> &ps, const std::vector<int32_t> &tets_ord, size_t budget,
-                        int nl_override = 0) {
-    const int NL = nl_override > 0 ? std::min(nl_override, 255) : choose_nl(p->N, sizeof(T), budget);
+                        int nl_override = 0, int size_mode = MODE_JVP) {
+    const int NL = nl_override > 0 ? std::min(nl_override, 255) : choose_nl(p->N, sizeof(T), budget, size_mode);
     const int EP = 3 * NL;
     HostPatches hp = build_patches(tets_ord, p->n_tets, p->n_nodes, NL, EP, std::max(1, 31 / p->N));
     ps.P = int(hp.eptr.size()) - 1;
@@ -323,11 +333,11 @@ hb_status make_patchset(hb_problem *p, PatchSetDev<T> &ps, const std::vector<int
 }
 
 template <typename T>
-PatchSetDev<T> &patches(hb_problem *p);
+PatchSetDev<T> &patches(hb_problem *p, int mode = MODE_JVP);
 template <>
-PatchSetDev<float> &patches<float>(hb_problem *p) { return p->ps32; }
+PatchSetDev<float> &patches<float>(hb_problem *p, int mode) { return mode == MODE_JVE ? p->ps32e : p->ps32; }
 template <>
-PatchSetDev<double> &patches<double>(hb_problem *p) { return p->ps64; }
+PatchSetDev<double> &patches<double>(hb_problem *p, int) { return p->ps64; }
 
 template <typename T>
 const T *Hmat(hb_problem *p);
@@ -485,6 +495,7 @@ hb_status prepare_bc(hb_problem *p) {
     HB_TRY(upload(p, p->d_dir_prof, dir_prof));
     HB_TRY(upload(p, p->d_flag, flag));
     HB_TRY(dirichlet_lists(p, p->ps32, flag));
+    HB_TRY(dirichlet_lists(p, p->ps32e, flag));
     HB_TRY(dirichlet_lists(p, p->ps64, flag));
     HB_TRY(dalloc(p, p->d_g, size_t(std::max(1, p->n_dir * 3 * N))));
     launch_dirichlet_values(p->d_dir_nodes.p, p->d_dir_wave.p, p->d_dir_prof.p, p->n_dir, p->d_W.p, N, p->d_g.p,
@@ -552,7 +563,7 @@ template <typename T>
 hb_status apply_op(hb_problem *p, int mode, const T *y, const T *v, T *out, double shift, cudaStream_t s,
                    const double *shift_dev = nullptr) {
     HB_TRY(prepare_bc(p));
-    PatchSetDev<T> &ps = patches<T>(p);
+    PatchSetDev<T> &ps = patches<T>(p, mode);
     const int N = p->N;
     HB_CUDA(cudaMemsetAsync(out, 0, size_t(p->n_nodes) * 4 * N * sizeof(T), s));
     ElemArgs<T> ea;
@@ -942,7 +953,7 @@ hb_status noalloc_scratch(int device, void **ptr) {
 template <typename T>
 hb_status apply_jv_noalloc(hb_problem *p, int mode, const T *y, const T *v, T *out, double shift, cudaStream_t s,
                            T *qscratch) {
-    PatchSetDev<T> &ps = patches<T>(p);
+    PatchSetDev<T> &ps = patches<T>(p, mode);
     const int N = p->N;
     HB_CUDA(cudaMemsetAsync(out, 0, size_t(p->n_nodes) * 4 * N * sizeof(T), s));
     ElemArgs<T> ea;
@@ -1194,8 +1205,9 @@ hb_status hb_create(const hb_mesh *mesh, double rho, double mu, double period_T,
     }
     hb_status st;
     if ((st = upload(p, p->d_xyz, p->xyz)) != HB_OK) return bail(st);
-    if ((st = make_patchset<float>(p, p->ps32, tets_ord, 110 * 1024)) != HB_OK) return bail(st);
-    if ((st = make_patchset<double>(p, p->ps64, tets_ord, 200 * 1024)) != HB_OK) return bail(st);
+    if ((st = make_patchset<float>(p, p->ps32, tets_ord, 112 * 1024, 0, MODE_JVP)) != HB_OK) return bail(st);
+    if ((st = make_patchset<float>(p, p->ps32e, tets_ord, 112 * 1024, 0, MODE_JVE)) != HB_OK) return bail(st);
+    if ((st = make_patchset<double>(p, p->ps64, tets_ord, 200 * 1024, 0, MODE_JVE)) != HB_OK) return bail(st);
     // H = E^-1 Omega E in real closed form: (w/2) (-1)^(j-k) / sin(pi (j-k) / N), zero diagonal
     {
         const int N = p->N;
@@ -1605,7 +1617,7 @@ hb_status batch_record(hb_batch *b) {
     size_t smem = 0;
     for (size_t q = 0; q < b->probs.size(); ++q) {
         hb_problem *p = b->probs[q];
-        PatchSetDev<T> &ps = patches<T>(p);
+        PatchSetDev<T> &ps = patches<T>(p, b->mode);
         ElemArgs<T> &ea = args[q];
         ea.pv = ps.view();
         ea.y = static_cast<const T *>(b->y[q]);
@@ -1626,6 +1638,10 @@ hb_status batch_record(hb_batch *b) {
     }();
     HB_TRY(dalloc(p0, dargs, args.size()));
     HB_CUDA(cudaMemcpy(dargs.p, args.data(), args.size() * sizeof(ElemArgs<T>), cudaMemcpyHostToDevice));
+    std::vector<int> first(b->probs.size() + 1, 0);
+    for (size_t q = 0; q < b->probs.size(); ++q) first[q + 1] = first[q] + args[q].pv.n_patches;
+    b->n_items = first.back();
+    HB_TRY(upload(p0, b->first_item, first));
     int max_blocks = 1;
     if (smem <= 113 * 1024 && sizeof(T) == 4) max_blocks = 2;
     b->grid = p0->sm_count * max_blocks;
@@ -1718,24 +1734,19 @@ hb_status hb_batch_create(hb_problem *const *problems, int count, int precision,
     b->probs.assign(problems, problems + count);
     b->precision = precision;
     b->device = dev;
-    std::vector<int> first(size_t(count) + 1, 0);
     for (int q = 0; q < count; ++q) {
         hb_status st = prepare_bc(problems[q]);
         if (st != HB_OK) {
             delete b;
             return st;
         }
-        const int P = precision == 0 ? problems[q]->ps64.P : problems[q]->ps32.P;
-        first[size_t(q) + 1] = first[size_t(q)] + P;
     }
-    b->n_items = first[size_t(count)];
     hb_problem *p0 = problems[0];
     if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
         delete b;
         return fail(HB_ERR_CUDA, "cudaStreamCreate failed");
     }
-    hb_status st = upload(p0, b->first_item, first);
-    if (st == HB_OK) st = dalloc(p0, b->counter, 1);
+    hb_status st = dalloc(p0, b->counter, 1);
     if (st != HB_OK) {
         cudaStreamDestroy(b->stream);
         delete b;
@@ -1805,7 +1816,7 @@ hb_status hb_tune_patches(hb_problem *p, int precision, const int *candidates, i
     double best = INFINITY;
     int bnl = 0;
     const size_t ts = precision == 0 ? sizeof(double) : sizeof(float);
-    const size_t budget = precision == 0 ? 200 * 1024 : 110 * 1024;
+    const size_t budget = precision == 0 ? 200 * 1024 : 112 * 1024;
     HB_TRY(dalloc(p, p->w64a, nd));
     HB_TRY(dalloc(p, p->w64b, nd));
     HB_TRY(dalloc(p, p->w32a, nd));
@@ -1824,7 +1835,9 @@ hb_status hb_tune_patches(hb_problem *p, int precision, const int *candidates, i
     };
     for (int c = 0; c < n_cand; ++c) {
         const int nl = candidates[c];
-        if (nl < 8 || size_t(nl) * 21 * p->N * ts > budget) continue;
+        bool fits = nl >= 8 && nl <= 255;
+        for (int m = 0; m < 4 && fits; ++m) fits = elem_smem_bytes(m, p->N, nl, 3 * nl, ts) <= 227 * 1024;
+        if (!fits) continue;
         HB_TRY(rebuild(nl));
         double ms = 0;
         const bool was = p->prof_on;
