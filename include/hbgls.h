@@ -76,6 +76,10 @@ const char *hb_last_error(void);
  * with a wall keep u = 0; nodes shared by two inflow caps take the values of the cap set last (a
  * repeated call for the same tag replaces it in place).  Errors: INVALID_ARG (tag 0 or unknown). */
 hb_status hb_set_inflow(hb_problem *p, int tag, const double *profile, const double *a, const double *b);
+/* Dirichlet inflow on cap `tag` from general per-point data (Eq. upgh_def gives Fourier coefficients
+ * g*_m(x) per point): harmonics [n_nodes][3][2 n_h + 1] in the real layout (a0, a1, b1, ...), read at
+ * the cap's nodes.  Same precedence rules as hb_set_inflow. */
+hb_status hb_set_inflow_harmonics(hb_problem *p, int tag, const double *harmonics);
 /* Outlet at fixed pressure P(t) (Sec. 3 uses steady values): traction h = -P on cap `tag`. */
 hb_status hb_set_outlet_pressure(hb_problem *p, int tag, const double *a, const double *b);
 /* Resistance outlet -- an extension the paper leaves out of scope (Sec. 3 and Sec. 4):

@@ -194,6 +194,10 @@ class HBProblem:
     def set_inflow(self, tag: int, profile, a, b):
         self.inflow[int(tag)] = (np.asarray(profile, dtype=np.float64), np.asarray(a, float), np.asarray(b, float))
 
+    def set_inflow_harmonics(self, tag: int, harmonics):
+        """General Dirichlet data: per-point real harmonics [n_nodes, 3, 2 n_h + 1] (Eq. upgh_def)."""
+        self.inflow[int(tag)] = ("harmonics", np.asarray(harmonics, dtype=np.float64), None)
+
     def set_outlet_pressure(self, tag: int, a, b):
         self.outlet_p[int(tag)] = (np.asarray(a, float), np.asarray(b, float))
 
@@ -208,8 +212,11 @@ class HBProblem:
         g = np.zeros((self.n_nodes, 3, N))
         for tag, (prof, a, b) in self.inflow.items():
             nodes = np.unique(self.faces[self.face_tag == tag].ravel())
-            q = sample_waveform(a, b, N, self.T)
-            g[nodes] = prof[nodes][:, :, None] * q[None, None, :]
+            if isinstance(prof, str):
+                g[nodes] = harmonics_to_instances(a[nodes], N, self.T)
+            else:
+                q = sample_waveform(a, b, N, self.T)
+                g[nodes] = prof[nodes][:, :, None] * q[None, None, :]
             mask[nodes] = True
         wall = np.unique(self.faces[self.face_tag == 0].ravel())
         g[wall] = 0.0

@@ -77,8 +77,9 @@ struct PatchSetDev {
 
 struct Inflow {
     int tag;
-    std::vector<double> profile;   // [n_nodes][3] or empty = parabolic
-    std::vector<double> coef;      // real series (a0, a1, b1, ...)
+    std::vector<double> profile;   // [n_nodes][3] or empty = parabolic (separable data)
+    std::vector<double> coef;      // real series (a0, a1, b1, ...) of the waveform (separable data)
+    std::vector<double> harm;      // [n_nodes][3][2 n_h + 1] per-point harmonics (general data) or empty
 };
 
 struct Outlet {
@@ -120,7 +121,7 @@ struct hb_problem {
     bool has_res = false;
     double u_c = 0;
     std::vector<double> level;       // mean outlet pressure per instance
-    DBuf<int> d_dir_nodes, d_dir_wave, d_nf_nodes, d_nf_out;
+    DBuf<int> d_dir_nodes, d_nf_nodes, d_nf_out;
     DBuf<uint8_t> d_flag;
     DBuf<double> d_dir_prof, d_g, d_W, d_coef;
     DBuf<double> d_nf_geo64, d_hbase64, d_R64, d_Q64;
@@ -432,7 +433,12 @@ hb_status prepare_bc(hb_problem *p) {
         const Inflow &in = p->inflows[k];
         std::vector<double> pp;
         const std::vector<double> *src = &in.profile;
-        if (in.profile.empty()) {
+        if (!in.harm.empty()) {            // general data: its mean (a0) stands for the profile
+            pp.assign(size_t(3 * n), 0.0);
+            for (int64_t a = 0; a < n; ++a)
+                for (int i = 0; i < 3; ++i) pp[size_t(3 * a + i)] = in.harm[size_t((3 * a + i) * M)];
+            src = &pp;
+        } else if (in.profile.empty()) {
             parabolic_profile(p, in.tag, pp);
             src = &pp;
         }
@@ -450,14 +456,26 @@ hb_status prepare_bc(hb_problem *p) {
             for (int b = 0; b < 3; ++b) wave[size_t(p->faces[size_t(3 * f + b)])] = -1;
     p->h_prof = prof;
     p->h_wave = wave;
-    std::vector<int> dir_nodes, dir_wave;
-    std::vector<double> dir_prof;
+    // harmonics of the Dirichlet data per Dirichlet node [n_dir][3][M]: 0 on walls, profile x waveform
+    // series for separable inflows, the given per-point series otherwise
+    std::vector<int> dir_nodes, dir_index(size_t(n), -1);
+    std::vector<double> dir_harm;
     std::vector<uint8_t> flag(size_t(n), 0);
     for (int64_t a = 0; a < n; ++a) {
-        if (wave[size_t(a)] == -2) continue;
+        const int w = wave[size_t(a)];
+        if (w == -2) continue;
+        dir_index[size_t(a)] = int(dir_nodes.size());
         dir_nodes.push_back(int(a));
-        dir_wave.push_back(wave[size_t(a)] >= 0 ? wave[size_t(a)] : -1);
-        for (int i = 0; i < 3; ++i) dir_prof.push_back(wave[size_t(a)] >= 0 ? prof[size_t(3 * a + i)] : 0.0);
+        for (int i = 0; i < 3; ++i)
+            for (int m = 0; m < M; ++m) {
+                double c = 0.0;
+                if (w >= 0) {
+                    const Inflow &in = p->inflows[size_t(w)];
+                    c = in.harm.empty() ? prof[size_t(3 * a + i)] * in.coef[size_t(m)]
+                                        : in.harm[size_t((3 * a + i) * M + m)];
+                }
+                dir_harm.push_back(c);
+            }
         flag[size_t(a)] = 1;
     }
     // Neumann faces: every cap that is not an inflow (walls are Dirichlet)
@@ -491,15 +509,14 @@ hb_status prepare_bc(hb_problem *p) {
     launch_sample_waveforms(p->d_coef.p, n_wave, p->n_h, N, p->T, p->d_W.p, p->stream);
     HB_LAUNCHED(p, n_wave > 0 ? 1 : 0);
     HB_TRY(upload(p, p->d_dir_nodes, dir_nodes));
-    HB_TRY(upload(p, p->d_dir_wave, dir_wave));
-    HB_TRY(upload(p, p->d_dir_prof, dir_prof));
+    HB_TRY(upload(p, p->d_dir_prof, dir_harm));
     HB_TRY(upload(p, p->d_flag, flag));
     HB_TRY(dirichlet_lists(p, p->ps32, flag));
     HB_TRY(dirichlet_lists(p, p->ps32e, flag));
     HB_TRY(dirichlet_lists(p, p->ps64, flag));
     HB_TRY(dalloc(p, p->d_g, size_t(std::max(1, p->n_dir * 3 * N))));
-    launch_dirichlet_values(p->d_dir_nodes.p, p->d_dir_wave.p, p->d_dir_prof.p, p->n_dir, p->d_W.p, N, p->d_g.p,
-                            p->stream);
+    // Dirichlet values at the instances: synthesis of the series at t_n (Eqs. upgh_def, upghharm)
+    launch_harmonics(p->d_dir_prof.p, p->d_g.p, int64_t(p->n_dir) * 3, N, p->n_h, 1, p->T, p->stream);
     HB_LAUNCHED(p, p->n_dir > 0 ? 1 : 0);
     HB_TRY(upload(p, p->d_nf_nodes, nf_nodes));
     HB_TRY(upload(p, p->d_nf_out, nf_out));
@@ -531,10 +548,16 @@ hb_status prepare_bc(hb_problem *p) {
     HB_TRY(dalloc(p, p->d_Q64, size_t(std::max(1, p->n_out * N))));
     HB_TRY(dalloc(p, p->d_Q32, size_t(std::max(1, p->n_out * N))));
     // characteristic inlet velocity of the CFL rule: largest mean inflow speed over the instances
+    std::vector<double> g(size_t(p->n_dir) * 3 * N);
+    if (!g.empty()) {
+        HB_CUDA(cudaMemcpyAsync(g.data(), p->d_g.p, g.size() * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+        HB_CUDA(cudaStreamSynchronize(p->stream));
+    }
     p->u_c = 0;
     for (int k = 0; k < n_in; ++k) {
         const Inflow &in = p->inflows[size_t(k)];
-        double A = 0, fl = 0;
+        double A = 0;
+        std::vector<double> fl(size_t(N), 0.0);
         for (int64_t f = 0; f < p->n_faces; ++f) {
             if (p->face_tag[size_t(f)] != in.tag) continue;
             const double S = p->farea[size_t(f)];
@@ -542,14 +565,16 @@ hb_status prepare_bc(hb_problem *p) {
             for (int b = 0; b < 3; ++b) {
                 const int nd = p->faces[size_t(3 * f + b)];
                 if (wave[size_t(nd)] != k) continue;
-                double un = 0;
-                for (int i = 0; i < 3; ++i) un += prof[size_t(3 * nd + i)] * p->fnormal[size_t(3 * f + i)];
-                fl += S / 3.0 * std::fabs(un);
+                const int d = dir_index[size_t(nd)];
+                for (int t = 0; t < N; ++t) {
+                    double un = 0;
+                    for (int i = 0; i < 3; ++i) un += g[(size_t(d) * 3 + i) * N + t] * p->fnormal[size_t(3 * f + i)];
+                    fl[size_t(t)] += S / 3.0 * std::fabs(un);
+                }
             }
         }
-        double qmax = 0;
-        for (int t = 0; t < N; ++t) qmax = std::max(qmax, std::fabs(W[size_t(k * N + t)]));
-        if (A > 0) p->u_c = std::max(p->u_c, fl * qmax / A);
+        for (int t = 0; t < N; ++t)
+            if (A > 0) p->u_c = std::max(p->u_c, fl[size_t(t)] / A);
     }
     HB_CUDA(cudaStreamSynchronize(p->stream));
     p->bc_dirty = false;
@@ -619,7 +644,7 @@ hb_status apply_op(hb_problem *p, int mode, const T *y, const T *v, T *out, doub
             fa.Q = p->d_Q64.p;
         }
         if (p->has_res) HB_CUDA(cudaMemsetAsync(fa.Q, 0, size_t(p->n_out) * N * sizeof(T), s));
-        launch_faces<T>(mode, fa, p->has_res, s);
+        launch_faces<T>(mode, fa, p->has_res, p->n_out, s);
         HB_LAUNCHED(p, p->has_res ? 2 : 1);
     }
     if (p->n_dir > 0) {
@@ -994,7 +1019,7 @@ hb_status apply_jv_noalloc(hb_problem *p, int mode, const T *y, const T *v, T *o
         }
         fa.Q = qscratch;   // the shared array keeps the last call's values: clear it first
         if (p->has_res) HB_CUDA(cudaMemsetAsync(qscratch, 0, size_t(p->n_out) * N * sizeof(T), s));
-        launch_faces<T>(mode, fa, p->has_res, s);
+        launch_faces<T>(mode, fa, p->has_res, p->n_out, s);
         HB_LAUNCHED(p, p->has_res ? 2 : 1);
     }
     if (p->n_dir > 0) {
@@ -1263,6 +1288,28 @@ hb_status hb_set_inflow(hb_problem *p, int tag, const double *profile, const dou
     in.coef = real_series(a, b, p->n_h);
     for (auto &o : p->outlets)
         if (o.tag == tag) return fail(HB_ERR_INVALID_ARG, "tag already set as an outlet");
+    for (auto &x : p->inflows)
+        if (x.tag == tag) {
+            x = in;
+            p->bc_dirty = true;
+            return HB_OK;
+        }
+    p->inflows.push_back(in);
+    p->bc_dirty = true;
+    return HB_OK;
+}
+
+hb_status hb_set_inflow_harmonics(hb_problem *p, int tag, const double *harmonics) {
+    HB_TRY(check_tag(p, tag));
+    if (!harmonics) return fail(HB_ERR_INVALID_ARG, "null harmonics");
+    for (auto &o : p->outlets)
+        if (o.tag == tag) return fail(HB_ERR_INVALID_ARG, "tag already set as an outlet");
+    const int M = 2 * p->n_h + 1;
+    Inflow in;
+    in.tag = tag;
+    in.harm.assign(harmonics, harmonics + size_t(p->n_nodes) * 3 * M);
+    in.coef.assign(size_t(M), 0.0);
+    in.coef[0] = 1.0;
     for (auto &x : p->inflows)
         if (x.tag == tag) {
             x = in;
@@ -1691,7 +1738,7 @@ hb_status batch_record(hb_batch *b) {
             }
             if (p->has_res && cudaMemsetAsync(fa.Q, 0, size_t(p->n_out) * p->N * sizeof(T), s) != cudaSuccess)
                 st = fail(HB_ERR_CUDA, "memset in batch capture");
-            launch_faces<T>(b->mode, fa, p->has_res, s);
+            launch_faces<T>(b->mode, fa, p->has_res, p->n_out, s);
             p0->launches += p->has_res ? 2 : 1;
         }
         if (p->n_dir > 0) {

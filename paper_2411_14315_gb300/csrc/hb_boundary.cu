@@ -1,0 +1,273 @@
+// Boundary and time-series kernels of libhbgls: Neumann faces (traction and backflow stabilisation,
+// Sec. 2.3), resistance-outlet flow rates, Dirichlet rows, sampling of boundary waveforms at the
+// instances (Eqs. upgh_def, upghharm) and the real discrete Fourier transforms of the state
+// (Eq. upghdft; reconstruction of Sec. 3.2).
+#include "hb_internal.cuh"
+
+namespace hb {
+
+namespace {
+
+// ---------------------------------------------------------------------------------------------------
+// Neumann faces: -int N_A h n_i and backflow -int N_A (rho/2) beta |u.n|_- u_i (3 edge midpoints)
+
+// Outlet flow rates Q[o][n] = sum over the outlet's faces of (S/3) sum_b x_b . n: one block per
+// instance n; outlets are handled in groups of 8 with per-thread register sums, a warp-shuffle
+// reduction and one shared-memory add per warp and outlet; one store per (outlet, instance).
+template <typename T, int MODE>
+__global__ void outlet_flux_kernel(FaceArgs<T> a, int n_out) {
+    constexpr int G = 8;
+    __shared__ T acc[G];
+    const int n = blockIdx.x, N4 = 4 * a.N, lane = threadIdx.x & 31;
+    const T *x = (MODE == MODE_RES) ? a.y : a.v;
+    for (int o0 = 0; o0 < n_out; o0 += G) {
+        if (threadIdx.x < G) acc[threadIdx.x] = T(0);
+        __syncthreads();
+        T sum[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) sum[g] = T(0);
+        for (int f = threadIdx.x; f < a.n_faces; f += blockDim.x) {
+            const int o = a.foutlet[f] - o0;
+            if (o < 0 || o >= G) continue;
+            const T nx = a.fgeo[4 * f], ny = a.fgeo[4 * f + 1], nz = a.fgeo[4 * f + 2], S = a.fgeo[4 * f + 3];
+            T s = 0;
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                const int nd = a.fnodes[3 * f + b];
+                if (MODE != MODE_RES && (a.flag[nd] & 1)) continue;
+                const T *r = x + size_t(nd) * N4 + n;
+                s += r[0] * nx + r[a.N] * ny + r[2 * a.N] * nz;
+            }
+#pragma unroll
+            for (int g = 0; g < G; ++g)
+                if (g == o) sum[g] += s * S / T(3);
+        }
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            T v = sum[g];
+            for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+            if (lane == 0 && v != T(0)) atomicAdd(acc + g, v);
+        }
+        __syncthreads();
+        for (int g = threadIdx.x; g < G && o0 + g < n_out; g += blockDim.x) a.Q[(o0 + g) * a.N + n] = acc[g];
+        __syncthreads();
+    }
+}
+
+template <typename T, int MODE>
+__global__ void face_kernel(FaceArgs<T> a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n_faces * a.N) return;
+    const int N = a.N, N4 = 4 * N;
+    const int f = i / N, n = i - f * N;
+    const T nrm[3] = {a.fgeo[4 * f], a.fgeo[4 * f + 1], a.fgeo[4 * f + 2]};
+    const T S3 = a.fgeo[4 * f + 3] / T(3);
+    int nd[3];
+    T u[3][3], v[3][3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        nd[b] = a.fnodes[3 * f + b];
+        const T *r = a.y + size_t(nd[b]) * N4 + n;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) u[b][k] = r[k * N];
+        if (MODE != MODE_RES) {
+            const bool dir = a.flag[nd[b]] & 1;
+            const T *rv = a.v + size_t(nd[b]) * N4 + n;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) v[b][k] = dir ? T(0) : rv[k * N];
+        }
+    }
+    const int o = a.foutlet[f];
+    T h = 0;
+    if (o >= 0) {
+        if (MODE == MODE_RES) h = a.hbase[o * N + n] - a.R[o] * a.Q[o * N + n];
+        else h = -a.R[o] * a.Q[o * N + n];
+    }
+    T c[3][3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) c[b][k] = -S3 * h * nrm[k];
+    const T cb = -S3 * T(0.5) * (T(0.5) * a.rho * a.beta);
+    const int e0[3] = {0, 1, 0}, e1[3] = {1, 2, 2};
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        T um[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) um[k] = T(0.5) * (u[e0[m]][k] + u[e1[m]][k]);
+        const T s = um[0] * nrm[0] + um[1] * nrm[1] + um[2] * nrm[2];
+        const T sm = s < T(0) ? s : T(0);
+        T term[3];
+        if (MODE == MODE_RES) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) term[k] = sm * um[k];
+        } else {
+            T vm[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) vm[k] = T(0.5) * (v[e0[m]][k] + v[e1[m]][k]);
+            const T vn = (MODE == MODE_JVE && s < T(0)) ? vm[0] * nrm[0] + vm[1] * nrm[1] + vm[2] * nrm[2] : T(0);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) term[k] = sm * vm[k] + vn * um[k];
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            c[e0[m]][k] += cb * term[k];
+            c[e1[m]][k] += cb * term[k];
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) atomicAdd(a.out + size_t(nd[b]) * N4 + k * N + n, c[b][k]);
+}
+
+// Dirichlet velocity rows: 0 (residual), 1 (diagonal) or v (Jacobian: identity).  One warp per node;
+// its 3 N velocity values are contiguous.
+template <typename T, int MODE>
+__global__ void dirichlet_rows_kernel(const int *__restrict__ dir_nodes, int n_dir, const T *__restrict__ v,
+                                      T *__restrict__ out, int N) {
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (w >= n_dir) return;
+    const size_t base = size_t(dir_nodes[w]) * 4 * N;
+    for (int r = lane; r < 3 * N; r += 32) {
+        if (MODE == MODE_RES) out[base + r] = T(0);
+        else if (MODE == MODE_DIAG) out[base + r] = T(1);
+        else out[base + r] = v[base + r];
+    }
+}
+
+// ---------------------------------------------------------------------------------------------------
+// boundary-condition sampling and harmonic transforms (Eqs. upgh_def, upghdft)
+
+// angle 2 pi k n / N reduced exactly to [0, 2 pi) through (k n mod N)
+__device__ __forceinline__ void cos_sin_kn(int k, int n, int N, double &c, double &s) {
+    const int r = int((long long)k * n % N);
+    sincospi(2.0 * double(r) / double(N), &s, &c);
+}
+
+__global__ void sample_waveforms_kernel(const double *__restrict__ coef, int n_wave, int n_h, int N,
+                                        double *__restrict__ W) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_wave * N) return;
+    const int w = i / N, n = i - w * N;
+    const double *c = coef + size_t(w) * (2 * n_h + 1);
+    double q = c[0];
+    for (int k = 1; k <= n_h; ++k) {
+        double cs, sn;
+        cos_sin_kn(k, n, N, cs, sn);
+        q += c[2 * k - 1] * cs + c[2 * k] * sn;
+    }
+    W[i] = q;
+}
+
+__global__ void apply_dirichlet_kernel(const int *__restrict__ dir_nodes, int n_dir,
+                                       const double *__restrict__ g, double *__restrict__ y, int N) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_dir * 3 * N) return;
+    const int d = i / (3 * N), r = i - d * 3 * N;
+    y[size_t(dir_nodes[d]) * 4 * N + r] = g[i];
+}
+
+// inverse = 0: coef[row][m] from y[row][n] (a0, a_k = 2/N sum y cos, b_k = 2/N sum y sin)
+// inverse = 1: y[row][n] from coef[row][m]
+__global__ void harmonics_kernel(const double *__restrict__ in, double *__restrict__ out, int64_t rows,
+                                 int N, int n_h) {
+    const int M = 2 * n_h + 1;
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= rows * M) return;
+    const int64_t row = i / M;
+    const int m = int(i - row * M);
+    const double *y = in + row * N;
+    double acc = 0.0;
+    if (m == 0) {
+        for (int n = 0; n < N; ++n) acc += y[n];
+        acc /= double(N);
+    } else {
+        const int k = (m + 1) / 2;
+        const bool is_sin = (m % 2) == 0;
+        for (int n = 0; n < N; ++n) {
+            double cs, sn;
+            cos_sin_kn(k, n, N, cs, sn);
+            acc += y[n] * (is_sin ? sn : cs);
+        }
+        acc *= 2.0 / double(N);
+    }
+    out[i] = acc;
+}
+
+__global__ void synthesis_kernel(const double *__restrict__ coef, double *__restrict__ y, int64_t rows,
+                                 int N, int n_h) {
+    const int M = 2 * n_h + 1;
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= rows * N) return;
+    const int64_t row = i / N;
+    const int n = int(i - row * N);
+    const double *c = coef + row * M;
+    double acc = c[0];
+    for (int k = 1; k <= n_h; ++k) {
+        double cs, sn;
+        cos_sin_kn(k, n, N, cs, sn);
+        acc += c[2 * k - 1] * cs + c[2 * k] * sn;
+    }
+    y[i] = acc;
+}
+
+inline int nblk(int64_t n, int b) { return int((n + b - 1) / b); }
+
+}  // namespace
+
+template <typename T>
+void launch_faces(int mode, const FaceArgs<T> &a, bool has_resistance, int n_out, cudaStream_t s) {
+    const int64_t n = int64_t(a.n_faces) * a.N;
+    if (n == 0 || mode == MODE_DIAG) return;
+    const int g = nblk(n, 128);
+    if (mode == MODE_RES) {
+        if (has_resistance) outlet_flux_kernel<T, MODE_RES><<<a.N, 256, 0, s>>>(a, n_out);
+        face_kernel<T, MODE_RES><<<g, 128, 0, s>>>(a);
+    } else if (mode == MODE_JVP) {
+        if (has_resistance) outlet_flux_kernel<T, MODE_JVP><<<a.N, 256, 0, s>>>(a, n_out);
+        face_kernel<T, MODE_JVP><<<g, 128, 0, s>>>(a);
+    } else {
+        if (has_resistance) outlet_flux_kernel<T, MODE_JVE><<<a.N, 256, 0, s>>>(a, n_out);
+        face_kernel<T, MODE_JVE><<<g, 128, 0, s>>>(a);
+    }
+}
+
+template <typename T>
+void launch_dirichlet_rows(int mode, const int *dir_nodes, int n_dir, const T *v, T *out, int N,
+                           cudaStream_t s) {
+    if (n_dir == 0) return;
+    const int g = nblk(int64_t(n_dir) * 32, 256);
+    if (mode == MODE_RES) dirichlet_rows_kernel<T, MODE_RES><<<g, 256, 0, s>>>(dir_nodes, n_dir, v, out, N);
+    else if (mode == MODE_DIAG) dirichlet_rows_kernel<T, MODE_DIAG><<<g, 256, 0, s>>>(dir_nodes, n_dir, v, out, N);
+    else dirichlet_rows_kernel<T, MODE_JVP><<<g, 256, 0, s>>>(dir_nodes, n_dir, v, out, N);
+}
+
+void launch_sample_waveforms(const double *coef, int n_wave, int n_h, int N, double T, double *W,
+                             cudaStream_t s) {
+    (void)T;
+    if (n_wave > 0) sample_waveforms_kernel<<<nblk(int64_t(n_wave) * N, 128), 128, 0, s>>>(coef, n_wave, n_h, N, W);
+}
+
+void launch_apply_dirichlet(const int *dir_nodes, int n_dir, const double *g, double *y, int N,
+                            cudaStream_t s) {
+    if (n_dir > 0)
+        apply_dirichlet_kernel<<<nblk(int64_t(n_dir) * 3 * N, 256), 256, 0, s>>>(dir_nodes, n_dir, g, y, N);
+}
+
+void launch_harmonics(const double *in, double *out, int64_t rows, int N, int n_h, int inverse, double T,
+                      cudaStream_t s) {
+    (void)T;
+    if (rows == 0) return;
+    if (!inverse)
+        harmonics_kernel<<<nblk(rows * (2 * n_h + 1), 256), 256, 0, s>>>(in, out, rows, N, n_h);
+    else
+        synthesis_kernel<<<nblk(rows * N, 256), 256, 0, s>>>(in, out, rows, N, n_h);
+}
+
+template void launch_faces<float>(int, const FaceArgs<float> &, bool, int, cudaStream_t);
+template void launch_faces<double>(int, const FaceArgs<double> &, bool, int, cudaStream_t);
+template void launch_dirichlet_rows<float>(int, const int *, int, const float *, float *, int, cudaStream_t);
+template void launch_dirichlet_rows<double>(int, const int *, int, const double *, double *, int, cudaStream_t);
+
+}  // namespace hb

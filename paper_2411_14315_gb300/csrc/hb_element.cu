@@ -677,196 +677,6 @@ __global__ void geom_kernel(const double *__restrict__ xyz, const int *__restric
     g[15] = T(0);
 }
 
-// ---------------------------------------------------------------------------------------------------
-// Neumann faces: -int N_A h n_i and backflow -int N_A (rho/2) beta |u.n|_- u_i (3 edge midpoints)
-
-template <typename T, int MODE>
-__global__ void outlet_flux_kernel(FaceArgs<T> a) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.n_faces * a.N) return;
-    const int f = i / a.N, n = i - f * a.N;
-    const int o = a.foutlet[f];
-    if (o < 0) return;
-    const int N4 = 4 * a.N;
-    const T *x = (MODE == MODE_RES) ? a.y : a.v;
-    const T nx = a.fgeo[4 * f], ny = a.fgeo[4 * f + 1], nz = a.fgeo[4 * f + 2], S = a.fgeo[4 * f + 3];
-    T s = 0;
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-        const int nd = a.fnodes[3 * f + b];
-        if (MODE != MODE_RES && (a.flag[nd] & 1)) continue;
-        const T *r = x + size_t(nd) * N4 + n;
-        s += r[0] * nx + r[a.N] * ny + r[2 * a.N] * nz;
-    }
-    atomicAdd(a.Q + o * a.N + n, s * S / T(3));
-}
-
-template <typename T, int MODE>
-__global__ void face_kernel(FaceArgs<T> a) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.n_faces * a.N) return;
-    const int N = a.N, N4 = 4 * N;
-    const int f = i / N, n = i - f * N;
-    const T nrm[3] = {a.fgeo[4 * f], a.fgeo[4 * f + 1], a.fgeo[4 * f + 2]};
-    const T S3 = a.fgeo[4 * f + 3] / T(3);
-    int nd[3];
-    T u[3][3], v[3][3];
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-        nd[b] = a.fnodes[3 * f + b];
-        const T *r = a.y + size_t(nd[b]) * N4 + n;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) u[b][k] = r[k * N];
-        if (MODE != MODE_RES) {
-            const bool dir = a.flag[nd[b]] & 1;
-            const T *rv = a.v + size_t(nd[b]) * N4 + n;
-#pragma unroll
-            for (int k = 0; k < 3; ++k) v[b][k] = dir ? T(0) : rv[k * N];
-        }
-    }
-    const int o = a.foutlet[f];
-    T h = 0;
-    if (o >= 0) {
-        if (MODE == MODE_RES) h = a.hbase[o * N + n] - a.R[o] * a.Q[o * N + n];
-        else h = -a.R[o] * a.Q[o * N + n];
-    }
-    T c[3][3];
-#pragma unroll
-    for (int b = 0; b < 3; ++b)
-#pragma unroll
-        for (int k = 0; k < 3; ++k) c[b][k] = -S3 * h * nrm[k];
-    const T cb = -S3 * T(0.5) * (T(0.5) * a.rho * a.beta);
-    const int e0[3] = {0, 1, 0}, e1[3] = {1, 2, 2};
-#pragma unroll
-    for (int m = 0; m < 3; ++m) {
-        T um[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) um[k] = T(0.5) * (u[e0[m]][k] + u[e1[m]][k]);
-        const T s = um[0] * nrm[0] + um[1] * nrm[1] + um[2] * nrm[2];
-        const T sm = s < T(0) ? s : T(0);
-        T term[3];
-        if (MODE == MODE_RES) {
-#pragma unroll
-            for (int k = 0; k < 3; ++k) term[k] = sm * um[k];
-        } else {
-            T vm[3];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) vm[k] = T(0.5) * (v[e0[m]][k] + v[e1[m]][k]);
-            const T vn = (MODE == MODE_JVE && s < T(0)) ? vm[0] * nrm[0] + vm[1] * nrm[1] + vm[2] * nrm[2] : T(0);
-#pragma unroll
-            for (int k = 0; k < 3; ++k) term[k] = sm * vm[k] + vn * um[k];
-        }
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            c[e0[m]][k] += cb * term[k];
-            c[e1[m]][k] += cb * term[k];
-        }
-    }
-#pragma unroll
-    for (int b = 0; b < 3; ++b)
-#pragma unroll
-        for (int k = 0; k < 3; ++k) atomicAdd(a.out + size_t(nd[b]) * N4 + k * N + n, c[b][k]);
-}
-
-template <typename T, int MODE>
-__global__ void dirichlet_rows_kernel(const int *__restrict__ dir_nodes, int n_dir, const T *__restrict__ v,
-                                      T *__restrict__ out, int N) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_dir * 3 * N) return;
-    const int d = i / (3 * N), r = i - d * 3 * N;
-    const size_t idx = size_t(dir_nodes[d]) * 4 * N + r;
-    if (MODE == MODE_RES) out[idx] = T(0);
-    else if (MODE == MODE_DIAG) out[idx] = T(1);
-    else out[idx] = v[idx];
-}
-
-// ---------------------------------------------------------------------------------------------------
-// boundary-condition sampling and harmonic transforms (Eqs. upgh_def, upghdft)
-
-// angle 2 pi k n / N reduced exactly to [0, 2 pi) through (k n mod N)
-__device__ __forceinline__ void cos_sin_kn(int k, int n, int N, double &c, double &s) {
-    const int r = int((long long)k * n % N);
-    sincospi(2.0 * double(r) / double(N), &s, &c);
-}
-
-__global__ void sample_waveforms_kernel(const double *__restrict__ coef, int n_wave, int n_h, int N,
-                                        double *__restrict__ W) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_wave * N) return;
-    const int w = i / N, n = i - w * N;
-    const double *c = coef + size_t(w) * (2 * n_h + 1);
-    double q = c[0];
-    for (int k = 1; k <= n_h; ++k) {
-        double cs, sn;
-        cos_sin_kn(k, n, N, cs, sn);
-        q += c[2 * k - 1] * cs + c[2 * k] * sn;
-    }
-    W[i] = q;
-}
-
-__global__ void dirichlet_values_kernel(const int *__restrict__ dir_nodes, const int *__restrict__ dir_wave,
-                                        const double *__restrict__ prof, int n_dir,
-                                        const double *__restrict__ W, int N, double *__restrict__ g) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_dir * 3 * N) return;
-    const int d = i / (3 * N), r = i - d * 3 * N, k = r / N, n = r - k * N;
-    const int wv = dir_wave[d];
-    g[i] = wv < 0 ? 0.0 : prof[3 * d + k] * W[wv * N + n];
-    (void)dir_nodes;
-}
-
-__global__ void apply_dirichlet_kernel(const int *__restrict__ dir_nodes, int n_dir,
-                                       const double *__restrict__ g, double *__restrict__ y, int N) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_dir * 3 * N) return;
-    const int d = i / (3 * N), r = i - d * 3 * N;
-    y[size_t(dir_nodes[d]) * 4 * N + r] = g[i];
-}
-
-// inverse = 0: coef[row][m] from y[row][n] (a0, a_k = 2/N sum y cos, b_k = 2/N sum y sin)
-// inverse = 1: y[row][n] from coef[row][m]
-__global__ void harmonics_kernel(const double *__restrict__ in, double *__restrict__ out, int64_t rows,
-                                 int N, int n_h) {
-    const int M = 2 * n_h + 1;
-    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i >= rows * M) return;
-    const int64_t row = i / M;
-    const int m = int(i - row * M);
-    const double *y = in + row * N;
-    double acc = 0.0;
-    if (m == 0) {
-        for (int n = 0; n < N; ++n) acc += y[n];
-        acc /= double(N);
-    } else {
-        const int k = (m + 1) / 2;
-        const bool is_sin = (m % 2) == 0;
-        for (int n = 0; n < N; ++n) {
-            double cs, sn;
-            cos_sin_kn(k, n, N, cs, sn);
-            acc += y[n] * (is_sin ? sn : cs);
-        }
-        acc *= 2.0 / double(N);
-    }
-    out[i] = acc;
-}
-
-__global__ void synthesis_kernel(const double *__restrict__ coef, double *__restrict__ y, int64_t rows,
-                                 int N, int n_h) {
-    const int M = 2 * n_h + 1;
-    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i >= rows * N) return;
-    const int64_t row = i / N;
-    const int n = int(i - row * N);
-    const double *c = coef + row * M;
-    double acc = c[0];
-    for (int k = 1; k <= n_h; ++k) {
-        double cs, sn;
-        cos_sin_kn(k, n, N, cs, sn);
-        acc += c[2 * k - 1] * cs + c[2 * k] * sn;
-    }
-    y[i] = acc;
-}
-
 inline int nblk(int64_t n, int b) { return int((n + b - 1) / b); }
 
 }  // namespace
@@ -927,63 +737,6 @@ void launch_geom(const double *xyz, const int *tets, int n_tets, double nu, T *g
     if (n_tets > 0) geom_kernel<T><<<nblk(n_tets, 128), 128, 0, s>>>(xyz, tets, n_tets, nu, geom);
 }
 
-template <typename T>
-void launch_faces(int mode, const FaceArgs<T> &a, bool has_resistance, cudaStream_t s) {
-    const int64_t n = int64_t(a.n_faces) * a.N;
-    if (n == 0 || mode == MODE_DIAG) return;
-    const int g = nblk(n, 128);
-    if (mode == MODE_RES) {
-        if (has_resistance) outlet_flux_kernel<T, MODE_RES><<<g, 128, 0, s>>>(a);
-        face_kernel<T, MODE_RES><<<g, 128, 0, s>>>(a);
-    } else if (mode == MODE_JVP) {
-        if (has_resistance) outlet_flux_kernel<T, MODE_JVP><<<g, 128, 0, s>>>(a);
-        face_kernel<T, MODE_JVP><<<g, 128, 0, s>>>(a);
-    } else {
-        if (has_resistance) outlet_flux_kernel<T, MODE_JVE><<<g, 128, 0, s>>>(a);
-        face_kernel<T, MODE_JVE><<<g, 128, 0, s>>>(a);
-    }
-}
-
-template <typename T>
-void launch_dirichlet_rows(int mode, const int *dir_nodes, int n_dir, const T *v, T *out, int N,
-                           cudaStream_t s) {
-    const int64_t n = int64_t(n_dir) * 3 * N;
-    if (n == 0) return;
-    const int g = nblk(n, 256);
-    if (mode == MODE_RES) dirichlet_rows_kernel<T, MODE_RES><<<g, 256, 0, s>>>(dir_nodes, n_dir, v, out, N);
-    else if (mode == MODE_DIAG) dirichlet_rows_kernel<T, MODE_DIAG><<<g, 256, 0, s>>>(dir_nodes, n_dir, v, out, N);
-    else dirichlet_rows_kernel<T, MODE_JVP><<<g, 256, 0, s>>>(dir_nodes, n_dir, v, out, N);
-}
-
-void launch_sample_waveforms(const double *coef, int n_wave, int n_h, int N, double T, double *W,
-                             cudaStream_t s) {
-    (void)T;
-    if (n_wave > 0) sample_waveforms_kernel<<<nblk(int64_t(n_wave) * N, 128), 128, 0, s>>>(coef, n_wave, n_h, N, W);
-}
-
-void launch_dirichlet_values(const int *dir_nodes, const int *dir_wave, const double *dir_profile,
-                             int n_dir, const double *W, int N, double *g, cudaStream_t s) {
-    if (n_dir > 0)
-        dirichlet_values_kernel<<<nblk(int64_t(n_dir) * 3 * N, 256), 256, 0, s>>>(dir_nodes, dir_wave, dir_profile,
-                                                                                n_dir, W, N, g);
-}
-
-void launch_apply_dirichlet(const int *dir_nodes, int n_dir, const double *g, double *y, int N,
-                            cudaStream_t s) {
-    if (n_dir > 0)
-        apply_dirichlet_kernel<<<nblk(int64_t(n_dir) * 3 * N, 256), 256, 0, s>>>(dir_nodes, n_dir, g, y, N);
-}
-
-void launch_harmonics(const double *in, double *out, int64_t rows, int N, int n_h, int inverse, double T,
-                      cudaStream_t s) {
-    (void)T;
-    if (rows == 0) return;
-    if (!inverse)
-        harmonics_kernel<<<nblk(rows * (2 * n_h + 1), 256), 256, 0, s>>>(in, out, rows, N, n_h);
-    else
-        synthesis_kernel<<<nblk(rows * N, 256), 256, 0, s>>>(in, out, rows, N, n_h);
-}
-
 template void launch_elem<float>(int, const ElemArgs<float> &, int, cudaStream_t);
 template void launch_elem<double>(int, const ElemArgs<double> &, int, cudaStream_t);
 template void launch_batch_elem<float>(int, const ElemArgs<float> *, const int *, int, int, int *, size_t, int,
@@ -992,9 +745,5 @@ template void launch_batch_elem<double>(int, const ElemArgs<double> *, const int
                                         cudaStream_t);
 template void launch_geom<float>(const double *, const int *, int, double, float *, cudaStream_t);
 template void launch_geom<double>(const double *, const int *, int, double, double *, cudaStream_t);
-template void launch_faces<float>(int, const FaceArgs<float> &, bool, cudaStream_t);
-template void launch_faces<double>(int, const FaceArgs<double> &, bool, cudaStream_t);
-template void launch_dirichlet_rows<float>(int, const int *, int, const float *, float *, int, cudaStream_t);
-template void launch_dirichlet_rows<double>(int, const int *, int, const double *, double *, int, cudaStream_t);
 
 }  // namespace hb

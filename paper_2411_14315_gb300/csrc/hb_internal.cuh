@@ -95,8 +95,9 @@ void launch_geom(const double *xyz, const int *tets_patch_order, int n_tets, dou
 template <typename T>
 void launch_batch_elem(int mode, const ElemArgs<T> *args, const int *first_item, int n_prob, int n_items,
                        int *counter, size_t smem, int grid, cudaStream_t s);
+// outlet flow rates (resistance outlets only; Q is fully written, no clearing needed) then face terms
 template <typename T>
-void launch_faces(int mode, const FaceArgs<T> &a, bool has_resistance, cudaStream_t s);
+void launch_faces(int mode, const FaceArgs<T> &a, bool has_resistance, int n_out, cudaStream_t s);
 template <typename T>
 void launch_dirichlet_rows(int mode, const int *dir_nodes, int n_dir, const T *v, T *out, int N,
                            cudaStream_t s);
@@ -104,8 +105,6 @@ void launch_dirichlet_rows(int mode, const int *dir_nodes, int n_dir, const T *v
 // sampling of boundary waveforms (Eq. upgh_def at the instances of Eq. upghharm)
 void launch_sample_waveforms(const double *coef, int n_wave, int n_h, int N, double T, double *W,
                              cudaStream_t s);
-void launch_dirichlet_values(const int *dir_nodes, const int *dir_wave, const double *dir_profile,
-                             int n_dir, const double *W, int N, double *g, cudaStream_t s);
 void launch_apply_dirichlet(const int *dir_nodes, int n_dir, const double *g, double *y, int N,
                             cudaStream_t s);
 void launch_harmonics(const double *y, double *coef, int64_t rows, int N, int n_h, int inverse,

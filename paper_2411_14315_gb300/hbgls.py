@@ -75,6 +75,7 @@ SIGNATURES = {
     "hb_last_error": ([], C.c_char_p),
     "hb_set_inflow": ([_P, C.c_int, _DP, _DP, _DP], C.c_int),
     "hb_set_outlet_pressure": ([_P, C.c_int, _DP, _DP], C.c_int),
+    "hb_set_inflow_harmonics": ([_P, C.c_int, _DP], C.c_int),
     "hb_set_outlet_resistance": ([_P, C.c_int, C.c_double, _DP, _DP], C.c_int),
     "hb_set_backflow": ([_P, C.c_double], C.c_int),
     "hb_set_initial": ([_P, _DP], C.c_int),
@@ -203,6 +204,8 @@ class Problem:
         p.set_backflow(spec.beta)
         for tag, prof, a, b in spec.inflows:
             p.set_inflow(tag, prof, a, b)
+        for tag, harm in getattr(spec, "inflows_harm", []):
+            p.set_inflow_harmonics(tag, harm)
         for tag, a, b in spec.outlets_p:
             p.set_outlet_pressure(tag, a, b)
         for tag, R, a, b in spec.outlets_r:
@@ -238,6 +241,10 @@ class Problem:
         a, b = self._wave(a, b)
         prof = None if profile is None else _f64(profile, (self.n_nodes, 3))
         _check(lib().hb_set_inflow(self._h, tag, None if prof is None else _dptr(prof), _dptr(a), _dptr(b)))
+
+    def set_inflow_harmonics(self, tag: int, harmonics):
+        h = _f64(harmonics, (self.n_nodes, 3, 2 * self.n_h + 1))
+        _check(lib().hb_set_inflow_harmonics(self._h, tag, _dptr(h)))
 
     def set_outlet_pressure(self, tag: int, a, b):
         a, b = self._wave(a, b)

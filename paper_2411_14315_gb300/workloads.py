@@ -27,6 +27,7 @@ class Spec:
     outlets_r: list = dataclasses.field(default_factory=list)    # (tag, R, a, b)
     tags: np.ndarray | None = None                               # face tags override
     name: str = ""
+    inflows_harm: list = dataclasses.field(default_factory=list)  # (tag, per-node harmonics [n, 3, M])
 
     @property
     def N(self):

@@ -15,6 +15,8 @@ def oracle_problem(spec: Spec, convection: bool = True):
         if prof is None:
             prof = I.parabolic_profile(m, tag)
         pr.set_inflow(tag, prof, a, b)
+    for tag, harm in spec.inflows_harm:
+        pr.set_inflow_harmonics(tag, harm)
     for tag, a, b in spec.outlets_p:
         pr.set_outlet_pressure(tag, a, b)
     for tag, R, a, b in spec.outlets_r:
