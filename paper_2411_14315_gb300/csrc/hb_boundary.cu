@@ -11,26 +11,22 @@ namespace {
 // ---------------------------------------------------------------------------------------------------
 // Neumann faces: -int N_A h n_i and backflow -int N_A (rho/2) beta |u.n|_- u_i (3 edge midpoints)
 
-// Outlet flow rates Q[o][n] = sum over the outlet's faces of (S/3) sum_b x_b . n: one block per
-// instance n; outlets are handled in groups of 8 with per-thread register sums, a warp-shuffle
-// reduction and one shared-memory add per warp and outlet; one store per (outlet, instance).
+// Outlet flow rates Q[o][n] += sum over the outlet's faces of (S/3) sum_b x_b . n (Q cleared by the
+// caller).  Grid: (face chunks of 256) x (instances); one face per thread, outlets in groups of 8,
+// warp-shuffle and shared-memory reduction, one global atomic per block, outlet and instance.
 template <typename T, int MODE>
 __global__ void outlet_flux_kernel(FaceArgs<T> a, int n_out) {
     constexpr int G = 8;
     __shared__ T acc[G];
-    const int n = blockIdx.x, N4 = 4 * a.N, lane = threadIdx.x & 31;
+    const int n = blockIdx.y, N4 = 4 * a.N, lane = threadIdx.x & 31;
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
     const T *x = (MODE == MODE_RES) ? a.y : a.v;
-    for (int o0 = 0; o0 < n_out; o0 += G) {
-        if (threadIdx.x < G) acc[threadIdx.x] = T(0);
-        __syncthreads();
-        T sum[G];
-#pragma unroll
-        for (int g = 0; g < G; ++g) sum[g] = T(0);
-        for (int f = threadIdx.x; f < a.n_faces; f += blockDim.x) {
-            const int o = a.foutlet[f] - o0;
-            if (o < 0 || o >= G) continue;
+    int o = -1;
+    T s = 0;
+    if (f < a.n_faces) {
+        o = a.foutlet[f];
+        if (o >= 0) {
             const T nx = a.fgeo[4 * f], ny = a.fgeo[4 * f + 1], nz = a.fgeo[4 * f + 2], S = a.fgeo[4 * f + 3];
-            T s = 0;
 #pragma unroll
             for (int b = 0; b < 3; ++b) {
                 const int nd = a.fnodes[3 * f + b];
@@ -38,18 +34,21 @@ __global__ void outlet_flux_kernel(FaceArgs<T> a, int n_out) {
                 const T *r = x + size_t(nd) * N4 + n;
                 s += r[0] * nx + r[a.N] * ny + r[2 * a.N] * nz;
             }
-#pragma unroll
-            for (int g = 0; g < G; ++g)
-                if (g == o) sum[g] += s * S / T(3);
+            s *= S / T(3);
         }
+    }
+    for (int o0 = 0; o0 < n_out; o0 += G) {
+        if (threadIdx.x < G) acc[threadIdx.x] = T(0);
+        __syncthreads();
 #pragma unroll
         for (int g = 0; g < G; ++g) {
-            T v = sum[g];
+            T v = (o == o0 + g) ? s : T(0);
             for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
             if (lane == 0 && v != T(0)) atomicAdd(acc + g, v);
         }
         __syncthreads();
-        for (int g = threadIdx.x; g < G && o0 + g < n_out; g += blockDim.x) a.Q[(o0 + g) * a.N + n] = acc[g];
+        if (threadIdx.x < G && o0 + threadIdx.x < n_out && acc[threadIdx.x] != T(0))
+            atomicAdd(a.Q + (o0 + threadIdx.x) * a.N + n, acc[threadIdx.x]);
         __syncthreads();
     }
 }
@@ -222,13 +221,13 @@ void launch_faces(int mode, const FaceArgs<T> &a, bool has_resistance, int n_out
     if (n == 0 || mode == MODE_DIAG) return;
     const int g = nblk(n, 128);
     if (mode == MODE_RES) {
-        if (has_resistance) outlet_flux_kernel<T, MODE_RES><<<a.N, 256, 0, s>>>(a, n_out);
+        if (has_resistance) outlet_flux_kernel<T, MODE_RES><<<dim3(nblk(a.n_faces, 256), a.N), 256, 0, s>>>(a, n_out);
         face_kernel<T, MODE_RES><<<g, 128, 0, s>>>(a);
     } else if (mode == MODE_JVP) {
-        if (has_resistance) outlet_flux_kernel<T, MODE_JVP><<<a.N, 256, 0, s>>>(a, n_out);
+        if (has_resistance) outlet_flux_kernel<T, MODE_JVP><<<dim3(nblk(a.n_faces, 256), a.N), 256, 0, s>>>(a, n_out);
         face_kernel<T, MODE_JVP><<<g, 128, 0, s>>>(a);
     } else {
-        if (has_resistance) outlet_flux_kernel<T, MODE_JVE><<<a.N, 256, 0, s>>>(a, n_out);
+        if (has_resistance) outlet_flux_kernel<T, MODE_JVE><<<dim3(nblk(a.n_faces, 256), a.N), 256, 0, s>>>(a, n_out);
         face_kernel<T, MODE_JVE><<<g, 128, 0, s>>>(a);
     }
 }

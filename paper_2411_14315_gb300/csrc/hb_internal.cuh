@@ -95,7 +95,7 @@ void launch_geom(const double *xyz, const int *tets_patch_order, int n_tets, dou
 template <typename T>
 void launch_batch_elem(int mode, const ElemArgs<T> *args, const int *first_item, int n_prob, int n_items,
                        int *counter, size_t smem, int grid, cudaStream_t s);
-// outlet flow rates (resistance outlets only; Q is fully written, no clearing needed) then face terms
+// outlet flow rates (resistance outlets only; Q must be cleared before) then face terms
 template <typename T>
 void launch_faces(int mode, const FaceArgs<T> &a, bool has_resistance, int n_out, cudaStream_t s);
 template <typename T>
