@@ -432,6 +432,24 @@ def run_ours(args, dist: Dist, spec, config):
                 tot += e0.elapsed_time(e1)
             rates[name] = units / (tot / reps / 1e3)
         result["other_rates"] = rates
+        # element-pass time of each launch variant of the FP32 paper-tangent pass
+        var0 = prob.launch_variant()
+        var_ms = {}
+        for var in range(3):
+            prob.set_launch_variant(var)
+            jv()
+            torch.cuda.synchronize()
+            prob.profile_read()
+            prob.profile_elem(True)
+            for i in range(20):
+                flush.fill_(float(i))
+                jv()
+            torch.cuda.synchronize()
+            prob.profile_elem(False)
+            t, c = prob.profile_read()
+            var_ms[str(var)] = t / max(1, c)
+        prob.set_launch_variant(var0)
+        result["jvp_variant_elem_ms"] = var_ms
 
     if dist.rank == 0 and dist.world == 1:
         if not args.skip_batch:

@@ -219,11 +219,12 @@ hb_status hb_mpnn_warm_start(hb_mpnn *net, hb_problem *p);
 /* Attach a network (not owned) so that hb_solve with use_learned = 1 starts from its prediction. */
 hb_status hb_attach_learned(hb_problem *p, hb_mpnn *net);
 
-/* ---- batches of problems (many vessels of uneven size and N in one launch) --------------------------
+/* ---- batches of problems (many vessels of uneven size and N in one graph) ---------------------------
  * A batch applies the operator of every member problem in one captured CUDA graph: the output
- * clearing, one persistent element pass whose work items (problem, patch) are taken from a global
- * counter (so large and small problems share the SMs) and dispatched on each problem's N, then the
- * boundary terms and Dirichlet rows of each problem.  All problems must live on one device; their
+ * clearing, one persistent element pass per distinct instance count N (specialised for that N) whose
+ * work items (problem, patch) are taken from a global counter (so large and small problems share the
+ * SMs; the FP32 paper-tangent pass takes the first problem's launch variant, see hb_set_launch_variant),
+ * then the boundary terms and Dirichlet rows of each problem.  All problems must live on one device; their
  * boundary data are prepared at creation.  The graph is captured on first use and again whenever the
  * operands, kind or shift change.  Work is ordered after `stream` (NULL: the first problem's stream) and
  * `stream` waits for it. */
@@ -236,8 +237,9 @@ hb_status hb_batch_jv_dev(hb_batch *b, const void *const *y, const void *const *
                           double shift, void *stream);
 int64_t hb_batch_launch_count(const hb_batch *b);
 /* Patch-size autotuning: rebuild the problem's element patches (precision 0 or 1) with each candidate
- * node cap, time `reps` paper-tangent Jv element passes with CUDA events, and keep the fastest.  Returns
- * the chosen cap and its time per pass (ms). */
+ * node cap (and, for precision 1, each launch variant, see hb_set_launch_variant), time `reps`
+ * paper-tangent Jv element passes with CUDA events, and keep the fastest.  Returns the chosen cap and
+ * its time per pass (ms); the chosen variant is left set on the problem. */
 hb_status hb_tune_patches(hb_problem *p, int precision, const int *candidates, int n_cand, int reps,
                           int *best_nl, double *best_ms);
 
@@ -253,6 +255,13 @@ typedef struct {
 hb_status hb_get_info(hb_problem *p, hb_info *info);
 /* Number of kernel launches queued by this problem since creation (all entry points). */
 int64_t hb_launch_count(const hb_problem *p);
+/* Launch variant of the FP32 paper-tangent element pass (no counterpart in the paper; a tuning knob):
+ * 0 = 256 threads per block, two instances per thread on paired FP32 instructions; 1 = 384 threads,
+ * one instance per thread (the default); 2 = 512 threads, one instance per thread.  All give the same
+ * operator up to FP32 rounding.  hb_tune_patches also searches it for precision 1.  HB_ERR_INVALID_ARG
+ * for another value.  hb_get_launch_variant returns the current variant (-1 for a null problem). */
+hb_status hb_set_launch_variant(hb_problem *p, int variant);
+int hb_get_launch_variant(const hb_problem *p);
 /* Element-kernel timing: when enabled, every launch of the fused element kernel is bracketed by CUDA
  * events on the stream it is launched on.  hb_profile_read synchronises with those events, returns the
  * summed device time in milliseconds and the number of launches since the last read, and resets. */

@@ -65,13 +65,12 @@ struct DBuf {
 template <typename T>
 struct PatchSetDev {
     int P = 0, nl_max = 0, ep_max = 0;
-    DBuf<int> eptr, nptr, nodes, dptr;
+    DBuf<int> slots;                    // [P][slot_ints(nl_max)], see PatchView
     DBuf<uint32_t> lconn;
-    DBuf<uint8_t> dloc;
     DBuf<T> geom;
-    std::vector<int> h_nptr, h_nodes;   // host copies, to rebuild the Dirichlet lists
+    std::vector<int> h_eptr, h_nptr, h_nodes;   // host copies, to rebuild the slots' Dirichlet bits
     PatchView<T> view() const {
-        return PatchView<T>{P, nl_max, ep_max, eptr.p, nptr.p, nodes.p, lconn.p, geom.p, dptr.p, dloc.p};
+        return PatchView<T>{P, nl_max, ep_max, slot_ints(nl_max), slots.p, lconn.p, geom.p};
     }
 };
 
@@ -152,6 +151,7 @@ struct hb_problem {
     double shift_host = 0;
     // element-kernel timing
     bool prof_on = false;
+    int jvp_variant = 1;                  // launch variant of the FP32 paper-tangent pass
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev;
     size_t prof_used = 0;
 };
@@ -303,6 +303,30 @@ int choose_nl(int N, size_t ts, size_t budget, int mode) {
     return nl;
 }
 
+// Per-patch slots: first element, element count, node count, Dirichlet node count, then the patch's
+// node ids with bit 31 set on nodes whose velocity is prescribed (flag bit 0).
+template <typename T>
+hb_status upload_slots(hb_problem *p, PatchSetDev<T> &ps, const std::vector<uint8_t> *flag) {
+    const int S = slot_ints(ps.nl_max);
+    std::vector<int> sl(size_t(std::max(1, ps.P)) * size_t(S), 0);
+    for (int q = 0; q < ps.P; ++q) {
+        int *o = sl.data() + size_t(q) * size_t(S);
+        const int k0 = ps.h_nptr[size_t(q)], k1 = ps.h_nptr[size_t(q + 1)];
+        o[0] = ps.h_eptr[size_t(q)];
+        o[1] = ps.h_eptr[size_t(q + 1)] - o[0];
+        o[2] = k1 - k0;
+        int nd = 0;
+        for (int k = k0; k < k1; ++k) {
+            const int node = ps.h_nodes[size_t(k)];
+            const bool dir = flag && ((*flag)[size_t(node)] & 1);
+            nd += dir ? 1 : 0;
+            o[4 + (k - k0)] = dir ? int(uint32_t(node) | 0x80000000u) : node;
+        }
+        o[3] = nd;
+    }
+    return upload(p, ps.slots, sl);
+}
+
 // Patches sized so that `size_mode`'s shared-memory layout fits `budget` (two blocks per SM for FP32,
 // one for FP64), unless nl_override gives the node cap.
 template <typename T>
@@ -314,14 +338,11 @@ hb_status make_patchset(hb_problem *p, PatchSetDev<T> &ps, const std::vector<int
     ps.P = int(hp.eptr.size()) - 1;
     ps.nl_max = hp.nl_max;
     ps.ep_max = hp.ep_max;
-    HB_TRY(upload(p, ps.eptr, hp.eptr));
-    HB_TRY(upload(p, ps.nptr, hp.nptr));
-    HB_TRY(upload(p, ps.nodes, hp.nodes));
     HB_TRY(upload(p, ps.lconn, hp.lconn));
+    ps.h_eptr = hp.eptr;
     ps.h_nptr = hp.nptr;
     ps.h_nodes = hp.nodes;
-    HB_TRY(upload(p, ps.dptr, std::vector<int>(size_t(ps.P + 1), 0)));   // no Dirichlet nodes until set
-    HB_TRY(dalloc(p, ps.dloc, 1));
+    HB_TRY(upload_slots(p, ps, nullptr));         // no Dirichlet nodes until boundary data are set
     std::vector<int> tets_p(size_t(4 * p->n_tets));
     for (int64_t k = 0; k < p->n_tets; ++k)
         for (int a = 0; a < 4; ++a) tets_p[size_t(4 * k + a)] = tets_ord[size_t(4 * hp.perm[size_t(k)] + a)];
@@ -410,17 +431,7 @@ void parabolic_profile(const hb_problem *p, int tag, std::vector<double> &prof) 
 
 template <typename T>
 hb_status dirichlet_lists(hb_problem *p, PatchSetDev<T> &ps, const std::vector<uint8_t> &flag) {
-    std::vector<int> dptr(size_t(ps.P + 1), 0);
-    std::vector<uint8_t> dloc;
-    for (int q = 0; q < ps.P; ++q) {
-        for (int k = ps.h_nptr[size_t(q)]; k < ps.h_nptr[size_t(q + 1)]; ++k)
-            if (flag[size_t(ps.h_nodes[size_t(k)])] & 1) dloc.push_back(uint8_t(k - ps.h_nptr[size_t(q)]));
-        dptr[size_t(q + 1)] = int(dloc.size());
-    }
-    if (dloc.empty()) dloc.push_back(0);
-    HB_TRY(upload(p, ps.dptr, dptr));
-    HB_TRY(upload(p, ps.dloc, dloc));
-    return HB_OK;
+    return upload_slots(p, ps, &flag);
 }
 
 hb_status prepare_bc(hb_problem *p) {
@@ -603,6 +614,7 @@ hb_status apply_op(hb_problem *p, int mode, const T *y, const T *v, T *out, doub
     ea.mu = T(p->mu);
     ea.shift = T(shift);
     ea.shift_dev = shift_dev;
+    ea.variant = p->jvp_variant;
     if (ps.P > 0) {
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (p->prof_on) {
@@ -992,6 +1004,7 @@ hb_status apply_jv_noalloc(hb_problem *p, int mode, const T *y, const T *v, T *o
     ea.rho = T(p->rho);
     ea.mu = T(p->mu);
     ea.shift = T(shift);
+    ea.variant = p->jvp_variant;
     if (ps.P > 0) {
         launch_elem<T>(mode, ea, ps.P, s);
         HB_LAUNCHED(p, 1);
@@ -1643,7 +1656,7 @@ struct hb_batch {
     cudaStream_t stream = nullptr;
     DBuf<ElemArgs<float>> args32;
     DBuf<ElemArgs<double>> args64;
-    DBuf<int> first_item, counter;
+    DBuf<int> bslots, counter;
     int n_items = 0, grid = 0;
     size_t smem = 0;
     cudaGraphExec_t exec = nullptr;
@@ -1660,12 +1673,22 @@ template <typename T>
 hb_status batch_record(hb_batch *b) {
     cudaStream_t s = b->stream;
     hb_problem *p0 = b->probs[0];
-    std::vector<ElemArgs<T>> args(b->probs.size());
+    // problems ordered by instance count: each run of equal N is one persistent launch of the pass
+    // specialised for that N
+    const size_t np = b->probs.size();
+    std::vector<size_t> ord(np);
+    for (size_t q = 0; q < np; ++q) ord[q] = q;
+    std::stable_sort(ord.begin(), ord.end(), [&](size_t x, size_t y) { return b->probs[x]->N < b->probs[y]->N; });
+    std::vector<ElemArgs<T>> args(np);
     size_t smem = 0;
-    for (size_t q = 0; q < b->probs.size(); ++q) {
+    int slot_cap = 0;
+    for (size_t r = 0; r < np; ++r) slot_cap = std::max(slot_cap, slot_ints(patches<T>(b->probs[ord[r]], b->mode).nl_max));
+    const int bstride = 4 + slot_cap;               // batch slot: [problem, 0, 0, 0, patch slot]
+    for (size_t r = 0; r < np; ++r) {
+        const size_t q = ord[r];
         hb_problem *p = b->probs[q];
         PatchSetDev<T> &ps = patches<T>(p, b->mode);
-        ElemArgs<T> &ea = args[q];
+        ElemArgs<T> &ea = args[r];
         ea.pv = ps.view();
         ea.y = static_cast<const T *>(b->y[q]);
         ea.v = static_cast<const T *>(b->v[q]);
@@ -1677,7 +1700,7 @@ hb_status batch_record(hb_batch *b) {
         ea.mu = T(p->mu);
         ea.shift = T(b->shift);
         ea.shift_dev = nullptr;
-        smem = std::max(smem, elem_smem_bytes(b->mode, p->N, ps.nl_max, ps.ep_max, sizeof(T)));
+        smem = std::max(smem, elem_smem_bytes(b->mode, p->N, ps.nl_max, ps.ep_max, sizeof(T), bstride));
     }
     DBuf<ElemArgs<T>> &dargs = [&]() -> DBuf<ElemArgs<T>> & {
         if constexpr (sizeof(T) == 4) return b->args32;
@@ -1685,10 +1708,44 @@ hb_status batch_record(hb_batch *b) {
     }();
     HB_TRY(dalloc(p0, dargs, args.size()));
     HB_CUDA(cudaMemcpy(dargs.p, args.data(), args.size() * sizeof(ElemArgs<T>), cudaMemcpyHostToDevice));
-    std::vector<int> first(b->probs.size() + 1, 0);
-    for (size_t q = 0; q < b->probs.size(); ++q) first[q + 1] = first[q] + args[q].pv.n_patches;
+    std::vector<int> first(np + 1, 0);
+    for (size_t r = 0; r < np; ++r) first[r + 1] = first[r] + args[r].pv.n_patches;
     b->n_items = first.back();
-    HB_TRY(upload(p0, b->first_item, first));
+    // batch slot table: each item's header (its problem) and a copy of its patch slot (the slots carry
+    // the current Dirichlet bits, so the table is rebuilt with every recording)
+    HB_TRY(dalloc(p0, b->bslots, size_t(std::max(1, b->n_items)) * size_t(bstride)));
+    {
+        std::vector<int> head(size_t(std::max(1, b->n_items)) * 4, 0);
+        for (size_t r = 0; r < np; ++r)
+            for (int k = first[r]; k < first[r + 1]; ++k) head[size_t(k) * 4] = int(r);
+        if (b->n_items > 0)
+            HB_CUDA(cudaMemcpy2DAsync(b->bslots.p, size_t(bstride) * 4, head.data(), 16, 16, size_t(b->n_items),
+                                      cudaMemcpyHostToDevice, s));
+        for (size_t r = 0; r < np; ++r) {
+            const PatchView<T> &pv = args[r].pv;
+            if (pv.n_patches == 0) continue;
+            HB_CUDA(cudaMemcpy2DAsync(b->bslots.p + size_t(first[r]) * bstride + 4, size_t(bstride) * 4, pv.slots,
+                                      size_t(pv.slot_stride) * 4, size_t(pv.slot_stride) * 4, size_t(pv.n_patches),
+                                      cudaMemcpyDeviceToDevice, s));
+        }
+        HB_CUDA(cudaStreamSynchronize(s));
+    }
+    std::vector<BatchGroup<T>> groups;
+    for (size_t r0 = 0; r0 < np;) {
+        size_t r1 = r0 + 1;
+        while (r1 < np && args[r1].N == args[r0].N) ++r1;
+        BatchGroup<T> g;
+        g.args = dargs.p;
+        g.bslots = b->bslots.p;
+        g.bslot_stride = bstride;
+        g.N = args[r0].N;
+        g.item_begin = first[r0];
+        g.item_end = first[r1];
+        g.variant = p0->jvp_variant;
+        g.counter = b->counter.p + groups.size();
+        groups.push_back(g);
+        r0 = r1;
+    }
     int max_blocks = 1;
     if (smem <= 113 * 1024 && sizeof(T) == 4) max_blocks = 2;
     b->grid = p0->sm_count * max_blocks;
@@ -1701,11 +1758,11 @@ hb_status batch_record(hb_batch *b) {
         if (cudaMemsetAsync(b->out[q], 0, size_t(p->n_nodes) * 4 * p->N * sizeof(T), s) != cudaSuccess)
             st = fail(HB_ERR_CUDA, "memset in batch capture");
     }
-    if (st == HB_OK && cudaMemsetAsync(b->counter.p, 0, sizeof(int), s) != cudaSuccess)
+    if (st == HB_OK && cudaMemsetAsync(b->counter.p, 0, groups.size() * sizeof(int), s) != cudaSuccess)
         st = fail(HB_ERR_CUDA, "memset in batch capture");
-    if (st == HB_OK) {
-        launch_batch_elem<T>(b->mode, dargs.p, b->first_item.p, int(b->probs.size()), b->n_items, b->counter.p,
-                             smem, b->grid, s);
+    for (size_t k = 0; k < groups.size() && st == HB_OK; ++k) {
+        const BatchGroup<T> &g = groups[k];
+        launch_batch_elem<T>(b->mode, g, smem, std::min(b->grid, g.item_end - g.item_begin), s);
         p0->launches += 1;
     }
     for (size_t q = 0; q < b->probs.size() && st == HB_OK; ++q) {
@@ -1793,7 +1850,7 @@ hb_status hb_batch_create(hb_problem *const *problems, int count, int precision,
         delete b;
         return fail(HB_ERR_CUDA, "cudaStreamCreate failed");
     }
-    hb_status st = dalloc(p0, b->counter, 1);
+    hb_status st = dalloc(p0, b->counter, size_t(count));
     if (st != HB_OK) {
         cudaStreamDestroy(b->stream);
         delete b;
@@ -1880,31 +1937,39 @@ hb_status hb_tune_patches(hb_problem *p, int precision, const int *candidates, i
         p->bc_dirty = true;                       // Dirichlet lists follow the new patches
         return prepare_bc(p);
     };
+    const int n_var = precision == 0 ? 1 : kJvpVariants;
+    int bvar = 0;
     for (int c = 0; c < n_cand; ++c) {
         const int nl = candidates[c];
         bool fits = nl >= 8 && nl <= 255;
         for (int m = 0; m < 4 && fits; ++m) fits = elem_smem_bytes(m, p->N, nl, 3 * nl, ts) <= 227 * 1024;
         if (!fits) continue;
         HB_TRY(rebuild(nl));
-        double ms = 0;
-        const bool was = p->prof_on;
-        p->prof_on = true;
-        double tmp = 0;
-        int64_t cnt = 0;
-        HB_TRY(hb_profile_read(p, &tmp, &cnt));
-        for (int r = 0; r < reps + 1; ++r) {
-            if (precision == 0) HB_TRY(apply_op<double>(p, MODE_JVP, p->w64a.p, p->w64b.p, p->kres.p, 0.0, p->stream));
-            else HB_TRY(apply_op<float>(p, MODE_JVP, p->w32a.p, p->w32c.p, p->w32b.p, 0.0, p->stream));
-            if (r == 0) HB_TRY(hb_profile_read(p, &tmp, &cnt));   // drop the first (cold) launch
-        }
-        HB_TRY(hb_profile_read(p, &ms, &cnt));
-        p->prof_on = was;
-        ms /= double(std::max<int64_t>(1, cnt));
-        if (ms < best) {
-            best = ms;
-            bnl = nl;
+        for (int var = 0; var < n_var; ++var) {
+            p->jvp_variant = var;
+            double ms = 0;
+            const bool was = p->prof_on;
+            p->prof_on = true;
+            double tmp = 0;
+            int64_t cnt = 0;
+            HB_TRY(hb_profile_read(p, &tmp, &cnt));
+            for (int r = 0; r < reps + 1; ++r) {
+                if (precision == 0)
+                    HB_TRY(apply_op<double>(p, MODE_JVP, p->w64a.p, p->w64b.p, p->kres.p, 0.0, p->stream));
+                else HB_TRY(apply_op<float>(p, MODE_JVP, p->w32a.p, p->w32c.p, p->w32b.p, 0.0, p->stream));
+                if (r == 0) HB_TRY(hb_profile_read(p, &tmp, &cnt));   // drop the first (cold) launch
+            }
+            HB_TRY(hb_profile_read(p, &ms, &cnt));
+            p->prof_on = was;
+            ms /= double(std::max<int64_t>(1, cnt));
+            if (ms < best) {
+                best = ms;
+                bnl = nl;
+                bvar = var;
+            }
         }
     }
+    p->jvp_variant = precision == 0 ? p->jvp_variant : bvar;
     if (bnl == 0) return fail(HB_ERR_INVALID_ARG, "no candidate fits the shared-memory budget");
     HB_TRY(rebuild(bnl));
     if (best_nl) *best_nl = bnl;
@@ -1936,6 +2001,15 @@ hb_status hb_get_info(hb_problem *p, hb_info *info) {
 }
 
 int64_t hb_launch_count(const hb_problem *p) { return p ? p->launches : 0; }
+
+hb_status hb_set_launch_variant(hb_problem *p, int variant) {
+    if (!p) return fail(HB_ERR_INVALID_ARG, "null problem");
+    if (variant < 0 || variant >= kJvpVariants) return fail(HB_ERR_INVALID_ARG, "unknown launch variant");
+    p->jvp_variant = variant;
+    return HB_OK;
+}
+
+int hb_get_launch_variant(const hb_problem *p) { return p ? p->jvp_variant : -1; }
 
 hb_status hb_profile_elem(hb_problem *p, int enable) {
     if (!p) return fail(HB_ERR_INVALID_ARG, "null problem");

@@ -10,6 +10,8 @@
 // index only, so applying it per patch and summing equals applying it after global assembly.
 #include "hb_internal.cuh"
 
+#include <algorithm>
+
 namespace hb {
 
 namespace {
@@ -20,10 +22,14 @@ struct Layout {
 
 __host__ __device__ inline size_t pad16(size_t b) { return (b + 15) & ~size_t(15); }
 
-__host__ __device__ inline Layout make_layout(int mode, int N, int nl, int ep, size_t ts) {
+// The two slot buffers come first, sized for slot_cap ints each (0: the patch set's own slot size), so
+// a batch of problems with different node caps can stage the next problem's slot while the current one
+// computes.
+__host__ __device__ inline Layout make_layout(int mode, int N, int nl, int ep, size_t ts, int slot_cap = 0) {
     Layout L;
     size_t o = 0;
     const size_t row4 = size_t(nl) * 4 * N * ts, row3 = size_t(nl) * 3 * N * ts;
+    L.node = o; o += pad16(size_t(2) * size_t(slot_cap > 0 ? slot_cap : slot_ints(nl)) * 4);
     L.H = o;    o += pad16(size_t(N) * N * ts);
     L.geom = o; o += pad16(size_t(ep) * kGeomStride * ts);
     L.Y = o;    o += pad16(row4);
@@ -31,7 +37,6 @@ __host__ __device__ inline Layout make_layout(int mode, int N, int nl, int ep, s
     L.HY = o;   if (mode == MODE_RES || mode == MODE_JVE) o += pad16(row3);
     L.HV = o;   if (mode == MODE_JVE || mode == MODE_JVP) o += pad16(row3);
     L.T = o;    if (mode == MODE_RES || mode == MODE_JVE) o += pad16(row3);
-    L.node = o; o += pad16(size_t(nl) * 4);
     L.conn = o; o += pad16(size_t(ep) * 4);
     L.total = o;
     return L;
@@ -75,6 +80,237 @@ __device__ __forceinline__ void load_geom(const double *g, double gN[4][3], doub
     g2 = v[13];
 }
 
+// ---------------------------------------------------------------------------------------------------
+// Lanes of the paper-tangent pass: FP64 runs one instance per thread (lane = double); FP32 runs two
+// instances per thread (lane = float2) on Blackwell's paired FP32 instructions, which halves the
+// issue slots of the arithmetic.
+
+template <typename T>
+struct LaneOf;
+template <>
+struct LaneOf<double> { using type = double; };
+template <>
+struct LaneOf<float> { using type = float2; };
+
+// Launch variants of the paper-tangent pass (the other passes always run variant 0):
+//   0: 256 threads per block; FP32 runs two instances per thread on paired instructions
+//   1: 384 threads per block, one instance per thread (fewer registers, more resident warps; default)
+//   2: 512 threads per block, one instance per thread
+template <typename T, int VAR>
+struct ElemCfg;
+template <typename T>
+struct ElemCfg<T, 0> { static constexpr int block = 256; using lane = typename LaneOf<T>::type; };
+template <typename T>
+struct ElemCfg<T, 1> { static constexpr int block = 384; using lane = T; };
+template <typename T>
+struct ElemCfg<T, 2> { static constexpr int block = 512; using lane = T; };
+
+__device__ __forceinline__ unsigned long long f2_bits(float2 a) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+    return r;
+}
+__device__ __forceinline__ float2 bits_f2(unsigned long long r) {
+    float2 a;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
+    return a;
+}
+__device__ __forceinline__ double lfma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float2 lfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ double lmul(double a, double b) { return a * b; }
+__device__ __forceinline__ float2 lmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ double ladd(double a, double b) { return a + b; }
+__device__ __forceinline__ float2 ladd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ double lsub(double a, double b) { return a - b; }
+__device__ __forceinline__ float2 lsub(float2 a, float2 b) {
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+    return bits_f2(r);
+}
+__device__ __forceinline__ float lfma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ float lmul(float a, float b) { return a * b; }
+__device__ __forceinline__ float ladd(float a, float b) { return a + b; }
+__device__ __forceinline__ float lsub(float a, float b) { return a - b; }
+template <typename L, typename T>
+__device__ __forceinline__ L lsplat(T s) {
+    if constexpr (sizeof(L) == 2 * sizeof(T)) return make_float2(s, s);
+    else return s;
+}
+__device__ __forceinline__ double lrsqrt(double x) { return rsqrt(x); }
+__device__ __forceinline__ float lrsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ float2 lrsqrt(float2 x) { return make_float2(rsqrtf(x.x), rsqrtf(x.y)); }
+// the lane's instances of a staged row: p[0] (and p[d1] for the second instance of a pair)
+template <typename L, typename T>
+__device__ __forceinline__ L lload(const T *p, int d1) {
+    if constexpr (sizeof(L) == 2 * sizeof(T)) return make_float2(p[0], p[d1]);
+    else return p[0];
+}
+// global accumulation; d1 = 0 marks a pair whose second instance does not exist
+__device__ __forceinline__ void lred(double *p, double v, int) { atomicAdd(p, v); }
+__device__ __forceinline__ void lred(float *p, float v, int) { atomicAdd(p, v); }
+__device__ __forceinline__ void lred(float *p, float2 v, int d1) {
+    atomicAdd(p, v.x);
+    if (d1) atomicAdd(p + d1, v.y);
+}
+template <typename L>
+__device__ __forceinline__ L ldot3(const L *a, const L *b, L c) {
+    return lfma(a[0], b[0], lfma(a[1], b[1], lfma(a[2], b[2], c)));
+}
+template <typename L>
+__device__ __forceinline__ L ldot3(const L *a, const L *b) {
+    return lfma(a[0], b[0], lfma(a[1], b[1], lmul(a[2], b[2])));
+}
+
+// Paper-tangent Jv (P + C) v of one element at the lane's instances n0 (and n0 + d1), Eqs. (ptangent),
+// (K_mat), (ctangent), (F_mat), with U and tau frozen at the state y.  sW holds W = shift v + rho H v
+// per patch node: the F block rho M (H v) and the pseudo-time mass shift M v share the mass matrix.
+//
+// The element sums are regrouped so that no per-node accumulator is carried through the quadrature
+// loop (exact algebra; only the rounding order differs from the term-by-term form):
+//   sum_q udN_q[a] X_q[i]            = grad N_a . Mx[:, i],  Mx[j][i] = sum_q u_q[j] X_q[i]
+//   sum_q (u_q . grad v_i)           = (sum_a u_a) . grad v_i  (the 4 points average to the centroid)
+//   visc, pressure and Mx terms      = grad N_a . Z[:, i],   Z = w rho Mx + mu V (grad v)^T - V pbar I
+// with X_q = tau_q (u_q . grad v + grad q / rho) the strong residual of the direction over rho.
+template <typename T, typename L, int NT>
+__device__ __forceinline__ void jvp_lanes(int e, int n0, int d1, int Nrt, T rho, T mu,
+                                          const T *__restrict__ sGeom, const uint32_t *__restrict__ sConn,
+                                          const T *__restrict__ sY, const T *__restrict__ sV,
+                                          const T *__restrict__ sW, const int *__restrict__ sNode,
+                                          T *__restrict__ gout) {
+    const int N = NT > 0 ? NT : Nrt, N4 = 4 * N, N3 = 3 * N;
+    const uint32_t c = sConn[e];
+    const int lo[4] = {int(c & 255u), int((c >> 8) & 255u), int((c >> 16) & 255u), int(c >> 24)};
+    int rY[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) rY[a] = lo[a] * N4 + n0;
+    T gs[4][3], V, g2s;
+    load_geom(sGeom + e * kGeomStride, gs, V, g2s);
+    L gN[3][3];   // grad N_a of the vertices a = 1, 2, 3 (grad N_0 = -(sum of these))
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) gN[a][j] = lsplat<L>(gs[a + 1][j]);
+
+    // gradients of the direction: grad v_i = sum_{a >= 1} (v_a - v_0)_i grad N_a, same for q
+    L gV[3][3], gVp[3], pbar;
+    {
+        L dv0[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) dv0[i] = lload<L>(sV + rY[0] + i * N, d1);
+        const L dp0 = lload<L>(sV + rY[0] + 3 * N, d1);
+        pbar = dp0;
+#pragma unroll
+        for (int a = 1; a < 4; ++a) {
+            const L dp = lload<L>(sV + rY[a] + 3 * N, d1);
+            pbar = ladd(pbar, dp);
+            const L ddp = lsub(dp, dp0);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) gVp[j] = a == 1 ? lmul(ddp, gN[0][j]) : lfma(ddp, gN[a - 1][j], gVp[j]);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const L dd = lsub(lload<L>(sV + rY[a] + i * N, d1), dv0[i]);
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+                    gV[i][j] = a == 1 ? lmul(dd, gN[0][j]) : lfma(dd, gN[a - 1][j], gV[i][j]);
+            }
+        }
+        pbar = lmul(pbar, lsplat<L>(T(0.25) * V));          // V times the element mean of q
+        const L ir = lsplat<L>(T(1) / rho);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) gVp[j] = lmul(gVp[j], ir);
+    }
+
+    // frozen velocity at the 4 nodes, turned into its values at the 4 quadrature points
+    L uq[4][3], usum[3], Ug[3];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) uq[a][i] = lload<L>(sY + rY[a] + i * N, d1);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) usum[i] = ladd(ladd(uq[0][i], uq[1][i]), ladd(uq[2][i], uq[3][i]));
+#pragma unroll
+    for (int i = 0; i < 3; ++i) Ug[i] = ldot3(usum, gV[i]);
+    {
+        const L qb = lsplat<L>(T(kQB)), qd = lsplat<L>(T(kQA - kQB));
+#pragma unroll
+        for (int i = 0; i < 3; ++i) usum[i] = lmul(usum[i], qb);
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) uq[a][i] = lfma(qd, uq[a][i], usum[i]);
+    }
+
+    // quadrature loop: tau_q, X_q and the two element sums Mx and S
+    L Mx[3][3], S[3];
+    const L g2 = lsplat<L>(g2s);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        L udN[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) udN[a] = ldot3(uq[q], gN[a]);
+        const L tau = lrsqrt(lfma(udN[0], udN[0], lfma(udN[1], udN[1], lfma(udN[2], udN[2], g2))));
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const L X = lmul(tau, ldot3(uq[q], gV[i], gVp[i]));
+            S[i] = q == 0 ? X : ladd(S[i], X);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) Mx[j][i] = q == 0 ? lmul(uq[q][j], X) : lfma(uq[q][j], X, Mx[j][i]);
+        }
+    }
+
+    const T w = V * T(0.25);
+    T *go[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) go[a] = gout + size_t(uint32_t(sNode[lo[a]]) & ~kDirBit) * N4 + n0;
+    // continuity rows: w div v + (w / rho) grad N_a . sum_q X_q (Eq. K_mat, G and D blocks)
+    {
+        const L wdiv = lmul(lsplat<L>(w), ladd(gV[0][0], ladd(gV[1][1], gV[2][2])));
+        L Sw[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) Sw[i] = lmul(lsplat<L>(w), S[i]);
+        L gS[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) gS[a] = ldot3(gN[a], Sw);
+        lred(go[0] + 3 * N, lsub(wdiv, ladd(gS[0], ladd(gS[1], gS[2]))), d1);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) lred(go[a + 1] + 3 * N, ladd(wdiv, gS[a]), d1);
+    }
+    // Z[j][i] = w rho Mx[j][i] + mu V d_j v_i - V pbar delta_ij
+    {
+        const L wr = lsplat<L>(w * rho), muV = lsplat<L>(mu * V);
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) Mx[j][i] = lfma(wr, Mx[j][i], lmul(muV, gV[i][j]));
+#pragma unroll
+        for (int i = 0; i < 3; ++i) Mx[i][i] = lsub(Mx[i][i], pbar);
+    }
+    // momentum rows
+    const L m20 = lsplat<L>(V * T(0.05));                  // int N_a N_b = V (1 + delta_ab) / 20
+    const L kb = lsplat<L>(w * rho * T(kQB)), kd = lsplat<L>(w * rho * T(kQA - kQB));
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        L Wa[4];
+        const int rW0 = i * N + n0;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) Wa[a] = lload<L>(sW + lo[a] * N3 + rW0, d1);
+        const L Wsum = ladd(ladd(Wa[0], Wa[1]), ladd(Wa[2], Wa[3]));
+        const L cW = lfma(kb, Ug[i], lmul(m20, Wsum));
+        const L Zi[3] = {Mx[0][i], Mx[1][i], Mx[2][i]};
+        L gz[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) gz[a] = ldot3(gN[a], Zi);
+        const L gz0 = ladd(gz[0], ladd(gz[1], gz[2]));
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            L val = a == 0 ? lsub(cW, gz0) : ladd(cW, gz[a - 1]);
+            val = lfma(kd, ldot3(uq[a], gV[i]), val);
+            val = lfma(m20, Wa[a], val);
+            lred(go[a] + i * N, val, d1);
+        }
+    }
+}
+
 // NT > 0: the number of instances is the compile-time constant NT; NT = 0: runtime N
 template <typename T, int MODE, int NT>
 __device__ __forceinline__ void element_instance(int e, int n, int Nrt, T rho, T mu, T shift,
@@ -92,7 +328,7 @@ __device__ __forceinline__ void element_instance(int e, int n, int Nrt, T rho, T
     // there directly (native global reductions)
     T *go[4];
 #pragma unroll
-    for (int a = 0; a < 4; ++a) go[a] = gout + size_t(sNode[lo[a]]) * N4 + n;
+    for (int a = 0; a < 4; ++a) go[a] = gout + size_t(uint32_t(sNode[lo[a]]) & ~kDirBit) * N4 + n;
     T gN[4][3], V, g2;
     load_geom(sGeom + e * kGeomStride, gN, V, g2);
     const T w = V * T(0.25);
@@ -209,77 +445,7 @@ __device__ __forceinline__ void element_instance(int e, int n, int Nrt, T rho, T
             atomicAdd(go[a] + 3 * N, qc);
         }
         return;
-    } else if constexpr (MODE == MODE_JVP) {
-        T dv[4][3], dvp[4], hdv[4][3];
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
-            dvp[a] = sV[lo[a] * N4 + 3 * N + n];
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                dv[a][i] = sV[lo[a] * N4 + i * N + n];
-                hdv[a][i] = sHV[lo[a] * N3 + i * N + n];
-            }
-        }
-        T gV[3][3], gVp[3], dvsum[3], hdvsum[3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            dvsum[i] = dv[0][i] + dv[1][i] + dv[2][i] + dv[3][i];
-            hdvsum[i] = hdv[0][i] + hdv[1][i] + hdv[2][i] + hdv[3][i];
-#pragma unroll
-            for (int j = 0; j < 3; ++j)
-                gV[i][j] = dv[0][i] * gN[0][j] + dv[1][i] * gN[1][j] + dv[2][i] * gN[2][j] + dv[3][i] * gN[3][j];
-        }
-#pragma unroll
-        for (int j = 0; j < 3; ++j)
-            gVp[j] = dvp[0] * gN[0][j] + dvp[1] * gN[1][j] + dvp[2] * gN[2][j] + dvp[3] * gN[3][j];
-        T qm[4][3];
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int i = 0; i < 3; ++i) qm[a][i] = T(0);
-        T S[3] = {0, 0, 0}, ugvs[3] = {0, 0, 0};
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            T uq[3];
-#pragma unroll
-            for (int i = 0; i < 3; ++i) uq[i] = qb * usum[i] + qd * u[q][i];
-            T udN[4];
-#pragma unroll
-            for (int a = 1; a < 4; ++a) udN[a] = uq[0] * gN[a][0] + uq[1] * gN[a][1] + uq[2] * gN[a][2];
-            udN[0] = -(udN[1] + udN[2] + udN[3]);
-            const T tau = rsqrt_t<T>(udN[1] * udN[1] + udN[2] * udN[2] + udN[3] * udN[3] + g2);
-            T X[3];
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                const T ugv = uq[0] * gV[i][0] + uq[1] * gV[i][1] + uq[2] * gV[i][2];
-                X[i] = tau * (rho * ugv + gVp[i]);
-                ugvs[i] += ugv;
-                S[i] += X[i];
-                qm[q][i] += w * rho * qd * ugv;
-            }
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-                for (int i = 0; i < 3; ++i) qm[a][i] += w * udN[a] * X[i];
-        }
-        const T pbar = T(0.25) * (dvp[0] + dvp[1] + dvp[2] + dvp[3]);
-        const T div = gV[0][0] + gV[1][1] + gV[2][2];
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                const T visc = gN[a][0] * gV[i][0] + gN[a][1] * gV[i][1] + gN[a][2] * gV[i][2];
-                const T mv = m20 * (dvsum[i] + dv[a][i]);
-                const T mhv = m20 * (hdvsum[i] + hdv[a][i]);     // F block: H (rho M v) = rho M (H v)
-                const T vq = qm[a][i] + w * rho * qb * ugvs[i] + mu * V * visc - V * gN[a][i] * pbar
-                           + shift * mv + rho * mhv;
-                atomicAdd(go[a] + i * N, vq);
-            }
-            const T qc = w * div + (w / rho) * (gN[a][0] * S[0] + gN[a][1] * S[1] + gN[a][2] * S[2]);
-            atomicAdd(go[a] + 3 * N, qc);
-        }
-        return;
-    } else {  // MODE_JVE
+    } else {  // MODE_JVE (MODE_JVP runs jvp_lanes)
         T p[4], hu[4][3], dv[4][3], dvp[4], hdv[4][3];
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
@@ -383,12 +549,35 @@ __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
     const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
 }
+__device__ __forceinline__ void cp_async4(void *smem_dst, const void *gmem_src) {
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Copy patch p's slot into shared memory (issued by one thread; completion: that thread's
+// cp_async_wait_all, then a block barrier).
+__device__ __forceinline__ void stage_slot(const int *slots, int stride, int p, int *dst) {
+    const int4 *src = reinterpret_cast<const int4 *>(slots + size_t(p) * stride);
+    for (int i = 0; i < stride / 4; ++i) cp_async16(dst + 4 * i, src + i);
+}
+
+// Prefetch of the next patch's slot, run by patch_pass on every thread (thread 0 issues the copies).
+struct SlotPrefetch {
+    const int *slots;
+    int stride, next, n_patches;
+    int *dst;
+    __device__ __forceinline__ void operator()() const {
+        if (threadIdx.x == 0 && next < n_patches) stage_slot(slots, stride, next, dst);
+    }
+};
 
 // H is circulant: H[j][k] = h[(j - k) mod N] with h its first column (h[0] = 0).  For a fixed N one row
 // of N values is multiplied with the kernel held in registers; x_in may equal x_out (read fully first).
-template <typename T, int NT>
-__device__ __forceinline__ void circulant_row(const T *__restrict__ hcol, const T *x_in, T *x_out) {
+// With SCALED, x_out = alpha (H x) + beta x.
+template <typename T, int NT, bool SCALED = false>
+__device__ __forceinline__ void circulant_row(const T *__restrict__ hcol, const T *x_in, T *x_out,
+                                              T alpha = T(1), T beta = T(0)) {
     T x[NT], h[NT];
 #pragma unroll
     for (int k = 0; k < NT; ++k) x[k] = x_in[k];
@@ -400,7 +589,7 @@ __device__ __forceinline__ void circulant_row(const T *__restrict__ hcol, const 
 #pragma unroll
         for (int k = 0; k < NT; ++k)
             if (k != m) acc += h[(m - k + NT) % NT] * x[k];
-        x_out[m] = acc;
+        x_out[m] = SCALED ? alpha * acc + beta * x[m] : acc;
     }
 }
 
@@ -408,13 +597,16 @@ __device__ __forceinline__ void circulant_row(const T *__restrict__ hcol, const 
 template <typename T>
 struct PatchSmem {
     T *H, *geom, *Y, *V, *HY, *HV, *T_;
-    int *node;
+    int *slot0;                    // slot buffer b at slot0 + b * slot_cap
+    int slot_cap;
     uint32_t *conn;
+    __device__ __forceinline__ int *slot(int b) const { return slot0 + b * slot_cap; }
 };
 
 template <typename T, int MODE>
-__device__ __forceinline__ PatchSmem<T> patch_smem(unsigned char *smem, int N, int nl_max, int ep_max) {
-    const Layout L = make_layout(MODE, N, nl_max, ep_max, sizeof(T));
+__device__ __forceinline__ PatchSmem<T> patch_smem(unsigned char *smem, int N, int nl_max, int ep_max,
+                                                   int slot_cap = 0) {
+    const Layout L = make_layout(MODE, N, nl_max, ep_max, sizeof(T), slot_cap);
     PatchSmem<T> m;
     m.H = reinterpret_cast<T *>(smem + L.H);
     m.geom = reinterpret_cast<T *>(smem + L.geom);
@@ -423,7 +615,8 @@ __device__ __forceinline__ PatchSmem<T> patch_smem(unsigned char *smem, int N, i
     m.HY = reinterpret_cast<T *>(smem + L.HY);
     m.HV = reinterpret_cast<T *>(smem + L.HV);
     m.T_ = reinterpret_cast<T *>(smem + L.T);
-    m.node = reinterpret_cast<int *>(smem + L.node);
+    m.slot0 = reinterpret_cast<int *>(smem + L.node);
+    m.slot_cap = slot_cap > 0 ? slot_cap : slot_ints(nl_max);
     m.conn = reinterpret_cast<uint32_t *>(smem + L.conn);
     return m;
 }
@@ -438,60 +631,69 @@ __device__ __forceinline__ void stage_H(const ElemArgs<T> &a, T *sH, int N) {
     }
 }
 
-// One patch: gather, Dirichlet masking, in-patch H products, element-instance work, H T flush.
-// Ends with a block barrier, so shared memory can be reused by the next patch.
-template <typename T, int MODE, int NT>
-__device__ __forceinline__ void patch_pass(const ElemArgs<T> &a, int p, const PatchSmem<T> &sm, T shift) {
+// One patch whose slot is staged in sSlot: gather, Dirichlet masking, in-patch H products,
+// element-instance work, H T flush.  `prefetch` runs on every thread once the staged rows are no longer
+// being written (the caller uses it to stage the next patch's slot).  Ends with a block barrier, so
+// shared memory can be reused by the next patch.
+template <typename T, int MODE, int NT, typename L, typename Prefetch>
+__device__ __forceinline__ void patch_pass(const ElemArgs<T> &a, const PatchSmem<T> &sm, const int *sSlot, T shift,
+                                           Prefetch prefetch) {
     const int N = NT > 0 ? NT : a.N, N4 = 4 * N, N3 = 3 * N;
     T *sH = sm.H, *sGeom = sm.geom, *sY = sm.Y, *sV = sm.V, *sHY = sm.HY, *sHV = sm.HV, *sT = sm.T_;
-    int *sNode = sm.node;
     uint32_t *sConn = sm.conn;
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int e0 = a.pv.eptr[p], ne = a.pv.eptr[p + 1] - e0;
-    const int q0 = a.pv.nptr[p], nl = a.pv.nptr[p + 1] - q0;
-    for (int i = tid; i < nl; i += nt) sNode[i] = a.pv.nodes[q0 + i];
-    for (int i = tid; i < ne; i += nt) sConn[i] = a.pv.lconn[e0 + i];
+    const int e0 = sSlot[0], ne = sSlot[1], nl = sSlot[2], nd = sSlot[3];
+    const int *sNode = sSlot + 4;           // global node ids, kDirBit on prescribed velocities
+    if constexpr (MODE == MODE_RES || MODE == MODE_JVE)
+        for (int i = tid; i < nl * N3; i += nt) sT[i] = T(0);
+
+    // asynchronous copies of the patch's element data and node rows (4 N values per node), so every
+    // thread keeps all of its loads in flight
     {
         const uint4 *src = reinterpret_cast<const uint4 *>(a.pv.geom + size_t(e0) * kGeomStride);
         uint4 *dst = reinterpret_cast<uint4 *>(sGeom);
         const int nvec = int(ne * kGeomStride * sizeof(T) / 16);
-        for (int i = tid; i < nvec; i += nt) dst[i] = src[i];
+        for (int i = tid; i < nvec; i += nt) cp_async16(dst + i, src + i);
+        for (int i = tid; i < ne; i += nt) cp_async4(sConn + i, a.pv.lconn + e0 + i);
     }
-    if constexpr (MODE == MODE_RES || MODE == MODE_JVE)
-        for (int i = tid; i < nl * N3; i += nt) sT[i] = T(0);
-    __syncthreads();
-
-    // gather the patch's node rows (4 N values per node) with asynchronous 16-byte copies, so every
-    // thread keeps all of its loads in flight
-    const int cpr = int(N4 * sizeof(T) / 16);
+    constexpr int VPC = int(16 / sizeof(T));       // values per 16-byte chunk
+    const int cpr = N4 / VPC;
     for (int i = tid; i < nl * cpr; i += nt) {
         const int l = i / cpr, c = i - l * cpr;
-        const size_t gidx = size_t(sNode[l]) * cpr + c;
+        const size_t gidx = size_t(uint32_t(sNode[l]) & ~kDirBit) * cpr + c;
         cp_async16(reinterpret_cast<uint4 *>(sY) + i, reinterpret_cast<const uint4 *>(a.y) + gidx);
         if constexpr (MODE == MODE_JVP || MODE == MODE_JVE)
             cp_async16(reinterpret_cast<uint4 *>(sV) + i, reinterpret_cast<const uint4 *>(a.v) + gidx);
     }
     cp_async_wait_all();
-    __syncthreads();
     if constexpr (MODE == MODE_JVP || MODE == MODE_JVE) {
-        // Dirichlet velocity entries of the direction are not unknowns: treat them as 0 (only the
-        // patches touching a Dirichlet boundary have any)
-        const int d0 = a.pv.dptr[p], nd = a.pv.dptr[p + 1] - d0;
+        // prescribed velocity entries of the direction are not unknowns: each thread zeroes them in the
+        // chunks it copied itself (complete after its own wait)
         if (nd > 0) {
-            for (int i = tid; i < nd * N3; i += nt) {
-                const int k = i / N3, r = i - k * N3;
-                sV[int(a.pv.dloc[d0 + k]) * N4 + r] = T(0);
+            for (int i = tid; i < nl * cpr; i += nt) {
+                const int l = i / cpr;
+                if (sNode[l] >= 0) continue;
+                const int c = i - l * cpr;
+#pragma unroll
+                for (int j = 0; j < VPC; ++j)
+                    if (c * VPC + j < N3) sV[l * N4 + c * VPC + j] = T(0);
             }
-            __syncthreads();
         }
     }
+    __syncthreads();
     if constexpr (MODE != MODE_DIAG) {
         // time coupling of the staged velocities: (H x)[l][i][n] = sum_k H[n][k] x[l][i][k] for
         // x = u (RES, JVE) and x = v (JVP, JVE)
         constexpr bool hy = (MODE == MODE_RES || MODE == MODE_JVE);
         constexpr bool hv = (MODE == MODE_JVP || MODE == MODE_JVE);
         constexpr int nsrc = (hy ? 1 : 0) + (hv ? 1 : 0);
-        if constexpr (NT > 0) {
+        if constexpr (NT > 0 && MODE == MODE_JVP) {
+            // JVP stages W = shift v + rho H v (the mass-matrix terms of the tangent)
+            for (int r = tid; r < nl * 3; r += nt) {
+                const int l = r / 3, f = r - 3 * l;
+                circulant_row<T, NT, true>(sH, sV + l * N4 + f * N, sHV + l * N3 + f * N, a.rho, shift);
+            }
+        } else if constexpr (NT > 0) {
             const int rows = nl * 3;
             for (int r = tid; r < nsrc * rows; r += nt) {
                 const int which = hy ? (r >= rows) : 1, rr = r - (r >= rows) * rows, l = rr / 3, f = rr - 3 * l;
@@ -513,17 +715,29 @@ __device__ __forceinline__ void patch_pass(const ElemArgs<T> &a, int p, const Pa
                     const T *xv = sV + l * N4 + f * N;
                     T acc2 = 0;
                     for (int k = 0; k < N; ++k) acc2 += h[k] * xv[k];
-                    sHV[i] = acc2;
+                    sHV[i] = MODE == MODE_JVP ? a.rho * acc2 + shift * xv[n] : acc2;
                 }
             }
         }
         __syncthreads();
     }
 
-    for (int i = tid; i < ne * N; i += nt) {
-        const int e = i / N, n = i - e * N;
-        element_instance<T, MODE, NT>(e, n, N, a.rho, a.mu, shift, sGeom, sConn, sY, sV, sHY, sHV, sNode,
-                                      a.out, sT);
+    prefetch();
+    if constexpr (MODE == MODE_JVP) {
+        // a thread takes instances k and k + NP of one element (FP32 pairs; FP64: NP = N, one instance)
+        constexpr int LW = int(sizeof(L) / sizeof(T));
+        const int NP = (N + LW - 1) / LW;
+        for (int i = tid; i < ne * NP; i += nt) {
+            const int e = i / NP, k = i - e * NP;
+            const int d1 = (LW == 2 && k + NP < N) ? NP : 0;
+            jvp_lanes<T, L, NT>(e, k, d1, N, a.rho, a.mu, sGeom, sConn, sY, sV, sHV, sNode, a.out);
+        }
+    } else {
+        for (int i = tid; i < ne * N; i += nt) {
+            const int e = i / N, n = i - e * N;
+            element_instance<T, MODE, NT>(e, n, N, a.rho, a.mu, shift, sGeom, sConn, sY, sV, sHY, sHV, sNode,
+                                          a.out, sT);
+        }
     }
     __syncthreads();
 
@@ -550,74 +764,87 @@ __device__ __forceinline__ void patch_pass(const ElemArgs<T> &a, int p, const Pa
                 val = T(0);
                 for (int k = 0; k < N; ++k) val += h[k] * t[k];
             }
-            atomicAdd(a.out + size_t(sNode[l]) * N4 + r, val);
+            atomicAdd(a.out + size_t(uint32_t(sNode[l]) & ~kDirBit) * N4 + r, val);
         }
     }
     __syncthreads();
 }
 
-template <typename T, int MODE, int NT>
-__global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 2 : 1)) elem_kernel(ElemArgs<T> a) {
+// Persistent element pass: block b takes patches b, b + G, b + 2G, ... (G = gridDim.x) and stages each
+// next patch's slot while the current one computes.
+template <typename T, int MODE, int NT, int VAR>
+__global__ void __launch_bounds__(ElemCfg<T, VAR>::block, (sizeof(T) == 4 ? 2 : 1)) elem_kernel(ElemArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int N = NT > 0 ? NT : a.N;
     const PatchSmem<T> sm = patch_smem<T, MODE>(smem, N, a.pv.nl_max, a.pv.ep_max);
     const T shift = a.shift_dev ? T(*a.shift_dev) : a.shift;
+    int p = blockIdx.x;
+    const int P = a.pv.n_patches;
+    if (p >= P) return;
     stage_H<T, NT>(a, sm.H, N);
-    for (int p = blockIdx.x; p < a.pv.n_patches; p += gridDim.x) patch_pass<T, MODE, NT>(a, p, sm, shift);
+    if (threadIdx.x == 0) stage_slot(a.pv.slots, a.pv.slot_stride, p, sm.slot(0));
+    cp_async_wait_all();
+    __syncthreads();
+    for (int cur = 0; p < P; p += gridDim.x, cur ^= 1) {
+        const SlotPrefetch pf{a.pv.slots, a.pv.slot_stride, p + int(gridDim.x), P, sm.slot(cur ^ 1)};
+        patch_pass<T, MODE, NT, typename ElemCfg<T, VAR>::lane>(a, sm, sm.slot(cur), shift, pf);
+        cp_async_wait_all();
+        __syncthreads();
+    }
 }
 
-// Persistent kernel over the patches of many problems: work items (problem, patch) are taken from a
-// global counter, so problems of uneven size share the SMs; each item runs the fixed-N pass of its
-// problem's instance count (9, 13, 21) or the generic one.
-template <typename T, int MODE>
-__global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 ? 2 : 1)) batch_elem_kernel(const ElemArgs<T> *__restrict__ args,
-                                                               const int *__restrict__ first_item, int n_prob,
-                                                               int n_items, int *counter) {
+// Persistent kernel over the patches of several problems with the same instance count.  Work items
+// [item_begin, item_end) are taken from a global counter, so problems of uneven size share the SMs; the
+// batch slot of item i (bslot_stride ints at bslots + i * bslot_stride) holds the owning problem's index
+// in its first int and the patch's own slot from int 4 on.  The next item is claimed, and its slot
+// staged, while the current one computes.
+struct BatchPrefetch {
+    const int *bslots;
+    int bslot_stride, item_begin, item_end;
+    int *counter, *s_next, *dst;
+    __device__ __forceinline__ void operator()() const {
+        if (threadIdx.x != 0) return;
+        const int item = item_begin + atomicAdd(counter, 1);
+        *s_next = item;
+        if (item < item_end) stage_slot(bslots, bslot_stride, item, dst);
+    }
+};
+
+template <typename T, int MODE, int NT, int VAR>
+__global__ void __launch_bounds__(ElemCfg<T, VAR>::block, (sizeof(T) == 4 ? 2 : 1))
+    batch_elem_kernel(const ElemArgs<T> *__restrict__ args, const int *__restrict__ bslots, int bslot_stride,
+                      int item_begin, int item_end, int *counter) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_item;
+    __shared__ int s_item[2];
+    __shared__ ElemArgs<T> s_args;                 // the current problem's arguments
+    // the batch slot buffers sit at the start of every member problem's layout (slot_cap = bslot_stride)
+    int *const slot0 = reinterpret_cast<int *>(smem);
+    BatchPrefetch{bslots, bslot_stride, item_begin, item_end, counter, &s_item[0], slot0}();
+    cp_async_wait_all();
+    __syncthreads();
     int last = -1;
-    while (true) {
-        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
-        __syncthreads();
-        const int item = s_item;
-        __syncthreads();
-        if (item >= n_items) break;
-        int lo = 0, hi = n_prob - 1;               // problem owning this item: first_item[q] <= item
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (first_item[mid] <= item) lo = mid;
-            else hi = mid - 1;
+    for (int cur = 0;; cur ^= 1) {
+        if (s_item[cur] >= item_end) break;
+        const int *bslot = slot0 + cur * bslot_stride;
+        const int q = bslot[0];
+        if (q != last) {
+            if (threadIdx.x == 0) s_args = args[q];
+            __syncthreads();
         }
-        const ElemArgs<T> &a = args[lo];
-        const int patch = item - first_item[lo];
+        const ElemArgs<T> &a = s_args;
+        const int N = NT > 0 ? NT : a.N;
+        const PatchSmem<T> sm = patch_smem<T, MODE>(smem, N, a.pv.nl_max, a.pv.ep_max, bslot_stride);
+        if (q != last) {
+            stage_H<T, NT>(a, sm.H, N);
+            __syncthreads();
+        }
         const T shift = a.shift_dev ? T(*a.shift_dev) : a.shift;
-        switch (a.N) {
-            case 9: {
-                const PatchSmem<T> sm = patch_smem<T, MODE>(smem, 9, a.pv.nl_max, a.pv.ep_max);
-                if (lo != last) { stage_H<T, 9>(a, sm.H, 9); __syncthreads(); }
-                patch_pass<T, MODE, 9>(a, patch, sm, shift);
-                break;
-            }
-            case 13: {
-                const PatchSmem<T> sm = patch_smem<T, MODE>(smem, 13, a.pv.nl_max, a.pv.ep_max);
-                if (lo != last) { stage_H<T, 13>(a, sm.H, 13); __syncthreads(); }
-                patch_pass<T, MODE, 13>(a, patch, sm, shift);
-                break;
-            }
-            case 21: {
-                const PatchSmem<T> sm = patch_smem<T, MODE>(smem, 21, a.pv.nl_max, a.pv.ep_max);
-                if (lo != last) { stage_H<T, 21>(a, sm.H, 21); __syncthreads(); }
-                patch_pass<T, MODE, 21>(a, patch, sm, shift);
-                break;
-            }
-            default: {
-                const PatchSmem<T> sm = patch_smem<T, MODE>(smem, a.N, a.pv.nl_max, a.pv.ep_max);
-                if (lo != last) { stage_H<T, 0>(a, sm.H, a.N); __syncthreads(); }
-                patch_pass<T, MODE, 0>(a, patch, sm, shift);
-                break;
-            }
-        }
-        last = lo;
+        const BatchPrefetch pf{bslots, bslot_stride, item_begin, item_end, counter, &s_item[cur ^ 1],
+                               slot0 + (cur ^ 1) * bslot_stride};
+        patch_pass<T, MODE, NT, typename ElemCfg<T, VAR>::lane>(a, sm, bslot + 4, shift, pf);
+        cp_async_wait_all();
+        __syncthreads();
+        last = q;
     }
 }
 
@@ -681,19 +908,52 @@ inline int nblk(int64_t n, int b) { return int((n + b - 1) / b); }
 
 }  // namespace
 
-size_t elem_smem_bytes(int mode, int N, int nl_max, int ep_max, size_t tsize) {
-    return make_layout(mode, N, nl_max, ep_max, tsize).total;
+size_t elem_smem_bytes(int mode, int N, int nl_max, int ep_max, size_t tsize, int slot_cap) {
+    return make_layout(mode, N, nl_max, ep_max, tsize, slot_cap).total;
+}
+
+// Resident blocks of a kernel on the current device for a dynamic shared-memory size (at least 1).
+template <typename K>
+static int resident_blocks(K kern, int block, size_t smem) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, smem);
+    return std::max(1, sms * std::max(1, per_sm));
+}
+
+// grid: upper bound on the blocks (the patch count); the persistent kernel runs at most one wave
+template <typename T, int MODE, int NT, int VAR>
+static void launch_elem_v(const ElemArgs<T> &a, int grid, cudaStream_t s) {
+    const size_t smem = elem_smem_bytes(MODE, a.N, a.pv.nl_max, a.pv.ep_max, sizeof(T));
+    static size_t configured = 0, occ_smem = 0;
+    static int occ_blocks = 0;
+    auto kern = elem_kernel<T, MODE, NT, VAR>;
+    if (smem > 48 * 1024 && smem > configured) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        configured = smem;
+    }
+    if (occ_blocks == 0 || occ_smem != smem) {
+        occ_blocks = resident_blocks(kern, ElemCfg<T, VAR>::block, smem);
+        occ_smem = smem;
+    }
+    grid = std::min(grid, occ_blocks);
+    if (grid > 0) kern<<<grid, ElemCfg<T, VAR>::block, smem, s>>>(a);
 }
 
 template <typename T, int MODE, int NT>
 static void launch_elem_n(const ElemArgs<T> &a, int grid, cudaStream_t s) {
-    const size_t smem = elem_smem_bytes(MODE, a.N, a.pv.nl_max, a.pv.ep_max, sizeof(T));
-    static size_t configured = 0;
-    if (smem > 48 * 1024 && smem > configured) {
-        cudaFuncSetAttribute(elem_kernel<T, MODE, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-        configured = smem;
+    if constexpr (MODE == MODE_JVP && sizeof(T) == 4) {
+        if (a.variant == 1) {
+            launch_elem_v<T, MODE, NT, 1>(a, grid, s);
+            return;
+        }
+        if (a.variant == 2) {
+            launch_elem_v<T, MODE, NT, 2>(a, grid, s);
+            return;
+        }
     }
-    elem_kernel<T, MODE, NT><<<grid, kBlock, smem, s>>>(a);
+    launch_elem_v<T, MODE, NT, 0>(a, grid, s);
 }
 
 // fixed-N instantiations for the instance counts of the workloads; any other N runs the generic kernel
@@ -717,18 +977,39 @@ void launch_elem(int mode, const ElemArgs<T> &a, int grid, cudaStream_t s) {
     }
 }
 
-template <typename T>
-void launch_batch_elem(int mode, const ElemArgs<T> *args, const int *first_item, int n_prob, int n_items,
-                       int *counter, size_t smem, int grid, cudaStream_t s) {
+template <typename T, int MODE, int VAR>
+static void launch_batch_var(const BatchGroup<T> &g, size_t smem, int grid, cudaStream_t s) {
     auto go = [&](auto kern) {
         if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-        kern<<<grid, kBlock, smem, s>>>(args, first_item, n_prob, n_items, counter);
+        grid = std::min(grid, resident_blocks(kern, ElemCfg<T, VAR>::block, smem));
+        kern<<<grid, ElemCfg<T, VAR>::block, smem, s>>>(g.args, g.bslots, g.bslot_stride, g.item_begin, g.item_end,
+                                                         g.counter);
     };
+    switch (g.N) {
+        case 9: go(batch_elem_kernel<T, MODE, 9, VAR>); break;
+        case 13: go(batch_elem_kernel<T, MODE, 13, VAR>); break;
+        case 21: go(batch_elem_kernel<T, MODE, 21, VAR>); break;
+        default: go(batch_elem_kernel<T, MODE, 0, VAR>); break;
+    }
+}
+
+// the paper-tangent pass in FP32 follows the batch's launch variant; every other pass runs variant 0
+template <typename T, int MODE>
+static void launch_batch_mode(const BatchGroup<T> &g, size_t smem, int grid, cudaStream_t s) {
+    if constexpr (MODE == MODE_JVP && sizeof(T) == 4) {
+        if (g.variant == 1) return launch_batch_var<T, MODE, 1>(g, smem, grid, s);
+        if (g.variant == 2) return launch_batch_var<T, MODE, 2>(g, smem, grid, s);
+    }
+    launch_batch_var<T, MODE, 0>(g, smem, grid, s);
+}
+
+template <typename T>
+void launch_batch_elem(int mode, const BatchGroup<T> &g, size_t smem, int grid, cudaStream_t s) {
     switch (mode) {
-        case MODE_RES: go(batch_elem_kernel<T, MODE_RES>); break;
-        case MODE_JVP: go(batch_elem_kernel<T, MODE_JVP>); break;
-        case MODE_JVE: go(batch_elem_kernel<T, MODE_JVE>); break;
-        default: go(batch_elem_kernel<T, MODE_DIAG>); break;
+        case MODE_RES: launch_batch_mode<T, MODE_RES>(g, smem, grid, s); break;
+        case MODE_JVP: launch_batch_mode<T, MODE_JVP>(g, smem, grid, s); break;
+        case MODE_JVE: launch_batch_mode<T, MODE_JVE>(g, smem, grid, s); break;
+        default: launch_batch_mode<T, MODE_DIAG>(g, smem, grid, s); break;
     }
 }
 
@@ -739,10 +1020,8 @@ void launch_geom(const double *xyz, const int *tets, int n_tets, double nu, T *g
 
 template void launch_elem<float>(int, const ElemArgs<float> &, int, cudaStream_t);
 template void launch_elem<double>(int, const ElemArgs<double> &, int, cudaStream_t);
-template void launch_batch_elem<float>(int, const ElemArgs<float> *, const int *, int, int, int *, size_t, int,
-                                       cudaStream_t);
-template void launch_batch_elem<double>(int, const ElemArgs<double> *, const int *, int, int, int *, size_t, int,
-                                        cudaStream_t);
+template void launch_batch_elem<float>(int, const BatchGroup<float> &, size_t, int, cudaStream_t);
+template void launch_batch_elem<double>(int, const BatchGroup<double> &, size_t, int, cudaStream_t);
 template void launch_geom<float>(const double *, const int *, int, double, float *, cudaStream_t);
 template void launch_geom<double>(const double *, const int *, int, double, double *, cudaStream_t);
 

@@ -18,15 +18,16 @@ enum Mode : int {
 };
 
 constexpr int kGeomStride = 16;       // per element: grad N_a (4 x 3), V, C_I nu^2 G:G, 2 pad
-constexpr int kBlock = 256;           // threads per CTA of the element kernel
-constexpr int kMaxN = 31;             // largest number of time instances supported
+constexpr int kMaxN = 31;
+constexpr int kJvpVariants = 3;       // launch variants of the FP32 paper-tangent element pass             // largest number of time instances supported
 constexpr double kCI = 3.0;           // Eq. (tau)
 // 4-point degree-2 Gauss rule on a tetrahedron (barycentric coordinates of the points)
 constexpr double kQA = 0.5854101966249685;
 constexpr double kQB = 0.1381966011250105;
 
 // Fields per local node staged in shared memory, by mode.
-// JVP stages y, v and H v (the F block is applied as rho M (H v): M and H commute); RES stages y and
+// JVP stages y, v and W = shift v + rho H v (the F block is applied as rho M (H v): M and H commute;
+// the pseudo-time shift uses the same mass matrix); RES stages y and
 // H u; JVE stages y, H u, v, H v.  Element contributions that need no instance coupling go straight to
 // global memory; RES and JVE accumulate T (3 fields) per patch node in shared memory for H T.
 __host__ __device__ constexpr int in_fields(int mode) {
@@ -38,18 +39,21 @@ __host__ __device__ constexpr int out_fields(int mode) {
 
 // Element patches: elements renumbered so each patch's elements are contiguous; each patch lists its
 // distinct nodes; each element stores its 4 nodes as local indices (uint8) into that list.
+// Per patch one slot of slot_ints(nl_max) ints (a multiple of 16 bytes): [0] first element, [1] element
+// count, [2] node count, [3] count of nodes with prescribed velocity, [4 + l] global id of local node l,
+// bit 31 set when its velocity is prescribed (Dirichlet).
+__host__ __device__ constexpr int slot_ints(int nl_max) { return 4 + ((nl_max + 3) & ~3); }
+constexpr uint32_t kDirBit = 0x80000000u;
+
 template <typename T>
 struct PatchView {
     int n_patches;
     int nl_max;                    // largest node count of a patch
     int ep_max;                    // largest element count of a patch
-    const int *eptr;               // [P+1]
-    const int *nptr;               // [P+1]
-    const int *nodes;              // [nptr[P]]
+    int slot_stride;               // ints per slot, slot_ints(nl_max)
+    const int *slots;              // [P][slot_stride]
     const uint32_t *lconn;         // [E]
     const T *geom;                 // [E][kGeomStride]
-    const int *dptr;               // [P+1] range of each patch's Dirichlet local nodes in dloc
-    const uint8_t *dloc;           // local indices of the patch nodes with Dirichlet velocity
 };
 
 template <typename T>
@@ -63,6 +67,7 @@ struct ElemArgs {
     int N;
     T rho, mu, shift;
     const double *shift_dev = nullptr;   // if set, the shift is read from device memory instead
+    int variant = 0;               // launch variant of the FP32 paper-tangent pass, [0, kJvpVariants)
 };
 
 // Boundary (Neumann) faces.
@@ -83,18 +88,28 @@ struct FaceArgs {
     T rho, beta;
 };
 
-size_t elem_smem_bytes(int mode, int N, int nl_max, int ep_max, size_t tsize);
+// shared memory of one element-pass block; slot_cap = 0: the patch set's own slot size
+size_t elem_smem_bytes(int mode, int N, int nl_max, int ep_max, size_t tsize, int slot_cap = 0);
 
 template <typename T>
 void launch_elem(int mode, const ElemArgs<T> &a, int grid, cudaStream_t s);
 template <typename T>
 void launch_geom(const double *xyz, const int *tets_patch_order, int n_tets, double nu, T *geom,
                  cudaStream_t s);
-// persistent element pass over the patches of several problems (args on the device; first_item[q] is the
-// first work item of problem q; *counter must be 0 at launch)
+// persistent element pass over the patches of several problems that share one instance count N: args on
+// the device; batch slot i (bslot_stride ints at bslots + i * bslot_stride) = [problem index, 0, 0, 0,
+// that problem's slot of the patch]; the group's items are [item_begin, item_end); *counter must be 0 at
+// launch; the layout's slot buffers take bslot_stride ints each
 template <typename T>
-void launch_batch_elem(int mode, const ElemArgs<T> *args, const int *first_item, int n_prob, int n_items,
-                       int *counter, size_t smem, int grid, cudaStream_t s);
+struct BatchGroup {
+    const ElemArgs<T> *args;
+    const int *bslots;
+    int bslot_stride, N, item_begin, item_end;
+    int variant;                   // launch variant of the FP32 paper-tangent pass
+    int *counter;
+};
+template <typename T>
+void launch_batch_elem(int mode, const BatchGroup<T> &g, size_t smem, int grid, cudaStream_t s);
 // outlet flow rates (resistance outlets only; Q must be cleared before) then face terms
 template <typename T>
 void launch_faces(int mode, const FaceArgs<T> &a, bool has_resistance, int n_out, cudaStream_t s);

@@ -92,6 +92,8 @@ SIGNATURES = {
     "hb_jacobi_diag_dev": ([_P, _VP, _VP, C.c_int, C.c_double, _VP], C.c_int),
     "hb_get_info": ([_P, C.POINTER(hb_info)], C.c_int),
     "hb_launch_count": ([_P], C.c_int64),
+    "hb_set_launch_variant": ([_P, C.c_int], C.c_int),
+    "hb_get_launch_variant": ([_P], C.c_int),
     "hb_profile_elem": ([_P, C.c_int], C.c_int),
     "hb_profile_read": ([_P, C.POINTER(C.c_double), C.POINTER(C.c_int64)], C.c_int),
     "hb_jv_dev_noalloc": ([_P, _VP, _VP, _VP, C.c_int, C.c_int, C.c_double, _VP], C.c_int),
@@ -336,6 +338,12 @@ class Problem:
 
     def launch_count(self) -> int:
         return int(lib().hb_launch_count(self._h))
+
+    def set_launch_variant(self, variant: int):
+        _check(lib().hb_set_launch_variant(self._h, int(variant)))
+
+    def launch_variant(self) -> int:
+        return int(lib().hb_get_launch_variant(self._h))
 
     def tune_patches(self, precision: int, candidates, reps: int = 5):
         """Autotune the element patch node cap; returns (best cap, ms per element pass)."""

@@ -1,5 +1,5 @@
-"""Batched operator application (one captured graph, one persistent element launch over many problems of
-different N) against per-problem calls, and patch autotuning."""
+"""Batched operator application (one captured graph, one persistent element launch per instance count over
+many problems of different N) against per-problem calls, and patch autotuning."""
 import numpy as np
 import pytest
 

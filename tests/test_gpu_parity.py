@@ -76,6 +76,24 @@ def test_residual_and_jv_across_instance_counts(n_h):
         assert relerr(gp.jv(y, v, 0, prec, 0.3), O.jv_paper(ora, y, v, shift=0.3)) < TOL[prec]
 
 
+@pytest.mark.parametrize("n_h", [0, 1, 4, 10, 15])
+def test_paper_tangent_launch_variants(n_h):
+    """Every launch variant of the FP32 paper-tangent pass (pairs of instances per thread, one instance
+    per thread at two block sizes) against the oracle, for compile-time and generic instance counts."""
+    spec = P.box_spec(seed=70 + n_h, n_h=n_h, n=(6, 5, 4))
+    ora = P.oracle_problem(spec)
+    gp = P.gpu_problem(spec)
+    y = I.random_state(spec.mesh.n_nodes, spec.N, 71)
+    v = I.random_state(spec.mesh.n_nodes, spec.N, 72)
+    ref = O.jv_paper(ora, y, v, shift=0.8)
+    for var in (0, 1, 2):
+        gp.set_launch_variant(var)
+        assert gp.launch_variant() == var
+        assert relerr(gp.jv(y, v, 0, 1, 0.8), ref) < TOL[1], var
+    with pytest.raises(RuntimeError):
+        gp.set_launch_variant(3)
+
+
 def test_womersley_pipe_parabolic_profile_and_patches():
     """Womersley pipe (~3,000 tets, N = 9) with the library's own parabolic profile (NULL) against the
     oracle given the input generator's profile: both follow the same definition independently."""
