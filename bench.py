@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
     ap.add_argument("--extra", action="store_true", help="also time residual / exact Jv / FP64 rates")
+    ap.add_argument("--krylov-probe", action="store_true",
+                    help="also run one outer solver step (mixed precision, GMRES(30), 60 iterations) on the "
+                         "benchmark workload, so the Arnoldi sweeps run at full vector size")
     return ap.parse_args()
 
 
@@ -464,6 +467,13 @@ def run_ours(args, dist: Dist, spec, config):
                 result["time_to_solve"] = {"error": repr(e)}
         if not args.skip_cpu:
             result["cpu_baseline"] = cpu_baseline(spec)
+    if args.krylov_probe:
+        torch.cuda.synchronize()
+        rep = prob.solve(precision=1, max_steps=1, gmres_restart=30, max_gmres=60, rtol=1e-12,
+                         gmres_rtol_pseudo=1e-12, gmres_rtol_newton=1e-12, verbose=0, check=False)
+        result["krylov_probe"] = {"gmres_iters": rep["gmres_iters"], "jv_calls": rep["jv_calls"],
+                                  "seconds": rep["seconds"], "unknowns": n * 4 * N,
+                                  "ms_per_gmres_iter": 1e3 * rep["seconds"] / max(1, rep["gmres_iters"])}
     prob.close()
     if dist.rank == 0:
         print(json.dumps(result), flush=True)

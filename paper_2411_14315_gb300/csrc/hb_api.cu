@@ -136,7 +136,7 @@ struct hb_problem {
     int sm_count = 148;
     // Krylov storage (lazily sized)
     int km = 0;
-    DBuf<double> kV, kz64, kdx, kdiag, kres, ktmp, kh;
+    DBuf<double> kV, kz64, kdx, kdiag, kres, ktmp, kh;   // kdiag: inverse Jacobi diagonal during a solve
     DBuf<float> kz32, kw32, ky32, kdiag32;
     // graph-captured GMRES restart cycles, one per operator (paper tangent / exact)
     struct CycleGraph {
@@ -796,9 +796,17 @@ hb_status record_cycle(hb_problem *p, const OpCtx &c, int m) {
     for (int j = 0; j < m; ++j) {
         double *vj = V + int64_t(j) * nd;
         double *w = V + int64_t(j + 1) * nd;
-        launch_precond<double>(vj, p->kdiag.p, p->kz64.p, nd, s);
-        HB_LAUNCHED(p, 1);
-        HB_TRY(apply_A(p, c, p->kz64.p, w));
+        if (c.precision == 1) {
+            // mixed path: the preconditioned direction goes straight to the FP32 operator
+            launch_precond<float>(vj, p->kdiag.p, p->kz32.p, nd, s);
+            HB_TRY(apply_op<float>(p, c.mode, p->ky32.p, p->kz32.p, p->kw32.p, c.shift, s, c.shift_dev));
+            launch_convert<float, double>(p->kw32.p, w, nd, s);
+            HB_LAUNCHED(p, 2);
+        } else {
+            launch_precond<double>(vj, p->kdiag.p, p->kz64.p, nd, s);
+            HB_LAUNCHED(p, 1);
+            HB_TRY(apply_op<double>(p, c.mode, p->y.p, p->kz64.p, w, c.shift, s, c.shift_dev));
+        }
         launch_multidot(V, nd, j + 1, w, nd, p->scratch.p, G + L.h1, s);
         launch_multiaxpy_norm(V, nd, j + 1, G + L.h1, w, nd, p->scratch.p, G + L.nrm2, s);
         launch_reorth_gate(G + L.h1 + (j + 1), G + L.nrm2, p->gate.p, s);
@@ -1569,6 +1577,8 @@ static hb_status solve_impl(hb_problem *p, const hb_solve_opts &o, hb_report *re
         } else {
             HB_TRY(apply_op<double>(p, MODE_DIAG, p->y.p, nullptr, p->kdiag.p, c.shift, p->stream, c.shift_dev));
         }
+        launch_reciprocal(p->kdiag.p, p->kdiag.p, nd, p->stream);   // kdiag holds the inverse diagonal
+        HB_LAUNCHED(p, 1);
         launch_scale_copy(-1.0, r, b, nd, p->stream);
         HB_LAUNCHED(p, 1);
         int its = 0, jvc = 0;

@@ -130,12 +130,13 @@ template <typename A, typename B>
 void launch_convert(const A *x, B *y, int64_t n, cudaStream_t s);
 void launch_axpy(double a, const double *x, double *y, int64_t n, cudaStream_t s);
 void launch_scale_copy(double a, const double *x, double *y, int64_t n, cudaStream_t s);
+// z = x * dinv in z's precision (right Jacobi preconditioning); dinv = 1 / d
 template <typename T>
-void launch_precond(const double *x, const double *d, T *z, int64_t n, cudaStream_t s);
+void launch_precond(const double *x, const double *dinv, T *z, int64_t n, cudaStream_t s);
+void launch_reciprocal(const double *d, double *dinv, int64_t n, cudaStream_t s);   // d == dinv allowed
 // partials[nb * (k + 1)]; result[k + 1] = (V_j . w for j < k, w . w)
 // With a non-null gate that holds 0 at run time, launch_multidot writes zeros and launch_multiaxpy_norm
 // leaves w and result unchanged (the second, conditional pass of classical Gram-Schmidt).
-int multidot_blocks(int64_t n);
 void launch_multidot(const double *V, int64_t ld, int k, const double *w, int64_t n, double *partials,
                      double *result, cudaStream_t s, const int *gate = nullptr);
 // w -= sum_j h[j] V_j; result[0] = ||w||^2 after the update (partials scratch as above)

@@ -4,12 +4,14 @@
 // scratch array, then one pass that sums the partials in a fixed order.
 #include "hb_internal.cuh"
 
+#include <algorithm>
+#include <utility>
+
 namespace hb {
 
 namespace {
 
 constexpr int kVB = 256;             // threads per block
-constexpr int kChunk = kVB * 8;      // vector elements per block-chunk in the batched dot
 constexpr int kMaxK = 256;           // largest number of simultaneous dot products
 
 inline int nblk(int64_t n, int b) { return int((n + b - 1) / b); }
@@ -41,11 +43,17 @@ __global__ void scale_copy_kernel(double a, const double *__restrict__ x, double
         y[i] = a * x[i];
 }
 
+// z = x * dinv (right Jacobi preconditioning with the stored inverse diagonal), in z's precision
 template <typename T>
-__global__ void precond_kernel(const double *__restrict__ x, const double *__restrict__ d, T *__restrict__ z,
+__global__ void precond_kernel(const double *__restrict__ x, const double *__restrict__ dinv, T *__restrict__ z,
                                int64_t n) {
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
-        z[i] = T(x[i] / d[i]);
+        z[i] = T(x[i] * dinv[i]);
+}
+
+__global__ void reciprocal_kernel(const double *d, double *dinv, int64_t n) {   // may run in place
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        dinv[i] = 1.0 / d[i];
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -54,46 +62,39 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// partials[b * (k+1) + j] = sum over this block's chunks of V_j . w (j < k) and w . w (j = k)
-__global__ void __launch_bounds__(kVB) multidot_kernel(const double *__restrict__ V, int64_t ld, int k,
+// partials[b * pstride + col0 + j] = this block's share of V_j . w (j < K) and partials[b * pstride + wcol]
+// its share of w . w.  Each thread keeps one FP64 accumulator per basis vector in registers over its whole
+// grid-stride range (K, the number of vectors, is a compile-time constant), so every element of w is read
+// once and all K + 1 loads of an element are in flight together; the cross-thread sums happen once per
+// block at the end.
+template <int K>
+__global__ void __launch_bounds__(kVB) multidot_kernel(const double *__restrict__ V, int64_t ld,
                                                        const double *__restrict__ w, int64_t n,
-                                                       double *__restrict__ partials, const int *gate) {
+                                                       double *__restrict__ partials, int pstride, int col0,
+                                                       int wcol, const int *gate) {
     if (gate && *gate == 0) return;
-    __shared__ double sw[kChunk];
-    __shared__ double sp[kVB / 32][kMaxK + 1];
+    __shared__ double sp[kVB / 32][K + 1];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int j = tid; j < (kVB / 32) * (kMaxK + 1); j += kVB) (&sp[0][0])[j] = 0.0;
-    __syncthreads();
-    for (int64_t c0 = int64_t(blockIdx.x) * kChunk; c0 < n; c0 += int64_t(gridDim.x) * kChunk) {
-        const int m = int(n - c0 < kChunk ? n - c0 : kChunk);
-        for (int t = tid; t < kChunk; t += kVB) sw[t] = t < m ? w[c0 + t] : 0.0;
-        __syncthreads();
-        for (int j = 0; j <= k; ++j) {
-            double s = 0.0;
-            if (j < k) {
-                const double *v = V + int64_t(j) * ld + c0;
+    double acc[K + 1];
 #pragma unroll
-                for (int t = 0; t < kChunk / kVB; ++t) {
-                    const int idx = tid + t * kVB;
-                    if (idx < m) s += v[idx] * sw[idx];
-                }
-            } else {
+    for (int j = 0; j <= K; ++j) acc[j] = 0.0;
+    for (int64_t i = int64_t(blockIdx.x) * kVB + tid; i < n; i += int64_t(gridDim.x) * kVB) {
+        const double wi = w[i];
 #pragma unroll
-                for (int t = 0; t < kChunk / kVB; ++t) {
-                    const int idx = tid + t * kVB;
-                    s += sw[idx] * sw[idx];
-                }
-            }
-            s = warp_sum(s);
-            if (lane == 0) sp[warp][j] += s;
-        }
-        __syncthreads();
+        for (int j = 0; j < K; ++j) acc[j] = fma(V[int64_t(j) * ld + i], wi, acc[j]);
+        acc[K] = fma(wi, wi, acc[K]);
     }
-    for (int j = tid; j <= k; j += kVB) {
-        double s = 0.0;
 #pragma unroll
-        for (int q = 0; q < kVB / 32; ++q) s += sp[q][j];
-        partials[int64_t(blockIdx.x) * (k + 1) + j] = s;
+    for (int j = 0; j <= K; ++j) {
+        const double t = warp_sum(acc[j]);
+        if (lane == 0) sp[warp][j] = t;
+    }
+    __syncthreads();
+    for (int j = tid; j <= K; j += kVB) {
+        double t = 0.0;
+#pragma unroll
+        for (int q = 0; q < kVB / 32; ++q) t += sp[q][j];
+        partials[int64_t(blockIdx.x) * pstride + (j < K ? col0 + j : wcol)] = t;
     }
 }
 
@@ -120,7 +121,8 @@ __global__ void finish_kernel(const double *__restrict__ partials, int nb, int s
     }
 }
 
-// w -= sum_j h[j] V_j, then partials[b] = this block's share of ||w||^2
+// w -= sum_j h[j] V_j, then partials[b] = this block's share of ||w||^2 (two elements per thread step,
+// so twice the loads are in flight)
 __global__ void __launch_bounds__(kVB) multiaxpy_norm_kernel(const double *__restrict__ V, int64_t ld, int k,
                                                              const double *__restrict__ h, double *__restrict__ w,
                                                              int64_t n, double *__restrict__ partials,
@@ -131,11 +133,22 @@ __global__ void __launch_bounds__(kVB) multiaxpy_norm_kernel(const double *__res
     for (int j = threadIdx.x; j < k; j += kVB) sh[j] = h[j];
     __syncthreads();
     double s = 0.0;
-    for (int64_t i = int64_t(blockIdx.x) * kVB + threadIdx.x; i < n; i += int64_t(gridDim.x) * kVB) {
-        double x = w[i];
-        for (int j = 0; j < k; ++j) x -= sh[j] * V[int64_t(j) * ld + i];
+    const int64_t stride = int64_t(gridDim.x) * kVB;
+    for (int64_t i = int64_t(blockIdx.x) * kVB + threadIdx.x; i < n; i += 2 * stride) {
+        const int64_t i2 = i + stride;
+        const bool two = i2 < n;
+        double x = w[i], x2 = two ? w[i2] : 0.0;
+        for (int j = 0; j < k; ++j) {
+            const double *vj = V + int64_t(j) * ld;
+            x = fma(-sh[j], vj[i], x);
+            if (two) x2 = fma(-sh[j], vj[i2], x2);
+        }
         w[i] = x;
-        s += x * x;
+        s = fma(x, x, s);
+        if (two) {
+            w[i2] = x2;
+            s = fma(x2, x2, s);
+        }
     }
     s = warp_sum(s);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
@@ -230,10 +243,38 @@ int stream_grid(int64_t n) {
 
 }  // namespace
 
+// One full wave of multidot_kernel<K> (the grid-stride loop gives every block the same share, so a
+// partial second wave would double the time), at most one block per 2048 elements.
+template <int K>
 int multidot_blocks(int64_t n) {
-    const int cap = sm_count() * 2;
-    const int need = nblk(n, kChunk);
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, multidot_kernel<K>, kVB, 0);
+        if (per_sm <= 0) per_sm = 1;
+    }
+    const int cap = sm_count() * per_sm;
+    const int need = nblk(n, kVB * 8);
     return need < cap ? (need > 0 ? need : 1) : cap;
+}
+
+// Partials of one tile of K vectors; returns the block count used.
+template <int K>
+int multidot_tile(const double *V, int64_t ld, const double *w, int64_t n, double *partials, int pstride,
+                  int col0, int wcol, int nb, cudaStream_t s, const int *gate) {
+    if (nb == 0) nb = multidot_blocks<K>(n);
+    multidot_kernel<K><<<nb, kVB, 0, s>>>(V, ld, w, n, partials, pstride, col0, wcol, gate);
+    return nb;
+}
+
+template <int... Ks>
+int multidot_dispatch(std::integer_sequence<int, Ks...>, int k, const double *V, int64_t ld, const double *w,
+                      int64_t n, double *partials, int pstride, int col0, int wcol, int nb, cudaStream_t s,
+                      const int *gate) {
+    int used = 0;
+    ((k == Ks + 1 ? (used = multidot_tile<Ks + 1>(V, ld, w, n, partials, pstride, col0, wcol, nb, s, gate), 0)
+                  : 0),
+     ...);
+    return used;
 }
 
 template <typename A, typename B>
@@ -250,20 +291,35 @@ void launch_scale_copy(double a, const double *x, double *y, int64_t n, cudaStre
 }
 
 template <typename T>
-void launch_precond(const double *x, const double *d, T *z, int64_t n, cudaStream_t s) {
-    if (n > 0) precond_kernel<T><<<stream_grid(n), kVB, 0, s>>>(x, d, z, n);
+void launch_precond(const double *x, const double *dinv, T *z, int64_t n, cudaStream_t s) {
+    if (n > 0) precond_kernel<T><<<stream_grid(n), kVB, 0, s>>>(x, dinv, z, n);
+}
+
+void launch_reciprocal(const double *d, double *dinv, int64_t n, cudaStream_t s) {
+    if (n > 0) reciprocal_kernel<<<stream_grid(n), kVB, 0, s>>>(d, dinv, n);
 }
 
 void launch_multidot(const double *V, int64_t ld, int k, const double *w, int64_t n, double *partials,
                      double *result, cudaStream_t s, const int *gate) {
-    const int nb = multidot_blocks(n);
-    multidot_kernel<<<nb, kVB, 0, s>>>(V, ld, k, w, n, partials, gate);
+    // tiles of up to 32 vectors (w is read once per tile), all with the first tile's block count; every
+    // tile also writes the same w . w column, computed identically
+    int nb = 0;
+    for (int j0 = 0; j0 < k; j0 += 32) {
+        const int kt = k - j0 < 32 ? k - j0 : 32;
+        nb = multidot_dispatch(std::make_integer_sequence<int, 32>{}, kt, V + int64_t(j0) * ld, ld, w, n, partials,
+                               k + 1, j0, k, nb, s, gate);
+    }
     finish_kernel<<<k + 1, 256, 0, s>>>(partials, nb, k + 1, k + 1, result, gate, 1);
 }
 
 void launch_multiaxpy_norm(const double *V, int64_t ld, int k, const double *h, double *w, int64_t n,
                            double *partials, double *result, cudaStream_t s, const int *gate) {
-    const int nb = stream_grid(n);
+    static int per_sm = 0;                      // one full wave (equal shares per block)
+    if (per_sm == 0) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, multiaxpy_norm_kernel, kVB, 0);
+        if (per_sm <= 0) per_sm = 1;
+    }
+    const int nb = std::min(stream_grid(n), sm_count() * per_sm);
     multiaxpy_norm_kernel<<<nb, kVB, 0, s>>>(V, ld, k, h, w, n, partials, gate);
     finish_kernel<<<1, 256, 0, s>>>(partials, nb, 1, 1, result, gate, 0);
 }

@@ -62,6 +62,30 @@ def box_spec(seed=11, n_h=2, n=(6, 4, 4), resistance=True, beta=0.2, jitter=0.2)
     return s
 
 
+def channel_spec(n=(4, 3, 3), n_h: int = 2, mu: float = 0.3, seed: int = 90) -> Spec:
+    """Jittered box channel: uniform inflow on x-min with harmonics 0.3/k (cos) and 0.2/k (sin) on a unit
+    mean, a pressure outlet on x-max (mean 0.3, first harmonic 0.1 cos / -0.05 sin), no-slip on the other
+    four faces; rho = 1.1, T = 1.7.  Small and well conditioned: the oracle's solve converges in seconds."""
+    m = I.box_mesh(*n, lx=1.5, jitter=0.2, seed=seed)
+    tag = m.face_tag.copy()
+    tag[tag >= 3] = 0
+    k = np.arange(1, n_h + 1)
+    a = np.zeros(n_h + 1)
+    b = np.zeros(n_h + 1)
+    a[0] = 1.0
+    a[1:] = 0.3 / k
+    b[1:] = 0.2 / k
+    pa = np.zeros(n_h + 1)
+    pb = np.zeros(n_h + 1)
+    pa[0] = 0.3
+    if n_h >= 1:
+        pa[1], pb[1] = 0.1, -0.05
+    s = Spec(m, 1.1, mu, 1.7, n_h, beta=0.2, tags=tag)
+    s.inflows.append((1, I.uniform_profile(m, [1], [1.0, 0.0, 0.0]), a, b))
+    s.outlets_p.append((2, pa, pb))
+    return s
+
+
 def womersley_spec(level: int = 1, n_h: int = 4, seed: int = 1001, parabolic_none: bool = True) -> Spec:
     """Straight pipe R = 1, L = 5, rho = 1, mu = 0.04, Womersley number 4 (omega = 16 nu), mean
     Reynolds number 100 (mean velocity 2), parabolic inflow scaled by seeded harmonics, traction-free

@@ -2,8 +2,8 @@
 from __future__ import annotations
 
 from paper_2411_14315_gb300 import inputs as I
-from paper_2411_14315_gb300.workloads import (Spec, box_spec, dirichlet_nodes, glenn_spec,  # noqa: F401
-                                              womersley_spec)
+from paper_2411_14315_gb300.workloads import (Spec, box_spec, channel_spec, dirichlet_nodes,  # noqa: F401
+                                              glenn_spec, womersley_spec)
 
 
 def oracle_problem(spec: Spec, convection: bool = True):
