@@ -224,8 +224,8 @@ hb_status hb_attach_learned(hb_problem *p, hb_mpnn *net);
  * clearing, one persistent element pass per distinct instance count N (specialised for that N) whose
  * work items (problem, patch) are taken from a global counter (so large and small problems share the
  * SMs; the FP32 paper-tangent pass takes the first problem's launch variant, see hb_set_launch_variant),
- * then the boundary terms and Dirichlet rows of each problem.  All problems must live on one device; their
- * boundary data are prepared at creation.  The graph is captured on first use and again whenever the
+ * then the boundary terms of each problem (prescribed velocity rows are written by the element pass).
+ * All problems must live on one device; their boundary data are prepared at creation.  The graph is captured on first use and again whenever the
  * operands, kind or shift change.  Work is ordered after `stream` (NULL: the first problem's stream) and
  * `stream` waits for it. */
 typedef struct hb_batch hb_batch;

@@ -659,10 +659,6 @@ hb_status apply_op(hb_problem *p, int mode, const T *y, const T *v, T *out, doub
         launch_faces<T>(mode, fa, p->has_res, p->n_out, s);
         HB_LAUNCHED(p, p->has_res ? 2 : 1);
     }
-    if (p->n_dir > 0) {
-        launch_dirichlet_rows<T>(mode, p->d_dir_nodes.p, p->n_dir, v, out, N, s);
-        HB_LAUNCHED(p, 1);
-    }
     return HB_OK;
 }
 
@@ -1042,10 +1038,6 @@ hb_status apply_jv_noalloc(hb_problem *p, int mode, const T *y, const T *v, T *o
         if (p->has_res) HB_CUDA(cudaMemsetAsync(qscratch, 0, size_t(p->n_out) * N * sizeof(T), s));
         launch_faces<T>(mode, fa, p->has_res, p->n_out, s);
         HB_LAUNCHED(p, p->has_res ? 2 : 1);
-    }
-    if (p->n_dir > 0) {
-        launch_dirichlet_rows<T>(mode, p->d_dir_nodes.p, p->n_dir, v, out, N, s);
-        HB_LAUNCHED(p, 1);
     }
     return HB_OK;
 }
@@ -1807,10 +1799,6 @@ hb_status batch_record(hb_batch *b) {
                 st = fail(HB_ERR_CUDA, "memset in batch capture");
             launch_faces<T>(b->mode, fa, p->has_res, p->n_out, s);
             p0->launches += p->has_res ? 2 : 1;
-        }
-        if (p->n_dir > 0) {
-            launch_dirichlet_rows<T>(b->mode, p->d_dir_nodes.p, p->n_dir, v, out, p->N, s);
-            p0->launches += 1;
         }
     }
     cudaGraph_t graph = nullptr;

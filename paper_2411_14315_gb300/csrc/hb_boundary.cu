@@ -1,5 +1,5 @@
 // Boundary and time-series kernels of libhbgls: Neumann faces (traction and backflow stabilisation,
-// Sec. 2.3), resistance-outlet flow rates, Dirichlet rows, sampling of boundary waveforms at the
+// Sec. 2.3), resistance-outlet flow rates, sampling of boundary waveforms at the
 // instances (Eqs. upgh_def, upghharm) and the real discrete Fourier transforms of the state
 // (Eq. upghdft; reconstruction of Sec. 3.2).
 #include "hb_internal.cuh"
@@ -115,23 +115,10 @@ __global__ void face_kernel(FaceArgs<T> a) {
         }
     }
 #pragma unroll
-    for (int b = 0; b < 3; ++b)
+    for (int b = 0; b < 3; ++b) {
+        if (a.flag[nd[b]] & 1) continue;       // prescribed velocity rows are set by the element pass
 #pragma unroll
         for (int k = 0; k < 3; ++k) atomicAdd(a.out + size_t(nd[b]) * N4 + k * N + n, c[b][k]);
-}
-
-// Dirichlet velocity rows: 0 (residual), 1 (diagonal) or v (Jacobian: identity).  One warp per node;
-// its 3 N velocity values are contiguous.
-template <typename T, int MODE>
-__global__ void dirichlet_rows_kernel(const int *__restrict__ dir_nodes, int n_dir, const T *__restrict__ v,
-                                      T *__restrict__ out, int N) {
-    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (w >= n_dir) return;
-    const size_t base = size_t(dir_nodes[w]) * 4 * N;
-    for (int r = lane; r < 3 * N; r += 32) {
-        if (MODE == MODE_RES) out[base + r] = T(0);
-        else if (MODE == MODE_DIAG) out[base + r] = T(1);
-        else out[base + r] = v[base + r];
     }
 }
 
@@ -232,16 +219,6 @@ void launch_faces(int mode, const FaceArgs<T> &a, bool has_resistance, int n_out
     }
 }
 
-template <typename T>
-void launch_dirichlet_rows(int mode, const int *dir_nodes, int n_dir, const T *v, T *out, int N,
-                           cudaStream_t s) {
-    if (n_dir == 0) return;
-    const int g = nblk(int64_t(n_dir) * 32, 256);
-    if (mode == MODE_RES) dirichlet_rows_kernel<T, MODE_RES><<<g, 256, 0, s>>>(dir_nodes, n_dir, v, out, N);
-    else if (mode == MODE_DIAG) dirichlet_rows_kernel<T, MODE_DIAG><<<g, 256, 0, s>>>(dir_nodes, n_dir, v, out, N);
-    else dirichlet_rows_kernel<T, MODE_JVP><<<g, 256, 0, s>>>(dir_nodes, n_dir, v, out, N);
-}
-
 void launch_sample_waveforms(const double *coef, int n_wave, int n_h, int N, double T, double *W,
                              cudaStream_t s) {
     (void)T;
@@ -266,7 +243,5 @@ void launch_harmonics(const double *in, double *out, int64_t rows, int N, int n_
 
 template void launch_faces<float>(int, const FaceArgs<float> &, bool, int, cudaStream_t);
 template void launch_faces<double>(int, const FaceArgs<double> &, bool, int, cudaStream_t);
-template void launch_dirichlet_rows<float>(int, const int *, int, const float *, float *, int, cudaStream_t);
-template void launch_dirichlet_rows<double>(int, const int *, int, const double *, double *, int, cudaStream_t);
 
 }  // namespace hb

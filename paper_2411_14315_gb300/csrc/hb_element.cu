@@ -306,7 +306,7 @@ __device__ __forceinline__ void jvp_lanes(int e, int n0, int d1, int Nrt, T rho,
             L val = a == 0 ? lsub(cW, gz0) : ladd(cW, gz[a - 1]);
             val = lfma(kd, ldot3(uq[a], gV[i]), val);
             val = lfma(m20, Wa[a], val);
-            lred(go[a] + i * N, val, d1);
+            if (sNode[lo[a]] >= 0) lred(go[a] + i * N, val, d1);   // prescribed velocity rows are set apart
         }
     }
 }
@@ -371,9 +371,11 @@ __device__ __forceinline__ void element_instance(int e, int n, int Nrt, T rho, T
             const T gg = gN[a][0] * gN[a][0] + gN[a][1] * gN[a][1] + gN[a][2] * gN[a][2];
             const T dv = dvel[a] + w * rho * qb * udNs[a] + mu * V * gg + shift * V * T(0.1);
             const T dp = (w / rho) * taus * gg;
-            atomicAdd(go[a], dv);
-            atomicAdd(go[a] + N, dv);
-            atomicAdd(go[a] + 2 * N, dv);
+            if (sNode[lo[a]] >= 0) {            // prescribed velocity rows are set apart
+                atomicAdd(go[a], dv);
+                atomicAdd(go[a] + N, dv);
+                atomicAdd(go[a] + 2 * N, dv);
+            }
             atomicAdd(go[a] + 3 * N, dp);
         }
         return;
@@ -438,8 +440,10 @@ __device__ __forceinline__ void element_instance(int e, int n, int Nrt, T rho, T
                 const T visc = gN[a][0] * gU[i][0] + gN[a][1] * gU[i][1] + gN[a][2] * gU[i][2];
                 const T vq = qm[a][i] + w * rho * qb * convs[i] + mu * V * visc - V * gN[a][i] * pbar;
                 const T vt = tt[a][i] + rho * m20 * (usum[i] + u[a][i]) - w * qb * S[i];
-                atomicAdd(go[a] + i * N, vq);
-                atomicAdd(sT + lo[a] * N3 + i * N + n, vt);
+                if (sNode[lo[a]] >= 0) {        // prescribed velocity rows are set apart
+                    atomicAdd(go[a] + i * N, vq);
+                    atomicAdd(sT + lo[a] * N3 + i * N + n, vt);
+                }
             }
             const T qc = w * div + (w / rho) * (gN[a][0] * S[0] + gN[a][1] * S[1] + gN[a][2] * S[2]);
             atomicAdd(go[a] + 3 * N, qc);
@@ -531,8 +535,10 @@ __device__ __forceinline__ void element_instance(int e, int n, int Nrt, T rho, T
                 const T mv = m20 * (dvsum[i] + dv[a][i]);
                 const T vq = qm[a][i] + w * rho * qb * dconvs[i] + mu * V * visc - V * gN[a][i] * pbar + shift * mv;
                 const T vt = tt[a][i] + rho * mv - w * qb * S[i];
-                atomicAdd(go[a] + i * N, vq);
-                atomicAdd(sT + lo[a] * N3 + i * N + n, vt);
+                if (sNode[lo[a]] >= 0) {        // prescribed velocity rows are set apart
+                    atomicAdd(go[a] + i * N, vq);
+                    atomicAdd(sT + lo[a] * N3 + i * N + n, vt);
+                }
             }
             const T qc = w * div + (w / rho) * (gN[a][0] * S[0] + gN[a][1] * S[1] + gN[a][2] * S[2]);
             atomicAdd(go[a] + 3 * N, qc);
@@ -723,6 +729,19 @@ __device__ __forceinline__ void patch_pass(const ElemArgs<T> &a, const PatchSmem
     }
 
     prefetch();
+    // prescribed velocity rows of the output (no element or face term reaches them): 0 for the
+    // residual (left from the clearing), 1 for the Jacobi diagonal, v (identity) for Jacobian products;
+    // patches sharing a node store the same values
+    if constexpr (MODE != MODE_RES) {
+        if (nd > 0) {
+            for (int i = tid; i < nl * N3; i += nt) {
+                const int l = i / N3;
+                if (sNode[l] >= 0) continue;
+                const size_t g = size_t(uint32_t(sNode[l]) & ~kDirBit) * N4 + (i - l * N3);
+                a.out[g] = MODE == MODE_DIAG ? T(1) : a.v[g];
+            }
+        }
+    }
     if constexpr (MODE == MODE_JVP) {
         // a thread takes instances k and k + NP of one element (FP32 pairs; FP64: NP = N, one instance)
         constexpr int LW = int(sizeof(L) / sizeof(T));
@@ -764,7 +783,7 @@ __device__ __forceinline__ void patch_pass(const ElemArgs<T> &a, const PatchSmem
                 val = T(0);
                 for (int k = 0; k < N; ++k) val += h[k] * t[k];
             }
-            atomicAdd(a.out + size_t(uint32_t(sNode[l]) & ~kDirBit) * N4 + r, val);
+            if (sNode[l] >= 0) atomicAdd(a.out + size_t(sNode[l]) * N4 + r, val);
         }
     }
     __syncthreads();

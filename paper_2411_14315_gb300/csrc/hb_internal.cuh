@@ -113,9 +113,6 @@ void launch_batch_elem(int mode, const BatchGroup<T> &g, size_t smem, int grid, 
 // outlet flow rates (resistance outlets only; Q must be cleared before) then face terms
 template <typename T>
 void launch_faces(int mode, const FaceArgs<T> &a, bool has_resistance, int n_out, cudaStream_t s);
-template <typename T>
-void launch_dirichlet_rows(int mode, const int *dir_nodes, int n_dir, const T *v, T *out, int N,
-                           cudaStream_t s);
 
 // sampling of boundary waveforms (Eq. upgh_def at the instances of Eq. upghharm)
 void launch_sample_waveforms(const double *coef, int n_wave, int n_h, int N, double T, double *W,
