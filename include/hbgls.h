@@ -109,7 +109,12 @@ typedef struct {
     int max_steps;            /* outer (pseudo + Newton) step cap                                      */
     double dt_pseudo;         /* pseudo time step; <= 0 selects the CFL rule of Sec. 2.3               */
     double cfl;               /* CFL number of that rule (1)                                           */
-    int use_learned;          /* 1: start from the learned warm start if one is attached               */
+    int use_learned;          /* with a network attached (not the paper's method): 1 = start from its
+                                 prediction (warm start); 2 = learned correction step: start from the
+                                 current state and, before each linear solve, take the least-squares
+                                 multiple of (prediction - state) against its Jacobian image, then plain
+                                 GMRES on the remaining residual (the fallback when the prediction does
+                                 not help); HB_ERR_INVALID_ARG for other values                          */
     int verbose;              /* print one line per outer step to stderr                               */
     int ser;                  /* 1: switched evolution relaxation -- the pseudo step grows as
                                  ||r0|| / ||r|| (an extension; the paper keeps dt fixed; the converged
@@ -216,7 +221,8 @@ hb_status hb_mpnn_graph(hb_mpnn *net, hb_problem *p, float *x, int32_t *src, int
                         int64_t *n_edges);
 /* Set the problem's state to the prediction (Dirichlet values imposed on top). */
 hb_status hb_mpnn_warm_start(hb_mpnn *net, hb_problem *p);
-/* Attach a network (not owned) so that hb_solve with use_learned = 1 starts from its prediction. */
+/* Attach a network (not owned) so that hb_solve with use_learned = 1 starts from its prediction and
+ * with use_learned = 2 takes learned correction steps towards it. */
 hb_status hb_attach_learned(hb_problem *p, hb_mpnn *net);
 
 /* ---- batches of problems (many vessels of uneven size and N in one graph) ---------------------------

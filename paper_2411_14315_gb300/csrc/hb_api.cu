@@ -151,6 +151,8 @@ struct hb_problem {
     double shift_host = 0;
     // element-kernel timing
     bool prof_on = false;
+    DBuf<double> ylearn, kd;              // learned prediction and the direction towards it (use_learned 2)
+    bool learned_dir = false;
     int jvp_variant = 1;                  // launch variant of the FP32 paper-tangent pass
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev;
     size_t prof_used = 0;
@@ -733,6 +735,15 @@ hb_status dev_norm(hb_problem *p, const double *x, int64_t n, double &out) {
     HB_CUDA(cudaMemcpyAsync(&v, p->small.p, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
     HB_CUDA(cudaStreamSynchronize(p->stream));
     out = std::sqrt(v);
+    return HB_OK;
+}
+
+hb_status dev_dot(hb_problem *p, const double *x, const double *y, int64_t n, double &out) {
+    HB_TRY(dalloc(p, p->small, 512));
+    launch_dot(x, y, n, p->scratch.p, p->small.p, p->stream);
+    HB_LAUNCHED(p, 2);
+    HB_CUDA(cudaMemcpyAsync(&out, p->small.p, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+    HB_CUDA(cudaStreamSynchronize(p->stream));
     return HB_OK;
 }
 
@@ -1487,9 +1498,26 @@ hb_status hb_solve(hb_problem *p, const hb_solve_opts *opts, hb_report *rep) {
     HB_TRY(check_precision(o.precision));
     if (o.gmres_restart < 1 || o.gmres_restart > 200) return fail(HB_ERR_INVALID_ARG, "gmres_restart must be in [1, 200]");
     HB_CUDA(cudaSetDevice(p->device));
+    if (o.use_learned < 0 || o.use_learned > 2) return fail(HB_ERR_INVALID_ARG, "use_learned must be 0, 1 or 2");
+    p->learned_dir = false;
     if (o.use_learned) {
         if (!p->learned) return fail(HB_ERR_STATE, "use_learned set but no network attached (hb_attach_learned)");
-        HB_TRY(hb_mpnn_warm_start(p->learned, p));
+        if (o.use_learned == 2) {
+            // keep the prediction as a target direction; the solve starts from the state it had
+            HB_TRY(prepare_bc(p));
+            if (!p->y_set) HB_TRY(default_initial(p));
+            const size_t nd = size_t(p->n_nodes) * 4 * p->N;
+            HB_TRY(dalloc(p, p->ylearn, nd));
+            HB_TRY(dalloc(p, p->kd, nd));
+            HB_CUDA(cudaMemcpyAsync(p->kd.p, p->y.p, nd * sizeof(double), cudaMemcpyDeviceToDevice, p->stream));
+            HB_TRY(hb_mpnn_warm_start(p->learned, p));
+            HB_CUDA(cudaMemcpyAsync(p->ylearn.p, p->y.p, nd * sizeof(double), cudaMemcpyDeviceToDevice, p->stream));
+            HB_CUDA(cudaMemcpyAsync(p->y.p, p->kd.p, nd * sizeof(double), cudaMemcpyDeviceToDevice, p->stream));
+            HB_CUDA(cudaStreamSynchronize(p->stream));
+            p->learned_dir = true;
+        } else {
+            HB_TRY(hb_mpnn_warm_start(p->learned, p));
+        }
     }
     if (p->own_stream) return solve_impl(p, o, rep);
     // the GMRES cycles are captured as CUDA graphs, which needs a stream of our own: order it after the
@@ -1587,8 +1615,39 @@ static hb_status solve_impl(hb_problem *p, const hb_solve_opts &o, hb_report *re
         }
         const double rn_before = rn;
         rn_prev = rn;
+        // learned correction step (use_learned 2): the least-squares multiple alpha of d = y_pred - y
+        // against A d is taken first, plain GMRES then works on what is left (alpha = 0 leaves plain
+        // GMRES); prescribed entries of y_pred and y agree, so d vanishes there
+        double alpha = 0, bscale = 1;
+        if (p->learned_dir) {
+            launch_scale_copy(1.0, p->ylearn.p, p->kd.p, nd, p->stream);
+            launch_axpy(-1.0, p->y.p, p->kd.p, nd, p->stream);
+            HB_LAUNCHED(p, 2);
+            double dn = 0;
+            HB_TRY(dev_norm(p, p->kd.p, nd, dn));
+            if (dn > 0) {
+                HB_TRY(apply_A(p, c, p->kd.p, p->ktmp.p));
+                ++jvc;
+                double qb = 0, qq = 0, b0 = 0, b1 = 0;
+                HB_TRY(dev_dot(p, p->ktmp.p, b, nd, qb));
+                HB_TRY(dev_dot(p, p->ktmp.p, p->ktmp.p, nd, qq));
+                HB_TRY(dev_norm(p, b, nd, b0));
+                if (qq > 0 && std::isfinite(qb / qq)) {
+                    alpha = qb / qq;
+                    launch_axpy(-alpha, p->ktmp.p, b, nd, p->stream);
+                    HB_LAUNCHED(p, 1);
+                    HB_TRY(dev_norm(p, b, nd, b1));
+                    bscale = b0 > 0 ? b1 / b0 : 1.0;
+                }
+            }
+        }
         double relres = 0;
-        HB_TRY(gmres(p, c, b, p->kdx.p, tol, o.gmres_restart, o.max_gmres, its, jvc, &relres));
+        HB_TRY(gmres(p, c, b, p->kdx.p, tol / bscale, o.gmres_restart, o.max_gmres, its, jvc, &relres));
+        relres *= bscale;                     // relative to the step's full right-hand side
+        if (alpha != 0) {
+            launch_axpy(alpha, p->kd.p, p->kdx.p, nd, p->stream);
+            HB_LAUNCHED(p, 1);
+        }
         R.gmres_iters += its;
         R.jv_calls += jvc;
         launch_axpy(1.0, p->kdx.p, p->y.p, nd, p->stream);

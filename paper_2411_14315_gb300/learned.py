@@ -67,9 +67,10 @@ def train(net: hbgls.MPNN, data, steps: int, lr: float = 2e-3, lr_final: float =
     return losses
 
 
-def evaluate(net: hbgls.MPNN, specs, **kw):
+def evaluate(net: hbgls.MPNN, specs, correction: bool = False, **kw):
     """Cold (default initial state) and warm (network prediction) solves of each spec to the same
-    absolute residual; returns per-case dictionaries."""
+    absolute residual; with correction, also a solve from the default state that takes learned
+    correction steps (use_learned = 2).  Returns per-case dictionaries."""
     res = []
     for s in specs:
         cold = hbgls.Problem.from_spec(s)
@@ -87,9 +88,19 @@ def evaluate(net: hbgls.MPNN, specs, **kw):
         err_pred_vel = float(np.linalg.norm(pred[:, :3] - hc[:, :3]) / np.linalg.norm(hc[:, :3]))
         yw = warm.instances()
         yc = cold.instances()
-        res.append(dict(cold=rc, warm=rw, t_cold=tc, t_warm=tw, pred_rel_err=err_pred,
-                        pred_rel_err_velocity=err_pred_vel,
-                        warm_vs_cold=float(np.linalg.norm(yw - yc) / np.linalg.norm(yc))))
+        case = dict(cold=rc, warm=rw, t_cold=tc, t_warm=tw, pred_rel_err=err_pred,
+                    pred_rel_err_velocity=err_pred_vel,
+                    warm_vs_cold=float(np.linalg.norm(yw - yc) / np.linalg.norm(yc)))
+        if correction:
+            corr = hbgls.Problem.from_spec(s)
+            net.attach(corr)
+            t0 = time.perf_counter()
+            rk = corr.solve(check=False, **solve_opts(r_ref=rc["res0"], use_learned=2, **kw))
+            case["correction"] = rk
+            case["t_correction"] = time.perf_counter() - t0
+            case["correction_vs_cold"] = float(np.linalg.norm(corr.instances() - yc) / np.linalg.norm(yc))
+            corr.close()
+        res.append(case)
         cold.close()
         warm.close()
     return res

@@ -1,8 +1,9 @@
 """What the trained warm-start network gains over the method without it.
 
 Trains the network on solves the method generates for seeded vessel-like pipes, then solves held-out
-vessels from the default initial state (cold) and from the network's prediction (warm) to the same
-absolute residual, and compares the outer (pseudo-time / Newton) steps.  Both end at the same state.
+vessels from the default initial state (cold), from the network's prediction (warm), and from the
+default state with learned correction steps, to the same absolute residual, and compares the outer
+(pseudo-time / Newton) steps.  All three end at the same state.
 """
 import numpy as np
 import pytest
@@ -20,12 +21,13 @@ def test_learned_warm_start_reduces_outer_steps():
     net = hbgls.MPNN(4, seed=1, p_scale=LR.pressure_scale(data))
     losses = LR.train(net, data, steps=6000, lr=3e-3, lr_final=3e-5)
     assert np.mean(losses[-100:]) < 0.05 * losses[0]
-    ev = LR.evaluate(net, test_specs)
+    ev = LR.evaluate(net, test_specs, correction=True)
     cold = sum(e["cold"]["steps"] for e in ev)
     warm = sum(e["warm"]["steps"] for e in ev)
     for e in ev:
-        assert e["cold"]["status"] == 0 and e["warm"]["status"] == 0
+        assert e["cold"]["status"] == 0 and e["warm"]["status"] == 0 and e["correction"]["status"] == 0
         assert e["warm_vs_cold"] < 1e-8
+        assert e["correction_vs_cold"] < 1e-8
     print(f"outer steps cold {cold} warm {warm}; GMRES iterations cold "
           f"{sum(e['cold']['gmres_iters'] for e in ev)} warm {sum(e['warm']['gmres_iters'] for e in ev)}")
     assert warm < cold
