@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
     ap.add_argument("--extra", action="store_true", help="also time residual / exact Jv / FP64 rates")
+    ap.add_argument("--march", action="store_true",
+                    help="also time the conventional time-marching solver against the HB solve on the Womersley "
+                         "pipe (~3,000 tets, N = 9)")
     ap.add_argument("--krylov-probe", action="store_true",
                     help="also run one outer solver step (mixed precision, GMRES(30), 60 iterations) on the "
                          "benchmark workload, so the Arnoldi sweeps run at full vector size")
@@ -257,6 +260,36 @@ def time_solves():
         p.close()
     ref.close()
     return out
+
+
+def time_march(spp: int = 1008, periods: int = 4):
+    """The paper's comparison (Sec. 3) on one GPU: the HB solve against the conventional time-marching
+    GLS solver (tau_hat, generalized-alpha, GMRES 0.03, Newton 1e-3 per step) marched from rest for
+    `periods` periods of `spp` steps, on the Womersley pipe (~3,000 tets, N = 9, mixed precision)."""
+    from paper_2411_14315_gb300 import hbgls
+    from paper_2411_14315_gb300 import workloads as W
+    spec = W.womersley_spec(level=1)
+    res = {"workload": f"womersley pipe {spec.mesh.n_tets} tets N={spec.N}"}
+    hb = hbgls.Problem.from_spec(spec)
+    for name, rtol in (("hb_paper_1e-3", 1e-3), ("hb_1e-8", 1e-8)):
+        hb.set_instances(None)
+        rep = hb.solve(precision=1, rtol=rtol, max_steps=300, check=False)
+        res[name] = {"seconds": rep["seconds"], "status": rep["status"], "steps": rep["steps"],
+                     "gmres_iters": rep["gmres_iters"]}
+    yh = hb.instances()
+    tm = hbgls.Problem.from_spec(spec)
+    rep = tm.march(precision=1, steps_per_period=spp, periods=periods, check=False)
+    ys = tm.march_samples()
+    dv = float(np.linalg.norm(ys[:, :3] - yh[:, :3]) / np.linalg.norm(yh[:, :3]))
+    res["time_marching"] = {"seconds": rep["seconds"], "status": rep["status"], "steps": rep["steps"],
+                            "steps_per_period": spp, "periods": periods, "newton_iters": rep["newton_iters"],
+                            "gmres_iters": rep["gmres_iters"], "period_change": rep["period_change"],
+                            "max_newton_rel": rep["max_newton_rel"],
+                            "velocity_rel_diff_vs_hb": dv}
+    res["speedup_hb_paper_vs_time_marching"] = rep["seconds"] / max(res["hb_paper_1e-3"]["seconds"], 1e-12)
+    hb.close()
+    tm.close()
+    return res
 
 
 def time_batch(reps: int = 20):
@@ -467,6 +500,11 @@ def run_ours(args, dist: Dist, spec, config):
                 result["time_to_solve"] = {"error": repr(e)}
         if not args.skip_cpu:
             result["cpu_baseline"] = cpu_baseline(spec)
+    if args.march and dist.rank == 0:
+        try:
+            result["time_marching_vs_hb"] = time_march()
+        except Exception as e:  # reported, not hidden
+            result["time_marching_vs_hb"] = {"error": repr(e)}
     if args.krylov_probe:
         torch.cuda.synchronize()
         rep = prob.solve(precision=1, max_steps=1, gmres_restart=30, max_gmres=60, rtol=1e-12,

@@ -225,6 +225,53 @@ hb_status hb_mpnn_warm_start(hb_mpnn *net, hb_problem *p);
  * with use_learned = 2 takes learned correction steps towards it. */
 hb_status hb_attach_learned(hb_problem *p, hb_mpnn *net);
 
+/* ---- time-domain march: the conventional solver the paper compares with (Sec. 3) ----------------------
+ * GLS of Eq. (NS-weak) in the time domain (du/dt in place of H u, no least-squares time term) with
+ * tau_hat of Eq. (tauhat), omega_hat = ||du/dt|| / ||u|| over the nodal velocities; generalized-alpha in
+ * time (alpha_m = (3 - rho_inf) / (2 (1 + rho_inf)), alpha_f = 1 / (1 + rho_inf), gamma = 1/2 + alpha_m -
+ * alpha_f; residual at (u, p)_{n+alpha_f} and du/dt_{n+alpha_m}); per step Newton on the paper's tangent
+ * (+ c1 rho / dt M) with Jacobi-preconditioned GMRES.  It marches from rest (Dirichlet values at t = 0,
+ * pressure at the mean outlet level) on a one-instance copy of the problem, with the Dirichlet and outlet
+ * values evaluated from the problem's harmonic data at each time; the HB state of the problem is not
+ * touched.  The state at the N instance times of the last period is kept for hb_get_march_samples. */
+typedef struct {
+    int precision;            /* 0: FP64 kernels; 1: FP32 Jacobian products, FP64 residual and Krylov   */
+    int steps_per_period;     /* a multiple of N (the instance times are sampled); <= 0: 100 N         */
+    int periods;              /* periods marched (4)                                                   */
+    double rho_inf;           /* generalized-alpha spectral radius at infinite step (0.5)              */
+    double newton_rtol;       /* per-step Newton stop on ||r|| / ||r_first|| (1e-3, as in Sec. 3)      */
+    int newton_max;           /* Newton iterations per step (10)                                       */
+    double gmres_rtol;        /* GMRES tolerance (0.03, as in Sec. 3)                                  */
+    int gmres_restart;        /* (15)                                                                  */
+    int max_gmres;            /* GMRES iteration cap per linear solve (300)                            */
+    int tau_acceleration;     /* 1: tau_hat with omega_hat (Eq. tauhat); 0: tau of Eq. (tau)           */
+    int verbose;              /* one line per instance time to stderr                                  */
+} hb_march_opts;
+
+typedef struct {
+    int steps, newton_iters, gmres_iters, jv_calls;
+    double seconds;
+    double period_change;     /* ||u(t_end) - u(t_end - T)|| / ||u(t_end)|| (periods > 1)              */
+    double max_newton_rel;    /* largest ||r|| / ||r_first|| left at the end of a step                 */
+    int status;
+} hb_march_report;
+
+hb_status hb_default_march_opts(hb_march_opts *o);
+/* HB_ERR_INVALID_ARG for bad options (steps_per_period not a multiple of N), HB_ERR_STATE without an
+ * inflow, HB_ERR_NAN if the march produced non-finite values. */
+hb_status hb_march(hb_problem *p, const hb_march_opts *o, hb_march_report *rep);
+/* Hot-path entry points of the march (host buffers, one time level [n_nodes][4]): the residual at time
+ * t (outlet levels at t; Dirichlet momentum rows 0; ydot's pressure column unused) and the paper tangent
+ * (+ shift M on the velocity; Dirichlet rows identity on v) at y, both with tau_hat for the given
+ * omega2 = omega_hat^2 (>= 0, else HB_ERR_INVALID_ARG). */
+hb_status hb_time_residual(hb_problem *p, const double *y, const double *ydot, double *r, int precision, double t,
+                           double omega2);
+hb_status hb_time_jv(hb_problem *p, const double *y, const double *v, double *jv, int precision, double omega2,
+                     double shift);
+/* State of the last march at t_j = j T / N of its last period, [n_nodes][4][N] (the instance layout, so
+ * it compares directly with hb_get_instances); HB_ERR_STATE before a march. */
+hb_status hb_get_march_samples(hb_problem *p, double *out);
+
 /* ---- batches of problems (many vessels of uneven size and N in one graph) ---------------------------
  * A batch applies the operator of every member problem in one captured CUDA graph: the output
  * clearing, one persistent element pass per distinct instance count N (specialised for that N) whose

@@ -22,9 +22,12 @@ not depend on time).  Readings (also in the design notes):
       pressures at t_{n+alpha_f}.  rho_inf = 0.5 unless stated.
   R14 omega_hat^2 = ||du/dt||^2 / ||u||^2 over the nodal velocity vectors (discrete 2-norms) of the
       current iterate.
-  R15 The tangent is the paper's (Eqs. K_mat, ctangent) at N = 1 with U and tau_hat frozen, plus
-      c1 rho / dt M on the velocity, c1 = alpha_m / (alpha_f gamma); the least-squares acceleration
-      terms are left out of it as the paper's HB tangent leaves out the least-squares H terms.
+  R15 The tangent is the paper's (Eqs. K_mat, ctangent) at N = 1 with U and tau_hat frozen, plus the
+      acceleration's derivative: c1 rho / dt M on the velocity (Galerkin) and c1 rho / dt v inside the
+      least-squares L of both rows, c1 = alpha_m / (alpha_f gamma).  (The HB tangent has no such term:
+      its time coupling is the F block.)  The Jacobi preconditioner takes the diagonal of this tangent
+      without the least-squares acceleration cross term (u . grad N_A) tau c1 rho / dt N_A, which has no
+      sign and can cancel the Galerkin mass diagonal; the Galerkin c1 rho / dt M_AA stays in it.
 
 Array layouts: one time level is [n_nodes, 4] (u1, u2, u3, p).
 """
@@ -149,8 +152,10 @@ def residual(prob: HB.HBProblem, y: np.ndarray, ydot: np.ndarray, t: float, omeg
     return np.concatenate([rm, rc[:, None]], axis=1)
 
 
-def jv_paper(prob: HB.HBProblem, y: np.ndarray, v: np.ndarray, omega2: float, shift: float) -> np.ndarray:
-    """Paper tangent at N = 1 with U and tau_hat frozen at y, plus shift M on the velocity (R15);
+def jv_paper(prob: HB.HBProblem, y: np.ndarray, v: np.ndarray, omega2: float, shift: float,
+             ls_acceleration: bool = True) -> np.ndarray:
+    """Paper tangent at N = 1 with U and tau_hat frozen at y, plus the acceleration's derivative (R15):
+    shift M on the velocity and, with ls_acceleration, shift v inside the least-squares L of both rows.
     Dirichlet velocity rows are the identity on v, whose Dirichlet velocity entries count as 0."""
     rho, mu = prob.rho, prob.mu
     mask, _ = dirichlet_at(prob, 0.0)
@@ -166,12 +171,15 @@ def jv_paper(prob: HB.HBProblem, y: np.ndarray, v: np.ndarray, omega2: float, sh
     udN = np.einsum("eqj,eaj->eqa", Uq, gN)
     w = V / 4.0
     Vb = V[:, None, None]
+    dUq = np.einsum("qa,eai->eqi", NQ, dU) * (1.0 if ls_acceleration else 0.0)
     Kv = (rho * np.einsum("e,qa,eqi->eai", w, NQ, ugv)
           + mu * Vb * np.einsum("eaj,eij->eai", gN, gradV)
           + rho * np.einsum("e,eq,eqa,eqi->eai", w, tau, udN, ugv)
-          + shift * Vb * np.einsum("ab,ebi->eai", MREF, dU))
+          + shift * Vb * np.einsum("ab,ebi->eai", MREF, dU)
+          + shift * np.einsum("e,eq,eqa,eqi->eai", w, tau, udN, dUq))
     Gv = -Vb * gN * dP.mean(axis=1)[:, None, None] + np.einsum("e,eq,eqa,ei->eai", w, tau, udN, gradVp)
-    Dv = (w * np.einsum("eii->e", gradV))[:, None] + np.einsum("e,eq,eaj,eqj->ea", w, tau, gN, ugv)
+    Dv = ((w * np.einsum("eii->e", gradV))[:, None] + np.einsum("e,eq,eaj,eqj->ea", w, tau, gN, ugv)
+          + (shift / rho) * np.einsum("e,eq,eaj,eqj->ea", w, tau, gN, dUq))
     Lv = (1.0 / rho) * np.einsum("e,eq,eaj,ej->ea", w, tau, gN, gradVp)
     rm = np.zeros((prob.n_nodes, 3))
     rc = np.zeros(prob.n_nodes)
@@ -201,7 +209,8 @@ def jv_paper(prob: HB.HBProblem, y: np.ndarray, v: np.ndarray, omega2: float, sh
 
 
 def jacobi_diag(prob: HB.HBProblem, y: np.ndarray, omega2: float, shift: float) -> np.ndarray:
-    """Diagonal of the volume part of jv_paper (1 on Dirichlet velocity rows), [n, 4]."""
+    """Diagonal of the volume part of jv_paper without the least-squares acceleration term (R15); 1 on
+    Dirichlet velocity rows; [n, 4]."""
     rho, mu = prob.rho, prob.mu
     tt, U, Uq, tau = _state(prob, y, omega2)
     gN, V = prob.geo.gradN, prob.geo.V

@@ -55,6 +55,10 @@ struct DBuf {
     DBuf(const DBuf &) = delete;
     DBuf &operator=(const DBuf &) = delete;
     ~DBuf() { release(); }
+    void swap(DBuf &o) {
+        std::swap(p, o.p);
+        std::swap(n, o.n);
+    }
     void release() {
         if (p) cudaFree(p);
         p = nullptr;
@@ -152,6 +156,11 @@ struct hb_problem {
     // element-kernel timing
     bool prof_on = false;
     DBuf<double> ylearn, kd;              // learned prediction and the direction towards it (use_learned 2)
+    double omega2 = 0;                    // acceleration term of tau_hat in the element passes (time domain)
+    int ls_mass = 0;                      // time domain: the shift enters the tangent's least-squares L too
+    hb_problem *tm = nullptr;             // internal one-instance copy that runs the time-domain march
+    DBuf<double> tm_un, tm_dun, tm_u1, tm_du1, tm_dya, tm_prev, d_march;
+    bool march_done = false;
     bool learned_dir = false;
     int jvp_variant = 1;                  // launch variant of the FP32 paper-tangent pass
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev;
@@ -616,6 +625,8 @@ hb_status apply_op(hb_problem *p, int mode, const T *y, const T *v, T *out, doub
     ea.mu = T(p->mu);
     ea.shift = T(shift);
     ea.shift_dev = shift_dev;
+    ea.omega2 = T(p->omega2);
+    ea.ls_mass = p->ls_mass;
     ea.variant = p->jvp_variant;
     if (ps.P > 0) {
         cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -672,7 +683,7 @@ hb_status check_precision(int precision) {
 // host-buffer wrapper: copies in, converts, applies, converts, copies out
 hb_status host_op(hb_problem *p, int mode, const double *y, const double *v, double *out, int precision,
                   double shift) {
-    if (!p || !y || !out || ((mode == MODE_JVP || mode == MODE_JVE) && !v))
+    if (!p || !y || !out || ((mode == MODE_JVP || mode == MODE_JVE || mode == MODE_TRES) && !v))
         return fail(HB_ERR_INVALID_ARG, "null argument");
     HB_TRY(check_precision(precision));
     const size_t nd = size_t(p->n_nodes) * 4 * p->N;
@@ -680,7 +691,7 @@ hb_status host_op(hb_problem *p, int mode, const double *y, const double *v, dou
     HB_TRY(dalloc(p, p->w64a, nd));
     HB_TRY(dalloc(p, p->w64b, nd));
     HB_CUDA(cudaMemcpyAsync(p->w64a.p, y, nd * sizeof(double), cudaMemcpyHostToDevice, p->stream));
-    const bool jv = (mode == MODE_JVP || mode == MODE_JVE);
+    const bool jv = (mode == MODE_JVP || mode == MODE_JVE || mode == MODE_TRES);   // second operand
     if (precision == 0) {
         double *vd = nullptr;
         if (jv) {
@@ -1280,6 +1291,7 @@ hb_status hb_create(const hb_mesh *mesh, double rho, double mu, double period_T,
 
 hb_status hb_destroy(hb_problem *p) {
     if (!p) return HB_OK;
+    if (p->tm) hb_destroy(p->tm);
     cudaSetDevice(p->device);
     if (p->stream) cudaStreamSynchronize(p->stream);
     const bool own = p->own_stream;
@@ -1703,6 +1715,281 @@ hb_status hb_jv_dev_noalloc(hb_problem *p, const void *y, const void *v, void *j
                                         static_cast<double *>(jv), shift, s, static_cast<double *>(q));
     return apply_jv_noalloc<float>(p, mode, static_cast<const float *>(y), static_cast<const float *>(v),
                                    static_cast<float *>(jv), shift, s, static_cast<float *>(q));
+}
+
+hb_status hb_default_march_opts(hb_march_opts *o) {
+    if (!o) return fail(HB_ERR_INVALID_ARG, "null options");
+    o->precision = 1;
+    o->steps_per_period = 0;
+    o->periods = 4;
+    o->rho_inf = 0.5;
+    o->newton_rtol = 1e-3;
+    o->newton_max = 10;
+    o->gmres_rtol = 0.03;
+    o->gmres_restart = 15;
+    o->max_gmres = 300;
+    o->tau_acceleration = 1;
+    o->verbose = 0;
+    return HB_OK;
+}
+
+static hb_status march_impl(hb_problem *p, const hb_march_opts &o, hb_march_report *rep);
+
+hb_status hb_march(hb_problem *p, const hb_march_opts *opts, hb_march_report *rep) {
+    if (!p) return fail(HB_ERR_INVALID_ARG, "null problem");
+    hb_march_opts o;
+    hb_default_march_opts(&o);
+    if (opts) o = *opts;
+    HB_TRY(check_precision(o.precision));
+    if (o.steps_per_period <= 0) o.steps_per_period = 100 * p->N;
+    if (o.steps_per_period % p->N != 0)
+        return fail(HB_ERR_INVALID_ARG, "steps_per_period must be a multiple of N (to sample the instance times)");
+    if (o.periods < 1 || o.newton_max < 1 || o.max_gmres < 1 || !(o.rho_inf >= 0 && o.rho_inf <= 1))
+        return fail(HB_ERR_INVALID_ARG, "periods, newton_max, max_gmres >= 1 and rho_inf in [0, 1] required");
+    if (o.gmres_restart < 1 || o.gmres_restart > 200) return fail(HB_ERR_INVALID_ARG, "gmres_restart must be in [1, 200]");
+    HB_CUDA(cudaSetDevice(p->device));
+    HB_TRY(prepare_bc(p));
+    if (p->inflows.empty()) return fail(HB_ERR_STATE, "no inflow set");
+    return march_impl(p, o, rep);
+}
+
+hb_status hb_get_march_samples(hb_problem *p, double *out) {
+    if (!p || !out) return fail(HB_ERR_INVALID_ARG, "null argument");
+    if (!p->march_done) return fail(HB_ERR_STATE, "no march has run (hb_march)");
+    HB_CUDA(cudaSetDevice(p->device));
+    HB_CUDA(cudaMemcpyAsync(out, p->d_march.p, size_t(p->n_nodes) * 4 * p->N * sizeof(double),
+                            cudaMemcpyDeviceToHost, p->tm->stream));
+    HB_CUDA(cudaStreamSynchronize(p->tm->stream));
+    return HB_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------------------
+// time-domain march (Sec. 3): the conventional GLS solver with tau_hat (Eq. tauhat), generalized-alpha in
+// time, Newton on the paper's tangent with Jacobi-preconditioned GMRES, on a one-instance copy of the
+// problem whose boundary values are re-evaluated from the harmonic data at every step
+
+namespace {
+
+// one-instance copy: same mesh, fluid and boundary tags; the series are cut to their means (only the
+// Dirichlet node set, the Neumann faces and the resistances matter: values are set per step)
+hb_status tm_copy(hb_problem *p) {
+    if (p->tm) return HB_OK;
+    hb_mesh m;
+    m.n_nodes = p->n_nodes;
+    m.n_tets = p->n_tets;
+    m.n_faces = p->n_faces;
+    m.xyz = p->xyz.data();
+    m.tets = p->tets.data();
+    m.faces = p->faces.data();
+    m.face_tag = p->face_tag.data();
+    hb_problem *c = nullptr;
+    HB_TRY(hb_create(&m, p->rho, p->mu, p->T, 0, p->device, nullptr, &c));
+    auto bail = [&](hb_status st) {
+        hb_destroy(c);
+        return st;
+    };
+    hb_status st = HB_OK;
+    const int M = 2 * p->n_h + 1;
+    for (const Inflow &in : p->inflows) {
+        if (!in.harm.empty()) {
+            std::vector<double> h0(size_t(p->n_nodes) * 3);
+            for (size_t r = 0; r < h0.size(); ++r) h0[r] = in.harm[r * size_t(M)];
+            st = hb_set_inflow_harmonics(c, in.tag, h0.data());
+        } else {
+            const double a0 = in.coef[0], b0 = 0.0;
+            st = hb_set_inflow(c, in.tag, in.profile.empty() ? nullptr : in.profile.data(), &a0, &b0);
+        }
+        if (st != HB_OK) return bail(st);
+    }
+    for (const Outlet &ou : p->outlets) {
+        const double a0 = ou.coef[0], b0 = 0.0;
+        st = ou.R > 0 ? hb_set_outlet_resistance(c, ou.tag, ou.R, &a0, &b0) : hb_set_outlet_pressure(c, ou.tag, &a0, &b0);
+        if (st != HB_OK) return bail(st);
+    }
+    if ((st = hb_set_backflow(c, p->beta)) != HB_OK) return bail(st);
+    if ((st = prepare_bc(c)) != HB_OK) return bail(st);
+    if (c->n_dir != p->n_dir || c->n_out != p->n_out) return bail(fail(HB_ERR_STATE, "time-domain copy differs"));
+    c->jvp_variant = p->jvp_variant;
+    c->ls_mass = 1;
+    p->tm = c;
+    return HB_OK;
+}
+
+// outlet traction levels -P(t) of the copy (h of the resistance outlets adds -R Q in the face kernel)
+hb_status tm_outlets_at(hb_problem *p, double t) {
+    hb_problem *c = p->tm;
+    if (p->n_out == 0) return HB_OK;
+    std::vector<double> hb(size_t(p->n_out));
+    const double w = p->omega;
+    for (int o = 0; o < p->n_out; ++o) {
+        const std::vector<double> &cf = p->outlets[size_t(o)].coef;
+        double v = cf[0];
+        for (int k = 1; k <= p->n_h; ++k) v += cf[size_t(2 * k - 1)] * std::cos(k * w * t) + cf[size_t(2 * k)] * std::sin(k * w * t);
+        hb[size_t(o)] = -v;
+    }
+    std::vector<float> hf(hb.begin(), hb.end());
+    HB_CUDA(cudaMemcpyAsync(c->d_hbase64.p, hb.data(), hb.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    HB_CUDA(cudaMemcpyAsync(c->d_hbase32.p, hf.data(), hf.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    HB_CUDA(cudaStreamSynchronize(c->stream));      // the host arrays go out of scope
+    return HB_OK;
+}
+
+hb_status vel_norm2(hb_problem *p, const double *x, int64_t n, double &out) {
+    HB_TRY(dalloc(p, p->small, 512));
+    launch_vel_norm2(x, n, p->scratch.p, p->small.p, p->stream);
+    HB_LAUNCHED(p, 2);
+    HB_CUDA(cudaMemcpyAsync(&out, p->small.p, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+    HB_CUDA(cudaStreamSynchronize(p->stream));
+    return HB_OK;
+}
+
+}  // namespace
+
+static hb_status march_impl(hb_problem *p, const hb_march_opts &o, hb_march_report *rep) {
+    const auto t0 = std::chrono::steady_clock::now();
+    HB_TRY(tm_copy(p));
+    hb_problem *c = p->tm;
+    cudaStream_t s = c->stream;
+    const int64_t n = c->n_nodes * 4;                // one time level
+    HB_TRY(ensure_krylov(c, o.gmres_restart));
+    for (DBuf<double> *b : {&p->tm_un, &p->tm_dun, &p->tm_u1, &p->tm_du1, &p->tm_dya, &p->tm_prev})
+        HB_TRY(dalloc(c, *b, size_t(n)));
+    HB_TRY(dalloc(c, p->d_march, size_t(n) * size_t(p->N)));
+    // generalized-alpha for first-order systems (reading R13); c1 = alpha_m / (alpha_f gamma)
+    const double ri = o.rho_inf;
+    const double am = (3.0 - ri) / (2.0 * (1.0 + ri)), af = 1.0 / (1.0 + ri), gam = 0.5 + am - af;
+    const int spp = o.steps_per_period;
+    const double dt = p->T / spp, inv_gdt = 1.0 / (gam * dt), cg = (gam - 1.0) / gam;
+    const double shift = am / (af * gam) * p->rho / dt;
+    const int stride = spp / p->N;
+    // initial state: zero interior velocity and acceleration, Dirichlet values at t = 0, pressure at the
+    // outlets' mean level
+    HB_TRY(default_initial(c));
+    launch_series_at(p->d_dir_prof.p, int64_t(3) * p->n_dir, p->n_h, 0.0, c->d_g.p, s);
+    launch_apply_dirichlet(c->d_dir_nodes.p, c->n_dir, c->d_g.p, c->y.p, 1, s);
+    HB_CUDA(cudaMemcpyAsync(p->tm_un.p, c->y.p, size_t(n) * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    HB_CUDA(cudaMemsetAsync(p->tm_dun.p, 0, size_t(n) * sizeof(double), s));
+    HB_LAUNCHED(c, 2);
+    hb_march_report R;
+    std::memset(&R, 0, sizeof(R));
+    hb_status result = HB_OK;
+    double *r = c->w64a.p, *b = c->w64b.p;
+    const int nsteps = spp * o.periods;
+    for (int k = 0; k < nsteps && result == HB_OK; ++k) {
+        const double frac1 = double((k + 1) % spp) / spp;          // t_{n+1} / T mod 1
+        const double t_af = (double(k) + af) * dt;
+        launch_series_at(p->d_dir_prof.p, int64_t(3) * p->n_dir, p->n_h, frac1, c->d_g.p, s);
+        launch_galpha_predict(p->tm_un.p, p->tm_dun.p, p->tm_u1.p, p->tm_du1.p, n, cg, c->d_dir_nodes.p, c->n_dir,
+                              c->d_g.p, inv_gdt, s);
+        HB_LAUNCHED(c, c->n_dir > 0 ? 3 : 2);
+        HB_TRY(tm_outlets_at(p, t_af));
+        double r0 = -1, rn = 0;
+        for (int it = 0; it < o.newton_max; ++it) {
+            // stage values; the tangent is frozen at c->y = (u, p)_{n+alpha_f}
+            launch_galpha_stage(p->tm_un.p, p->tm_u1.p, p->tm_dun.p, p->tm_du1.p, c->y.p, p->tm_dya.p, n, af, am, s);
+            HB_LAUNCHED(c, 1);
+            c->omega2 = 0;
+            if (o.tau_acceleration) {
+                double a2 = 0, u2 = 0;
+                HB_TRY(vel_norm2(c, p->tm_dya.p, n, a2));
+                HB_TRY(vel_norm2(c, c->y.p, n, u2));
+                c->omega2 = u2 > 0 ? a2 / u2 : 0.0;              // reading R14
+            }
+            HB_TRY(apply_op<double>(c, MODE_TRES, c->y.p, p->tm_dya.p, r, 0.0, s));
+            HB_TRY(dev_norm(c, r, n, rn));
+            if (!std::isfinite(rn)) {
+                result = fail(HB_ERR_NAN, "non-finite residual in the time-domain march");
+                break;
+            }
+            if (r0 < 0) r0 = rn;
+            if (rn == 0.0 || (it > 0 && rn <= o.newton_rtol * r0)) break;
+            // Jacobi diagonal of the tangent (+ c1 rho / dt M), stored inverted
+            if (o.precision == 1) {
+                launch_convert<double, float>(c->y.p, c->ky32.p, n, s);
+                HB_LAUNCHED(c, 1);
+                HB_TRY(apply_op<float>(c, MODE_DIAG, c->ky32.p, nullptr, c->kdiag32.p, shift, s));
+                launch_convert<float, double>(c->kdiag32.p, c->kdiag.p, n, s);
+                HB_LAUNCHED(c, 1);
+            } else {
+                HB_TRY(apply_op<double>(c, MODE_DIAG, c->y.p, nullptr, c->kdiag.p, shift, s));
+            }
+            launch_reciprocal(c->kdiag.p, c->kdiag.p, n, s);
+            launch_scale_copy(-1.0 / af, r, b, n, s);
+            HB_LAUNCHED(c, 2);
+            int its = 0, jvc = 0;
+            OpCtx ctx{MODE_JVP, shift, o.precision, nullptr};
+            HB_TRY(gmres(c, ctx, b, c->kdx.p, o.gmres_rtol, o.gmres_restart, o.max_gmres, its, jvc));
+            launch_galpha_correct(p->tm_u1.p, p->tm_du1.p, c->kdx.p, n, inv_gdt, s);
+            HB_LAUNCHED(c, 1);
+            R.newton_iters++;
+            R.gmres_iters += its;
+            R.jv_calls += jvc;
+        }
+        if (r0 > 0) R.max_newton_rel = std::max(R.max_newton_rel, rn / r0);
+        p->tm_un.swap(p->tm_u1);
+        p->tm_dun.swap(p->tm_du1);
+        R.steps++;
+        if ((k + 1) % spp == 0 && k + 1 < nsteps)       // state at the end of each period but the last
+            HB_CUDA(cudaMemcpyAsync(p->tm_prev.p, p->tm_un.p, size_t(n) * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        if (k + 1 > nsteps - spp && (k + 1) % stride == 0) {    // last period: the instance times t_j = j T / N
+            const int j = ((k + 1) % spp) / stride;
+            launch_put_instance(p->tm_un.p, p->d_march.p, n, j, p->N, s);
+            HB_LAUNCHED(c, 1);
+        }
+        if (o.verbose && ((k + 1) % stride == 0))
+            std::fprintf(stderr, "hb_march step %d t/T %.4f |r|/|r0| %.3e\n", k + 1, double(k + 1) / spp,
+                         r0 > 0 ? rn / r0 : 0.0);
+    }
+    if (result == HB_OK && o.periods > 1) {
+        // relative change over the last period: ||u(T_end) - u(T_end - T)|| / ||u(T_end)||
+        launch_axpy(-1.0, p->tm_un.p, p->tm_prev.p, n, s);
+        HB_LAUNCHED(c, 1);
+        double dn = 0, un = 0;
+        HB_TRY(dev_norm(c, p->tm_prev.p, n, dn));
+        HB_TRY(dev_norm(c, p->tm_un.p, n, un));
+        R.period_change = un > 0 ? dn / un : 0.0;
+    }
+    HB_CUDA(cudaStreamSynchronize(s));
+    p->launches += c->launches;
+    c->launches = 0;
+    p->march_done = result == HB_OK;
+    R.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    R.status = result;
+    if (rep) *rep = R;
+    return result;
+}
+
+extern "C" {
+
+hb_status hb_time_residual(hb_problem *p, const double *y, const double *ydot, double *r, int precision, double t,
+                           double omega2) {
+    if (!p || !y || !ydot || !r) return fail(HB_ERR_INVALID_ARG, "null argument");
+    HB_TRY(check_precision(precision));
+    if (!(omega2 >= 0)) return fail(HB_ERR_INVALID_ARG, "omega2 must be >= 0");
+    HB_CUDA(cudaSetDevice(p->device));
+    HB_TRY(prepare_bc(p));
+    HB_TRY(tm_copy(p));
+    HB_TRY(tm_outlets_at(p, t));
+    p->tm->omega2 = omega2;
+    const hb_status st = host_op(p->tm, MODE_TRES, y, ydot, r, precision, 0.0);
+    p->tm->omega2 = 0;
+    return st;
+}
+
+hb_status hb_time_jv(hb_problem *p, const double *y, const double *v, double *jv, int precision, double omega2,
+                     double shift) {
+    if (!p || !y || !v || !jv) return fail(HB_ERR_INVALID_ARG, "null argument");
+    HB_TRY(check_precision(precision));
+    if (!(omega2 >= 0)) return fail(HB_ERR_INVALID_ARG, "omega2 must be >= 0");
+    HB_CUDA(cudaSetDevice(p->device));
+    HB_TRY(prepare_bc(p));
+    HB_TRY(tm_copy(p));
+    p->tm->omega2 = omega2;
+    const hb_status st = host_op(p->tm, MODE_JVP, y, v, jv, precision, shift);
+    p->tm->omega2 = 0;
+    return st;
 }
 
 }  // extern "C"

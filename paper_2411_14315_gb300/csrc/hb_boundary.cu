@@ -207,7 +207,7 @@ void launch_faces(int mode, const FaceArgs<T> &a, bool has_resistance, int n_out
     const int64_t n = int64_t(a.n_faces) * a.N;
     if (n == 0 || mode == MODE_DIAG) return;
     const int g = nblk(n, 128);
-    if (mode == MODE_RES) {
+    if (mode == MODE_RES || mode == MODE_TRES) {   // a time level's residual has the same boundary terms
         if (has_resistance) outlet_flux_kernel<T, MODE_RES><<<dim3(nblk(a.n_faces, 256), a.N), 256, 0, s>>>(a, n_out);
         face_kernel<T, MODE_RES><<<g, 128, 0, s>>>(a);
     } else if (mode == MODE_JVP) {

@@ -33,7 +33,7 @@ __host__ __device__ inline Layout make_layout(int mode, int N, int nl, int ep, s
     L.H = o;    o += pad16(size_t(N) * N * ts);
     L.geom = o; o += pad16(size_t(ep) * kGeomStride * ts);
     L.Y = o;    o += pad16(row4);
-    L.V = o;    if (mode == MODE_JVP || mode == MODE_JVE) o += pad16(row4);
+    L.V = o;    if (mode == MODE_JVP || mode == MODE_JVE || mode == MODE_TRES) o += pad16(row4);
     L.HY = o;   if (mode == MODE_RES || mode == MODE_JVE) o += pad16(row3);
     L.HV = o;   if (mode == MODE_JVE || mode == MODE_JVP) o += pad16(row3);
     L.T = o;    if (mode == MODE_RES || mode == MODE_JVE) o += pad16(row3);
@@ -172,7 +172,7 @@ __device__ __forceinline__ L ldot3(const L *a, const L *b) {
 //   visc, pressure and Mx terms      = grad N_a . Z[:, i],   Z = w rho Mx + mu V (grad v)^T - V pbar I
 // with X_q = tau_q (u_q . grad v + grad q / rho) the strong residual of the direction over rho.
 template <typename T, typename L, int NT>
-__device__ __forceinline__ void jvp_lanes(int e, int n0, int d1, int Nrt, T rho, T mu,
+__device__ __forceinline__ void jvp_lanes(int e, int n0, int d1, int Nrt, T rho, T mu, T omega2, T cs,
                                           const T *__restrict__ sGeom, const uint32_t *__restrict__ sConn,
                                           const T *__restrict__ sY, const T *__restrict__ sV,
                                           const T *__restrict__ sW, const int *__restrict__ sNode,
@@ -193,10 +193,18 @@ __device__ __forceinline__ void jvp_lanes(int e, int n0, int d1, int Nrt, T rho,
 
     // gradients of the direction: grad v_i = sum_{a >= 1} (v_a - v_0)_i grad N_a, same for q
     L gV[3][3], gVp[3], pbar;
+    // time domain (NT = 1): the direction's velocity at the quadrature points, for the least-squares
+    // acceleration term cs v_q inside L (cs = shift / rho, 0 when unused)
+    constexpr int NVQ = NT == 1 ? 4 : 1;
+    L vn[NVQ][3];
     {
         L dv0[3];
 #pragma unroll
         for (int i = 0; i < 3; ++i) dv0[i] = lload<L>(sV + rY[0] + i * N, d1);
+        if constexpr (NT == 1) {
+#pragma unroll
+            for (int i = 0; i < 3; ++i) vn[0][i] = dv0[i];
+        }
         const L dp0 = lload<L>(sV + rY[0] + 3 * N, d1);
         pbar = dp0;
 #pragma unroll
@@ -208,7 +216,9 @@ __device__ __forceinline__ void jvp_lanes(int e, int n0, int d1, int Nrt, T rho,
             for (int j = 0; j < 3; ++j) gVp[j] = a == 1 ? lmul(ddp, gN[0][j]) : lfma(ddp, gN[a - 1][j], gVp[j]);
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
-                const L dd = lsub(lload<L>(sV + rY[a] + i * N, d1), dv0[i]);
+                const L va = lload<L>(sV + rY[a] + i * N, d1);
+                if constexpr (NT == 1) vn[a][i] = va;
+                const L dd = lsub(va, dv0[i]);
 #pragma unroll
                 for (int j = 0; j < 3; ++j)
                     gV[i][j] = a == 1 ? lmul(dd, gN[0][j]) : lfma(dd, gN[a - 1][j], gV[i][j]);
@@ -242,7 +252,7 @@ __device__ __forceinline__ void jvp_lanes(int e, int n0, int d1, int Nrt, T rho,
 
     // quadrature loop: tau_q, X_q and the two element sums Mx and S
     L Mx[3][3], S[3];
-    const L g2 = lsplat<L>(g2s);
+    const L g2 = lsplat<L>(g2s + omega2);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         L udN[3];
@@ -251,7 +261,14 @@ __device__ __forceinline__ void jvp_lanes(int e, int n0, int d1, int Nrt, T rho,
         const L tau = lrsqrt(lfma(udN[0], udN[0], lfma(udN[1], udN[1], lfma(udN[2], udN[2], g2))));
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-            const L X = lmul(tau, ldot3(uq[q], gV[i], gVp[i]));
+            L Lv = ldot3(uq[q], gV[i], gVp[i]);
+            if constexpr (NT == 1) {
+                // + cs v_q: v at quadrature point q is qb sum_a v_a + qd v_q (barycentric weights)
+                const L vq = lfma(lsplat<L>(T(kQA - kQB)), vn[q][i],
+                                  lmul(lsplat<L>(T(kQB)), ladd(ladd(vn[0][i], vn[1][i]), ladd(vn[2][i], vn[3][i]))));
+                Lv = lfma(lsplat<L>(cs), vq, Lv);
+            }
+            const L X = lmul(tau, Lv);
             S[i] = q == 0 ? X : ladd(S[i], X);
 #pragma unroll
             for (int j = 0; j < 3; ++j) Mx[j][i] = q == 0 ? lmul(uq[q][j], X) : lfma(uq[q][j], X, Mx[j][i]);
@@ -313,7 +330,7 @@ __device__ __forceinline__ void jvp_lanes(int e, int n0, int d1, int Nrt, T rho,
 
 // NT > 0: the number of instances is the compile-time constant NT; NT = 0: runtime N
 template <typename T, int MODE, int NT>
-__device__ __forceinline__ void element_instance(int e, int n, int Nrt, T rho, T mu, T shift,
+__device__ __forceinline__ void element_instance(int e, int n, int Nrt, T rho, T mu, T shift, T omega2,
                                                  const T *__restrict__ sGeom,
                                                  const uint32_t *__restrict__ sConn,
                                                  const T *__restrict__ sY, const T *__restrict__ sV,
@@ -331,6 +348,7 @@ __device__ __forceinline__ void element_instance(int e, int n, int Nrt, T rho, T
     for (int a = 0; a < 4; ++a) go[a] = gout + size_t(uint32_t(sNode[lo[a]]) & ~kDirBit) * N4 + n;
     T gN[4][3], V, g2;
     load_geom(sGeom + e * kGeomStride, gN, V, g2);
+    g2 += omega2;                 // tau_hat (Eq. tauhat) of the time-domain passes; 0 for HB
     const T w = V * T(0.25);
     const T qb = T(kQB), qd = T(kQA - kQB);
     const T m20 = V * T(0.05);   // int N_a N_b = V (1 + delta_ab) / 20
@@ -379,13 +397,16 @@ __device__ __forceinline__ void element_instance(int e, int n, int Nrt, T rho, T
             atomicAdd(go[a] + 3 * N, dp);
         }
         return;
-    } else if constexpr (MODE == MODE_RES) {
+    } else if constexpr (MODE == MODE_RES || MODE == MODE_TRES) {
+        // HB: hu = (H u) at the nodes, T = rho M u - int N tau L goes through H at the flush.
+        // Time domain (TRES): hu = du/dt, and the Galerkin term rho M du/dt is added directly.
+        constexpr bool TM = MODE == MODE_TRES;
         T p[4], hu[4][3];
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
             p[a] = sY[lo[a] * N4 + 3 * N + n];
 #pragma unroll
-            for (int i = 0; i < 3; ++i) hu[a][i] = sHY[lo[a] * N3 + i * N + n];
+            for (int i = 0; i < 3; ++i) hu[a][i] = TM ? sV[lo[a] * N4 + i * N + n] : sHY[lo[a] * N3 + i * N + n];
         }
         T gU[3][3], gP[3], husum[3];
 #pragma unroll
@@ -438,11 +459,16 @@ __device__ __forceinline__ void element_instance(int e, int n, int Nrt, T rho, T
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
                 const T visc = gN[a][0] * gU[i][0] + gN[a][1] * gU[i][1] + gN[a][2] * gU[i][2];
-                const T vq = qm[a][i] + w * rho * qb * convs[i] + mu * V * visc - V * gN[a][i] * pbar;
-                const T vt = tt[a][i] + rho * m20 * (usum[i] + u[a][i]) - w * qb * S[i];
+                T vq = qm[a][i] + w * rho * qb * convs[i] + mu * V * visc - V * gN[a][i] * pbar;
                 if (sNode[lo[a]] >= 0) {        // prescribed velocity rows are set apart
-                    atomicAdd(go[a] + i * N, vq);
-                    atomicAdd(sT + lo[a] * N3 + i * N + n, vt);
+                    if constexpr (TM) {
+                        vq += rho * m20 * (husum[i] + hu[a][i]);
+                        atomicAdd(go[a] + i * N, vq);
+                    } else {
+                        const T vt = tt[a][i] + rho * m20 * (usum[i] + u[a][i]) - w * qb * S[i];
+                        atomicAdd(go[a] + i * N, vq);
+                        atomicAdd(sT + lo[a] * N3 + i * N + n, vt);
+                    }
                 }
             }
             const T qc = w * div + (w / rho) * (gN[a][0] * S[0] + gN[a][1] * S[1] + gN[a][2] * S[2]);
@@ -668,7 +694,7 @@ __device__ __forceinline__ void patch_pass(const ElemArgs<T> &a, const PatchSmem
         const int l = i / cpr, c = i - l * cpr;
         const size_t gidx = size_t(uint32_t(sNode[l]) & ~kDirBit) * cpr + c;
         cp_async16(reinterpret_cast<uint4 *>(sY) + i, reinterpret_cast<const uint4 *>(a.y) + gidx);
-        if constexpr (MODE == MODE_JVP || MODE == MODE_JVE)
+        if constexpr (MODE == MODE_JVP || MODE == MODE_JVE || MODE == MODE_TRES)
             cp_async16(reinterpret_cast<uint4 *>(sV) + i, reinterpret_cast<const uint4 *>(a.v) + gidx);
     }
     cp_async_wait_all();
@@ -687,7 +713,7 @@ __device__ __forceinline__ void patch_pass(const ElemArgs<T> &a, const PatchSmem
         }
     }
     __syncthreads();
-    if constexpr (MODE != MODE_DIAG) {
+    if constexpr (MODE != MODE_DIAG && MODE != MODE_TRES) {
         // time coupling of the staged velocities: (H x)[l][i][n] = sum_k H[n][k] x[l][i][k] for
         // x = u (RES, JVE) and x = v (JVP, JVE)
         constexpr bool hy = (MODE == MODE_RES || MODE == MODE_JVE);
@@ -732,7 +758,7 @@ __device__ __forceinline__ void patch_pass(const ElemArgs<T> &a, const PatchSmem
     // prescribed velocity rows of the output (no element or face term reaches them): 0 for the
     // residual (left from the clearing), 1 for the Jacobi diagonal, v (identity) for Jacobian products;
     // patches sharing a node store the same values
-    if constexpr (MODE != MODE_RES) {
+    if constexpr (MODE != MODE_RES && MODE != MODE_TRES) {
         if (nd > 0) {
             for (int i = tid; i < nl * N3; i += nt) {
                 const int l = i / N3;
@@ -749,13 +775,14 @@ __device__ __forceinline__ void patch_pass(const ElemArgs<T> &a, const PatchSmem
         for (int i = tid; i < ne * NP; i += nt) {
             const int e = i / NP, k = i - e * NP;
             const int d1 = (LW == 2 && k + NP < N) ? NP : 0;
-            jvp_lanes<T, L, NT>(e, k, d1, N, a.rho, a.mu, sGeom, sConn, sY, sV, sHV, sNode, a.out);
+            jvp_lanes<T, L, NT>(e, k, d1, N, a.rho, a.mu, a.omega2, a.ls_mass ? shift / a.rho : T(0), sGeom, sConn,
+                                sY, sV, sHV, sNode, a.out);
         }
     } else {
         for (int i = tid; i < ne * N; i += nt) {
             const int e = i / N, n = i - e * N;
-            element_instance<T, MODE, NT>(e, n, N, a.rho, a.mu, shift, sGeom, sConn, sY, sV, sHY, sHV, sNode,
-                                          a.out, sT);
+            element_instance<T, MODE, NT>(e, n, N, a.rho, a.mu, shift, a.omega2, sGeom, sConn, sY, sV, sHY, sHV,
+                                          sNode, a.out, sT);
         }
     }
     __syncthreads();
@@ -979,6 +1006,7 @@ static void launch_elem_n(const ElemArgs<T> &a, int grid, cudaStream_t s) {
 template <typename T, int MODE>
 static void launch_elem_mode(const ElemArgs<T> &a, int grid, cudaStream_t s) {
     switch (a.N) {
+        case 1: launch_elem_n<T, MODE, 1>(a, grid, s); break;
         case 9: launch_elem_n<T, MODE, 9>(a, grid, s); break;
         case 13: launch_elem_n<T, MODE, 13>(a, grid, s); break;
         case 21: launch_elem_n<T, MODE, 21>(a, grid, s); break;
@@ -992,6 +1020,7 @@ void launch_elem(int mode, const ElemArgs<T> &a, int grid, cudaStream_t s) {
         case MODE_RES: launch_elem_mode<T, MODE_RES>(a, grid, s); break;
         case MODE_JVP: launch_elem_mode<T, MODE_JVP>(a, grid, s); break;
         case MODE_JVE: launch_elem_mode<T, MODE_JVE>(a, grid, s); break;
+        case MODE_TRES: launch_elem_n<T, MODE_TRES, 1>(a, grid, s); break;   // one time level
         default: launch_elem_mode<T, MODE_DIAG>(a, grid, s); break;
     }
 }

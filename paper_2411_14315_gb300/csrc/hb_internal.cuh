@@ -14,7 +14,9 @@ enum Mode : int {
     MODE_RES = 0,    // residual, Eq. (Rmc)
     MODE_JVP = 1,    // paper tangent (P + C) v, Eqs. (ptangent), (K_mat), (ctangent), (F_mat)
     MODE_JVE = 2,    // exact Jacobian-vector product
-    MODE_DIAG = 3    // Jacobi diagonal of P (+ pseudo mass), Sec. 2.3
+    MODE_DIAG = 3,   // Jacobi diagonal of P (+ pseudo mass), Sec. 2.3
+    MODE_TRES = 4    // time-domain GLS residual of one time level (Sec. 3, Eq. tauhat): the argument
+                     // slot of the direction holds du/dt; Galerkin rho M du/dt, no H terms
 };
 
 constexpr int kGeomStride = 16;       // per element: grad N_a (4 x 3), V, C_I nu^2 G:G, 2 pad
@@ -31,10 +33,10 @@ constexpr double kQB = 0.1381966011250105;
 // H u; JVE stages y, H u, v, H v.  Element contributions that need no instance coupling go straight to
 // global memory; RES and JVE accumulate T (3 fields) per patch node in shared memory for H T.
 __host__ __device__ constexpr int in_fields(int mode) {
-    return mode == MODE_RES ? 7 : mode == MODE_JVP ? 11 : mode == MODE_JVE ? 14 : 4;
+    return mode == MODE_RES ? 7 : mode == MODE_JVP ? 11 : mode == MODE_JVE ? 14 : mode == MODE_TRES ? 8 : 4;
 }
 __host__ __device__ constexpr int out_fields(int mode) {
-    return (mode == MODE_DIAG || mode == MODE_JVP) ? 0 : 3;
+    return (mode == MODE_RES || mode == MODE_JVE) ? 3 : 0;
 }
 
 // Element patches: elements renumbered so each patch's elements are contiguous; each patch lists its
@@ -60,12 +62,15 @@ template <typename T>
 struct ElemArgs {
     PatchView<T> pv;
     const T *y;                    // state, instance layout [n][4][N]
-    const T *v;                    // direction (JVP, JVE)
+    const T *v;                    // direction (JVP, JVE); du/dt (TRES)
     T *out;                        // accumulated output, instance layout (zeroed by the caller)
     const T *H;                    // [N][N]
     const uint8_t *flag;           // per node, bit 0: Dirichlet velocity
     int N;
     T rho, mu, shift;
+    T omega2 = 0;                  // acceleration term of tau_hat (Eq. tauhat); 0 for the HB passes
+    int ls_mass = 0;               // time domain (one instance): the shift also enters the least-squares L
+                                   // of the tangent (d(du/dt) = shift / rho d u); not its Jacobi diagonal
     const double *shift_dev = nullptr;   // if set, the shift is read from device memory instead
     int variant = 0;               // launch variant of the FP32 paper-tangent pass, [0, kJvpVariants)
 };
@@ -150,6 +155,19 @@ void launch_combine(const double *V, int64_t ld, int k, const double *c, double 
                     cudaStream_t s);
 void launch_dot(const double *x, const double *y, int64_t n, double *partials, double *result,
                 cudaStream_t s);
+
+// time-domain marching (generalized-alpha; node rows of 4 values, [n][4])
+// out[r] = series r at the period fraction frac (real series [rows][2 n_h + 1]: a0, a1, b1, ...)
+void launch_series_at(const double *coef, int64_t rows, int n_h, double frac, double *out, cudaStream_t s);
+// u1 = un, du1 = cg dun (cg = (gamma - 1) / gamma); prescribed velocities u1 = g (rows [n_dir][3]) with
+// du1 = (g - un) inv_gdt + cg dun
+void launch_galpha_predict(const double *un, const double *dun, double *u1, double *du1, int64_t n, double cg,
+                           const int *dir_nodes, int n_dir, const double *g, double inv_gdt, cudaStream_t s);
+void launch_galpha_stage(const double *un, const double *u1, const double *dun, const double *du1, double *ya,
+                         double *dya, int64_t n, double af, double am, cudaStream_t s);
+void launch_galpha_correct(double *u1, double *du1, const double *d, int64_t n, double inv_gdt, cudaStream_t s);
+void launch_put_instance(const double *src, double *dst, int64_t n4, int k, int N, cudaStream_t s);
+void launch_vel_norm2(const double *x, int64_t n, double *partials, double *result, cudaStream_t s);
 
 // Inputs of the learned warm start taken from a problem (host copies).
 constexpr int kLearnedFeatures = 32;  // per-node input features of the network

@@ -187,6 +187,93 @@ __global__ void __launch_bounds__(kVB) dot_kernel(const double *__restrict__ x, 
     }
 }
 
+// ---------------------------------------------------------------------------------------------------
+// time-domain marching (generalized-alpha, one time level per node row of 4 values)
+
+// out[r] = c0 + sum_k (c_{2k-1} cos k omega t + c_{2k} sin k omega t) for rows of real series
+// [rows][2 n_h + 1]; the phase is reduced exactly through the period fraction frac = t / T mod 1
+__global__ void series_at_kernel(const double *__restrict__ coef, int64_t rows, int n_h, double frac,
+                                 double *__restrict__ out) {
+    const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    const double *c = coef + r * (2 * n_h + 1);
+    double v = c[0];
+    for (int k = 1; k <= n_h; ++k) {
+        double f = double(k) * frac;
+        f -= floor(f);
+        double sn, cs;
+        sincospi(2.0 * f, &sn, &cs);
+        v += c[2 * k - 1] * cs + c[2 * k] * sn;
+    }
+    out[r] = v;
+}
+
+// predictor: u1 = un, du1 = (gamma - 1) / gamma dun (velocity; pressure rate unused)
+__global__ void galpha_predict_kernel(const double *__restrict__ un, const double *__restrict__ dun,
+                                      double *__restrict__ u1, double *__restrict__ du1, int64_t n, double cg) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    u1[i] = un[i];
+    du1[i] = (i & 3) == 3 ? 0.0 : cg * dun[i];
+}
+
+// prescribed velocities at t_{n+1}: u1 = g, du1 = (g - un) / (gamma dt) + (gamma - 1) / gamma dun
+__global__ void galpha_dirichlet_kernel(const int *__restrict__ nodes, int n_dir, const double *__restrict__ g,
+                                        const double *__restrict__ un, const double *__restrict__ dun,
+                                        double *__restrict__ u1, double *__restrict__ du1, double inv_gdt,
+                                        double cg) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= 3 * n_dir) return;
+    const int d = r / 3, i = r - 3 * d;
+    const int64_t k = int64_t(nodes[d]) * 4 + i;
+    u1[k] = g[r];
+    du1[k] = (g[r] - un[k]) * inv_gdt + cg * dun[k];
+}
+
+// stage values: ya = un + af (u1 - un), dya = dun + am (du1 - dun)
+__global__ void galpha_stage_kernel(const double *__restrict__ un, const double *__restrict__ u1,
+                                    const double *__restrict__ dun, const double *__restrict__ du1,
+                                    double *__restrict__ ya, double *__restrict__ dya, int64_t n, double af,
+                                    double am) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    ya[i] = un[i] + af * (u1[i] - un[i]);
+    dya[i] = dun[i] + am * (du1[i] - dun[i]);
+}
+
+// corrector: u1 += d, du1 += d / (gamma dt) on the velocity
+__global__ void galpha_correct_kernel(double *__restrict__ u1, double *__restrict__ du1,
+                                      const double *__restrict__ d, int64_t n, double inv_gdt) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    u1[i] += d[i];
+    if ((i & 3) != 3) du1[i] += d[i] * inv_gdt;
+}
+
+// dst[node][f][k] = src[node][f] for one instance column k of an [n][4][N] array
+__global__ void put_instance_kernel(const double *__restrict__ src, double *__restrict__ dst, int64_t n4, int k,
+                                    int N) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < n4) dst[i * N + k] = src[i];
+}
+
+// partials[b] = this block's share of sum over velocity entries (i mod 4 != 3) of x_i^2
+__global__ void __launch_bounds__(kVB) vel_norm2_kernel(const double *__restrict__ x, int64_t n,
+                                                        double *__restrict__ partials) {
+    __shared__ double red[kVB / 32];
+    double s = 0.0;
+    for (int64_t i = int64_t(blockIdx.x) * kVB + threadIdx.x; i < n; i += int64_t(gridDim.x) * kVB)
+        if ((i & 3) != 3) s = fma(x[i], x[i], s);
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < kVB / 32; ++q) t += red[q];
+        partials[blockIdx.x] = t;
+    }
+}
+
 // gate = 1 when classical Gram-Schmidt lost more than half of ||w||^2 (a second pass is needed)
 __global__ void reorth_gate_kernel(const double *before2, const double *after2, int *gate) {
     *gate = (*after2 < 0.5 * *before2) ? 1 : 0;
@@ -350,6 +437,37 @@ void launch_dot(const double *x, const double *y, int64_t n, double *partials, d
                 cudaStream_t s) {
     const int nb = stream_grid(n);
     dot_kernel<<<nb, kVB, 0, s>>>(x, y, n, partials);
+    finish_kernel<<<1, 256, 0, s>>>(partials, nb, 1, 1, result);
+}
+
+void launch_series_at(const double *coef, int64_t rows, int n_h, double frac, double *out, cudaStream_t s) {
+    if (rows > 0) series_at_kernel<<<nblk(rows, 128), 128, 0, s>>>(coef, rows, n_h, frac, out);
+}
+
+void launch_galpha_predict(const double *un, const double *dun, double *u1, double *du1, int64_t n, double cg,
+                           const int *dir_nodes, int n_dir, const double *g, double inv_gdt, cudaStream_t s) {
+    if (n > 0) galpha_predict_kernel<<<nblk(n, kVB), kVB, 0, s>>>(un, dun, u1, du1, n, cg);
+    if (n_dir > 0)
+        galpha_dirichlet_kernel<<<nblk(int64_t(3) * n_dir, kVB), kVB, 0, s>>>(dir_nodes, n_dir, g, un, dun, u1, du1,
+                                                                              inv_gdt, cg);
+}
+
+void launch_galpha_stage(const double *un, const double *u1, const double *dun, const double *du1, double *ya,
+                         double *dya, int64_t n, double af, double am, cudaStream_t s) {
+    if (n > 0) galpha_stage_kernel<<<nblk(n, kVB), kVB, 0, s>>>(un, u1, dun, du1, ya, dya, n, af, am);
+}
+
+void launch_galpha_correct(double *u1, double *du1, const double *d, int64_t n, double inv_gdt, cudaStream_t s) {
+    if (n > 0) galpha_correct_kernel<<<nblk(n, kVB), kVB, 0, s>>>(u1, du1, d, n, inv_gdt);
+}
+
+void launch_put_instance(const double *src, double *dst, int64_t n4, int k, int N, cudaStream_t s) {
+    if (n4 > 0) put_instance_kernel<<<nblk(n4, kVB), kVB, 0, s>>>(src, dst, n4, k, N);
+}
+
+void launch_vel_norm2(const double *x, int64_t n, double *partials, double *result, cudaStream_t s) {
+    const int nb = stream_grid(n);
+    vel_norm2_kernel<<<nb, kVB, 0, s>>>(x, n, partials);
     finish_kernel<<<1, 256, 0, s>>>(partials, nb, 1, 1, result);
 }
 

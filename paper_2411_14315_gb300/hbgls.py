@@ -52,6 +52,22 @@ class hb_report(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class hb_march_opts(C.Structure):
+    _fields_ = [("precision", C.c_int), ("steps_per_period", C.c_int), ("periods", C.c_int),
+                ("rho_inf", C.c_double), ("newton_rtol", C.c_double), ("newton_max", C.c_int),
+                ("gmres_rtol", C.c_double), ("gmres_restart", C.c_int), ("max_gmres", C.c_int),
+                ("tau_acceleration", C.c_int), ("verbose", C.c_int)]
+
+
+class hb_march_report(C.Structure):
+    _fields_ = [("steps", C.c_int), ("newton_iters", C.c_int), ("gmres_iters", C.c_int), ("jv_calls", C.c_int),
+                ("seconds", C.c_double), ("period_change", C.c_double), ("max_newton_rel", C.c_double),
+                ("status", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class hb_info(C.Structure):
     _fields_ = [("n_nodes", C.c_int64), ("n_tets", C.c_int64), ("n_faces", C.c_int64),
                 ("n_dirichlet_nodes", C.c_int64), ("n_neumann_faces", C.c_int64), ("n_h", C.c_int),
@@ -84,6 +100,11 @@ SIGNATURES = {
     "hb_solve": ([_P, C.POINTER(hb_solve_opts), C.POINTER(hb_report)], C.c_int),
     "hb_get_harmonics": ([_P, _DP], C.c_int),
     "hb_get_instances": ([_P, _DP], C.c_int),
+    "hb_default_march_opts": ([C.POINTER(hb_march_opts)], C.c_int),
+    "hb_march": ([_P, C.POINTER(hb_march_opts), C.POINTER(hb_march_report)], C.c_int),
+    "hb_get_march_samples": ([_P, _DP], C.c_int),
+    "hb_time_residual": ([_P, _DP, _DP, _DP, C.c_int, C.c_double, C.c_double], C.c_int),
+    "hb_time_jv": ([_P, _DP, _DP, _DP, C.c_int, C.c_double, C.c_double], C.c_int),
     "hb_residual": ([_P, _DP, _DP, C.c_int], C.c_int),
     "hb_jv": ([_P, _DP, _DP, _DP, C.c_int, C.c_int, C.c_double], C.c_int),
     "hb_jacobi_diag": ([_P, _DP, _DP, C.c_int, C.c_double], C.c_int),
@@ -329,6 +350,40 @@ class Problem:
     def instances(self):
         out = np.empty(self.shape)
         _check(lib().hb_get_instances(self._h, _dptr(out)))
+        return out
+
+    def march(self, check: bool = True, **kw):
+        """Time-domain march (hb_march); keyword arguments set hb_march_opts fields."""
+        o = hb_march_opts()
+        _check(lib().hb_default_march_opts(C.byref(o)))
+        for k, v in kw.items():
+            setattr(o, k, v)
+        rep = hb_march_report()
+        st = lib().hb_march(self._h, C.byref(o), C.byref(rep))
+        if check:
+            _check(st)
+        return rep.as_dict()
+
+    def time_residual(self, y, ydot, t: float, omega2: float = 0.0, precision: int = 0):
+        """Residual of one time level [n_nodes, 4] (hb_time_residual)."""
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        yd = np.ascontiguousarray(ydot, dtype=np.float64)
+        out = np.empty((self.n_nodes, 4))
+        _check(lib().hb_time_residual(self._h, _dptr(y), _dptr(yd), _dptr(out), precision, t, omega2))
+        return out
+
+    def time_jv(self, y, v, omega2: float = 0.0, shift: float = 0.0, precision: int = 0):
+        """Paper tangent of one time level along v [n_nodes, 4] (hb_time_jv)."""
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        v = np.ascontiguousarray(v, dtype=np.float64)
+        out = np.empty((self.n_nodes, 4))
+        _check(lib().hb_time_jv(self._h, _dptr(y), _dptr(v), _dptr(out), precision, omega2, shift))
+        return out
+
+    def march_samples(self):
+        """State of the last march at the N instance times of its last period, [n_nodes, 4, N]."""
+        out = np.empty(self.shape)
+        _check(lib().hb_get_march_samples(self._h, _dptr(out)))
         return out
 
     def info(self):

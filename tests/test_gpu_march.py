@@ -1,0 +1,104 @@
+"""The time-domain march (the conventional solver the paper compares with, Sec. 3) against the
+time-marching oracle: one time level's residual and paper tangent with tau_hat, element by element (FP64
+1e-12, FP32 1e-5) at random states and times, and a short march driven to tight tolerances whose states
+at the instance times are the oracle march's; then, at the paper's solver settings, a march of the
+Womersley pipe against the closed form, next to the HB solution."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import hb_oracle as O
+from oracle import tm_oracle as TM
+from oracle import womersley as Wo
+from paper_2411_14315_gb300 import workloads as W
+from tests import problems as P
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-12, 1: 1e-5}
+
+
+def relerr(a, b):
+    out = 0.0
+    for f in range(b.shape[1]):
+        n = np.linalg.norm(b[:, f])
+        d = np.linalg.norm(a[:, f] - b[:, f])
+        out = max(out, d / n if n > 0 else d)
+    return out
+
+
+@pytest.fixture(scope="module")
+def box():
+    spec = P.box_spec(n=(6, 5, 4), n_h=3)
+    return spec, P.oracle_problem(spec), P.gpu_problem(spec)
+
+
+def _state(ora, t, seed):
+    rng = np.random.default_rng(seed)
+    y = rng.uniform(-1, 1, (ora.n_nodes, 4))
+    mask, g = TM.dirichlet_at(ora, t)
+    y[mask, :3] = g[mask]
+    return y, rng.uniform(-1, 1, (ora.n_nodes, 4))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("t,omega2", [(0.0, 0.0), (0.61, 2.5), (1.3, 0.04)])
+def test_time_residual_matches_oracle(box, precision, t, omega2):
+    spec, ora, gp = box
+    y, yd = _state(ora, t, 17)
+    ref = TM.residual(ora, y, yd, t, omega2)
+    assert relerr(gp.time_residual(y, yd, t, omega2, precision), ref) < TOL[precision]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_time_tangent_matches_oracle(box, precision):
+    spec, ora, gp = box
+    y, v = _state(ora, 0.4, 18)
+    ref = TM.jv_paper(ora, y, v, 1.7, 3.1)
+    assert relerr(gp.time_jv(y, v, 1.7, 3.1, precision), ref) < TOL[precision]
+
+
+def test_march_matches_oracle_march():
+    spec = P.channel_spec(n_h=1)
+    ora = P.oracle_problem(spec)
+    N, spp = spec.N, 12
+    # the library starts from rest with the pressure at the outlets' mean level
+    y0 = np.zeros((ora.n_nodes, 4))
+    y0[:, 3] = np.mean([a[0] for (a, b) in ora.outlet_p.values()])
+    _, _, recs = TM.march(ora, spp, 1, rho_inf=0.5, newton_tol=1e-12, newton_max=40, gmres_tol=1e-13, y0=y0,
+                          record_every=spp // N)
+    gp = P.gpu_problem(spec)
+    rep = gp.march(precision=0, steps_per_period=spp, periods=1, newton_rtol=1e-12, newton_max=40,
+                   gmres_rtol=1e-13, gmres_restart=60, max_gmres=3000)
+    assert rep["status"] == 0 and rep["steps"] == spp
+    s = gp.march_samples()
+    for j in range(N):
+        ref = recs[(j - 1) % N]                 # record i holds t = (i + 1) T / N; sample j holds t = j T / N
+        assert relerr(s[:, :, j], ref) < 1e-9, j
+    gp.close()
+
+
+def test_march_of_womersley_pipe_against_closed_form():
+    """Marched from rest for 3 periods (252 steps each, GMRES 0.03, Newton 1e-3 per step), the pipe's last
+    period is periodic to 1 % and as close to Womersley's solution as the HB solution is (bound 0.08)."""
+    spec = W.womersley_spec(level=1)
+    tag, _, a, b = spec.inflows[0]
+    omega = 2 * math.pi / spec.T
+    exact = Wo.pipe_solution(spec.mesh.xyz, a, b, 1.0, 5.0, spec.rho, spec.mu, omega)
+    spec.inflows = []
+    spec.inflows_harm = [(tag, exact[:, :3])]
+    ex = O.harmonics_to_instances(exact, spec.N, spec.T)
+    hb = P.gpu_problem(spec)
+    assert hb.solve(precision=1, rtol=1e-8, max_steps=300)["status"] == 0
+    e_hb = float(np.linalg.norm(hb.instances()[:, :3] - ex[:, :3]) / np.linalg.norm(ex[:, :3]))
+    tm = P.gpu_problem(spec)
+    rep = tm.march(precision=1, steps_per_period=28 * spec.N, periods=3)
+    s = tm.march_samples()
+    e_tm = float(np.linalg.norm(s[:, :3] - ex[:, :3]) / np.linalg.norm(ex[:, :3]))
+    print(f"velocity error vs closed form: HB {e_hb:.4f}, time marching {e_tm:.4f}; "
+          f"period change {rep['period_change']:.2e}, {rep['seconds']:.1f} s")
+    assert rep["period_change"] < 1e-2
+    assert e_tm < 0.08
+    hb.close()
+    tm.close()

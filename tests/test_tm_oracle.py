@@ -47,14 +47,63 @@ def test_zero_acceleration_is_the_steady_hb_problem():
     r_tm = TM.residual(pr, y, np.zeros_like(y), 0.3, 0.0)
     r_hb = O.residual(pr, y[:, :, None])[:, :, 0]
     assert np.max(np.abs(r_tm - r_hb)) <= 1e-12 * np.max(np.abs(r_hb))
-    j_tm = TM.jv_paper(pr, y, v, 0.0, 2.5)
-    j_hb = O.jv_paper(pr, y[:, :, None], v[:, :, None], shift=2.5)[:, :, 0]
+    # without a step (no acceleration term) the tangent and its diagonal are the steady ones
+    j_tm = TM.jv_paper(pr, y, v, 0.0, 0.0)
+    j_hb = O.jv_paper(pr, y[:, :, None], v[:, :, None], shift=0.0)[:, :, 0]
     assert np.max(np.abs(j_tm - j_hb)) <= 1e-12 * np.max(np.abs(j_hb))
-    d_tm = TM.jacobi_diag(pr, y, 0.0, 2.5)
-    d_hb = O.jacobi_diag(pr, y[:, :, None], shift=2.5)[:, :, 0]
+    d_tm = TM.jacobi_diag(pr, y, 0.0, 0.0)
+    d_hb = O.jacobi_diag(pr, y[:, :, None], shift=0.0)[:, :, 0]
     assert np.max(np.abs(d_tm - d_hb)) <= 1e-12 * np.max(np.abs(d_hb))
     # the acceleration term of tau_hat only lowers tau: a large omega_hat changes the residual
     assert np.max(np.abs(TM.residual(pr, y, np.zeros_like(y), 0.3, 1e3) - r_tm)) > 1e-6
+
+
+@pytest.mark.parametrize("omega2", [0.0, 2.0])
+def test_tangent_acceleration_terms_are_exact(omega2):
+    """For a given omega_hat the residual is affine in du/dt, so the part of the tangent that the step
+    adds (shift M v and the least-squares c1 rho / dt v terms of both rows) must equal the central
+    difference of r along du/dt = shift / rho v_velocity, at any state; at rest with a uniform pressure
+    (L = 0) the whole tangent is the exact derivative along (v, shift / rho v_velocity)."""
+    m, pr = _random_problem(1)
+    rng = np.random.default_rng(8)
+    mask, g = TM.dirichlet_at(pr, 0.2)
+    v = rng.uniform(-1, 1, (m.n_nodes, 4))
+    v[mask, :3] = 0.0
+    rho, shift, eps = pr.rho, 7.3, 1e-3
+    dyd = np.zeros_like(v)
+    dyd[:, :3] = shift / rho * v[:, :3]
+    # any state: the acceleration part
+    y = rng.uniform(-1, 1, (m.n_nodes, 4))
+    y[mask, :3] = g[mask]
+    yd = rng.uniform(-1, 1, (m.n_nodes, 4))
+    fd = (TM.residual(pr, y, yd + eps * dyd, 0.2, omega2) - TM.residual(pr, y, yd - eps * dyd, 0.2, omega2)) / (2 * eps)
+    part = TM.jv_paper(pr, y, v, omega2, shift) - TM.jv_paper(pr, y, v, omega2, 0.0)
+    assert np.max(np.abs(part - fd)) <= 1e-10 * np.max(np.abs(fd))
+    # at rest with a uniform pressure: the whole tangent
+    y = np.zeros((m.n_nodes, 4))
+    y[:, 3] = 0.7
+    yd = np.zeros((m.n_nodes, 4))
+    fd = (TM.residual(pr, y + eps * v, yd + eps * dyd, 0.2, omega2)
+          - TM.residual(pr, y - eps * v, yd - eps * dyd, 0.2, omega2)) / (2 * eps)
+    jv = TM.jv_paper(pr, y, v, omega2, shift)
+    jv[mask, :3] = 0.0                        # Dirichlet rows: identity on v vs zero rows of r
+    # (the backflow term is one-sided at rest: its central difference is O(eps))
+    assert np.max(np.abs(jv - fd)) <= eps * np.max(np.abs(fd))
+    # Jacobi diagonal = e_k^T J e_k, J without the least-squares acceleration term, for free velocity and
+    # pressure unknowns off the Neumann faces (the diagonal holds the volume terms) at a random state
+    y = rng.uniform(-1, 1, (m.n_nodes, 4))
+    y[mask, :3] = g[mask]
+    d = TM.jacobi_diag(pr, y, omega2, shift)
+    on_faces = np.zeros(m.n_nodes, dtype=bool)
+    on_faces[pr.faces[pr.neumann_faces()].ravel()] = True
+    nodes = np.nonzero(~mask & ~on_faces)[0][:4]
+    assert nodes.size > 0
+    for node in nodes:
+        for f in (0, 3):
+            e = np.zeros_like(v)
+            e[node, f] = 1.0
+            jk = TM.jv_paper(pr, y, e, omega2, shift, ls_acceleration=False)[node, f]
+            assert abs(jk - d[node, f]) <= 1e-12 * abs(d[node, f])
 
 
 def _plug(T=2.0, rho=1.3, mu=0.05, seed=1, n=(4, 3, 3), a1=0.12, b1=-0.08):
