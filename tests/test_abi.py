@@ -12,7 +12,7 @@ HEADER = os.path.join(ROOT, "include", "hbgls.h")
 def declared_functions():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    names = re.findall(r"^\s*(?:hb_status|const char \*|int64_t)\s*\**\s*(hb_\w+)\s*\(", text, flags=re.M)
+    names = re.findall(r"^\s*(?:hb_status|const char \*|int64_t|int)\s*\**\s*(hb_\w+)\s*\(", text, flags=re.M)
     return sorted(set(names))
 
 
