@@ -122,6 +122,8 @@ typedef struct {
     double ser_max;           /* cap of that growth factor                                             */
     double r_ref;             /* > 0: residual scale of rtol and switch_rtol instead of ||r0|| (lets a
                                  warm-started solve stop at the same absolute residual as a cold one)  */
+    int assembled;            /* 1: in the paper-tangent phase assemble the tangent once per step
+                                 (hb_assemble_dev) and let GMRES apply it as a sparse product          */
 } hb_solve_opts;
 
 typedef struct {
@@ -145,7 +147,9 @@ hb_status hb_get_instances(hb_problem *p, double *out);
  * rows of Dirichlet nodes are 0.  precision 0 = FP64 kernels, 1 = FP32 kernels (inputs rounded). */
 hb_status hb_residual(hb_problem *p, const double *y, double *r, int precision);
 /* Jacobian-vector product at state y along v.  kind 0: the paper's tangent (P + C, Eqs. ptangent,
- * K_mat, ctangent, F_mat) with U and tau frozen at y; kind 1: the exact derivative of hb_residual.
+ * K_mat, ctangent, F_mat) with U and tau frozen at y; kind 1: the exact derivative of hb_residual;
+ * kind 2: the paper's tangent assembled at y (Sec. 4's condensed storage, see hb_assemble_dev) and
+ * applied as a sparse product (same operator as kind 0 up to rounding).
  * shift adds shift * M v on the velocity rows (pseudo time term, Sec. 2.3: shift = c1 rho / dt).
  * Dirichlet velocity rows return v (identity); v's Dirichlet velocity entries are treated as 0. */
 hb_status hb_jv(hb_problem *p, const double *y, const double *v, double *jv, int kind, int precision,
@@ -159,6 +163,12 @@ hb_status hb_jacobi_diag(hb_problem *p, const double *y, double *d, int precisio
 hb_status hb_residual_dev(hb_problem *p, const void *y, void *r, int precision, void *stream);
 hb_status hb_jv_dev(hb_problem *p, const void *y, const void *v, void *jv, int kind, int precision,
                     double shift, void *stream);
+/* Assemble the paper's tangent at the device state y (double for precision 0, float for 1): per node pair
+ * and instance the blocks K, G, D, L of Eqs. (K_mat), (ctangent) with U and tau frozen at y, and per pair
+ * the mass matrix (for the F block and the pseudo-time shift, applied as M (shift v + rho H v)); stored in
+ * the problem (about 32 N bytes per node pair in FP32).  hb_jv_dev with kind 2 then applies the last
+ * assembly (HB_ERR_STATE before one); the y argument of that call is used for the boundary terms. */
+hb_status hb_assemble_dev(hb_problem *p, const void *y, int precision, void *stream);
 hb_status hb_jacobi_diag_dev(hb_problem *p, const void *y, void *d, int precision, double shift,
                              void *stream);
 
@@ -304,6 +314,7 @@ typedef struct {
     double h_char;            /* edge of the regular tetrahedron of mean element volume (Sec. 2.3) */
     double u_ref;             /* largest mean inlet speed over the instances (CFL rule of Sec. 2.3)  */
     double p_ref;             /* mean outlet pressure level over outlets and instances              */
+    int64_t assembled_pairs;  /* node pairs of the assembled tangent (0 before hb_assemble_dev)     */
 } hb_info;
 hb_status hb_get_info(hb_problem *p, hb_info *info);
 /* Number of kernel launches queued by this problem since creation (all entry points). */

@@ -148,7 +148,7 @@ struct hb_problem {
         int m = 0, precision = -1;
         double shift = 0;
         int64_t launches = 0;
-    } cycle[2];
+    } cycle[3];                        // paper tangent, exact Jacobian, assembled paper tangent
     DBuf<double> gm;
     DBuf<int> gate;
     DBuf<double> shift_dev;
@@ -156,6 +156,15 @@ struct hb_problem {
     // element-kernel timing
     bool prof_on = false;
     DBuf<double> ylearn, kd;              // learned prediction and the direction towards it (use_learned 2)
+    // assembled paper tangent (Sec. 4's condensed storage): CSR of node pairs, element -> pair slots
+    struct Assembled {
+        int64_t nnz = 0;
+        DBuf<int> rowptr, col, epos, tets;
+        DBuf<float> geom32, coef32, mass32, W32;
+        DBuf<double> geom64, coef64, mass64, W64;
+        bool ready32 = false, ready64 = false;   // coefficients assembled (at the last state given)
+        bool mass32_done = false, mass64_done = false;
+    } as;
     double omega2 = 0;                    // acceleration term of tau_hat in the element passes (time domain)
     int ls_mass = 0;                      // time domain: the shift enters the tangent's least-squares L too
     hb_problem *tm = nullptr;             // internal one-instance copy that runs the time-domain march
@@ -604,15 +613,158 @@ hb_status prepare_bc(hb_problem *p) {
 }
 
 // ---------------------------------------------------------------------------------------------------
+// assembled paper tangent: structure (host, once), assembly at a state, application
+
+hb_status asm_structure(hb_problem *p) {
+    hb_problem::Assembled &A = p->as;
+    if (A.nnz > 0) return HB_OK;
+    const int64_t n = p->n_nodes, E = p->n_tets;
+    // rows: each node's neighbours over its elements (itself included), sorted
+    std::vector<std::vector<int>> nb(static_cast<size_t>(n));
+    for (int64_t e = 0; e < E; ++e)
+        for (int a = 0; a < 4; ++a)
+            for (int b = 0; b < 4; ++b) nb[size_t(p->tets[size_t(4 * e + a)])].push_back(p->tets[size_t(4 * e + b)]);
+    std::vector<int> rowptr(static_cast<size_t>(n + 1), 0), col;
+    for (int64_t i = 0; i < n; ++i) {
+        std::vector<int> &r = nb[size_t(i)];
+        std::sort(r.begin(), r.end());
+        r.erase(std::unique(r.begin(), r.end()), r.end());
+        col.insert(col.end(), r.begin(), r.end());
+        rowptr[size_t(i + 1)] = int(col.size());
+    }
+    if (col.size() >= size_t(1) << 31) return fail(HB_ERR_INVALID_ARG, "too many node pairs for the assembled operator");
+    // elements in Morton order; pair slot of each (a, b)
+    std::vector<int> tets(static_cast<size_t>(4 * E)), epos(static_cast<size_t>(16 * E));
+    for (int64_t k = 0; k < E; ++k) {
+        const int32_t *t = p->tets_morton.data() + 4 * k;
+        for (int a = 0; a < 4; ++a) {
+            tets[size_t(4 * k + a)] = t[a];
+            const int r0 = rowptr[size_t(t[a])], r1 = rowptr[size_t(t[a]) + 1];
+            for (int b = 0; b < 4; ++b) {
+                const int *f = std::lower_bound(col.data() + r0, col.data() + r1, t[b]);
+                epos[size_t(16 * k + 4 * a + b)] = int(f - col.data());
+            }
+        }
+    }
+    HB_TRY(upload(p, A.rowptr, rowptr));
+    HB_TRY(upload(p, A.col, col));
+    HB_TRY(upload(p, A.tets, tets));
+    HB_TRY(upload(p, A.epos, epos));
+    A.nnz = int64_t(col.size());
+    return HB_OK;
+}
+
+template <typename T>
+struct AsmBufs;
+template <>
+struct AsmBufs<float> {
+    static DBuf<float> &geom(hb_problem::Assembled &A) { return A.geom32; }
+    static DBuf<float> &coef(hb_problem::Assembled &A) { return A.coef32; }
+    static DBuf<float> &mass(hb_problem::Assembled &A) { return A.mass32; }
+    static DBuf<float> &W(hb_problem::Assembled &A) { return A.W32; }
+    static bool &ready(hb_problem::Assembled &A) { return A.ready32; }
+    static bool &mass_done(hb_problem::Assembled &A) { return A.mass32_done; }
+};
+template <>
+struct AsmBufs<double> {
+    static DBuf<double> &geom(hb_problem::Assembled &A) { return A.geom64; }
+    static DBuf<double> &coef(hb_problem::Assembled &A) { return A.coef64; }
+    static DBuf<double> &mass(hb_problem::Assembled &A) { return A.mass64; }
+    static DBuf<double> &W(hb_problem::Assembled &A) { return A.W64; }
+    static bool &ready(hb_problem::Assembled &A) { return A.ready64; }
+    static bool &mass_done(hb_problem::Assembled &A) { return A.mass64_done; }
+};
+
+// Assemble the paper tangent's volume blocks at state y (device, precision T) on stream s.
+template <typename T>
+hb_status assemble_at(hb_problem *p, const T *y, cudaStream_t s) {
+    HB_TRY(prepare_bc(p));
+    HB_TRY(asm_structure(p));
+    hb_problem::Assembled &A = p->as;
+    using B = AsmBufs<T>;
+    const int N = p->N;
+    if (!B::geom(A).p) {
+        HB_TRY(dalloc(p, B::geom(A), size_t(p->n_tets) * kGeomStride));
+        launch_geom<T>(p->d_xyz.p, A.tets.p, int(p->n_tets), p->mu / p->rho, B::geom(A).p, s);
+        HB_LAUNCHED(p, 1);
+    }
+    HB_TRY(dalloc(p, B::coef(A), size_t(A.nnz) * 8 * size_t(N)));
+    HB_TRY(dalloc(p, B::mass(A), size_t(A.nnz)));
+    HB_TRY(dalloc(p, B::W(A), size_t(p->n_nodes) * 3 * size_t(N)));
+    AsmArgs<T> a;
+    a.n_tets = p->n_tets;
+    a.N = N;
+    a.tets = A.tets.p;
+    a.geom = B::geom(A).p;
+    a.epos = A.epos.p;
+    a.flag = p->d_flag.p;
+    a.y = y;
+    a.coef = B::coef(A).p;
+    a.mass = B::mass(A).p;
+    a.rho = T(p->rho);
+    a.mu = T(p->mu);
+    if (!B::mass_done(A)) {
+        HB_CUDA(cudaMemsetAsync(a.mass, 0, size_t(A.nnz) * sizeof(T), s));
+        launch_assemble_mass<T>(a, s);
+        HB_LAUNCHED(p, 1);
+        B::mass_done(A) = true;
+    }
+    HB_CUDA(cudaMemsetAsync(a.coef, 0, size_t(A.nnz) * 8 * size_t(N) * sizeof(T), s));
+    launch_assemble<T>(a, s);
+    HB_LAUNCHED(p, 1);
+    B::ready(A) = true;
+    return HB_OK;
+}
+
+// ---------------------------------------------------------------------------------------------------
 // operators
 
 template <typename T>
 hb_status apply_op(hb_problem *p, int mode, const T *y, const T *v, T *out, double shift, cudaStream_t s,
                    const double *shift_dev = nullptr) {
     HB_TRY(prepare_bc(p));
-    PatchSetDev<T> &ps = patches<T>(p, mode);
     const int N = p->N;
-    HB_CUDA(cudaMemsetAsync(out, 0, size_t(p->n_nodes) * 4 * N * sizeof(T), s));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto prof_begin = [&]() -> hb_status {
+        if (p->prof_on) {
+            if (p->prof_used == p->prof_ev.size()) {
+                HB_CUDA(cudaEventCreate(&e0));
+                HB_CUDA(cudaEventCreate(&e1));
+                p->prof_ev.push_back({e0, e1});
+            }
+            e0 = p->prof_ev[p->prof_used].first;
+            e1 = p->prof_ev[p->prof_used].second;
+            ++p->prof_used;
+            HB_CUDA(cudaEventRecord(e0, s));
+        }
+        return HB_OK;
+    };
+    if (mode == MODE_JVA) {
+        // assembled paper tangent: W = shift v + rho H v per node, then the row-wise product (every entry
+        // of out written); the boundary terms follow as for the element path
+        hb_problem::Assembled &A = p->as;
+        using B = AsmBufs<T>;
+        if (!B::ready(A)) return fail(HB_ERR_STATE, "no assembled operator in this precision (hb_assemble_dev)");
+        launch_spectral_w<T>(v, Hmat<T>(p), p->d_flag.p, B::W(A).p, p->n_nodes, N, T(p->rho), T(shift), shift_dev, s);
+        SpmvArgs<T> sa;
+        sa.n_nodes = p->n_nodes;
+        sa.N = N;
+        sa.rowptr = A.rowptr.p;
+        sa.col = A.col.p;
+        sa.coef = B::coef(A).p;
+        sa.mass = B::mass(A).p;
+        sa.v = v;
+        sa.W = B::W(A).p;
+        sa.out = out;
+        sa.flag = p->d_flag.p;
+        HB_TRY(prof_begin());
+        launch_spmv<T>(sa, s);
+        if (p->prof_on) HB_CUDA(cudaEventRecord(e1, s));
+        HB_LAUNCHED(p, 2);
+    }
+    const int fmode = mode == MODE_JVA ? MODE_JVP : mode;     // boundary terms of the paper tangent
+    PatchSetDev<T> &ps = patches<T>(p, fmode);
+    if (mode != MODE_JVA) HB_CUDA(cudaMemsetAsync(out, 0, size_t(p->n_nodes) * 4 * N * sizeof(T), s));
     ElemArgs<T> ea;
     ea.pv = ps.view();
     ea.y = y;
@@ -628,19 +780,8 @@ hb_status apply_op(hb_problem *p, int mode, const T *y, const T *v, T *out, doub
     ea.omega2 = T(p->omega2);
     ea.ls_mass = p->ls_mass;
     ea.variant = p->jvp_variant;
-    if (ps.P > 0) {
-        cudaEvent_t e0 = nullptr, e1 = nullptr;
-        if (p->prof_on) {
-            if (p->prof_used == p->prof_ev.size()) {
-                HB_CUDA(cudaEventCreate(&e0));
-                HB_CUDA(cudaEventCreate(&e1));
-                p->prof_ev.push_back({e0, e1});
-            }
-            e0 = p->prof_ev[p->prof_used].first;
-            e1 = p->prof_ev[p->prof_used].second;
-            ++p->prof_used;
-            HB_CUDA(cudaEventRecord(e0, s));
-        }
+    if (ps.P > 0 && mode != MODE_JVA) {
+        HB_TRY(prof_begin());
         launch_elem<T>(mode, ea, ps.P, s);
         HB_LAUNCHED(p, 1);
         if (p->prof_on) HB_CUDA(cudaEventRecord(e1, s));
@@ -669,7 +810,7 @@ hb_status apply_op(hb_problem *p, int mode, const T *y, const T *v, T *out, doub
             fa.Q = p->d_Q64.p;
         }
         if (p->has_res) HB_CUDA(cudaMemsetAsync(fa.Q, 0, size_t(p->n_out) * N * sizeof(T), s));
-        launch_faces<T>(mode, fa, p->has_res, p->n_out, s);
+        launch_faces<T>(fmode, fa, p->has_res, p->n_out, s);
         HB_LAUNCHED(p, p->has_res ? 2 : 1);
     }
     return HB_OK;
@@ -683,7 +824,7 @@ hb_status check_precision(int precision) {
 // host-buffer wrapper: copies in, converts, applies, converts, copies out
 hb_status host_op(hb_problem *p, int mode, const double *y, const double *v, double *out, int precision,
                   double shift) {
-    if (!p || !y || !out || ((mode == MODE_JVP || mode == MODE_JVE || mode == MODE_TRES) && !v))
+    if (!p || !y || !out || ((mode == MODE_JVP || mode == MODE_JVE || mode == MODE_TRES || mode == MODE_JVA) && !v))
         return fail(HB_ERR_INVALID_ARG, "null argument");
     HB_TRY(check_precision(precision));
     const size_t nd = size_t(p->n_nodes) * 4 * p->N;
@@ -691,7 +832,7 @@ hb_status host_op(hb_problem *p, int mode, const double *y, const double *v, dou
     HB_TRY(dalloc(p, p->w64a, nd));
     HB_TRY(dalloc(p, p->w64b, nd));
     HB_CUDA(cudaMemcpyAsync(p->w64a.p, y, nd * sizeof(double), cudaMemcpyHostToDevice, p->stream));
-    const bool jv = (mode == MODE_JVP || mode == MODE_JVE || mode == MODE_TRES);   // second operand
+    const bool jv = (mode == MODE_JVP || mode == MODE_JVE || mode == MODE_TRES || mode == MODE_JVA);   // second operand
     if (precision == 0) {
         double *vd = nullptr;
         if (jv) {
@@ -699,6 +840,7 @@ hb_status host_op(hb_problem *p, int mode, const double *y, const double *v, dou
             HB_CUDA(cudaMemcpyAsync(p->kres.p, v, nd * sizeof(double), cudaMemcpyHostToDevice, p->stream));
             vd = p->kres.p;
         }
+        if (mode == MODE_JVA) HB_TRY(assemble_at<double>(p, p->w64a.p, p->stream));   // at y, then apply
         HB_TRY(apply_op<double>(p, mode, p->w64a.p, vd, p->w64b.p, shift, p->stream));
     } else {
         HB_TRY(dalloc(p, p->w32a, nd));
@@ -711,6 +853,7 @@ hb_status host_op(hb_problem *p, int mode, const double *y, const double *v, dou
             launch_convert<double, float>(p->w64b.p, p->w32c.p, int64_t(nd), p->stream);
             HB_LAUNCHED(p, 1);
         }
+        if (mode == MODE_JVA) HB_TRY(assemble_at<float>(p, p->w32a.p, p->stream));     // at y, then apply
         HB_TRY(apply_op<float>(p, mode, p->w32a.p, jv ? p->w32c.p : nullptr, p->w32b.p, shift, p->stream));
         launch_convert<float, double>(p->w32b.p, p->w64b.p, int64_t(nd), p->stream);
         HB_LAUNCHED(p, 1);
@@ -722,7 +865,7 @@ hb_status host_op(hb_problem *p, int mode, const double *y, const double *v, dou
 
 hb_status dev_op(hb_problem *p, int mode, const void *y, const void *v, void *out, int precision, double shift,
                  void *stream) {
-    if (!p || !y || !out || ((mode == MODE_JVP || mode == MODE_JVE) && !v))
+    if (!p || !y || !out || ((mode == MODE_JVP || mode == MODE_JVE || mode == MODE_JVA) && !v))
         return fail(HB_ERR_INVALID_ARG, "null argument");
     HB_TRY(check_precision(precision));
     if (out == y || (v && out == v)) return fail(HB_ERR_INVALID_ARG, "output aliases an input");
@@ -839,7 +982,7 @@ hb_status record_cycle(hb_problem *p, const OpCtx &c, int m) {
 }
 
 hb_status cycle_graph(hb_problem *p, const OpCtx &c, int m, hb_problem::CycleGraph *&out) {
-    hb_problem::CycleGraph &gc = p->cycle[c.mode == MODE_JVE ? 1 : 0];
+    hb_problem::CycleGraph &gc = p->cycle[c.mode == MODE_JVE ? 1 : c.mode == MODE_JVA ? 2 : 0];
     out = &gc;
     const double key = c.shift_dev ? -1.0 : c.shift;
     if (gc.exec && gc.m == m && gc.precision == c.precision && gc.shift == key) return HB_OK;
@@ -1451,9 +1594,12 @@ hb_status hb_residual(hb_problem *p, const double *y, double *r, int precision) 
     return host_op(p, MODE_RES, y, nullptr, r, precision, 0.0);
 }
 
+static int jv_mode(int kind) { return kind == 0 ? MODE_JVP : kind == 1 ? MODE_JVE : MODE_JVA; }
+
 hb_status hb_jv(hb_problem *p, const double *y, const double *v, double *jv, int kind, int precision, double shift) {
-    if (kind != 0 && kind != 1) return fail(HB_ERR_INVALID_ARG, "kind must be 0 (paper tangent) or 1 (exact)");
-    return host_op(p, kind == 0 ? MODE_JVP : MODE_JVE, y, v, jv, precision, shift);
+    if (kind < 0 || kind > 2)
+        return fail(HB_ERR_INVALID_ARG, "kind must be 0 (paper tangent), 1 (exact) or 2 (assembled paper tangent)");
+    return host_op(p, jv_mode(kind), y, v, jv, precision, shift);
 }
 
 hb_status hb_jacobi_diag(hb_problem *p, const double *y, double *d, int precision, double shift) {
@@ -1466,8 +1612,18 @@ hb_status hb_residual_dev(hb_problem *p, const void *y, void *r, int precision, 
 
 hb_status hb_jv_dev(hb_problem *p, const void *y, const void *v, void *jv, int kind, int precision, double shift,
                     void *stream) {
-    if (kind != 0 && kind != 1) return fail(HB_ERR_INVALID_ARG, "kind must be 0 (paper tangent) or 1 (exact)");
-    return dev_op(p, kind == 0 ? MODE_JVP : MODE_JVE, y, v, jv, precision, shift, stream);
+    if (kind < 0 || kind > 2)
+        return fail(HB_ERR_INVALID_ARG, "kind must be 0 (paper tangent), 1 (exact) or 2 (assembled paper tangent)");
+    return dev_op(p, jv_mode(kind), y, v, jv, precision, shift, stream);
+}
+
+hb_status hb_assemble_dev(hb_problem *p, const void *y, int precision, void *stream) {
+    if (!p || !y) return fail(HB_ERR_INVALID_ARG, "null argument");
+    HB_TRY(check_precision(precision));
+    HB_CUDA(cudaSetDevice(p->device));
+    cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : p->stream;
+    if (precision == 0) return assemble_at<double>(p, static_cast<const double *>(y), s);
+    return assemble_at<float>(p, static_cast<const float *>(y), s);
 }
 
 hb_status hb_jacobi_diag_dev(hb_problem *p, const void *y, void *d, int precision, double shift, void *stream) {
@@ -1491,6 +1647,7 @@ hb_status hb_default_opts(hb_solve_opts *o) {
     o->ser = 1;
     o->ser_max = 1e4;
     o->r_ref = 0.0;
+    o->assembled = 0;
     return HB_OK;
 }
 
@@ -1611,6 +1768,12 @@ static hb_status solve_impl(hb_problem *p, const hb_solve_opts &o, hb_report *re
         }
         launch_reciprocal(p->kdiag.p, p->kdiag.p, nd, p->stream);   // kdiag holds the inverse diagonal
         HB_LAUNCHED(p, 1);
+        if (o.assembled && c.mode == MODE_JVP) {
+            // the paper's tangent assembled once for this step; GMRES applies it as a sparse product
+            c.mode = MODE_JVA;
+            if (o.precision == 1) HB_TRY(assemble_at<float>(p, p->ky32.p, p->stream));
+            else HB_TRY(assemble_at<double>(p, p->y.p, p->stream));
+        }
         launch_scale_copy(-1.0, r, b, nd, p->stream);
         HB_LAUNCHED(p, 1);
         int its = 0, jvc = 0;
@@ -2341,6 +2504,7 @@ hb_status hb_get_info(hb_problem *p, hb_info *info) {
     double pr = 0;
     for (double v : p->level) pr += v / double(std::max<size_t>(1, p->level.size()));
     info->p_ref = pr;
+    info->assembled_pairs = p->as.nnz;
     return HB_OK;
 }
 

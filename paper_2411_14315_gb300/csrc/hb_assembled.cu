@@ -1,0 +1,240 @@
+// Assembled ("condensed") paper tangent of the HB-GLS method (arXiv 2411.14315, Sec. 2.3 and Sec. 4):
+// the blocks K, G, D, L of Eqs. (K_mat), (ctangent) stored per node pair and instance, so that a
+// Jacobian-vector product becomes a row-wise sparse product that streams the stored coefficients.
+//
+// Per node pair (A, B) and instance n eight values, [pair][8][N]:
+//   0    K_AB   = int rho N_A u.grad N_B + mu grad N_A . grad N_B + rho tau (u.grad N_A)(u.grad N_B)
+//   1-3  G_AB,i = - int dN_A/dx_i N_B + int (u.grad N_A) tau dN_B/dx_i
+//   4-6  D_AB,j =   int N_A dN_B/dx_j + int dN_A/dx_j tau (u.grad N_B)
+//   7    L_AB   = (1 / rho) int tau grad N_A . grad N_B
+// with U and tau frozen at the state of the assembly (the paper's tangent), and per pair the consistent
+// mass M_AB, instance independent.  The F block rho M (H v) and the pseudo-time mass shift M v enter as
+// M_AB W_B with W = shift v + rho H v per node (M and H commute).  Prescribed velocities are built in at
+// assembly: their rows carry no K, G, M terms (the product writes v there) and their columns no K, D
+// terms (v's prescribed entries count as zero).
+#include "hb_internal.cuh"
+
+namespace hb {
+
+namespace {
+
+inline int nblk(int64_t n, int b) { return int((n + b - 1) / b); }
+
+template <typename T>
+__device__ __forceinline__ T rsqrt_a(T x);
+template <>
+__device__ __forceinline__ float rsqrt_a<float>(float x) { return rsqrtf(x); }
+template <>
+__device__ __forceinline__ double rsqrt_a<double>(double x) { return rsqrt(x); }
+
+// One thread per (element, instance): the element's 16 (a, b) blocks at instance n, reduced into the
+// pair slots epos[e][4 a + b] (coalesced over n).
+template <typename T>
+__global__ void assemble_kernel(AsmArgs<T> a) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int N = a.N;
+    if (i >= a.n_tets * int64_t(N)) return;
+    const int64_t e = i / N;
+    const int n = int(i - e * N);
+    const int N4 = 4 * N;
+    int nd[4];
+    bool dir[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        nd[k] = a.tets[4 * e + k];
+        dir[k] = a.flag[nd[k]] & 1;
+    }
+    const T *g = a.geom + e * kGeomStride;
+    T gN[4][3];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) gN[k][j] = g[3 * k + j];
+    const T V = g[12], g2 = g[13];
+    const T w = V * T(0.25), rho = a.rho, mu = a.mu;
+    T u[4][3];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) u[k][j] = a.y[int64_t(nd[k]) * N4 + j * N + n];
+    const T qa = T(kQA), qb = T(kQB);
+    T udN[4][4], tau[4];               // udN[q][b] = u_q . grad N_b
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        T uq[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) uq[j] = qb * (u[0][j] + u[1][j] + u[2][j] + u[3][j]) + (qa - qb) * u[q][j];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) udN[q][b] = uq[0] * gN[b][0] + uq[1] * gN[b][1] + uq[2] * gN[b][2];
+        tau[q] = rsqrt_a<T>(udN[q][1] * udN[q][1] + udN[q][2] * udN[q][2] + udN[q][3] * udN[q][3] + g2);
+    }
+    const int *pos = a.epos + e * 16;
+#pragma unroll
+    for (int ra = 0; ra < 4; ++ra) {
+#pragma unroll
+        for (int cb = 0; cb < 4; ++cb) {
+            T kgal = 0, ksupg = 0, gs = 0, ds = 0, lt = 0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const T Na = (q == ra) ? qa : qb;
+                kgal += Na * udN[q][cb];
+                ksupg += tau[q] * udN[q][ra] * udN[q][cb];
+                gs += tau[q] * udN[q][ra];             // times dN_B/dx_i
+                ds += tau[q] * udN[q][cb];             // times dN_A/dx_j
+                lt += tau[q];
+            }
+            const T gg = gN[ra][0] * gN[cb][0] + gN[ra][1] * gN[cb][1] + gN[ra][2] * gN[cb][2];
+            T *c = a.coef + int64_t(pos[4 * ra + cb]) * 8 * N + n;
+            if (!dir[ra]) {
+                if (!dir[cb]) atomicAdd(c, w * rho * kgal + mu * V * gg + w * rho * ksupg);
+#pragma unroll
+                for (int j = 0; j < 3; ++j) atomicAdd(c + (1 + j) * N, -w * gN[ra][j] + w * gs * gN[cb][j]);
+            }
+            if (!dir[cb]) {
+#pragma unroll
+                for (int j = 0; j < 3; ++j) atomicAdd(c + (4 + j) * N, w * gN[cb][j] + w * ds * gN[ra][j]);
+            }
+            atomicAdd(c + 7 * N, (w / rho) * lt * gg);
+        }
+    }
+}
+
+// Consistent mass per pair, int N_A N_B = V (1 + delta_ab) / 20, rows of prescribed velocity left out.
+template <typename T>
+__global__ void assemble_mass_kernel(AsmArgs<T> a) {
+    const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e >= a.n_tets) return;
+    const T V = a.geom[e * kGeomStride + 12];
+    for (int ra = 0; ra < 4; ++ra) {
+        if (a.flag[a.tets[4 * e + ra]] & 1) continue;
+        for (int cb = 0; cb < 4; ++cb) atomicAdd(a.mass + a.epos[e * 16 + 4 * ra + cb], V * T(ra == cb ? 0.1 : 0.05));
+    }
+}
+
+// W = shift v + rho H v on the velocity rows of every node, 0 on prescribed velocities; one thread per
+// (node, field) row.  H is [N][N]; it is circulant, so for fixed N its first column (H[d][0]) is the
+// whole kernel, held in registers.
+template <typename T, int NT>
+__global__ void spectral_w_kernel(const T *__restrict__ v, const T *__restrict__ H, const uint8_t *__restrict__ flag,
+                                  T *__restrict__ W, int64_t n_nodes, int Nrt, T rho, T shift,
+                                  const double *__restrict__ shift_dev) {
+    const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (r >= 3 * n_nodes) return;
+    const int N = NT > 0 ? NT : Nrt;
+    const int64_t node = r / 3;
+    const int f = int(r - 3 * node);
+    const T sh = shift_dev ? T(*shift_dev) : shift;
+    const T *x = v + node * 4 * N + f * N;
+    T *o = W + node * 3 * N + f * N;
+    if (flag[node] & 1) {
+        for (int m = 0; m < N; ++m) o[m] = T(0);
+        return;
+    }
+    if constexpr (NT > 0) {
+        T xv[NT], h[NT];
+#pragma unroll
+        for (int k = 0; k < NT; ++k) xv[k] = x[k];
+#pragma unroll
+        for (int d = 0; d < NT; ++d) h[d] = H[d * NT];
+#pragma unroll
+        for (int m = 0; m < NT; ++m) {
+            T acc = T(0);
+#pragma unroll
+            for (int k = 0; k < NT; ++k)
+                if (k != m) acc += h[(m - k + NT) % NT] * xv[k];
+            o[m] = rho * acc + sh * xv[m];
+        }
+    } else {
+        for (int m = 0; m < N; ++m) {
+            T acc = T(0);
+            for (int k = 0; k < N; ++k) acc += H[m * N + k] * x[k];
+            o[m] = rho * acc + sh * x[m];
+        }
+    }
+}
+
+// out = (assembled tangent) v: one thread per (row, instance), rows_per_block rows of a block; each
+// thread sums its row's pairs in registers and stores once (no atomics).  Prescribed velocity rows
+// return v.
+template <typename T>
+__global__ void __launch_bounds__(256) spmv_kernel(SpmvArgs<T> a, int rows_per_block) {
+    const int N = a.N, N4 = 4 * N;
+    const int r = threadIdx.x / N, n = threadIdx.x - r * N;
+    if (r >= rows_per_block) return;
+    const int64_t A = int64_t(blockIdx.x) * rows_per_block + r;
+    if (A >= a.n_nodes) return;
+    T s0 = 0, s1 = 0, s2 = 0, sp = 0;
+    const int j1 = a.rowptr[A + 1];
+    for (int j = a.rowptr[A]; j < j1; ++j) {
+        const int64_t B = a.col[j];
+        const T *c = a.coef + int64_t(j) * 8 * N + n;
+        const T *vb = a.v + B * N4 + n;
+        const T *wb = a.W + B * 3 * N + n;
+        const T m = a.mass[j];
+        const T v0 = vb[0], v1 = vb[N], v2 = vb[2 * N], q = vb[3 * N];
+        const T K = c[0];
+        s0 += K * v0 + c[N] * q + m * wb[0];
+        s1 += K * v1 + c[2 * N] * q + m * wb[N];
+        s2 += K * v2 + c[3 * N] * q + m * wb[2 * N];
+        sp += c[4 * N] * v0 + c[5 * N] * v1 + c[6 * N] * v2 + c[7 * N] * q;
+    }
+    T *o = a.out + A * N4 + n;
+    if (a.flag[A] & 1) {
+        const T *va = a.v + A * N4 + n;
+        o[0] = va[0];
+        o[N] = va[N];
+        o[2 * N] = va[2 * N];
+    } else {
+        o[0] = s0;
+        o[N] = s1;
+        o[2 * N] = s2;
+    }
+    o[3 * N] = sp;
+}
+
+}  // namespace
+
+template <typename T>
+void launch_assemble(const AsmArgs<T> &a, cudaStream_t s) {
+    const int64_t n = a.n_tets * int64_t(a.N);
+    if (n > 0) assemble_kernel<T><<<nblk(n, 128), 128, 0, s>>>(a);
+}
+
+template <typename T>
+void launch_assemble_mass(const AsmArgs<T> &a, cudaStream_t s) {
+    if (a.n_tets > 0) assemble_mass_kernel<T><<<nblk(a.n_tets, 128), 128, 0, s>>>(a);
+}
+
+template <typename T>
+void launch_spectral_w(const T *v, const T *H, const uint8_t *flag, T *W, int64_t n_nodes, int N, T rho, T shift,
+                       const double *shift_dev, cudaStream_t s) {
+    const int64_t rows = 3 * n_nodes;
+    if (rows == 0) return;
+    const int g = nblk(rows, 128);
+    switch (N) {
+        case 1: spectral_w_kernel<T, 1><<<g, 128, 0, s>>>(v, H, flag, W, n_nodes, N, rho, shift, shift_dev); break;
+        case 9: spectral_w_kernel<T, 9><<<g, 128, 0, s>>>(v, H, flag, W, n_nodes, N, rho, shift, shift_dev); break;
+        case 13: spectral_w_kernel<T, 13><<<g, 128, 0, s>>>(v, H, flag, W, n_nodes, N, rho, shift, shift_dev); break;
+        case 21: spectral_w_kernel<T, 21><<<g, 128, 0, s>>>(v, H, flag, W, n_nodes, N, rho, shift, shift_dev); break;
+        default: spectral_w_kernel<T, 0><<<g, 128, 0, s>>>(v, H, flag, W, n_nodes, N, rho, shift, shift_dev); break;
+    }
+}
+
+template <typename T>
+void launch_spmv(const SpmvArgs<T> &a, cudaStream_t s) {
+    const int rpb = a.N <= 256 ? 256 / a.N : 1;
+    if (a.n_nodes > 0) spmv_kernel<T><<<nblk(a.n_nodes, rpb), rpb * a.N, 0, s>>>(a, rpb);
+}
+
+template void launch_assemble<float>(const AsmArgs<float> &, cudaStream_t);
+template void launch_assemble<double>(const AsmArgs<double> &, cudaStream_t);
+template void launch_assemble_mass<float>(const AsmArgs<float> &, cudaStream_t);
+template void launch_assemble_mass<double>(const AsmArgs<double> &, cudaStream_t);
+template void launch_spectral_w<float>(const float *, const float *, const uint8_t *, float *, int64_t, int, float, float,
+                                       const double *, cudaStream_t);
+template void launch_spectral_w<double>(const double *, const double *, const uint8_t *, double *, int64_t, int, double,
+                                        double, const double *, cudaStream_t);
+template void launch_spmv<float>(const SpmvArgs<float> &, cudaStream_t);
+template void launch_spmv<double>(const SpmvArgs<double> &, cudaStream_t);
+
+}  // namespace hb

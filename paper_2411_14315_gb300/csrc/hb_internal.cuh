@@ -15,8 +15,9 @@ enum Mode : int {
     MODE_JVP = 1,    // paper tangent (P + C) v, Eqs. (ptangent), (K_mat), (ctangent), (F_mat)
     MODE_JVE = 2,    // exact Jacobian-vector product
     MODE_DIAG = 3,   // Jacobi diagonal of P (+ pseudo mass), Sec. 2.3
-    MODE_TRES = 4    // time-domain GLS residual of one time level (Sec. 3, Eq. tauhat): the argument
+    MODE_TRES = 4,   // time-domain GLS residual of one time level (Sec. 3, Eq. tauhat): the argument
                      // slot of the direction holds du/dt; Galerkin rho M du/dt, no H terms
+    MODE_JVA = 5     // paper tangent through the assembled operator (host-side dispatch only)
 };
 
 constexpr int kGeomStride = 16;       // per element: grad N_a (4 x 3), V, C_I nu^2 G:G, 2 pad
@@ -168,6 +169,43 @@ void launch_galpha_stage(const double *un, const double *u1, const double *dun, 
 void launch_galpha_correct(double *u1, double *du1, const double *d, int64_t n, double inv_gdt, cudaStream_t s);
 void launch_put_instance(const double *src, double *dst, int64_t n4, int k, int N, cudaStream_t s);
 void launch_vel_norm2(const double *x, int64_t n, double *partials, double *result, cudaStream_t s);
+
+// Assembled paper tangent (hb_assembled.cu): per node pair and instance [pair][8][N] = K, G_1..3, D_1..3,
+// L, and per pair the consistent mass.
+template <typename T>
+struct AsmArgs {
+    int64_t n_tets;
+    int N;
+    const int *tets;               // [E][4] global node ids (the assembly's element order)
+    const T *geom;                 // [E][kGeomStride] in the same order
+    const int *epos;               // [E][16] pair slot of (local a, local b) = 4 a + b
+    const uint8_t *flag;           // per node, bit 0: prescribed velocity
+    const T *y;                    // frozen state [n][4][N]
+    T *coef;                       // [nnz][8][N], cleared before the assembly
+    T *mass;                       // [nnz], cleared before the assembly
+    T rho, mu;
+};
+template <typename T>
+struct SpmvArgs {
+    int64_t n_nodes;
+    int N;
+    const int *rowptr, *col;       // CSR of the node pairs (rows = nodes, the diagonal included)
+    const T *coef, *mass;
+    const T *v;                    // direction [n][4][N]
+    const T *W;                    // shift v + rho H v [n][3][N], 0 on prescribed velocities
+    T *out;                        // [n][4][N], every entry written
+    const uint8_t *flag;
+};
+template <typename T>
+void launch_assemble(const AsmArgs<T> &a, cudaStream_t s);
+template <typename T>
+void launch_assemble_mass(const AsmArgs<T> &a, cudaStream_t s);
+// W = shift v + rho H v (velocity rows; H [N][N]; shift from shift_dev if set)
+template <typename T>
+void launch_spectral_w(const T *v, const T *H, const uint8_t *flag, T *W, int64_t n_nodes, int N, T rho, T shift,
+                       const double *shift_dev, cudaStream_t s);
+template <typename T>
+void launch_spmv(const SpmvArgs<T> &a, cudaStream_t s);
 
 // Inputs of the learned warm start taken from a problem (host copies).
 constexpr int kLearnedFeatures = 32;  // per-node input features of the network

@@ -18,7 +18,7 @@ HB_OK = 0
 STATUS = {0: "HB_OK", 1: "HB_ERR_INVALID_ARG", 2: "HB_ERR_MESH", 3: "HB_ERR_CUDA", 4: "HB_ERR_OOM",
           5: "HB_ERR_NOT_CONVERGED", 6: "HB_ERR_NAN", 7: "HB_ERR_TIMEOUT", 8: "HB_ERR_STATE"}
 
-PAPER, EXACT = 0, 1
+PAPER, EXACT, ASSEMBLED = 0, 1, 2
 FP64, FP32 = 0, 1
 
 
@@ -39,7 +39,8 @@ class hb_solve_opts(C.Structure):
                 ("gmres_rtol_pseudo", C.c_double), ("gmres_rtol_newton", C.c_double),
                 ("gmres_restart", C.c_int), ("max_gmres", C.c_int), ("max_steps", C.c_int),
                 ("dt_pseudo", C.c_double), ("cfl", C.c_double), ("use_learned", C.c_int),
-                ("verbose", C.c_int), ("ser", C.c_int), ("ser_max", C.c_double), ("r_ref", C.c_double)]
+                ("verbose", C.c_int), ("ser", C.c_int), ("ser_max", C.c_double), ("r_ref", C.c_double),
+                ("assembled", C.c_int)]
 
 
 class hb_report(C.Structure):
@@ -74,7 +75,7 @@ class hb_info(C.Structure):
                 ("N", C.c_int), ("n_patches32", C.c_int), ("n_patches64", C.c_int),
                 ("patch_nodes_max32", C.c_int), ("patch_elems_max32", C.c_int),
                 ("device_bytes", C.c_int64), ("h_char", C.c_double), ("u_ref", C.c_double),
-                ("p_ref", C.c_double)]
+                ("p_ref", C.c_double), ("assembled_pairs", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -103,6 +104,7 @@ SIGNATURES = {
     "hb_default_march_opts": ([C.POINTER(hb_march_opts)], C.c_int),
     "hb_march": ([_P, C.POINTER(hb_march_opts), C.POINTER(hb_march_report)], C.c_int),
     "hb_get_march_samples": ([_P, _DP], C.c_int),
+    "hb_assemble_dev": ([_P, _VP, C.c_int, _VP], C.c_int),
     "hb_time_residual": ([_P, _DP, _DP, _DP, C.c_int, C.c_double, C.c_double], C.c_int),
     "hb_time_jv": ([_P, _DP, _DP, _DP, C.c_int, C.c_double, C.c_double], C.c_int),
     "hb_residual": ([_P, _DP, _DP, C.c_int], C.c_int),
@@ -315,6 +317,10 @@ class Problem:
     def jv_dev(self, y, v, out, kind: int, precision: int, shift: float = 0.0, stream=None):
         _check(lib().hb_jv_dev(self._h, y.data_ptr(), v.data_ptr(), out.data_ptr(), kind, precision, shift,
                                _stream_handle(stream)))
+
+    def assemble_dev(self, y, precision: int, stream=None):
+        """Assemble the paper tangent at the device state y (hb_assemble_dev); kind 2 then applies it."""
+        _check(lib().hb_assemble_dev(self._h, y.data_ptr(), precision, _stream_handle(stream)))
 
     def jv_dev_noalloc(self, y, v, out, kind: int, precision: int, shift: float = 0.0, stream=None):
         """hb_jv_dev without any device allocation (see include/hbgls.h for the conditions)."""
