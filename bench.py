@@ -250,9 +250,9 @@ def time_solves():
     rep = ref.solve(precision=0, rtol=1e-13, check=False)
     yref = ref.instances()
     out["reference"] = {"status": rep["status"], "res_rel": rep["res_final"] / max(rep["res0"], 1e-300)}
-    for name, prec in (("mixed", 1), ("fp64", 0)):
+    for name, prec, asm in (("mixed", 1, 0), ("mixed_assembled", 1, 1), ("fp64", 0, 0)):
         p = hbgls.Problem.from_spec(spec)
-        rep = p.solve(precision=prec, rtol=1e-10, check=False)
+        rep = p.solve(precision=prec, rtol=1e-10, assembled=asm, check=False)
         y = p.instances()
         err = float(np.linalg.norm(y - yref) / np.linalg.norm(yref))
         out[name] = {"seconds": rep["seconds"], "rel_err_vs_fp64_ref": err, "status": rep["status"],

@@ -165,6 +165,7 @@ __global__ void __launch_bounds__(256) spmv_kernel(SpmvArgs<T> a, int rows_per_b
     if (A >= a.n_nodes) return;
     T s0 = 0, s1 = 0, s2 = 0, sp = 0;
     const int j1 = a.rowptr[A + 1];
+#pragma unroll 4
     for (int j = a.rowptr[A]; j < j1; ++j) {
         const int64_t B = a.col[j];
         const T *c = a.coef + int64_t(j) * 8 * N + n;
