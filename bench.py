@@ -262,6 +262,43 @@ def time_solves():
     return out
 
 
+def time_workloads(flush, stream, reps: int = 20):
+    """FP32 paper-tangent Jv rates (fused element pass, and the assembled operator) on the other vessel
+    stand-ins: cerebral-like (~2.2M tets) and stenosed coronary-like (~300k tets), N = 21."""
+    import torch
+
+    from paper_2411_14315_gb300 import hbgls
+    from paper_2411_14315_gb300 import inputs as I
+    from paper_2411_14315_gb300 import workloads as W
+    out = {}
+    for name, mk in (("cerebral_like", lambda: W.cerebral_spec()), ("coronary_like", lambda: W.coronary_spec())):
+        spec = mk()
+        prob = hbgls.Problem.from_spec(spec, stream=stream)
+        n, N = spec.mesh.n_nodes, spec.N
+        units = spec.mesh.n_tets * N
+        y = torch.tensor(I.random_state(n, N, 7), dtype=torch.float32, device="cuda")
+        v = torch.tensor(I.random_state(n, N, 8), dtype=torch.float32, device="cuda")
+        o = torch.empty_like(y)
+        res = {"n_tets": spec.mesh.n_tets, "n_nodes": n, "N": N}
+        prob.assemble_dev(y, hbgls.FP32, stream=stream)
+        for kind, key in ((hbgls.PAPER, "fused_element_pass"), (hbgls.ASSEMBLED, "assembled")):
+            prob.jv_dev(y, v, o, kind, hbgls.FP32, 300.0, stream=stream)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            tot = 0.0
+            for i in range(reps):
+                flush.fill_(float(i))
+                e0.record(stream)
+                prob.jv_dev(y, v, o, kind, hbgls.FP32, 300.0, stream=stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                tot += e0.elapsed_time(e1)
+            res[key] = {"ms_per_jv": tot / reps, "element_instances_per_s": units / (tot / reps / 1e3)}
+        out[name] = res
+        prob.close()
+    return out
+
+
 def time_assembled(prob, y32, v32, out32, flush, stream, shift, units, hbm_peak, reps: int = 20):
     """Assembly of the paper tangent at the benchmark state, then `reps` applications (L2 flushed
     between them).  Algorithmic bytes of the sparse product: the pair coefficients (8 N values) and pair
@@ -547,6 +584,7 @@ def run_ours(args, dist: Dist, spec, config):
             var_ms[str(var)] = t / max(1, c)
         prob.set_launch_variant(var0)
         result["jvp_variant_elem_ms"] = var_ms
+        result["other_workloads"] = time_workloads(flush, stream)
 
     if dist.rank == 0 and dist.world == 1:
         if not args.skip_batch:

@@ -118,6 +118,22 @@ def glenn_spec(n_tets=1_000_000, n_h=10, seed=2000) -> Spec:
     return s
 
 
+def cerebral_spec(n_tets=2_000_000, n_h=10, seed=3000) -> Spec:
+    """Cerebral-like vessel (tube of radius 0.2 cm along a seeded spline with a saccular bulge) in cgs
+    units: rho 1.06, mu 0.04, T 1 s, parabolic inflow with 10 seeded harmonics at a mean velocity of
+    15 cm/s, outlet at a steady 115 mmHg (Sec. 3.2 stand-in)."""
+    m = I.cerebral_like(n_tets, seed)
+    mmHg = 1333.22
+    a, b = I.waveform_harmonics(n_h, math.pi * 0.04 * 15.0, seed + 11)
+    pa = np.zeros(n_h + 1)
+    pb = np.zeros(n_h + 1)
+    pa[0] = 115.0 * mmHg
+    s = Spec(m, 1.06, 0.04, 1.0, n_h, name=f"cerebral_s{seed}")
+    s.inflows.append((1, None, a, b))
+    s.outlets_p.append((2, pa, pb))
+    return s
+
+
 def coronary_spec(n_tets=300_000, n_h=10, seed=4000, reynolds=100.0, severity=(0.3, 0.7)) -> Spec:
     """Stenosed coronary-like tube (radius U(0.15, 0.25) cm, 30-70 % diameter reduction) in cgs units:
     rho 1.06, mu 0.04, T 0.8 s, parabolic inflow with 10 seeded harmonics at a mean Reynolds number of

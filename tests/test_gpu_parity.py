@@ -173,6 +173,30 @@ def _sampled_oracle(spec, y, v, nodes, fn):
     return out[np.searchsorted(used, nodes)]
 
 
+def test_full_size_cerebral_sampled_parity():
+    """Cerebral-like vessel at full size (~2.2M tets, ~727k nodes, N = 21): residual and the paper's
+    tangent at 48 sampled interior nodes against the oracle."""
+    from paper_2411_14315_gb300 import workloads as W
+    spec = W.cerebral_spec()
+    gp = P.gpu_problem(spec)
+    m = spec.mesh
+    n = m.n_nodes
+    y = I.random_state(n, spec.N, 64)
+    v = I.random_state(n, spec.N, 65)
+    v[P.dirichlet_nodes(spec), :3] = 0.0
+    interior = np.setdiff1d(np.arange(n), np.unique(m.faces.ravel()))
+    nodes = np.sort(np.random.default_rng(66).choice(interior, 48, replace=False))
+    checks = [
+        (lambda: gp.residual(y, 1), lambda pr, yy: O.residual(pr, yy), None),
+        (lambda: gp.jv(y, v, 0, 1, 0.0), lambda pr, yy, vv: O.jv_paper(pr, yy, vv), v),
+    ]
+    for run, fn, vv in checks:
+        got = run()[nodes]
+        ref = _sampled_oracle(spec, y, vv, nodes, fn)
+        assert relerr(got, ref) < 1e-5
+    gp.close()
+
+
 def test_full_size_glenn_sampled_parity():
     """Glenn-like T-junction at full size (~1M tets, N = 21) in the launch configuration the benchmark
     times: residual and both Jv kinds at 64 sampled interior nodes against the oracle."""
