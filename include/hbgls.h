@@ -124,6 +124,10 @@ typedef struct {
                                  warm-started solve stop at the same absolute residual as a cold one)  */
     int assembled;            /* 1: in the paper-tangent phase assemble the tangent once per step
                                  (hb_assemble_dev) and let GMRES apply it as a sparse product          */
+    int precond;              /* 0: Jacobi on diag(P) + shift M (Sec. 2.3); 1: node blocks (4 x 4 per
+                                 node and instance) of the assembled paper tangent + shift M, inverted
+                                 through their pressure Schur complement (an extension; assembles the
+                                 tangent every outer step)                                            */
 } hb_solve_opts;
 
 typedef struct {

@@ -145,7 +145,7 @@ struct hb_problem {
     // graph-captured GMRES restart cycles, one per operator (paper tangent / exact)
     struct CycleGraph {
         cudaGraphExec_t exec = nullptr;
-        int m = 0, precision = -1;
+        int m = 0, precision = -1, precond = -1;
         double shift = 0;
         int64_t launches = 0;
     } cycle[3];                        // paper tangent, exact Jacobian, assembled paper tangent
@@ -159,7 +159,7 @@ struct hb_problem {
     // assembled paper tangent (Sec. 4's condensed storage): CSR of node pairs, element -> pair slots
     struct Assembled {
         int64_t nnz = 0;
-        DBuf<int> rowptr, col, epos, tets;
+        DBuf<int> rowptr, col, epos, tets, dpos;   // dpos[A]: slot of the pair (A, A)
         DBuf<float> geom32, coef32, mass32, W32;
         DBuf<double> geom64, coef64, mass64, W64;
         bool ready32 = false, ready64 = false;   // coefficients assembled (at the last state given)
@@ -646,6 +646,11 @@ hb_status asm_structure(hb_problem *p) {
             }
         }
     }
+    std::vector<int> dpos(static_cast<size_t>(n));
+    for (int64_t i = 0; i < n; ++i)
+        dpos[size_t(i)] = int(std::lower_bound(col.data() + rowptr[size_t(i)], col.data() + rowptr[size_t(i + 1)], int(i)) -
+                              col.data());
+    HB_TRY(upload(p, A.dpos, dpos));
     HB_TRY(upload(p, A.rowptr, rowptr));
     HB_TRY(upload(p, A.col, col));
     HB_TRY(upload(p, A.tets, tets));
@@ -906,7 +911,32 @@ struct OpCtx {
     double shift;
     int precision;
     const double *shift_dev = nullptr;   // pseudo shift read from device memory (graph-stable)
+    int precond = 0;                     // 0: Jacobi (inverse diagonal in kdiag); 1: node blocks of the
+                                         // assembled tangent
 };
+
+// z = M^-1 x for the preconditioner of c (x: FP64 Krylov vector); Z = float writes the mixed path's
+// operand, Z = double the FP64 one
+template <typename Z>
+hb_status apply_precond(hb_problem *p, const OpCtx &c, const double *x, Z *z, cudaStream_t s) {
+    const int64_t nd = p->n_nodes * 4 * p->N;
+    if (c.precond == 1) {
+        const hb_problem::Assembled &A = p->as;
+        if (c.precision == 1) {      // coefficients assembled in FP32
+            launch_block_jacobi<float, Z>(A.coef32.p, A.mass32.p, A.dpos.p, p->d_flag.p, x, z, p->n_nodes, p->N, c.shift,
+                                          c.shift_dev, s);
+        } else if constexpr (sizeof(Z) == 8) {
+            launch_block_jacobi<double, double>(A.coef64.p, A.mass64.p, A.dpos.p, p->d_flag.p, x, z, p->n_nodes, p->N,
+                                                c.shift, c.shift_dev, s);
+        } else {
+            return fail(HB_ERR_STATE, "FP32 preconditioner output requested in the FP64 path");
+        }
+    } else {
+        launch_precond<Z>(x, p->kdiag.p, z, nd, s);
+    }
+    HB_LAUNCHED(p, 1);
+    return HB_OK;
+}
 
 // w(double) = A z, with z given in double (z64) and, for the mixed path, its float copy made here
 hb_status apply_A(hb_problem *p, const OpCtx &c, const double *z64, double *w) {
@@ -959,13 +989,12 @@ hb_status record_cycle(hb_problem *p, const OpCtx &c, int m) {
         double *w = V + int64_t(j + 1) * nd;
         if (c.precision == 1) {
             // mixed path: the preconditioned direction goes straight to the FP32 operator
-            launch_precond<float>(vj, p->kdiag.p, p->kz32.p, nd, s);
+            HB_TRY(apply_precond<float>(p, c, vj, p->kz32.p, s));
             HB_TRY(apply_op<float>(p, c.mode, p->ky32.p, p->kz32.p, p->kw32.p, c.shift, s, c.shift_dev));
             launch_convert<float, double>(p->kw32.p, w, nd, s);
-            HB_LAUNCHED(p, 2);
-        } else {
-            launch_precond<double>(vj, p->kdiag.p, p->kz64.p, nd, s);
             HB_LAUNCHED(p, 1);
+        } else {
+            HB_TRY(apply_precond<double>(p, c, vj, p->kz64.p, s));
             HB_TRY(apply_op<double>(p, c.mode, p->y.p, p->kz64.p, w, c.shift, s, c.shift_dev));
         }
         launch_multidot(V, nd, j + 1, w, nd, p->scratch.p, G + L.h1, s);
@@ -985,7 +1014,7 @@ hb_status cycle_graph(hb_problem *p, const OpCtx &c, int m, hb_problem::CycleGra
     hb_problem::CycleGraph &gc = p->cycle[c.mode == MODE_JVE ? 1 : c.mode == MODE_JVA ? 2 : 0];
     out = &gc;
     const double key = c.shift_dev ? -1.0 : c.shift;
-    if (gc.exec && gc.m == m && gc.precision == c.precision && gc.shift == key) return HB_OK;
+    if (gc.exec && gc.m == m && gc.precision == c.precision && gc.shift == key && gc.precond == c.precond) return HB_OK;
     if (gc.exec) {
         cudaGraphExecDestroy(gc.exec);
         gc.exec = nullptr;
@@ -1008,6 +1037,7 @@ hb_status cycle_graph(hb_problem *p, const OpCtx &c, int m, hb_problem::CycleGra
     }
     gc.m = m;
     gc.precision = c.precision;
+    gc.precond = c.precond;
     gc.shift = key;
     gc.launches = p->launches - l0;
     p->launches = l0;
@@ -1073,9 +1103,9 @@ hb_status gmres(hb_problem *p, const OpCtx &c, const double *b, double *x, doubl
         }
         HB_CUDA(cudaMemcpyAsync(p->kh.p, yk.data(), size_t(k) * sizeof(double), cudaMemcpyHostToDevice, s));
         launch_combine(V, nd, k, p->kh.p, p->ktmp.p, nd, s);
-        launch_precond<double>(p->ktmp.p, p->kdiag.p, p->kz64.p, nd, s);
+        HB_TRY(apply_precond<double>(p, c, p->ktmp.p, p->kz64.p, s));
         launch_axpy(1.0, p->kz64.p, x, nd, s);
-        HB_LAUNCHED(p, 3);
+        HB_LAUNCHED(p, 2);
         HB_CUDA(cudaStreamSynchronize(s));   // yk consumed
         iters += k;
         if (relres) *relres = resid[size_t(k - 1)] / bnorm;
@@ -1648,6 +1678,7 @@ hb_status hb_default_opts(hb_solve_opts *o) {
     o->ser_max = 1e4;
     o->r_ref = 0.0;
     o->assembled = 0;
+    o->precond = 0;
     return HB_OK;
 }
 
@@ -1666,6 +1697,7 @@ hb_status hb_solve(hb_problem *p, const hb_solve_opts *opts, hb_report *rep) {
     if (opts) o = *opts;
     HB_TRY(check_precision(o.precision));
     if (o.gmres_restart < 1 || o.gmres_restart > 200) return fail(HB_ERR_INVALID_ARG, "gmres_restart must be in [1, 200]");
+    if (o.precond != 0 && o.precond != 1) return fail(HB_ERR_INVALID_ARG, "precond must be 0 (Jacobi) or 1 (node blocks)");
     HB_CUDA(cudaSetDevice(p->device));
     if (o.use_learned < 0 || o.use_learned > 2) return fail(HB_ERR_INVALID_ARG, "use_learned must be 0, 1 or 2");
     p->learned_dir = false;
@@ -1768,11 +1800,13 @@ static hb_status solve_impl(hb_problem *p, const hb_solve_opts &o, hb_report *re
         }
         launch_reciprocal(p->kdiag.p, p->kdiag.p, nd, p->stream);   // kdiag holds the inverse diagonal
         HB_LAUNCHED(p, 1);
-        if (o.assembled && c.mode == MODE_JVP) {
-            // the paper's tangent assembled once for this step; GMRES applies it as a sparse product
-            c.mode = MODE_JVA;
+        if ((o.assembled && c.mode == MODE_JVP) || o.precond == 1) {
+            // the paper's tangent assembled once for this step: GMRES applies it as a sparse product
+            // (assembled, paper-tangent phase) and / or takes its node blocks as the preconditioner
             if (o.precision == 1) HB_TRY(assemble_at<float>(p, p->ky32.p, p->stream));
             else HB_TRY(assemble_at<double>(p, p->y.p, p->stream));
+            if (o.assembled && c.mode == MODE_JVP) c.mode = MODE_JVA;
+            c.precond = o.precond;
         }
         launch_scale_copy(-1.0, r, b, nd, p->stream);
         HB_LAUNCHED(p, 1);

@@ -193,7 +193,51 @@ __global__ void __launch_bounds__(256) spmv_kernel(SpmvArgs<T> a, int rows_per_b
     o[3 * N] = sp;
 }
 
+// Node-block Jacobi preconditioner from the assembled tangent: per node and instance the 4 x 4 diagonal
+// block [[(k + s) I, g], [d^T, l]] (k = K_AA, g = G_AA, d = D_AA, l = L_AA, s = shift M_AA; the F block's
+// diagonal is rho M_AA H_nn = 0) is inverted through its pressure Schur complement
+// l - d . g / (k + s).  z = block^-1 x; prescribed velocities keep z_u = x_u (their rows are the identity).
+template <typename T, typename Z>
+__global__ void block_jacobi_kernel(const T *__restrict__ coef, const T *__restrict__ mass,
+                                    const int *__restrict__ dpos, const uint8_t *__restrict__ flag,
+                                    const double *__restrict__ x, Z *__restrict__ z, int64_t n_nodes, int N,
+                                    double shift, const double *__restrict__ shift_dev) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n_nodes * N) return;
+    const int64_t A = i / N;
+    const int n = int(i - A * N);
+    const double sh = shift_dev ? *shift_dev : shift;
+    const int64_t base = A * 4 * N + n;
+    const double r0 = x[base], r1 = x[base + N], r2 = x[base + 2 * N], rp = x[base + 3 * N];
+    const T *c = coef + int64_t(dpos[A]) * 8 * N + n;
+    const double l = double(c[7 * N]);
+    if (flag[A] & 1) {
+        z[base] = Z(r0);
+        z[base + N] = Z(r1);
+        z[base + 2 * N] = Z(r2);
+        z[base + 3 * N] = Z(l != 0.0 ? rp / l : rp);
+        return;
+    }
+    const double ks = double(c[0]) + sh * double(mass[dpos[A]]);
+    const double g0 = c[N], g1 = c[2 * N], g2 = c[3 * N], d0 = c[4 * N], d1 = c[5 * N], d2 = c[6 * N];
+    const double ik = 1.0 / ks;
+    const double S = l - (d0 * g0 + d1 * g1 + d2 * g2) * ik;
+    const double zp = (rp - (d0 * r0 + d1 * r1 + d2 * r2) * ik) / S;
+    z[base] = Z((r0 - g0 * zp) * ik);
+    z[base + N] = Z((r1 - g1 * zp) * ik);
+    z[base + 2 * N] = Z((r2 - g2 * zp) * ik);
+    z[base + 3 * N] = Z(zp);
+}
+
 }  // namespace
+
+template <typename T, typename Z>
+void launch_block_jacobi(const T *coef, const T *mass, const int *dpos, const uint8_t *flag, const double *x, Z *z,
+                         int64_t n_nodes, int N, double shift, const double *shift_dev, cudaStream_t s) {
+    const int64_t n = n_nodes * N;
+    if (n > 0)
+        block_jacobi_kernel<T, Z><<<nblk(n, 256), 256, 0, s>>>(coef, mass, dpos, flag, x, z, n_nodes, N, shift, shift_dev);
+}
 
 template <typename T>
 void launch_assemble(const AsmArgs<T> &a, cudaStream_t s) {
@@ -236,6 +280,15 @@ template void launch_spectral_w<float>(const float *, const float *, const uint8
 template void launch_spectral_w<double>(const double *, const double *, const uint8_t *, double *, int64_t, int, double,
                                         double, const double *, cudaStream_t);
 template void launch_spmv<float>(const SpmvArgs<float> &, cudaStream_t);
+template void launch_block_jacobi<float, float>(const float *, const float *, const int *, const uint8_t *,
+                                                const double *, float *, int64_t, int, double, const double *,
+                                                cudaStream_t);
+template void launch_block_jacobi<float, double>(const float *, const float *, const int *, const uint8_t *,
+                                                 const double *, double *, int64_t, int, double, const double *,
+                                                 cudaStream_t);
+template void launch_block_jacobi<double, double>(const double *, const double *, const int *, const uint8_t *,
+                                                  const double *, double *, int64_t, int, double, const double *,
+                                                  cudaStream_t);
 template void launch_spmv<double>(const SpmvArgs<double> &, cudaStream_t);
 
 }  // namespace hb

@@ -206,6 +206,11 @@ void launch_spectral_w(const T *v, const T *H, const uint8_t *flag, T *W, int64_
                        const double *shift_dev, cudaStream_t s);
 template <typename T>
 void launch_spmv(const SpmvArgs<T> &a, cudaStream_t s);
+// z = (node-block diagonal of the assembled tangent + shift M_AA)^-1 x per node and instance; dpos[A] is
+// the slot of the pair (A, A)
+template <typename T, typename Z>
+void launch_block_jacobi(const T *coef, const T *mass, const int *dpos, const uint8_t *flag, const double *x, Z *z,
+                         int64_t n_nodes, int N, double shift, const double *shift_dev, cudaStream_t s);
 
 // Inputs of the learned warm start taken from a problem (host copies).
 constexpr int kLearnedFeatures = 32;  // per-node input features of the network

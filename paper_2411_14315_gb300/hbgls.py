@@ -40,7 +40,7 @@ class hb_solve_opts(C.Structure):
                 ("gmres_restart", C.c_int), ("max_gmres", C.c_int), ("max_steps", C.c_int),
                 ("dt_pseudo", C.c_double), ("cfl", C.c_double), ("use_learned", C.c_int),
                 ("verbose", C.c_int), ("ser", C.c_int), ("ser_max", C.c_double), ("r_ref", C.c_double),
-                ("assembled", C.c_int)]
+                ("assembled", C.c_int), ("precond", C.c_int)]
 
 
 class hb_report(C.Structure):

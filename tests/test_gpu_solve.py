@@ -29,11 +29,12 @@ def channel_root():
     return spec, ora, y
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_solution_matches_oracle_root(channel_root, precision):
+@pytest.mark.parametrize("precision,precond", [(0, 0), (1, 0), (0, 1), (1, 1)])
+def test_solution_matches_oracle_root(channel_root, precision, precond):
+    """Plain Jacobi (the paper's) and node-block preconditioning reach the same root."""
     spec, ora, y_ref = channel_root
     gp = P.gpu_problem(spec)
-    rep = gp.solve(precision=precision, rtol=1e-12)
+    rep = gp.solve(precision=precision, rtol=1e-12, precond=precond)
     assert rep["status"] == 0
     y = gp.instances()
     assert relerr(y, y_ref) < 1e-8
