@@ -695,7 +695,7 @@ hb_status assemble_at(hb_problem *p, const T *y, cudaStream_t s) {
     }
     HB_TRY(dalloc(p, B::coef(A), size_t(A.nnz) * 8 * size_t(N)));
     HB_TRY(dalloc(p, B::mass(A), size_t(A.nnz)));
-    HB_TRY(dalloc(p, B::W(A), size_t(p->n_nodes) * 3 * size_t(N)));
+    HB_TRY(dalloc(p, B::W(A), size_t(p->n_nodes) * size_t(w_stride(N, int(sizeof(T))))));
     AsmArgs<T> a;
     a.n_tets = p->n_tets;
     a.N = N;
@@ -750,10 +750,12 @@ hb_status apply_op(hb_problem *p, int mode, const T *y, const T *v, T *out, doub
         hb_problem::Assembled &A = p->as;
         using B = AsmBufs<T>;
         if (!B::ready(A)) return fail(HB_ERR_STATE, "no assembled operator in this precision (hb_assemble_dev)");
-        launch_spectral_w<T>(v, Hmat<T>(p), p->d_flag.p, B::W(A).p, p->n_nodes, N, T(p->rho), T(shift), shift_dev, s);
+        const int ws = w_stride(N, int(sizeof(T)));
+        launch_spectral_w<T>(v, Hmat<T>(p), p->d_flag.p, B::W(A).p, ws, p->n_nodes, N, T(p->rho), T(shift), shift_dev, s);
         SpmvArgs<T> sa;
         sa.n_nodes = p->n_nodes;
         sa.N = N;
+        sa.w_stride = ws;
         sa.rowptr = A.rowptr.p;
         sa.col = A.col.p;
         sa.coef = B::coef(A).p;
@@ -786,6 +788,16 @@ hb_status apply_op(hb_problem *p, int mode, const T *y, const T *v, T *out, doub
     ea.ls_mass = p->ls_mass;
     ea.variant = p->jvp_variant;
     if (ps.P > 0 && mode != MODE_JVA) {
+        if (mode == MODE_JVP) {
+            // spectral pass over the nodes (each once): W = shift v + rho H v, gathered by the patches
+            using B = AsmBufs<T>;
+            DBuf<T> &W = B::W(p->as);
+            const int ws = w_stride(N, int(sizeof(T)));
+            HB_TRY(dalloc(p, W, size_t(p->n_nodes) * size_t(ws)));
+            launch_spectral_w<T>(v, Hmat<T>(p), p->d_flag.p, W.p, ws, p->n_nodes, N, T(p->rho), T(shift), shift_dev, s);
+            HB_LAUNCHED(p, 1);
+            ea.W = W.p;
+        }
         HB_TRY(prof_begin());
         launch_elem<T>(mode, ea, ps.P, s);
         HB_LAUNCHED(p, 1);
@@ -1134,6 +1146,10 @@ hb_status ensure_krylov(hb_problem *p, int m) {
     HB_TRY(dalloc(p, p->kdiag32, nd));
     HB_TRY(dalloc(p, p->w64a, nd));
     HB_TRY(dalloc(p, p->w64b, nd));
+    // spectral pass output of the paper-tangent operator, allocated here so that no allocation falls
+    // inside the captured GMRES cycles
+    HB_TRY(dalloc(p, p->as.W32, size_t(p->n_nodes) * size_t(w_stride(p->N, 4))));
+    HB_TRY(dalloc(p, p->as.W64, size_t(p->n_nodes) * size_t(w_stride(p->N, 8))));
     return HB_OK;
 }
 

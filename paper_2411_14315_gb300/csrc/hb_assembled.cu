@@ -111,45 +111,90 @@ __global__ void assemble_mass_kernel(AsmArgs<T> a) {
     }
 }
 
-// W = shift v + rho H v on the velocity rows of every node, 0 on prescribed velocities; one thread per
-// (node, field) row.  H is [N][N]; it is circulant, so for fixed N its first column (H[d][0]) is the
-// whole kernel, held in registers.
+// W = shift v + rho H v on the velocity rows of every node, 0 on prescribed velocities and in the row
+// padding.  A block stages NB nodes of v in shared memory with 16-byte loads (a node's 4N values are a
+// multiple of 16 bytes), one thread per (node, field) row forms its N outputs, and the block writes the
+// padded W rows back contiguously.  H is circulant, so for fixed N its first column H[d][0] is the whole
+// operator, held in registers.
 template <typename T, int NT>
-__global__ void spectral_w_kernel(const T *__restrict__ v, const T *__restrict__ H, const uint8_t *__restrict__ flag,
-                                  T *__restrict__ W, int64_t n_nodes, int Nrt, T rho, T shift,
-                                  const double *__restrict__ shift_dev) {
-    const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (r >= 3 * n_nodes) return;
-    const int N = NT > 0 ? NT : Nrt;
-    const int64_t node = r / 3;
-    const int f = int(r - 3 * node);
-    const T sh = shift_dev ? T(*shift_dev) : shift;
-    const T *x = v + node * 4 * N + f * N;
-    T *o = W + node * 3 * N + f * N;
-    if (flag[node] & 1) {
-        for (int m = 0; m < N; ++m) o[m] = T(0);
-        return;
+struct SpecTile {
+    static constexpr int NB = (sizeof(T) == 4 ? 64 : 32) / (NT == 0 ? 2 : 1);   // nodes per block
+    static constexpr int NM = NT > 0 ? NT : kMaxN;
+    static constexpr int PER = 16 / int(sizeof(T));                              // values per 16 bytes
+    static constexpr int WP = w_stride(NM, int(sizeof(T))) + PER;                // shared row pitch (16 B
+                                                                                  // aligned, skewed banks)
+    static constexpr int MINB = sizeof(T) == 4 ? 8 : 1;  // FP32: 8 resident blocks; FP64: no register cap
+};
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(3 * SpecTile<T, NT>::NB, SpecTile<T, NT>::MINB)
+    spectral_w_kernel(const T *__restrict__ v, const T *__restrict__ H, const uint8_t *__restrict__ flag,
+                      T *__restrict__ W, int ws, int64_t n_nodes, int Nrt, T rho, T shift,
+                      const double *__restrict__ shift_dev) {
+    using S = SpecTile<T, NT>;
+    // for fixed N each thread holds its row in registers, so the W tile overwrites the staged v tile
+    // (half the shared memory, twice the resident blocks); the generic N path keeps two tiles
+    constexpr bool inplace = NT > 0;
+    constexpr int XS = S::NB * 4 * S::NM, WSZ = S::NB * S::WP;
+    __shared__ __align__(16) T sbuf[inplace ? (XS > WSZ ? XS : WSZ) : XS + WSZ];
+    T *sx = sbuf, *sw = inplace ? sbuf : sbuf + XS;
+    const int N = NT > 0 ? NT : Nrt, N4 = 4 * N, wp = ws + S::PER;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int64_t node0 = int64_t(blockIdx.x) * S::NB;
+    const int nn = int(n_nodes - node0 < S::NB ? n_nodes - node0 : S::NB);
+    {
+        const int chunks = nn * N4 * int(sizeof(T)) / 16;
+        const uint4 *src = reinterpret_cast<const uint4 *>(v + node0 * N4);
+        uint4 *dst = reinterpret_cast<uint4 *>(sx);
+        for (int i = tid; i < chunks; i += nt) dst[i] = src[i];
     }
+    const T sh = shift_dev ? T(*shift_dev) : shift;
+    __syncthreads();
+    const int l = tid / 3, f = tid - 3 * l;
+    const bool live = l < nn && !(flag[node0 + l] & 1);
+    T *o = sw + l * wp + f * N;
     if constexpr (NT > 0) {
         T xv[NT], h[NT];
+        if (live) {
+            const T *x = sx + l * N4 + f * N;
 #pragma unroll
-        for (int k = 0; k < NT; ++k) xv[k] = x[k];
-#pragma unroll
-        for (int d = 0; d < NT; ++d) h[d] = H[d * NT];
-#pragma unroll
-        for (int m = 0; m < NT; ++m) {
-            T acc = T(0);
-#pragma unroll
-            for (int k = 0; k < NT; ++k)
-                if (k != m) acc += h[(m - k + NT) % NT] * xv[k];
-            o[m] = rho * acc + sh * xv[m];
+            for (int k = 0; k < NT; ++k) xv[k] = x[k];
         }
-    } else {
+        __syncthreads();                       // every row is in registers before the tile is overwritten
+        if (live) {
+#pragma unroll
+            for (int d = 0; d < NT; ++d) h[d] = H[d * NT];
+#pragma unroll
+            for (int m = 0; m < NT; ++m) {
+                T acc = T(0);
+#pragma unroll
+                for (int k = 0; k < NT; ++k)
+                    if (k != m) acc += h[(m - k + NT) % NT] * xv[k];
+                o[m] = rho * acc + sh * xv[m];
+            }
+        }
+    } else if (live) {
+        const T *x = sx + l * N4 + f * N;
         for (int m = 0; m < N; ++m) {
             T acc = T(0);
             for (int k = 0; k < N; ++k) acc += H[m * N + k] * x[k];
             o[m] = rho * acc + sh * x[m];
         }
+    }
+    if (l < nn) {
+        if (!live)
+            for (int m = 0; m < N; ++m) o[m] = T(0);
+        if (f == 2)
+            for (int c = 3 * N; c < ws; ++c) sw[l * wp + c] = T(0);
+    }
+    __syncthreads();
+    // rows of ws values are whole 16-byte chunks; wq is a compile-time constant for fixed N
+    const int wq = NT > 0 ? w_stride(NT, int(sizeof(T))) / S::PER : ws / S::PER, pq = wq + 1;
+    uint4 *dst = reinterpret_cast<uint4 *>(W + node0 * ws);
+    const uint4 *src = reinterpret_cast<const uint4 *>(sw);
+    for (int i = tid; i < nn * wq; i += nt) {
+        const int r = i / wq;
+        dst[i] = src[r * pq + (i - r * wq)];
     }
 }
 
@@ -170,7 +215,7 @@ __global__ void __launch_bounds__(256) spmv_kernel(SpmvArgs<T> a, int rows_per_b
         const int64_t B = a.col[j];
         const T *c = a.coef + int64_t(j) * 8 * N + n;
         const T *vb = a.v + B * N4 + n;
-        const T *wb = a.W + B * 3 * N + n;
+        const T *wb = a.W + B * a.w_stride + n;
         const T m = a.mass[j];
         const T v0 = vb[0], v1 = vb[N], v2 = vb[2 * N], q = vb[3 * N];
         const T K = c[0];
@@ -251,18 +296,20 @@ void launch_assemble_mass(const AsmArgs<T> &a, cudaStream_t s) {
 }
 
 template <typename T>
-void launch_spectral_w(const T *v, const T *H, const uint8_t *flag, T *W, int64_t n_nodes, int N, T rho, T shift,
-                       const double *shift_dev, cudaStream_t s) {
-    const int64_t rows = 3 * n_nodes;
-    if (rows == 0) return;
-    const int g = nblk(rows, 128);
+void launch_spectral_w(const T *v, const T *H, const uint8_t *flag, T *W, int ws, int64_t n_nodes, int N, T rho,
+                       T shift, const double *shift_dev, cudaStream_t s) {
+    if (n_nodes == 0) return;
+#define HB_SPEC(NTV)                                                                                              \
+    spectral_w_kernel<T, NTV><<<nblk(n_nodes, SpecTile<T, NTV>::NB), 3 * SpecTile<T, NTV>::NB, 0, s>>>(        \
+        v, H, flag, W, ws, n_nodes, N, rho, shift, shift_dev)
     switch (N) {
-        case 1: spectral_w_kernel<T, 1><<<g, 128, 0, s>>>(v, H, flag, W, n_nodes, N, rho, shift, shift_dev); break;
-        case 9: spectral_w_kernel<T, 9><<<g, 128, 0, s>>>(v, H, flag, W, n_nodes, N, rho, shift, shift_dev); break;
-        case 13: spectral_w_kernel<T, 13><<<g, 128, 0, s>>>(v, H, flag, W, n_nodes, N, rho, shift, shift_dev); break;
-        case 21: spectral_w_kernel<T, 21><<<g, 128, 0, s>>>(v, H, flag, W, n_nodes, N, rho, shift, shift_dev); break;
-        default: spectral_w_kernel<T, 0><<<g, 128, 0, s>>>(v, H, flag, W, n_nodes, N, rho, shift, shift_dev); break;
+        case 1: HB_SPEC(1); break;
+        case 9: HB_SPEC(9); break;
+        case 13: HB_SPEC(13); break;
+        case 21: HB_SPEC(21); break;
+        default: HB_SPEC(0); break;
     }
+#undef HB_SPEC
 }
 
 template <typename T>
@@ -275,10 +322,10 @@ template void launch_assemble<float>(const AsmArgs<float> &, cudaStream_t);
 template void launch_assemble<double>(const AsmArgs<double> &, cudaStream_t);
 template void launch_assemble_mass<float>(const AsmArgs<float> &, cudaStream_t);
 template void launch_assemble_mass<double>(const AsmArgs<double> &, cudaStream_t);
-template void launch_spectral_w<float>(const float *, const float *, const uint8_t *, float *, int64_t, int, float, float,
-                                       const double *, cudaStream_t);
-template void launch_spectral_w<double>(const double *, const double *, const uint8_t *, double *, int64_t, int, double,
-                                        double, const double *, cudaStream_t);
+template void launch_spectral_w<float>(const float *, const float *, const uint8_t *, float *, int, int64_t, int, float,
+                                       float, const double *, cudaStream_t);
+template void launch_spectral_w<double>(const double *, const double *, const uint8_t *, double *, int, int64_t, int,
+                                        double, double, const double *, cudaStream_t);
 template void launch_spmv<float>(const SpmvArgs<float> &, cudaStream_t);
 template void launch_block_jacobi<float, float>(const float *, const float *, const int *, const uint8_t *,
                                                 const double *, float *, int64_t, int, double, const double *,

@@ -35,7 +35,9 @@ __host__ __device__ inline Layout make_layout(int mode, int N, int nl, int ep, s
     L.Y = o;    o += pad16(row4);
     L.V = o;    if (mode == MODE_JVP || mode == MODE_JVE || mode == MODE_TRES) o += pad16(row4);
     L.HY = o;   if (mode == MODE_RES || mode == MODE_JVE) o += pad16(row3);
-    L.HV = o;   if (mode == MODE_JVE || mode == MODE_JVP) o += pad16(row3);
+    L.HV = o;
+    if (mode == MODE_JVE) o += pad16(row3);
+    if (mode == MODE_JVP) o += pad16(size_t(nl) * w_stride(N, int(ts)) * ts);   // W rows, padded
     L.T = o;    if (mode == MODE_RES || mode == MODE_JVE) o += pad16(row3);
     L.conn = o; o += pad16(size_t(ep) * 4);
     L.total = o;
@@ -177,7 +179,7 @@ __device__ __forceinline__ void jvp_lanes(int e, int n0, int d1, int Nrt, T rho,
                                           const T *__restrict__ sY, const T *__restrict__ sV,
                                           const T *__restrict__ sW, const int *__restrict__ sNode,
                                           T *__restrict__ gout) {
-    const int N = NT > 0 ? NT : Nrt, N4 = 4 * N, N3 = 3 * N;
+    const int N = NT > 0 ? NT : Nrt, N4 = 4 * N, WS = w_stride(N, int(sizeof(T)));
     const uint32_t c = sConn[e];
     const int lo[4] = {int(c & 255u), int((c >> 8) & 255u), int((c >> 16) & 255u), int(c >> 24)};
     int rY[4];
@@ -310,7 +312,7 @@ __device__ __forceinline__ void jvp_lanes(int e, int n0, int d1, int Nrt, T rho,
         L Wa[4];
         const int rW0 = i * N + n0;
 #pragma unroll
-        for (int a = 0; a < 4; ++a) Wa[a] = lload<L>(sW + lo[a] * N3 + rW0, d1);
+        for (int a = 0; a < 4; ++a) Wa[a] = lload<L>(sW + lo[a] * WS + rW0, d1);
         const L Wsum = ladd(ladd(Wa[0], Wa[1]), ladd(Wa[2], Wa[3]));
         const L cW = lfma(kb, Ug[i], lmul(m20, Wsum));
         const L Zi[3] = {Mx[0][i], Mx[1][i], Mx[2][i]};
@@ -697,6 +699,16 @@ __device__ __forceinline__ void patch_pass(const ElemArgs<T> &a, const PatchSmem
         if constexpr (MODE == MODE_JVP || MODE == MODE_JVE || MODE == MODE_TRES)
             cp_async16(reinterpret_cast<uint4 *>(sV) + i, reinterpret_cast<const uint4 *>(a.v) + gidx);
     }
+    if constexpr (MODE == MODE_JVP) {
+        if (a.W) {              // W = shift v + rho H v from the global spectral pass
+            const int wpr = w_stride(N, int(sizeof(T))) * int(sizeof(T)) / 16;
+            for (int i = tid; i < nl * wpr; i += nt) {
+                const int l = i / wpr, c = i - l * wpr;
+                const size_t gidx = size_t(uint32_t(sNode[l]) & ~kDirBit) * wpr + c;
+                cp_async16(reinterpret_cast<uint4 *>(sHV) + i, reinterpret_cast<const uint4 *>(a.W) + gidx);
+            }
+        }
+    }
     cp_async_wait_all();
     if constexpr (MODE == MODE_JVP || MODE == MODE_JVE) {
         // prescribed velocity entries of the direction are not unknowns: each thread zeroes them in the
@@ -713,7 +725,7 @@ __device__ __forceinline__ void patch_pass(const ElemArgs<T> &a, const PatchSmem
         }
     }
     __syncthreads();
-    if constexpr (MODE != MODE_DIAG && MODE != MODE_TRES) {
+    if (MODE != MODE_DIAG && MODE != MODE_TRES && !(MODE == MODE_JVP && a.W)) {
         // time coupling of the staged velocities: (H x)[l][i][n] = sum_k H[n][k] x[l][i][k] for
         // x = u (RES, JVE) and x = v (JVP, JVE)
         constexpr bool hy = (MODE == MODE_RES || MODE == MODE_JVE);
@@ -721,9 +733,10 @@ __device__ __forceinline__ void patch_pass(const ElemArgs<T> &a, const PatchSmem
         constexpr int nsrc = (hy ? 1 : 0) + (hv ? 1 : 0);
         if constexpr (NT > 0 && MODE == MODE_JVP) {
             // JVP stages W = shift v + rho H v (the mass-matrix terms of the tangent)
+            const int WS = w_stride(N, int(sizeof(T)));
             for (int r = tid; r < nl * 3; r += nt) {
                 const int l = r / 3, f = r - 3 * l;
-                circulant_row<T, NT, true>(sH, sV + l * N4 + f * N, sHV + l * N3 + f * N, a.rho, shift);
+                circulant_row<T, NT, true>(sH, sV + l * N4 + f * N, sHV + l * WS + f * N, a.rho, shift);
             }
         } else if constexpr (NT > 0) {
             const int rows = nl * 3;
@@ -747,7 +760,8 @@ __device__ __forceinline__ void patch_pass(const ElemArgs<T> &a, const PatchSmem
                     const T *xv = sV + l * N4 + f * N;
                     T acc2 = 0;
                     for (int k = 0; k < N; ++k) acc2 += h[k] * xv[k];
-                    sHV[i] = MODE == MODE_JVP ? a.rho * acc2 + shift * xv[n] : acc2;
+                    if constexpr (MODE == MODE_JVP) sHV[l * w_stride(N, int(sizeof(T))) + r] = a.rho * acc2 + shift * xv[n];
+                    else sHV[i] = acc2;
                 }
             }
         }

@@ -36,6 +36,9 @@ constexpr double kQB = 0.1381966011250105;
 __host__ __device__ constexpr int in_fields(int mode) {
     return mode == MODE_RES ? 7 : mode == MODE_JVP ? 11 : mode == MODE_JVE ? 14 : mode == MODE_TRES ? 8 : 4;
 }
+// Row stride of the staged / gathered W = shift v + rho H v rows (3 N values): padded to 16 bytes, so a
+// node's W row can be copied with 16-byte asynchronous copies.
+__host__ __device__ constexpr int w_stride(int N, int tsize) { return (3 * N * tsize + 15) / 16 * 16 / tsize; }
 __host__ __device__ constexpr int out_fields(int mode) {
     return (mode == MODE_RES || mode == MODE_JVE) ? 3 : 0;
 }
@@ -69,6 +72,8 @@ struct ElemArgs {
     const uint8_t *flag;           // per node, bit 0: Dirichlet velocity
     int N;
     T rho, mu, shift;
+    const T *W = nullptr;          // JVP: W = shift v + rho H v per node, rows of w_stride(N) (a global
+                                   // spectral pass), gathered instead of formed per patch; nullptr: per patch
     T omega2 = 0;                  // acceleration term of tau_hat (Eq. tauhat); 0 for the HB passes
     int ls_mass = 0;               // time domain (one instance): the shift also enters the least-squares L
                                    // of the tangent (d(du/dt) = shift / rho d u); not its Jacobi diagonal
@@ -188,11 +193,11 @@ struct AsmArgs {
 template <typename T>
 struct SpmvArgs {
     int64_t n_nodes;
-    int N;
+    int N, w_stride;               // W rows of w_stride values
     const int *rowptr, *col;       // CSR of the node pairs (rows = nodes, the diagonal included)
     const T *coef, *mass;
     const T *v;                    // direction [n][4][N]
-    const T *W;                    // shift v + rho H v [n][3][N], 0 on prescribed velocities
+    const T *W;                    // shift v + rho H v, rows [n][w_stride], 0 on prescribed velocities
     T *out;                        // [n][4][N], every entry written
     const uint8_t *flag;
 };
@@ -200,10 +205,10 @@ template <typename T>
 void launch_assemble(const AsmArgs<T> &a, cudaStream_t s);
 template <typename T>
 void launch_assemble_mass(const AsmArgs<T> &a, cudaStream_t s);
-// W = shift v + rho H v (velocity rows; H [N][N]; shift from shift_dev if set)
+// W = shift v + rho H v (velocity rows; H [N][N]; shift from shift_dev if set), rows of ws values
 template <typename T>
-void launch_spectral_w(const T *v, const T *H, const uint8_t *flag, T *W, int64_t n_nodes, int N, T rho, T shift,
-                       const double *shift_dev, cudaStream_t s);
+void launch_spectral_w(const T *v, const T *H, const uint8_t *flag, T *W, int ws, int64_t n_nodes, int N, T rho,
+                       T shift, const double *shift_dev, cudaStream_t s);
 template <typename T>
 void launch_spmv(const SpmvArgs<T> &a, cudaStream_t s);
 // z = (node-block diagonal of the assembled tangent + shift M_AA)^-1 x per node and instance; dpos[A] is
