@@ -569,7 +569,7 @@ def run_ours(args, dist: Dist, spec, config):
         # element-pass time of each launch variant of the FP32 paper-tangent pass
         var0 = prob.launch_variant()
         var_ms = {}
-        for var in range(3):
+        for var in range(4):
             prob.set_launch_variant(var)
             jv()
             torch.cuda.synchronize()

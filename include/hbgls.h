@@ -325,8 +325,9 @@ hb_status hb_get_info(hb_problem *p, hb_info *info);
 int64_t hb_launch_count(const hb_problem *p);
 /* Launch variant of the FP32 paper-tangent element pass (no counterpart in the paper; a tuning knob):
  * 0 = 256 threads per block, two instances per thread on paired FP32 instructions; 1 = 384 threads,
- * one instance per thread (the default); 2 = 512 threads, one instance per thread.  All give the same
- * operator up to FP32 rounding.  hb_tune_patches also searches it for precision 1.  HB_ERR_INVALID_ARG
+ * one instance per thread (the default); 2 = 512 threads, one instance per thread; 3 = 192 threads, one
+ * instance per thread, four resident blocks per SM (pays with patches small enough for four blocks'
+ * shared memory, see hb_tune_patches).  All give the same operator up to FP32 rounding.  hb_tune_patches also searches it for precision 1.  HB_ERR_INVALID_ARG
  * for another value.  hb_get_launch_variant returns the current variant (-1 for a null problem). */
 hb_status hb_set_launch_variant(hb_problem *p, int variant);
 int hb_get_launch_variant(const hb_problem *p);

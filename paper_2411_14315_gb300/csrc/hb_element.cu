@@ -98,14 +98,20 @@ struct LaneOf<float> { using type = float2; };
 //   0: 256 threads per block; FP32 runs two instances per thread on paired instructions
 //   1: 384 threads per block, one instance per thread (fewer registers, more resident warps; default)
 //   2: 512 threads per block, one instance per thread
+//   3: 192 threads per block, one instance per thread, four resident blocks per SM (with patches small
+//      enough for four blocks' shared memory, the gather and barrier phases of one block overlap the
+//      element work of the others)
+// minb: resident blocks per SM the register allocation is bounded for
 template <typename T, int VAR>
 struct ElemCfg;
 template <typename T>
-struct ElemCfg<T, 0> { static constexpr int block = 256; using lane = typename LaneOf<T>::type; };
+struct ElemCfg<T, 0> { static constexpr int block = 256, minb = sizeof(T) == 4 ? 2 : 1; using lane = typename LaneOf<T>::type; };
 template <typename T>
-struct ElemCfg<T, 1> { static constexpr int block = 384; using lane = T; };
+struct ElemCfg<T, 1> { static constexpr int block = 384, minb = sizeof(T) == 4 ? 2 : 1; using lane = T; };
 template <typename T>
-struct ElemCfg<T, 2> { static constexpr int block = 512; using lane = T; };
+struct ElemCfg<T, 2> { static constexpr int block = 512, minb = sizeof(T) == 4 ? 2 : 1; using lane = T; };
+template <typename T>
+struct ElemCfg<T, 3> { static constexpr int block = 192, minb = sizeof(T) == 4 ? 4 : 1; using lane = T; };
 
 __device__ __forceinline__ unsigned long long f2_bits(float2 a) {
     unsigned long long r;
@@ -833,7 +839,7 @@ __device__ __forceinline__ void patch_pass(const ElemArgs<T> &a, const PatchSmem
 // Persistent element pass: block b takes patches b, b + G, b + 2G, ... (G = gridDim.x) and stages each
 // next patch's slot while the current one computes.
 template <typename T, int MODE, int NT, int VAR>
-__global__ void __launch_bounds__(ElemCfg<T, VAR>::block, (sizeof(T) == 4 ? 2 : 1)) elem_kernel(ElemArgs<T> a) {
+__global__ void __launch_bounds__(ElemCfg<T, VAR>::block, ElemCfg<T, VAR>::minb) elem_kernel(ElemArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int N = NT > 0 ? NT : a.N;
     const PatchSmem<T> sm = patch_smem<T, MODE>(smem, N, a.pv.nl_max, a.pv.ep_max);
@@ -871,7 +877,7 @@ struct BatchPrefetch {
 };
 
 template <typename T, int MODE, int NT, int VAR>
-__global__ void __launch_bounds__(ElemCfg<T, VAR>::block, (sizeof(T) == 4 ? 2 : 1))
+__global__ void __launch_bounds__(ElemCfg<T, VAR>::block, ElemCfg<T, VAR>::minb)
     batch_elem_kernel(const ElemArgs<T> *__restrict__ args, const int *__restrict__ bslots, int bslot_stride,
                       int item_begin, int item_end, int *counter) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1012,6 +1018,10 @@ static void launch_elem_n(const ElemArgs<T> &a, int grid, cudaStream_t s) {
             launch_elem_v<T, MODE, NT, 2>(a, grid, s);
             return;
         }
+        if (a.variant == 3) {
+            launch_elem_v<T, MODE, NT, 3>(a, grid, s);
+            return;
+        }
     }
     launch_elem_v<T, MODE, NT, 0>(a, grid, s);
 }
@@ -1061,6 +1071,7 @@ static void launch_batch_mode(const BatchGroup<T> &g, size_t smem, int grid, cud
     if constexpr (MODE == MODE_JVP && sizeof(T) == 4) {
         if (g.variant == 1) return launch_batch_var<T, MODE, 1>(g, smem, grid, s);
         if (g.variant == 2) return launch_batch_var<T, MODE, 2>(g, smem, grid, s);
+        if (g.variant == 3) return launch_batch_var<T, MODE, 3>(g, smem, grid, s);
     }
     launch_batch_var<T, MODE, 0>(g, smem, grid, s);
 }

@@ -22,7 +22,7 @@ enum Mode : int {
 
 constexpr int kGeomStride = 16;       // per element: grad N_a (4 x 3), V, C_I nu^2 G:G, 2 pad
 constexpr int kMaxN = 31;
-constexpr int kJvpVariants = 3;       // launch variants of the FP32 paper-tangent element pass             // largest number of time instances supported
+constexpr int kJvpVariants = 4;       // launch variants of the FP32 paper-tangent element pass             // largest number of time instances supported
 constexpr double kCI = 3.0;           // Eq. (tau)
 // 4-point degree-2 Gauss rule on a tetrahedron (barycentric coordinates of the points)
 constexpr double kQA = 0.5854101966249685;

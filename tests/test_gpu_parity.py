@@ -79,19 +79,19 @@ def test_residual_and_jv_across_instance_counts(n_h):
 @pytest.mark.parametrize("n_h", [0, 1, 4, 10, 15])
 def test_paper_tangent_launch_variants(n_h):
     """Every launch variant of the FP32 paper-tangent pass (pairs of instances per thread, one instance
-    per thread at two block sizes) against the oracle, for compile-time and generic instance counts."""
+    per thread at three block sizes) against the oracle, for compile-time and generic instance counts."""
     spec = P.box_spec(seed=70 + n_h, n_h=n_h, n=(6, 5, 4))
     ora = P.oracle_problem(spec)
     gp = P.gpu_problem(spec)
     y = I.random_state(spec.mesh.n_nodes, spec.N, 71)
     v = I.random_state(spec.mesh.n_nodes, spec.N, 72)
     ref = O.jv_paper(ora, y, v, shift=0.8)
-    for var in (0, 1, 2):
+    for var in (0, 1, 2, 3):
         gp.set_launch_variant(var)
         assert gp.launch_variant() == var
         assert relerr(gp.jv(y, v, 0, 1, 0.8), ref) < TOL[1], var
     with pytest.raises(RuntimeError):
-        gp.set_launch_variant(3)
+        gp.set_launch_variant(4)
 
 
 def test_womersley_pipe_parabolic_profile_and_patches():
