@@ -14,6 +14,8 @@
 // terms (v's prescribed entries count as zero).
 #include "hb_internal.cuh"
 
+#include <algorithm>
+
 namespace hb {
 
 namespace {
@@ -198,6 +200,166 @@ __global__ void __launch_bounds__(3 * SpecTile<T, NT>::NB, SpecTile<T, NT>::MINB
     }
 }
 
+// Tensor-core form of the same pass for FP32 and N = 9, 13, 21.  A block's velocity rows (node, field)
+// form X [rows][N], and W = X B with B[k][m] = rho H[m][k] + shift delta_km.  TF32 products on the tensor
+// cores (mma.sync m16n8k8, FP32 accumulation) with every operand split into a TF32 head and a TF32 tail,
+// x = hi + lo: W = Xlo Bhi + Xhi Blo + Xhi Bhi keeps FP32 accuracy (the dropped Xlo Blo is ~2^-22
+// relative).  One warp per 16-row tile; K and the output columns are padded to multiples of 8.
+__device__ __forceinline__ uint32_t tf32_bits(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+                 "{%8, %9}, {%0, %1, %2, %3};"
+                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void cpa16(void *smem_dst, const void *gmem_src) {
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cpa_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cpa_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Persistent over tiles of 64 nodes with two tile buffers: the copies of the block's next tile are in
+// flight while the current one is multiplied and written back.
+template <int NT>
+struct SpecTc {
+    static constexpr int NB = 64, ROWS = 3 * NB, TILES = ROWS / 16, TPW = (TILES + 5) / 6;
+    static constexpr int N4 = 4 * NT, KP = (NT + 7) / 8 * 8, NS = KP / 8;
+    static constexpr int WS = w_stride(NT, 4), WP = WS + 4, WQ = WS / 4, PQ = WP / 4;
+    static constexpr int XS = NB * N4 > NB * WP ? NB * N4 : NB * WP;
+};
+
+template <int NT>
+__global__ void __launch_bounds__(192) spectral_w_tc_kernel(const float *__restrict__ v, const float *__restrict__ H,
+                                                            const uint8_t *__restrict__ flag, float *__restrict__ W,
+                                                            int64_t n_nodes, float rho, float shift,
+                                                            const double *__restrict__ shift_dev) {
+    using S = SpecTc<NT>;
+    constexpr int NB = S::NB, N4 = S::N4, KP = S::KP, NS = S::NS, TPW = S::TPW;
+    constexpr int WS = S::WS, WP = S::WP, WQ = S::WQ, PQ = S::PQ;
+    __shared__ __align__(16) float sx[2][S::XS];                  // v tiles; W rows written in place
+    __shared__ uint32_t sBh[KP * KP], sBl[KP * KP];               // B as TF32 head and tail, [k][m]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t n_tiles = (n_nodes + NB - 1) / NB;
+    int64_t t = blockIdx.x;
+    if (t >= n_tiles) return;
+    const float sh = shift_dev ? float(*shift_dev) : shift;
+    for (int i = tid; i < KP * KP; i += 192) {
+        const int k = i / KP, m = i - k * KP;
+        const float b = (k < NT && m < NT) ? rho * H[m * NT + k] + (k == m ? sh : 0.f) : 0.f;
+        const uint32_t hi = tf32_bits(b);
+        sBh[i] = hi;
+        sBl[i] = tf32_bits(b - __uint_as_float(hi));
+    }
+    auto load = [&](int64_t tile, int buf) {
+        const int64_t n0 = tile * NB;
+        const int nn = int(n_nodes - n0 < NB ? n_nodes - n0 : NB);
+        const uint4 *src = reinterpret_cast<const uint4 *>(v + n0 * N4);
+        uint4 *dst = reinterpret_cast<uint4 *>(sx[buf]);
+        for (int i = tid; i < nn * N4 / 4; i += 192) cpa16(dst + i, src + i);
+        cpa_commit();
+    };
+    load(t, 0);
+    const int g = lane >> 2, q = lane & 3;
+    for (int b = 0; t < n_tiles; t += gridDim.x, b ^= 1) {
+        if (t + gridDim.x < n_tiles) load(t + gridDim.x, b ^ 1);
+        else cpa_commit();                                         // empty group: uniform counting
+        cpa_wait1();                                               // this thread's copies of tile t
+        __syncthreads();                                           // everyone's (and B)
+        const int64_t node0 = t * NB;
+        const int nn = int(n_nodes - node0 < NB ? n_nodes - node0 : NB);
+        float *x = sx[b];
+        float acc[TPW][NS][4];
+#pragma unroll
+        for (int u = 0; u < TPW; ++u) {
+            const int tile = warp + 6 * u;
+#pragma unroll
+            for (int j = 0; j < NS; ++j) acc[u][j][0] = acc[u][j][1] = acc[u][j][2] = acc[u][j][3] = 0.f;
+            if (tile >= S::TILES) continue;
+            // rows past the last node hold stale values; their outputs are never written
+            const int r0 = tile * 16 + g, r1 = r0 + 8;
+            const float *x0 = x + (r0 / 3) * N4 + (r0 % 3) * NT;
+            const float *x1 = x + (r1 / 3) * N4 + (r1 % 3) * NT;
+#pragma unroll
+            for (int ks = 0; ks < NS; ++ks) {
+                const int k0 = ks * 8 + q, k1 = k0 + 4;
+                const float av[4] = {k0 < NT ? x0[k0] : 0.f, k0 < NT ? x1[k0] : 0.f, k1 < NT ? x0[k1] : 0.f,
+                                     k1 < NT ? x1[k1] : 0.f};
+                uint32_t ah[4], al[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    ah[i] = tf32_bits(av[i]);
+                    al[i] = tf32_bits(av[i] - __uint_as_float(ah[i]));
+                }
+#pragma unroll
+                for (int j = 0; j < NS; ++j) {
+                    const int c = j * 8 + g;
+                    const uint32_t bh0 = sBh[k0 * KP + c], bh1 = sBh[k1 * KP + c];
+                    const uint32_t bl0 = sBl[k0 * KP + c], bl1 = sBl[k1 * KP + c];
+                    mma_tf32(acc[u][j], al, bh0, bh1);
+                    mma_tf32(acc[u][j], ah, bl0, bl1);
+                    mma_tf32(acc[u][j], ah, bh0, bh1);
+                }
+            }
+        }
+        __syncthreads();                                           // every v row read: W overwrites it
+#pragma unroll
+        for (int u = 0; u < TPW; ++u) {
+            const int tile = warp + 6 * u;
+            if (tile >= S::TILES) continue;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int r = tile * 16 + g + 8 * h, l = r / 3, f = r - 3 * l;
+                if (l >= nn) continue;
+                const bool dir = flag[node0 + l] & 1;
+                float *o = x + l * WP + f * NT;
+#pragma unroll
+                for (int j = 0; j < NS; ++j) {
+                    const int m = j * 8 + 2 * q;
+                    if (m < NT) o[m] = dir ? 0.f : acc[u][j][2 * h];
+                    if (m + 1 < NT) o[m + 1] = dir ? 0.f : acc[u][j][2 * h + 1];
+                }
+            }
+        }
+        for (int i = tid; i < nn * (WS - 3 * NT); i += 192) {
+            const int l = i / (WS - 3 * NT);
+            x[l * WP + 3 * NT + (i - l * (WS - 3 * NT))] = 0.f;    // row padding
+        }
+        __syncthreads();
+        uint4 *dst = reinterpret_cast<uint4 *>(W + node0 * WS);
+        const uint4 *src = reinterpret_cast<const uint4 *>(x);
+        for (int i = tid; i < nn * WQ; i += 192) {
+            const int r = i / WQ;
+            dst[i] = src[r * PQ + (i - r * WQ)];
+        }
+        __syncthreads();                                           // buffer b free for tile t + 2 G
+    }
+    cpa_wait0();
+}
+
+template <int NT>
+void launch_spectral_tc(const float *v, const float *H, const uint8_t *flag, float *W, int64_t n_nodes, float rho,
+                        float shift, const double *shift_dev, cudaStream_t s) {
+    static int grid_cap = 0;
+    if (grid_cap == 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, spectral_w_tc_kernel<NT>, 192, 0);
+        grid_cap = std::max(1, sms * std::max(1, per_sm));
+    }
+    const int64_t tiles = (n_nodes + SpecTc<NT>::NB - 1) / SpecTc<NT>::NB;
+    const int grid = int(std::min<int64_t>(tiles, grid_cap));
+    spectral_w_tc_kernel<NT><<<grid, 192, 0, s>>>(v, H, flag, W, n_nodes, rho, shift, shift_dev);
+}
+
 // out = (assembled tangent) v: one thread per (row, instance), rows_per_block rows of a block; each
 // thread sums its row's pairs in registers and stores once (no atomics).  Prescribed velocity rows
 // return v.
@@ -299,6 +461,15 @@ template <typename T>
 void launch_spectral_w(const T *v, const T *H, const uint8_t *flag, T *W, int ws, int64_t n_nodes, int N, T rho,
                        T shift, const double *shift_dev, cudaStream_t s) {
     if (n_nodes == 0) return;
+    if constexpr (sizeof(T) == 4) {
+        // FP32 at the compile-time instance counts: the tensor-core form
+        switch (N) {
+            case 9: launch_spectral_tc<9>(v, H, flag, W, n_nodes, rho, shift, shift_dev, s); return;
+            case 13: launch_spectral_tc<13>(v, H, flag, W, n_nodes, rho, shift, shift_dev, s); return;
+            case 21: launch_spectral_tc<21>(v, H, flag, W, n_nodes, rho, shift, shift_dev, s); return;
+            default: break;
+        }
+    }
 #define HB_SPEC(NTV)                                                                                              \
     spectral_w_kernel<T, NTV><<<nblk(n_nodes, SpecTile<T, NTV>::NB), 3 * SpecTile<T, NTV>::NB, 0, s>>>(        \
         v, H, flag, W, ws, n_nodes, N, rho, shift, shift_dev)
