@@ -30,42 +30,66 @@ def central_difference(M: int, T: float) -> np.ndarray:
     return D
 
 
-@pytest.fixture(scope="module")
-def channel_hb():
-    """Channel forced by two inflow harmonics, solved by HB with N = 9 (4 harmonics: room for the
-    products the convective term forms)."""
-    spec = P.channel_spec(n_h=2)
+M1, M2 = 15, 25
+
+
+def hb_harmonics(spec, h_scale: float = 1.0) -> np.ndarray:
+    """HB solution (N = 9) of the channel; h_scale != 1 plants a mistake in the oracle's H."""
     spec.n_h = 4
     pr = P.oracle_problem(spec)
+    pr.H = h_scale * pr.H
     y, hist = O.solve(pr, rtol=1e-12)
     assert hist[-1] <= 1e-12 * hist[0]
-    return spec, O.instances_to_harmonics(y, 4)
+    return O.instances_to_harmonics(y, 4)
 
 
-def fd_periodic_harmonics(spec, c_hb, M: int) -> np.ndarray:
-    """Periodic solution on M time levels with the central difference, from the HB solution sampled
-    on the fine grid; its first 9 real harmonics."""
+def fd_periodic_harmonics(spec, c_start, M: int) -> np.ndarray:
+    """Periodic solution on M time levels with the central difference, from c_start sampled on the fine
+    grid (exact Newton throughout); its first 9 real harmonics."""
     spec.n_h = (M - 1) // 2
     pr = P.oracle_problem(spec)
     pr.H = central_difference(M, spec.T)
-    y0 = O.harmonics_to_instances(c_hb, M, spec.T)
-    y, hist = O.solve(pr, y0=y0, switch_tol=10.0, rtol=1e-9, gmres_tol=1e-3)   # exact Newton throughout
+    y0 = O.harmonics_to_instances(c_start, M, spec.T)
+    y, hist = O.solve(pr, y0=y0, switch_tol=10.0, rtol=1e-9, gmres_tol=1e-3)
     assert hist[-1] <= 1e-10 * hist[0]
-    return O.instances_to_harmonics(y, (M - 1) // 2)[:, :, :c_hb.shape[-1]]
+    return O.instances_to_harmonics(y, (M - 1) // 2)[:, :, :c_start.shape[-1]]
 
 
-def test_central_difference_periodic_solution_converges_to_hb_at_second_order(channel_hb):
-    spec, c_hb = channel_hb
-    m1, m2 = 15, 25
-    c1 = fd_periodic_harmonics(spec, c_hb, m1)
-    c2 = fd_periodic_harmonics(spec, c_hb, m2)
+@pytest.fixture(scope="module")
+def brute_force():
+    """Channel forced by two inflow harmonics: its HB solution with N = 9 (4 harmonics, room for the
+    products the convective term forms) and the central-difference periodic solutions on 15 and 25
+    levels."""
+    spec = P.channel_spec(n_h=2)
+    c_hb = hb_harmonics(spec)
+    return spec, c_hb, fd_periodic_harmonics(spec, c_hb, M1), fd_periodic_harmonics(spec, c_hb, M2)
+
+
+def convergence(c_hb, c1, c2):
+    """(e1, e2, Richardson error) of the two grids' harmonics against c_hb, relative."""
     nrm = np.linalg.norm(c_hb)
-    e1 = np.linalg.norm(c1 - c_hb) / nrm
-    e2 = np.linalg.norm(c2 - c_hb) / nrm
-    # measured: 1.97e-2 and 7.25e-3, ratio 2.72 against (25 / 15)^2 = 2.78
+    rich = (M2 * M2 * c2 - M1 * M1 * c1) / (M2 * M2 - M1 * M1)
+    return (np.linalg.norm(c1 - c_hb) / nrm, np.linalg.norm(c2 - c_hb) / nrm, np.linalg.norm(rich - c_hb) / nrm)
+
+
+def second_order_to(c_hb, c1, c2) -> bool:
+    e1, e2, er = convergence(c_hb, c1, c2)
+    return 0.9 * (M2 / M1) ** 2 < e1 / e2 < 1.1 * (M2 / M1) ** 2 and er < 0.1 * e2
+
+
+def test_central_difference_periodic_solution_converges_to_hb_at_second_order(brute_force):
+    spec, c_hb, c1, c2 = brute_force
+    e1, e2, er = convergence(c_hb, c1, c2)
+    # measured: 1.97e-2 and 7.25e-3, ratio 2.72 against (25 / 15)^2 = 2.78; Richardson extrapolation
+    # removes the dt^2 term and what is left (dt^4, HB's own truncation) is 2.6e-4
     assert e2 < 1.5e-2
-    assert 0.9 * (m2 / m1) ** 2 < e1 / e2 < 1.1 * (m2 / m1) ** 2
-    # Richardson extrapolation removes the dt^2 term: what is left (dt^4 and HB's own truncation) is
-    # far below the finer grid's error (measured 2.6e-4)
-    rich = (m2 * m2 * c2 - m1 * m1 * c1) / (m2 * m2 - m1 * m1)
-    assert np.linalg.norm(rich - c_hb) / nrm < 0.1 * e2
+    assert second_order_to(c_hb, c1, c2), (e1, e2, er)
+
+
+@pytest.mark.parametrize("h_scale", [-1.0, 1.01])
+def test_planted_mistake_in_H_breaks_the_agreement(brute_force, h_scale):
+    """The same check against an oracle whose H has the wrong sign (time reversed) or a 1 % frequency
+    error: the brute-force solutions no longer converge to its HB solution."""
+    spec, c_hb, c1, c2 = brute_force
+    c_wrong = hb_harmonics(spec, h_scale)
+    assert not second_order_to(c_wrong, c1, c2)
