@@ -105,7 +105,8 @@ def instances_to_harmonics(y: np.ndarray, n_h: int) -> np.ndarray:
 
 
 def harmonics_to_instances(coef: np.ndarray, N: int, T: float) -> np.ndarray:
-    """Inverse of instances_to_harmonics: the real series evaluated at the instances."""
+    """Inverse of instances_to_harmonics: the real series of Eq. (upgh_def) evaluated at the instances
+    of Eq. (upghharm)."""
     n_h = (coef.shape[-1] - 1) // 2
     t = instance_times(N, T)
     w = 2.0 * math.pi / T
@@ -141,7 +142,8 @@ class Geometry:
 
 
 class HBProblem:
-    """Mesh + fluid + boundary conditions of one HB solve.
+    """Mesh + fluid + boundary conditions of one HB solve (the problem statement of Sec. 2.1: domain,
+    rho, mu, period, N_h; inflow and outlet data as harmonics, Sec. 2.1 and Sec. 3).
 
     Face tags: 0 = no-slip wall.  Inflow tags carry Dirichlet g = profile(x) q(t); pressure outlets
     h = -P(t); resistance outlets h = -(P_d(t) + R Q(t)); other tags are traction-free (h = 0).
@@ -169,6 +171,7 @@ class HBProblem:
 
     # boundary faces: outward unit normal (away from the owning tetrahedron's opposite vertex) and area
     def _face_geometry(self):
+        """Outward unit normal and area of every boundary face (for the surface integrals of Eq. NS-weak)."""
         loc = np.array([(1, 2, 3), (0, 2, 3), (0, 1, 3), (0, 1, 2)])
         tf = np.sort(self.tets[:, loc].reshape(-1, 3), axis=1)
         n = self.n_nodes
@@ -192,6 +195,7 @@ class HBProblem:
         self.face_normal = nrm
 
     def set_inflow(self, tag: int, profile, a, b):
+        """Separable Dirichlet data g = profile(x) q(t), q a real Fourier series (Eq. upgh_def)."""
         self.inflow[int(tag)] = (np.asarray(profile, dtype=np.float64), np.asarray(a, float), np.asarray(b, float))
 
     def set_inflow_harmonics(self, tag: int, harmonics):
@@ -199,14 +203,17 @@ class HBProblem:
         self.inflow[int(tag)] = ("harmonics", np.asarray(harmonics, dtype=np.float64), None)
 
     def set_outlet_pressure(self, tag: int, a, b):
+        """Outlet pressure P(t) as a real Fourier series; traction h = -P (reading R5)."""
         self.outlet_p[int(tag)] = (np.asarray(a, float), np.asarray(b, float))
 
     def set_outlet_resistance(self, tag: int, R: float, a, b):
+        """Resistance outlet h = -(P_d(t) + R Q(t)) (reading R8; an extension, not in the paper)."""
         self.outlet_r[int(tag)] = (float(R), np.asarray(a, float), np.asarray(b, float))
 
     # derived boundary data
     def dirichlet(self):
-        """(mask [n_nodes] bool, g [n_nodes, 3, N]): wall nodes (u = 0) take priority over inflow."""
+        """(mask [n_nodes] bool, g [n_nodes, 3, N]) at the instances: wall nodes (u = 0) take priority over
+        inflow (reading R11)."""
         N = self.N
         mask = np.zeros(self.n_nodes, dtype=bool)
         g = np.zeros((self.n_nodes, 3, N))
@@ -224,6 +231,7 @@ class HBProblem:
         return mask, g
 
     def neumann_faces(self) -> np.ndarray:
+        """Faces of the Neumann part of the boundary (every tag that is neither wall nor inflow)."""
         dir_tags = set(self.inflow) | {0}
         return np.nonzero(~np.isin(self.face_tag, list(dir_tags)))[0]
 
@@ -240,6 +248,7 @@ class HBProblem:
         return y
 
     def apply_dirichlet(self, y: np.ndarray) -> np.ndarray:
+        """y with the prescribed velocities of Sec. 2.3 built in."""
         mask, g = self.dirichlet()
         y = y.copy()
         y[mask, :3] = g[mask]
@@ -251,11 +260,13 @@ class HBProblem:
 
 
 def _apply_H(prob: HBProblem, x: np.ndarray) -> np.ndarray:
-    """Instance coupling: (H x)[..., j] = sum_k H[j, k] x[..., k]."""
+    """Instance coupling of Eq. (NS-harm): (H x)[..., j] = sum_k H[j, k] x[..., k]."""
     return x @ prob.H.T
 
 
 def _element_state(prob: HBProblem, y: np.ndarray, elems):
+    """Per element and quadrature point: u, H u, grad u, grad p and tau of Eq. (tau) at every instance
+    (readings R2, R3)."""
     t = prob.tets[elems]
     g = prob.geo
     U = y[t][:, :, :3, :]                               # [e, a, i, n]
@@ -305,6 +316,7 @@ def element_residual(prob: HBProblem, y: np.ndarray, elems=None):
 
 
 def _assemble(prob: HBProblem, t, Qm, T, Qc):
+    """Element-to-node sums of Q^m, T and Q^c (the assembly behind Eq. Rmc; reading R4)."""
     n, N = prob.n_nodes, prob.N
     rm = np.zeros((n, 3, N))
     tm = np.zeros((n, 3, N))
@@ -323,7 +335,7 @@ _MID = np.array([[0.5, 0.5, 0.0], [0.0, 0.5, 0.5], [0.5, 0.0, 0.5]])   # N at th
 
 
 def _outlet_h(prob: HBProblem, y: np.ndarray) -> np.ndarray:
-    """Traction level h per face and instance [n_faces, N]."""
+    """Traction level h per face and instance [n_faces, N]: -P (reading R5) or -(P_d + R Q) (R8)."""
     N = prob.N
     h = np.zeros((prob.faces.shape[0], N))
     for tag, (a, b) in prob.outlet_p.items():
@@ -335,14 +347,16 @@ def _outlet_h(prob: HBProblem, y: np.ndarray) -> np.ndarray:
 
 
 def outlet_flux(prob: HBProblem, y: np.ndarray, tag: int) -> np.ndarray:
-    """Q_n = int_Gamma u_n . n for P1 velocity (exact: face area / 3 times the nodal sum)."""
+    """Q_n = int_Gamma u_n . n for P1 velocity (exact: face area / 3 times the nodal sum); the flow rate
+    of a resistance outlet (reading R8)."""
     f = np.nonzero(prob.face_tag == tag)[0]
     un = np.einsum("fbin,fi->fbn", y[prob.faces[f]][:, :, :3, :], prob.face_normal[f])
     return np.einsum("f,fbn->n", prob.face_area[f] / 3.0, un)
 
 
 def boundary_residual(prob: HBProblem, y: np.ndarray) -> np.ndarray:
-    """Momentum contributions of the Neumann faces [n_nodes, 3, N]."""
+    """Momentum contributions of the Neumann faces [n_nodes, 3, N]: the traction term of Eq. (NS-weak)
+    and the backflow stabilisation of Sec. 2.3 as printed (reading R5)."""
     out = np.zeros((prob.n_nodes, 3, prob.N))
     fn = prob.neumann_faces()
     if fn.size == 0:
@@ -379,6 +393,7 @@ def residual(prob: HBProblem, y: np.ndarray) -> np.ndarray:
 
 
 def _mask_v(prob: HBProblem, v: np.ndarray):
+    """(mask, v with its prescribed velocity entries zeroed): they are not unknowns (Sec. 2.3)."""
     mask, _ = prob.dirichlet()
     vm = v.copy()
     vm[mask, :3] = 0.0
@@ -425,7 +440,8 @@ def jv_paper(prob: HBProblem, y: np.ndarray, v: np.ndarray, shift: float = 0.0) 
 
 
 def jv_exact(prob: HBProblem, y: np.ndarray, v: np.ndarray, shift: float = 0.0) -> np.ndarray:
-    """Exact derivative of residual() along v (plus shift M_vel v); Dirichlet rows identity."""
+    """Exact derivative of residual() (Eq. Rmc) along v (plus shift M_vel v); Dirichlet rows identity
+    (reading R7: the Newton phase's Jacobian)."""
     mask, vm = _mask_v(prob, v)
     elems = np.arange(prob.tets.shape[0])
     s = _element_state(prob, y, elems)
@@ -537,8 +553,8 @@ def jacobi_diag(prob: HBProblem, y: np.ndarray, shift: float = 0.0) -> np.ndarra
 
 def gmres(matvec, b: np.ndarray, precond_inv, tol: float, restart: int = 50, maxiter: int = 2000,
           x0=None):
-    """Right-preconditioned restarted GMRES (Saad & Schultz) with modified Gram-Schmidt and Givens
-    rotations, all FP64.  Solves A x = b to ||b - A x|| <= tol ||b||.  Returns (x, iterations)."""
+    """Right-preconditioned restarted GMRES (Saad & Schultz; the linear solver of every Newton step,
+    Sec. 2.3) with modified Gram-Schmidt and Givens rotations, all FP64.  Solves A x = b to ||b - A x|| <= tol ||b||.  Returns (x, iterations)."""
     n = b.size
     x = np.zeros(n) if x0 is None else x0.copy()
     bnorm = np.linalg.norm(b)

@@ -35,6 +35,7 @@ def layer_shapes(f_in: int, f_e: int, f_out: int, hidden: int = 64, layers: int 
 
 
 def init_params(shapes, seed: int):
+    """Seeded parameters for the tests (an input of the definition above, not part of it)."""
     rng = np.random.default_rng(seed)
     ps = []
     for (i, h, o) in shapes:
@@ -44,6 +45,7 @@ def init_params(shapes, seed: int):
 
 
 def _mlp_fwd(p, X):
+    """mlp(p, X) of the definition above; also returns what the backward pass needs."""
     W1, b1, W2, b2 = p
     Z = X @ W1 + b1
     A = np.maximum(Z, 0.0)
@@ -51,6 +53,7 @@ def _mlp_fwd(p, X):
 
 
 def _mlp_bwd(p, cache, dY):
+    """Backward pass of mlp (chain rule): gradients of its parameters and of its input."""
     W1, b1, W2, b2 = p
     X, A = cache
     dW2 = A.T @ dY
@@ -64,7 +67,7 @@ def _mlp_bwd(p, cache, dY):
 
 
 def forward(params, x, src, dst, e, layers: int):
-    """Returns (out, caches)."""
+    """The network of the definition above on one graph; returns (out, caches)."""
     H = params[0][2].shape[1]
     h, c_enc = _mlp_fwd(params[0], x)
     caches = [c_enc]
@@ -83,7 +86,8 @@ def forward(params, x, src, dst, e, layers: int):
 
 
 def loss_and_grad(params, x, src, dst, e, target, layers: int):
-    """Mean squared error and its gradient with respect to every parameter."""
+    """The loss of the definition above and its gradient with respect to every parameter (backward pass
+    through the layers in reverse order)."""
     H = params[0][2].shape[1]
     out, caches = forward(params, x, src, dst, e, layers)
     diff = out - target
@@ -108,10 +112,12 @@ def loss_and_grad(params, x, src, dst, e, target, layers: int):
 
 
 def flatten(ps):
+    """Parameters in order as one vector (W1, b1, W2, b2 of each MLP, row-major)."""
     return np.concatenate([np.concatenate([W1.ravel(), b1, W2.ravel(), b2]) for (W1, b1, W2, b2) in ps])
 
 
 def unflatten(vec, shapes):
+    """Inverse of flatten."""
     ps = []
     o = 0
     for (i, h, out) in shapes:

@@ -51,13 +51,15 @@ def galpha(rho_inf: float = 0.5):
 
 
 def series(a, b, omega: float, t: float) -> float:
-    """a0 + sum_k (a_k cos k omega t + b_k sin k omega t)."""
+    """a0 + sum_k (a_k cos k omega t + b_k sin k omega t): the boundary data's real series (Eq. upgh_def)
+    at time t."""
     k = np.arange(1, len(a))
     return float(a[0] + np.sum(a[1:] * np.cos(k * omega * t)) + np.sum(b[1:] * np.sin(k * omega * t)))
 
 
 def dirichlet_at(prob: HB.HBProblem, t: float):
-    """(mask [n], g [n, 3]) at time t: inflow profile x waveform(t), or per-point harmonics at t; walls 0."""
+    """(mask [n], g [n, 3]) at time t: inflow profile x waveform(t), or per-point harmonics at t; walls 0
+    (reading R11, evaluated at one time instead of the instances)."""
     mask = np.zeros(prob.n_nodes, dtype=bool)
     g = np.zeros((prob.n_nodes, 3))
     w = prob.omega
@@ -80,7 +82,8 @@ def dirichlet_at(prob: HB.HBProblem, t: float):
 
 
 def _outlet_h(prob: HB.HBProblem, y: np.ndarray, t: float) -> np.ndarray:
-    """Traction level h per face at time t: -P(t), or -(P_d(t) + R Q) for resistance outlets."""
+    """Traction level h per face at time t: -P(t) (reading R5), or -(P_d(t) + R Q) for resistance outlets
+    (R8)."""
     h = np.zeros(prob.faces.shape[0])
     for tag, (a, b) in prob.outlet_p.items():
         h[prob.face_tag == tag] = -series(a, b, prob.omega, t)
@@ -110,6 +113,7 @@ def _boundary(prob: HB.HBProblem, y: np.ndarray, h: np.ndarray) -> np.ndarray:
 
 
 def _state(prob: HB.HBProblem, y: np.ndarray, omega2: float):
+    """Per element and quadrature point: u and tau_hat of Eq. (tauhat) with omega_hat^2 = omega2 (R14)."""
     t = prob.tets
     g = prob.geo
     U = y[t][:, :, :3]                                     # [e, a, i]
@@ -121,7 +125,8 @@ def _state(prob: HB.HBProblem, y: np.ndarray, omega2: float):
 
 
 def residual(prob: HB.HBProblem, y: np.ndarray, ydot: np.ndarray, t: float, omega2: float) -> np.ndarray:
-    """Time-domain GLS residual [n, 4] of one time level (module docstring); Dirichlet momentum rows 0."""
+    """Time-domain GLS residual [n, 4] of one time level of the conventional solver of Sec. 3 (module
+    docstring; readings R13, R14); Dirichlet momentum rows 0."""
     rho, mu = prob.rho, prob.mu
     tt, U, Uq, tau = _state(prob, y, omega2)
     gN, V = prob.geo.gradN, prob.geo.V

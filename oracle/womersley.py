@@ -1,5 +1,8 @@
 """Womersley's closed form for fully developed oscillatory flow in a straight pipe (test infrastructure).
 
+A textbook exact solution of the Navier-Stokes equations, not a case of the paper: it checks the unsteady
+solution of both the HB method (Sec. 2) and the conventional time marching (Sec. 3) on a pipe.
+
 For axial velocity w(r, t) in a pipe of radius R driven by G(t) = -dp/dz, rho dw/dt = G + mu (w'' + w'/r)
 with w(R) = 0.  Mode k >= 1 (time factor e^{i k w t}): W_k(r) = G_k / (i rho k w) (1 - J0(b r) / J0(b R)),
 b = i^{3/2} sqrt(k w / nu); mode 0 is Poiseuille flow, W_0 = G_0 (R^2 - r^2) / (4 mu).  The flow rate of
@@ -33,7 +36,8 @@ def pressure_gradient_modes(a, b, R, rho, mu, omega):
 
 
 def velocity_modes(r, G, R, rho, mu, omega):
-    """Complex modes W_k(r) [len(r), n_h + 1] of the axial velocity."""
+    """Complex modes W_k(r) [len(r), n_h + 1] of the axial velocity (the Bessel-function solution of the
+    module docstring)."""
     nu = mu / rho
     r = np.asarray(r, dtype=float)
     W = np.zeros((r.size, len(G)), dtype=complex)
