@@ -113,7 +113,8 @@ __global__ void assemble_mass_kernel(AsmArgs<T> a) {
     }
 }
 
-// W = shift v + rho H v on the velocity rows of every node, 0 on prescribed velocities and in the row
+// W = shift v + rho H v on the velocity rows of every node (the F block rho M (H v) of Eq. F_mat and the
+// pseudo-time mass of Sec. 2.3 enter the tangent as M W), 0 on prescribed velocities and in the row
 // padding.  A block stages NB nodes of v in shared memory with 16-byte loads (a node's 4N values are a
 // multiple of 16 bytes), one thread per (node, field) row forms its N outputs, and the block writes the
 // padded W rows back contiguously.  H is circulant, so for fixed N its first column H[d][0] is the whole
