@@ -1299,6 +1299,36 @@ hb_status learned_set_initial(hb_problem *p, const double *harmonics_host) {
     return hb_set_initial(p, harmonics_host);
 }
 
+// Host checks of a mesh that need no device: node indices in range, face tags >= 0, no tetrahedron of
+// (relative) zero volume.  Inverted orientation is allowed: the geometry uses |det J|.
+hb_status validate_mesh(const hb_mesh *m) {
+    const int64_t n = m->n_nodes;
+    for (int64_t k = 0; k < 4 * m->n_tets; ++k)
+        if (m->tets[k] < 0 || m->tets[k] >= n) return fail(HB_ERR_MESH, "tetrahedron node index out of range");
+    for (int64_t k = 0; k < 3 * m->n_faces; ++k)
+        if (m->faces[k] < 0 || m->faces[k] >= n) return fail(HB_ERR_MESH, "face node index out of range");
+    for (int64_t k = 0; k < m->n_faces; ++k)
+        if (m->face_tag[k] < 0) return fail(HB_ERR_MESH, "negative face tag");
+    double vsum = 0, vmin = 1e300;
+    for (int64_t e = 0; e < m->n_tets; ++e) {
+        const int32_t *t = m->tets + 4 * e;
+        const double *x0 = m->xyz + 3 * t[0], *x1 = m->xyz + 3 * t[1], *x2 = m->xyz + 3 * t[2],
+                     *x3 = m->xyz + 3 * t[3];
+        double u[3], v[3], w[3];
+        for (int i = 0; i < 3; ++i) {
+            u[i] = x1[i] - x0[i];
+            v[i] = x2[i] - x0[i];
+            w[i] = x3[i] - x0[i];
+        }
+        const double vol = std::fabs(u[0] * (v[1] * w[2] - v[2] * w[1]) - u[1] * (v[0] * w[2] - v[2] * w[0]) +
+                                     u[2] * (v[0] * w[1] - v[1] * w[0])) / 6.0;
+        vsum += vol;
+        vmin = std::min(vmin, vol);
+    }
+    if (!(vmin > 1e-14 * (vsum / double(m->n_tets)))) return fail(HB_ERR_MESH, "degenerate tetrahedron (zero volume)");
+    return HB_OK;
+}
+
 }  // namespace hb
 
 // =====================================================================================================
@@ -1319,6 +1349,7 @@ hb_status hb_create(const hb_mesh *mesh, double rho, double mu, double period_T,
         return fail(HB_ERR_INVALID_ARG, "mesh too large (n_nodes must be < 2^21)");
     if (!(rho > 0) || !(mu > 0) || !(period_T > 0)) return fail(HB_ERR_INVALID_ARG, "rho, mu and T must be > 0");
     if (n_h < 0 || 2 * n_h + 1 > kMaxN) return fail(HB_ERR_INVALID_ARG, "n_h must be in [0, 15]");
+    HB_TRY(validate_mesh(mesh));
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
         cudaGetLastError();

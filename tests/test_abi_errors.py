@@ -58,6 +58,42 @@ def test_create_rejects_bad_arguments(lib, case):
     assert len(lib.hb_last_error()) > 0
 
 
+MESH = 2
+
+
+@pytest.mark.parametrize("case", ["tet index", "negative tet index", "face index", "negative tag", "flat tet"])
+def test_create_rejects_bad_meshes_before_any_device_work(lib, case):
+    """Mesh checks run on the host before the device is touched, so they answer HB_ERR_MESH with or
+    without a GPU; an inverted (negatively oriented) tetrahedron is not an error."""
+    m, (xyz, tets, faces, tags) = _mesh()
+    xyz[:] = [[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]]
+    if case == "tet index":
+        tets[0, 2] = 4
+    elif case == "negative tet index":
+        tets[0, 0] = -1
+    elif case == "face index":
+        faces[1, 1] = 7
+    elif case == "negative tag":
+        tags[3] = -2
+    elif case == "flat tet":
+        xyz[3] = [0.3, 0.3, 0.0]                  # the fourth vertex in the plane of the first three
+    out = C.c_void_p()
+    st = lib.hb_create(C.byref(m), 1.0, 0.04, 1.0, 2, 0, None, C.byref(out))
+    assert st == MESH, (case, st, lib.hb_last_error())
+    assert not out.value
+
+
+def test_inverted_tetrahedron_passes_the_mesh_checks(lib):
+    m, (xyz, tets, faces, tags) = _mesh()
+    xyz[:] = [[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]]
+    tets[0] = [1, 0, 2, 3]                        # negative orientation
+    out = C.c_void_p()
+    st = lib.hb_create(C.byref(m), 1.0, 0.04, 1.0, 2, 0, None, C.byref(out))
+    assert st != MESH, lib.hb_last_error()        # HB_OK on a GPU machine, HB_ERR_CUDA without one
+    if out.value:
+        assert lib.hb_destroy(out) == 0
+
+
 def test_defaults_are_filled(lib):
     o = hbgls.hb_solve_opts()
     assert lib.hb_default_opts(C.byref(o)) == 0
