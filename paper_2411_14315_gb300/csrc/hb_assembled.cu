@@ -348,14 +348,8 @@ __global__ void __launch_bounds__(192) spectral_w_tc_kernel(const float *__restr
 template <int NT>
 void launch_spectral_tc(const float *v, const float *H, const uint8_t *flag, float *W, int64_t n_nodes, float rho,
                         float shift, const double *shift_dev, cudaStream_t s) {
-    static int grid_cap = 0;
-    if (grid_cap == 0) {
-        int dev = 0, sms = 0, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, spectral_w_tc_kernel<NT>, 192, 0);
-        grid_cap = std::max(1, sms * std::max(1, per_sm));
-    }
+    static LaunchCache cache;
+    const int grid_cap = device_sms() * cached_blocks_per_sm(cache, spectral_w_tc_kernel<NT>, 192, 0);
     const int64_t tiles = (n_nodes + SpecTc<NT>::NB - 1) / SpecTc<NT>::NB;
     const int grid = int(std::min<int64_t>(tiles, grid_cap));
     spectral_w_tc_kernel<NT><<<grid, 192, 0, s>>>(v, H, flag, W, n_nodes, rho, shift, shift_dev);

@@ -978,32 +978,13 @@ size_t elem_smem_bytes(int mode, int N, int nl_max, int ep_max, size_t tsize, in
     return make_layout(mode, N, nl_max, ep_max, tsize, slot_cap).total;
 }
 
-// Resident blocks of a kernel on the current device for a dynamic shared-memory size (at least 1).
-template <typename K>
-static int resident_blocks(K kern, int block, size_t smem) {
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, smem);
-    return std::max(1, sms * std::max(1, per_sm));
-}
-
 // grid: upper bound on the blocks (the patch count); the persistent kernel runs at most one wave
 template <typename T, int MODE, int NT, int VAR>
 static void launch_elem_v(const ElemArgs<T> &a, int grid, cudaStream_t s) {
     const size_t smem = elem_smem_bytes(MODE, a.N, a.pv.nl_max, a.pv.ep_max, sizeof(T));
-    static size_t configured = 0, occ_smem = 0;
-    static int occ_blocks = 0;
+    static LaunchCache cache;
     auto kern = elem_kernel<T, MODE, NT, VAR>;
-    if (smem > 48 * 1024 && smem > configured) {
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-        configured = smem;
-    }
-    if (occ_blocks == 0 || occ_smem != smem) {
-        occ_blocks = resident_blocks(kern, ElemCfg<T, VAR>::block, smem);
-        occ_smem = smem;
-    }
-    grid = std::min(grid, occ_blocks);
+    grid = std::min(grid, cached_blocks_per_sm(cache, kern, ElemCfg<T, VAR>::block, smem) * device_sms());
     if (grid > 0) kern<<<grid, ElemCfg<T, VAR>::block, smem, s>>>(a);
 }
 
@@ -1052,8 +1033,8 @@ void launch_elem(int mode, const ElemArgs<T> &a, int grid, cudaStream_t s) {
 template <typename T, int MODE, int VAR>
 static void launch_batch_var(const BatchGroup<T> &g, size_t smem, int grid, cudaStream_t s) {
     auto go = [&](auto kern) {
-        if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-        grid = std::min(grid, resident_blocks(kern, ElemCfg<T, VAR>::block, smem));
+        static LaunchCache cache;
+        grid = std::min(grid, cached_blocks_per_sm(cache, kern, ElemCfg<T, VAR>::block, smem) * device_sms());
         kern<<<grid, ElemCfg<T, VAR>::block, smem, s>>>(g.args, g.bslots, g.bslot_stride, g.item_begin, g.item_end,
                                                          g.counter);
     };

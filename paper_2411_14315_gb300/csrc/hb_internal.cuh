@@ -3,11 +3,64 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <utility>
 #include <vector>
 
 namespace hb {
+
+// SM count of the current device (cached per device; problems may live on several devices).
+inline int device_sms() {
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    int n = cache[dev].load(std::memory_order_relaxed);
+    if (n <= 0) {
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        n = std::max(1, n);
+        cache[dev].store(n, std::memory_order_relaxed);
+    }
+    return n;
+}
+
+// Launch setup of kernels, per kernel and device: the dynamic shared memory a kernel was opted into and
+// its resident blocks per SM for a given dynamic shared-memory size.  The kernels are shared by every
+// problem, on any device and host thread, so the cache is keyed by kernel and device and guarded.
+struct LaunchCache {
+    std::mutex m;
+    std::map<std::pair<const void *, int>, size_t> opted;              // (kernel, device) -> opted smem
+    std::map<std::tuple<const void *, int, size_t>, int> per_sm;       // (kernel, device, smem) -> blocks/SM
+};
+
+template <typename K>
+int cached_blocks_per_sm(LaunchCache &c, K kern, int block, size_t smem) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const void *kf = reinterpret_cast<const void *>(kern);
+    std::lock_guard<std::mutex> lock(c.m);
+    if (smem > 48 * 1024) {
+        size_t &o = c.opted[std::make_pair(kf, dev)];
+        if (smem > o) {
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+            o = smem;
+        }
+    }
+    const auto key = std::make_tuple(kf, dev, smem);
+    const auto it = c.per_sm.find(key);
+    if (it != c.per_sm.end()) return it->second;
+    int per = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, block, smem);
+    per = std::max(1, per);
+    c.per_sm[key] = per;
+    return per;
+}
 
 // Kernel variants of the fused element pass.
 enum Mode : int {
@@ -21,8 +74,8 @@ enum Mode : int {
 };
 
 constexpr int kGeomStride = 16;       // per element: grad N_a (4 x 3), V, C_I nu^2 G:G, 2 pad
-constexpr int kMaxN = 31;
-constexpr int kJvpVariants = 4;       // launch variants of the FP32 paper-tangent element pass             // largest number of time instances supported
+constexpr int kMaxN = 31;             // largest number of time instances supported
+constexpr int kJvpVariants = 4;       // launch variants of the FP32 paper-tangent element pass
 constexpr double kCI = 3.0;           // Eq. (tau)
 // 4-point degree-2 Gauss rule on a tetrahedron (barycentric coordinates of the points)
 constexpr double kQA = 0.5854101966249685;

@@ -16,16 +16,7 @@ constexpr int kMaxK = 256;           // largest number of simultaneous dot produ
 
 inline int nblk(int64_t n, int b) { return int((n + b - 1) / b); }
 
-int g_sm_count = 0;
-int sm_count() {
-    if (g_sm_count == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev);
-        if (g_sm_count <= 0) g_sm_count = 148;
-    }
-    return g_sm_count;
-}
+int sm_count() { return device_sms(); }
 
 template <typename A, typename B>
 __global__ void convert_kernel(const A *__restrict__ x, B *__restrict__ y, int64_t n) {
@@ -334,12 +325,8 @@ int stream_grid(int64_t n) {
 // partial second wave would double the time), at most one block per 2048 elements.
 template <int K>
 int multidot_blocks(int64_t n) {
-    static int per_sm = 0;
-    if (per_sm == 0) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, multidot_kernel<K>, kVB, 0);
-        if (per_sm <= 0) per_sm = 1;
-    }
-    const int cap = sm_count() * per_sm;
+    static LaunchCache cache;
+    const int cap = sm_count() * cached_blocks_per_sm(cache, multidot_kernel<K>, kVB, 0);
     const int need = nblk(n, kVB * 8);
     return need < cap ? (need > 0 ? need : 1) : cap;
 }
@@ -401,12 +388,8 @@ void launch_multidot(const double *V, int64_t ld, int k, const double *w, int64_
 
 void launch_multiaxpy_norm(const double *V, int64_t ld, int k, const double *h, double *w, int64_t n,
                            double *partials, double *result, cudaStream_t s, const int *gate) {
-    static int per_sm = 0;                      // one full wave (equal shares per block)
-    if (per_sm == 0) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, multiaxpy_norm_kernel, kVB, 0);
-        if (per_sm <= 0) per_sm = 1;
-    }
-    const int nb = std::min(stream_grid(n), sm_count() * per_sm);
+    static LaunchCache cache;                   // one full wave (equal shares per block)
+    const int nb = std::min(stream_grid(n), sm_count() * cached_blocks_per_sm(cache, multiaxpy_norm_kernel, kVB, 0));
     multiaxpy_norm_kernel<<<nb, kVB, 0, s>>>(V, ld, k, h, w, n, partials, gate);
     finish_kernel<<<1, 256, 0, s>>>(partials, nb, 1, 1, result, gate, 0);
 }
