@@ -1,5 +1,6 @@
-"""Closed-form pin of the oracle's outlet terms (Sec. 2.3 and reading R5): for a velocity that is uniform
-over an outlet, the traction term - int N_A h n_i with h = -P and the backflow stabilisation
+"""Closed-form pin of the oracle's outlet terms (Sec. 2.3 and readings R5, R8): for a velocity that is
+uniform over an outlet, the traction term - int N_A h n_i with h = -P (or -(P_d + R Q) at a resistance
+outlet, Q = sum over the outlet's faces of |f| u.n) and the backflow stabilisation
 - int N_A (rho/2) beta ((u.n - |u.n|)/2) u_i reduce to
 
     r_{A,i}(t_n) = sum over outlet faces f containing A of |f| / 3 (P(t_n) n_i + (rho/2) beta max(0, -u.n) u_i),
@@ -26,12 +27,17 @@ def _outlet_faces(spec):
     return m.faces[f], area, n
 
 
+@pytest.mark.parametrize("resistance", [0.0, 2.5])       # pressure outlet, or resistance outlet (R8)
 @pytest.mark.parametrize("ux", [-0.7, 0.7])               # inflow through the outlet (backflow) or outflow
-def test_outlet_traction_and_backflow_match_the_closed_form(ux):
+def test_outlet_traction_and_backflow_match_the_closed_form(ux, resistance):
     spec = P.channel_spec(n_h=1)
     pr = P.oracle_problem(spec)                            # inflow cap Dirichlet; the outlet is the only
     assert set(spec.face_tag[pr.neumann_faces()].tolist()) == {2}       # Neumann part of the boundary
     (tag, pa, pb), = spec.outlets_p
+    if resistance:
+        # h = -(P_d + R Q) with Q the outlet flow rate: for a uniform velocity Q = sum_f |f| (u . n_f)
+        pr.outlet_p.clear()
+        pr.set_outlet_resistance(tag, resistance, pa, pb)
     N = pr.N
     t = spec.T * np.arange(N) / N
     w = 2.0 * math.pi / spec.T
@@ -41,6 +47,8 @@ def test_outlet_traction_and_backflow_match_the_closed_form(ux):
     y[:, :3, :] = u[None, :, None]
     y[:, 3, :] = 1.7                                       # pressure does not enter the boundary terms
     faces, area, n = _outlet_faces(spec)
+    if resistance:
+        Pn = Pn + resistance * sum(area[f] * float(u @ n[f]) for f in range(len(faces)))
     expect = np.zeros((pr.n_nodes, 3, N))
     for f in range(len(faces)):
         back = 0.5 * spec.rho * spec.beta * max(0.0, -float(u @ n[f]))
