@@ -226,9 +226,10 @@ def run_reference(args, dist: Dist, spec, config):
 # GPU arm
 
 
-def traffic_from_profile():
+def traffic_from_profile(n_tets: int, n_nodes: int):
     """DRAM bytes per launch of the element kernel from the committed ncu summary, if it was taken on
-    the current kernel source (same SHA-256), else None."""
+    the current kernel source (same SHA-256) and on this workload (same tetrahedron and node counts),
+    else None."""
     try:
         text = open(PROFILE_SUMMARY).read()
         sha = hashlib.sha256(open(KERNEL_SOURCE, "rb").read()).hexdigest()
@@ -240,6 +241,8 @@ def traffic_from_profile():
             k, v = line.strip()[1:].split(":", 1)
             vals[k.strip()] = v.strip().strip("`")
     if vals.get("kernel_source_sha256") != sha:
+        return None
+    if vals.get("workload_tets") != str(n_tets) or vals.get("workload_nodes") != str(n_nodes):
         return None
     try:
         return float(vals["dram_bytes_per_launch_full_size"])
@@ -502,7 +505,7 @@ def run_ours(args, dist: Dist, spec, config):
             "kernel": "elem_kernel<float, MODE_JVP>", "kernel_ms": elem_avg_ms,
             "flops_per_unit": FLOPS_PER_UNIT_JVP, "units_per_launch": units,
             "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (derived, not measured)"}
-    tr = traffic_from_profile()
+    tr = traffic_from_profile(spec.mesh.n_tets, spec.mesh.n_nodes)
     if tr is not None:
         roof["traffic"] = tr
     peaks = {}

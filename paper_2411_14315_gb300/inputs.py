@@ -263,11 +263,73 @@ def pipe_by_size(n_tets_target: int, seed: int, R: float = 1.0) -> Mesh:
 # voxel meshes from a signed inside-test
 
 
-def voxel_mesh(inside, lo, hi, h: float, cap_planes, inlet_tags, outlet_tags, name: str) -> Mesh:
+def _block_tables():
+    """For the 256 occupancy patterns of a 2 x 2 x 2 block of cells (bit i + 2 j + 4 k for cell (i, j, k)):
+    whether the block is non-manifold at its centre vertex (its inside cells, or its outside cells, form
+    more than one face-connected group), and which empty cell to fill to repair it (the first one whose
+    filling leaves fewer groups)."""
+    cells = [(i, j, k) for k in range(2) for j in range(2) for i in range(2)]
+    nbr = [[b for b in range(8) if sum(abs(x - y) for x, y in zip(cells[a], cells[b])) == 1] for a in range(8)]
+
+    def groups(code, want):
+        seen, count = set(), 0
+        for a in range(8):
+            if ((code >> a) & 1) != want or a in seen:
+                continue
+            count += 1
+            stack = [a]
+            seen.add(a)
+            while stack:
+                c = stack.pop()
+                for b in nbr[c]:
+                    if ((code >> b) & 1) == want and b not in seen:
+                        seen.add(b)
+                        stack.append(b)
+        return count
+
+    bad = np.zeros(256, dtype=bool)
+    fill = np.full(256, -1, dtype=np.int64)
+    for code in range(256):
+        g_in, g_out = groups(code, 1), groups(code, 0)
+        if g_in <= 1 and g_out <= 1:
+            continue
+        bad[code] = True
+        for a in range(8):
+            if not (code >> a) & 1:
+                new = code | (1 << a)
+                if groups(new, 1) + groups(new, 0) < g_in + g_out:
+                    fill[code] = a
+                    break
+        if fill[code] < 0:
+            fill[code] = next(a for a in range(8) if not (code >> a) & 1)
+    return bad, fill, cells
+
+
+def _manifold_cells(occ: np.ndarray) -> np.ndarray:
+    """Add cells to a boolean cell grid until the boundary of the union is a 2-manifold: no two inside
+    cells, and no two outside cells, meet only along an edge or at a vertex of a 2 x 2 x 2 block."""
+    bad, fill, cells = _block_tables()
+    P = np.pad(occ, 1)
+    while True:
+        code = np.zeros(tuple(d - 1 for d in P.shape), dtype=np.int64)
+        for b, (i, j, k) in enumerate(cells):
+            code |= P[i:P.shape[0] - 1 + i, j:P.shape[1] - 1 + j, k:P.shape[2] - 1 + k].astype(np.int64) << b
+        w = np.nonzero(bad[code])
+        if len(w[0]) == 0:
+            return P[1:-1, 1:-1, 1:-1]
+        f = fill[code[w]]
+        off = np.array(cells)[f]
+        P[w[0] + off[:, 0], w[1] + off[:, 1], w[2] + off[:, 2]] = True
+
+
+def voxel_mesh(inside, lo, hi, h: float, cap_planes, inlet_tags, outlet_tags, name: str,
+               manifold: bool = False) -> Mesh:
     """Cells of a lattice of spacing ~h over the box [lo, hi] whose centre satisfies inside(points).
 
     cap_planes: list of (tag, axis, side) -- boundary faces lying on the box face `axis`=lo/hi
-    (side 0/1) get that tag; all other boundary faces are walls (tag 0)."""
+    (side 0/1) get that tag; all other boundary faces are walls (tag 0).  manifold: add the cells that
+    make the boundary a 2-manifold (cells that would touch the rest only along an edge or at a vertex
+    get a face-sharing neighbour)."""
     lo = np.asarray(lo, dtype=np.float64)
     hi = np.asarray(hi, dtype=np.float64)
     n = np.maximum(1, np.round((hi - lo) / h).astype(np.int64))
@@ -275,12 +337,18 @@ def voxel_mesh(inside, lo, hi, h: float, cap_planes, inlet_tags, outlet_tags, na
     ci = [lo[d] + hh[d] * (np.arange(n[d]) + 0.5) for d in range(3)]
     keep = []
     for k in range(n[2]):              # slab by slab to bound memory
-        X, Y = np.meshgrid(ci[0], ci[1], indexing="ij")
+        # x fastest: cell (x, y, z) has index x + n0 (y + n1 z), the order decoded below
+        X, Y = np.meshgrid(ci[0], ci[1], indexing="xy")
         pts = np.stack([X.ravel(), Y.ravel(), np.full(X.size, ci[2][k])], 1)
         m = inside(pts)
         ii = np.nonzero(m)[0]
         keep.append(ii + k * n[0] * n[1])
     cells = np.concatenate(keep)
+    if manifold:
+        occ = np.zeros(int(n[0] * n[1] * n[2]), dtype=bool)
+        occ[cells] = True
+        occ = _manifold_cells(occ.reshape(int(n[2]), int(n[1]), int(n[0])).transpose(2, 1, 0))
+        cells = np.nonzero(occ.transpose(2, 1, 0).ravel())[0]
     ci_x = cells % n[0]
     ci_y = (cells // n[0]) % n[1]
     ci_z = cells // (n[0] * n[1])

@@ -174,7 +174,7 @@ def _sampled_oracle(spec, y, v, nodes, fn):
 
 
 def test_full_size_cerebral_sampled_parity():
-    """Cerebral-like vessel at full size (~2.2M tets, ~727k nodes, N = 21): residual and the paper's
+    """Cerebral-like vessel at full size (~2.2M tets, ~405k nodes, N = 21): residual and the paper's
     tangent at 48 sampled interior nodes against the oracle."""
     from paper_2411_14315_gb300 import workloads as W
     spec = W.cerebral_spec()
