@@ -35,7 +35,15 @@ import numpy as np  # noqa: E402
 METRIC = "HB Jv element-instances/s"
 UNIT = "element-instances/s"
 FLOPS_PER_UNIT_JVP = 800.0        # algorithmic FP32 flops per element-instance, paper-tangent Jv
-BYTES_PER_UNIT_JVP = 11.0         # algorithmic HBM bytes per element-instance at N = 21
+
+
+def jvp_algorithmic_bytes(n_nodes: int, n_tets: int, N: int) -> float:
+    """Algorithmic HBM bytes of one paper-tangent element pass in FP32: per node the state's velocity
+    (3N values), the direction (4N), the rows of W = shift v + rho H v (3N) and the output (4N); per
+    tetrahedron its geometry (16 values) and connectivity (4 ints)."""
+    return 4.0 * 14 * N * n_nodes + 80.0 * n_tets
+
+
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12   # 80.5
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "elem_jvp_fp32_glenn_like.md")
@@ -514,8 +522,9 @@ def run_ours(args, dist: Dist, spec, config):
     except OSError:
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    hbm = {"algorithmic_bytes_per_unit": BYTES_PER_UNIT_JVP,
-           "achieved_gbs": BYTES_PER_UNIT_JVP * units / (elem_avg_ms / 1e3) / 1e9,
+    alg_bytes = jvp_algorithmic_bytes(spec.mesh.n_nodes, spec.mesh.n_tets, spec.N)
+    hbm = {"algorithmic_bytes_per_launch": alg_bytes, "algorithmic_bytes_per_unit": alg_bytes / units,
+           "achieved_gbs": alg_bytes / (elem_avg_ms / 1e3) / 1e9,
            "peak_gbs": hbm_peak, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
     hbm["frac"] = hbm["achieved_gbs"] / hbm_peak
 
