@@ -59,3 +59,41 @@ def test_outlet_traction_and_backflow_match_the_closed_form(ux, resistance):
     assert np.abs(got - expect).max() <= 1e-13 * np.abs(expect).max()
     if ux > 0:
         assert all(float(u @ n[f]) > 0 for f in range(len(faces)))   # outflow: no backflow term at all
+
+
+@pytest.mark.parametrize("exact", [False, True])
+@pytest.mark.parametrize("resistance", [0.0, 2.5])
+@pytest.mark.parametrize("ux", [-0.7, 0.7])
+def test_outlet_tangent_matches_the_closed_form(ux, resistance, exact):
+    """The derivative of the outlet terms along a direction v, for u and v uniform over the outlet:
+    the paper's tangent freezes the backflow coefficient (reading R7), -(rho/2) beta (u.n)_- v_i; the
+    exact derivative adds -(rho/2) beta (v.n) u_i where u.n < 0; a resistance outlet contributes
+    R Q(v) n_i with Q(v) = sum_f |f| v.n_f (R8), in both."""
+    spec = P.channel_spec(n_h=1)
+    pr = P.oracle_problem(spec)
+    (tag, pa, pb), = spec.outlets_p
+    if resistance:
+        pr.outlet_p.clear()
+        pr.set_outlet_resistance(tag, resistance, pa, pb)
+    N = pr.N
+    u = np.array([ux, 0.4, 0.25])
+    vv = np.array([0.3, -0.2, 0.5])
+    y = np.zeros((pr.n_nodes, 4, N))
+    y[:, :3, :] = u[None, :, None]
+    v = np.zeros((pr.n_nodes, 4, N))
+    v[:, :3, :] = vv[None, :, None]
+    faces, area, n = _outlet_faces(spec)
+    Qv = sum(area[f] * float(vv @ n[f]) for f in range(len(faces)))
+    expect = np.zeros((pr.n_nodes, 3, N))
+    k = 0.5 * spec.rho * spec.beta
+    for f in range(len(faces)):
+        un = float(u @ n[f])
+        back = k * max(0.0, -un) * vv
+        if exact and un < 0:
+            back = back - k * float(vv @ n[f]) * u
+        contrib = area[f] / 3.0 * (resistance * Qv * n[f] + back)
+        for a in faces[f]:
+            expect[a] += contrib[:, None]
+    got = O.boundary_jv(pr, y, v, exact)
+    scale = max(np.abs(expect).max(), 1e-300)
+    assert np.abs(got - expect).max() <= 1e-13 * scale
