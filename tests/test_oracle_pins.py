@@ -488,3 +488,25 @@ def test_stokes_modes_solve_hb_equations():
     r = O.residual(pr, y)
     scale = np.abs(O.residual(pr, np.zeros_like(y))).max()
     assert np.abs(r).max() < 1e-11 * scale
+
+
+def test_pseudo_step_rule_on_a_regular_tetrahedron():
+    """Sec. 2.3's CFL rule dt = h_c / u_c: on one regular tetrahedron of edge 2 sqrt(2) the edge of the
+    regular tetrahedron of mean volume is that edge, and a uniform inflow U q(t) normal to the inlet face
+    has the largest mean inlet speed U max_n |q(t_n)|."""
+    xyz = np.array([[1.0, 1, 1], [1, -1, -1], [-1, 1, -1], [-1, -1, 1]])
+    tets = np.array([[0, 1, 2, 3]])
+    faces = np.array([[1, 2, 3], [0, 2, 3], [0, 1, 3], [0, 1, 2]])
+    tags = np.array([1, 2, 2, 2])                  # inlet opposite vertex 0; the rest traction-free
+    T, n_h, U = 0.8, 2, 1.7
+    pr = O.HBProblem(xyz, tets, faces, tags, 1.0, 0.1, T, n_h)
+    inward = xyz[0] - xyz[1:].mean(0)              # from the inlet face towards vertex 0
+    inward /= np.linalg.norm(inward)
+    profile = np.zeros((4, 3))
+    profile[1:] = U * inward
+    a, b = np.array([1.0, 0.6, -0.3]), np.array([0.0, 0.4, 0.2])
+    pr.set_inflow(1, profile, a, b)
+    t = T * np.arange(pr.N) / pr.N
+    w = 2 * math.pi / T
+    q = a[0] + sum(a[k] * np.cos(k * w * t) + b[k] * np.sin(k * w * t) for k in (1, 2))
+    assert abs(O.pseudo_dt(pr) - 2 * math.sqrt(2) / (U * np.abs(q).max())) < 1e-12
