@@ -156,3 +156,14 @@ def test_generalized_alpha_march_is_second_order():
         assert np.max(np.abs(y[:, 0] - ye[:, 0])) < 1e-12
         errs.append(np.max(np.abs(y[:, 3] - ye[:, 3])))
     assert errs[1] < errs[0] / 3.5
+
+
+def test_omega_hat_is_the_velocity_norm_ratio():
+    """Reading R14: omega_hat^2 = ||du/dt||^2 / ||u||^2 over the nodal velocity vectors only; for
+    du/dt = c u on the velocity it is c^2 whatever the pressures."""
+    rng = np.random.default_rng(5)
+    y = rng.uniform(-1, 1, (40, 4))
+    yd = np.empty_like(y)
+    yd[:, :3] = -2.5 * y[:, :3]
+    yd[:, 3] = rng.uniform(-50, 50, 40)
+    assert abs(TM.omega_hat2(y, yd) - 6.25) < 1e-12
