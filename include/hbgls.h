@@ -66,7 +66,9 @@ typedef struct {
  * stream) orders all later device work of this problem.  Errors: INVALID_ARG, MESH, CUDA, OOM. */
 hb_status hb_create(const hb_mesh *mesh, double rho, double mu, double period_T, int n_h, int device,
                     void *cuda_stream, hb_problem **out);
+/* Free a problem and all its device memory; NULL is accepted (HB_OK). */
 hb_status hb_destroy(hb_problem *p);
+/* Message of this thread's last error (thread-local; empty after success is not guaranteed). */
 const char *hb_last_error(void);
 
 /* Dirichlet inflow on cap `tag` (Eq. NS-time, u = g on Gamma_g): g(x, t) = profile(x) q(t) with
@@ -136,6 +138,9 @@ typedef struct {
     int status;               /* hb_status of the solve */
 } hb_report;
 
+/* Fill the defaults of every field (the paper's settings of Sec. 2.3 where it states them: GMRES
+ * tolerance 0.03 in the pseudo-time phase, switch to Newton at ||r|| / ||r0|| < 1e-3).  INVALID_ARG for
+ * NULL. */
 hb_status hb_default_opts(hb_solve_opts *o);
 /* Solve for the periodic state (Eq. NR with the split tangent of Eq. splitK and pseudo time stepping).
  * The state of the problem is updated in place; NOT_CONVERGED / NAN keep the best finite state. */
@@ -215,8 +220,12 @@ typedef struct {
     double p_scale;           /* pressure normalisation: (p - mean outlet level) / (p_scale rho U^2); <= 0
                                  means 1 */
 } hb_mpnn_config;
+/* Create a network with seeded parameters on `device`; INVALID_ARG for a config out of range (hidden
+ * in [32, 64], layers in [1, 8], n_h in [0, 11]). */
 hb_status hb_mpnn_create(const hb_mpnn_config *cfg, int device, hb_mpnn **out);
+/* Free a network; NULL is accepted. */
 hb_status hb_mpnn_destroy(hb_mpnn *net);
+/* Number of FP32 parameters (the length of get/set and gradient arrays); 0 for NULL. */
 int64_t hb_mpnn_num_params(const hb_mpnn *net);
 hb_status hb_mpnn_get_params(hb_mpnn *net, float *params);          /* host [num_params] */
 hb_status hb_mpnn_set_params(hb_mpnn *net, const float *params);    /* also resets the optimiser */
@@ -270,6 +279,8 @@ typedef struct {
     int status;
 } hb_march_report;
 
+/* Fill the defaults: the paper's settings for its conventional solver (Sec. 3: GMRES 0.03, Newton 1e-3
+ * per step), rho_inf = 0.5 (reading R13), 4 periods; INVALID_ARG for NULL. */
 hb_status hb_default_march_opts(hb_march_opts *o);
 /* HB_ERR_INVALID_ARG for bad options (steps_per_period not a multiple of N), HB_ERR_STATE without an
  * inflow, HB_ERR_NAN if the march produced non-finite values. */
@@ -296,12 +307,16 @@ hb_status hb_get_march_samples(hb_problem *p, double *out);
  * operands, kind or shift change.  Work is ordered after `stream` (NULL: the first problem's stream) and
  * `stream` waits for it. */
 typedef struct hb_batch hb_batch;
+/* Create a batch over `count` problems (not owned; they must outlive the batch) at precision 0 or 1. */
 hb_status hb_batch_create(hb_problem *const *problems, int count, int precision, hb_batch **out);
+/* Free a batch (not its problems); NULL is accepted. */
 hb_status hb_batch_destroy(hb_batch *b);
 /* y[q], v[q], jv[q]: device arrays of problem q (double for precision 0, float for 1), instance
  * layout; same semantics as hb_jv_dev for each problem. */
 hb_status hb_batch_jv_dev(hb_batch *b, const void *const *y, const void *const *v, void *const *jv, int kind,
                           double shift, void *stream);
+/* Kernel launches queued by the batch since creation: its graph's launches times its replays (0 for
+ * NULL). */
 int64_t hb_batch_launch_count(const hb_batch *b);
 /* Patch-size autotuning: rebuild the problem's element patches (precision 0 or 1) with each candidate
  * node cap (and, for precision 1, each launch variant, see hb_set_launch_variant), time `reps`
@@ -320,6 +335,8 @@ typedef struct {
     double p_ref;             /* mean outlet pressure level over outlets and instances              */
     int64_t assembled_pairs;  /* node pairs of the assembled tangent (0 before hb_assemble_dev)     */
 } hb_info;
+/* Sizes and derived quantities of a problem; also prepares pending boundary data (see
+ * hb_jv_dev_noalloc). */
 hb_status hb_get_info(hb_problem *p, hb_info *info);
 /* Number of kernel launches queued by this problem since creation (all entry points). */
 int64_t hb_launch_count(const hb_problem *p);
