@@ -68,7 +68,7 @@ hb_status hb_create(const hb_mesh *mesh, double rho, double mu, double period_T,
                     void *cuda_stream, hb_problem **out);
 /* Free a problem and all its device memory; NULL is accepted (HB_OK). */
 hb_status hb_destroy(hb_problem *p);
-/* Message of this thread's last error (thread-local; empty after success is not guaranteed). */
+/* Message of the last failed call on this thread (thread-local; later successful calls keep it). */
 const char *hb_last_error(void);
 
 /* Dirichlet inflow on cap `tag` (Eq. NS-time, u = g on Gamma_g): g(x, t) = profile(x) q(t) with
