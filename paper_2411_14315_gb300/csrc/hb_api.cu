@@ -1299,10 +1299,12 @@ hb_status learned_set_initial(hb_problem *p, const double *harmonics_host) {
     return hb_set_initial(p, harmonics_host);
 }
 
-// Host checks of a mesh that need no device: node indices in range, face tags >= 0, no tetrahedron of
-// (relative) zero volume.  Inverted orientation is allowed: the geometry uses |det J|.
+// Host checks of a mesh that need no device: finite coordinates, node indices in range, face tags >= 0,
+// no tetrahedron of (relative) zero volume.  Inverted orientation is allowed: the geometry uses |det J|.
 hb_status validate_mesh(const hb_mesh *m) {
     const int64_t n = m->n_nodes;
+    for (int64_t k = 0; k < 3 * n; ++k)
+        if (!std::isfinite(m->xyz[k])) return fail(HB_ERR_MESH, "non-finite node coordinate");
     for (int64_t k = 0; k < 4 * m->n_tets; ++k)
         if (m->tets[k] < 0 || m->tets[k] >= n) return fail(HB_ERR_MESH, "tetrahedron node index out of range");
     for (int64_t k = 0; k < 3 * m->n_faces; ++k)

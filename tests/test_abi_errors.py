@@ -61,7 +61,8 @@ def test_create_rejects_bad_arguments(lib, case):
 MESH = 2
 
 
-@pytest.mark.parametrize("case", ["tet index", "negative tet index", "face index", "negative tag", "flat tet"])
+@pytest.mark.parametrize("case", ["tet index", "negative tet index", "face index", "negative tag", "flat tet",
+                                  "nan coordinate", "infinite coordinate"])
 def test_create_rejects_bad_meshes_before_any_device_work(lib, case):
     """Mesh checks run on the host before the device is touched, so they answer HB_ERR_MESH with or
     without a GPU; an inverted (negatively oriented) tetrahedron is not an error."""
@@ -77,6 +78,10 @@ def test_create_rejects_bad_meshes_before_any_device_work(lib, case):
         tags[3] = -2
     elif case == "flat tet":
         xyz[3] = [0.3, 0.3, 0.0]                  # the fourth vertex in the plane of the first three
+    elif case == "nan coordinate":
+        xyz[2, 1] = float("nan")
+    elif case == "infinite coordinate":
+        xyz[1, 0] = float("inf")
     out = C.c_void_p()
     st = lib.hb_create(C.byref(m), 1.0, 0.04, 1.0, 2, 0, None, C.byref(out))
     assert st == MESH, (case, st, lib.hb_last_error())
