@@ -44,8 +44,13 @@ def jvp_algorithmic_bytes(n_nodes: int, n_tets: int, N: int) -> float:
     return 4.0 * 14 * N * n_nodes + 80.0 * n_tets
 
 
-SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
-FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12   # 80.5
+FP32_LANES = 128                  # FP32 lanes per SM (Blackwell)
+
+
+def fp32_peak_tflops(sm_count: int, sm_max_mhz: float) -> float:
+    """FP32 FMA peak derived from the device's SM count, the lanes per SM and the maximum SM clock
+    (an FMA is 2 flops)."""
+    return sm_count * FP32_LANES * 2 * sm_max_mhz * 1e6 / 1e12
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "elem_jvp_fp32_glenn_like.md")
 KERNEL_SOURCE = os.path.join(ROOT, "paper_2411_14315_gb300", "csrc", "hb_element.cu")
 
@@ -508,11 +513,15 @@ def run_ours(args, dist: Dist, spec, config):
     prob_jv_ms_cache["mf"] = ms
     elem_avg_ms = elem_ms / max(1, elem_n)
     achieved = FLOPS_PER_UNIT_JVP * units / (elem_avg_ms / 1e3) / 1e12
-    roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+    sm_count = int(torch.cuda.get_device_properties(dev).multi_processor_count)
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+    peak = fp32_peak_tflops(sm_count, sm_max)
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None,
             "kernel": "elem_kernel<float, MODE_JVP>", "kernel_ms": elem_avg_ms,
-            "flops_per_unit": FLOPS_PER_UNIT_JVP, "units_per_launch": units,
-            "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (derived, not measured)"}
+            "flops_per_unit": FLOPS_PER_UNIT_JVP, "units_per_launch": units, "sm_count": sm_count,
+            "peak_source": f"{sm_count} SMs (read from the device) x {FP32_LANES} FP32 lanes x 2 flop x "
+                           f"{sm_max:.0f} MHz (maximum SM clock, sampled) (derived, not measured)"}
     tr = traffic_from_profile(spec.mesh.n_tets, spec.mesh.n_nodes)
     if tr is not None:
         roof["traffic"] = tr

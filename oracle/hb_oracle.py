@@ -11,24 +11,26 @@ Everything follows the paper's Sec. 2 (arXiv 2411.14315):
   * Eqs. (splitK), (ptangent), (K_mat), (ctangent), (F_mat): the paper's tangent L~ = C + P;
   * Sec. 2.3 pseudo time stepping (c1 = 1.5), CFL rule, backflow stabilisation, Jacobi + GMRES.
 
-Readings of points the paper leaves open (each is also listed in the design notes):
-  R1  H is the real Fourier spectral differentiation matrix on t_n = n T / N (odd N):
+Readings of points the paper leaves open, each with the passage it interprets (the labels R1-R9 are
+the same in the library's headers and tests):
+  R1  (Eq. NS-harm, Eqs. upghdft/upghharm) H is the real Fourier spectral differentiation matrix on
+      t_n = n T / N (odd N):
       H[j,k] = (w/2) (-1)^(j-k) / sin(pi (j-k) / N), H[j,j] = 0.  This is what E^-1 Omega E means once
       Omega's mode index is taken as the signed frequency of each DFT row.
-  R2  Volume integrals use the 4-point degree-2 Gauss rule; tau is evaluated per quadrature point.
-  R3  xi (Eq. tau) is the metric of the map to the parent tetrahedron (0,0,0),(1,0,0),(0,1,0),(0,0,1)
+  R2  (Eq. Rmc; the paper names no rule) Volume integrals use the 4-point degree-2 Gauss rule; tau is evaluated per quadrature point.
+  R3  (Eq. tau) xi is the metric of the map to the parent tetrahedron (0,0,0),(1,0,0),(0,1,0),(0,0,1)
       with local node 0 at the origin: G = J^-T J^-1, so tau depends on the local vertex order.
-  R4  The "-H N_A" least-squares term and the Galerkin rho N_A H u term are applied as one H product
+  R4  (Eq. Rmc) The "-H N_A" least-squares term and the Galerkin rho N_A H u term are applied as one H product
       after spatial assembly: r^m = Q^m + H T, T_A = rho M u - sum_e int N_A tau L (exact algebra).
-  R5  Outlet pressure P gives h = -P; backflow term kept literally as printed, (rho/2) beta |u.n|_-
+  R5  (Sec. 2.1 traction condition; Sec. 2.3 backflow) Outlet pressure P gives h = -P; backflow term kept literally as printed, (rho/2) beta |u.n|_-
       with |x|_- = (x - |x|)/2, integrated with the 3-point edge-midpoint face rule.
-  R6  Pseudo time stepping is pseudo-transient continuation: each pseudo step solves
+  R6  (Sec. 2.3, Eq. NR) Pseudo time stepping is pseudo-transient continuation: each pseudo step solves
       (L~ + c1 rho / dt M_vel) d = -r(y), r the steady HB residual, so the root is unchanged.
-  R7  The paper's tangent freezes U and tau at y and keeps only the Galerkin H term (Eq. F_mat); the
+  R7  (Eqs. splitK, ptangent, K_mat, ctangent, F_mat) The paper's tangent freezes U and tau at y and keeps only the Galerkin H term (Eq. F_mat); the
       backflow term enters it with its coefficient frozen.  The exact Jacobian is the full derivative.
-  R8  Resistance outlets (h = -(P_d + R Q), Q the instantaneous outlet flux) are an extension; the
+  R8  (Sec. 3, Sec. 4 future work) Resistance outlets (h = -(P_d + R Q), Q the instantaneous outlet flux) are an extension; the
       paper leaves them out of scope (Sec. 3).
-  R9  The Jacobi preconditioner is diag(P) + c1 rho/dt M_AA over the volume terms (Sec. 2.3); C has a
+  R9  (Sec. 2.3) The Jacobi preconditioner is diag(P) + c1 rho/dt M_AA over the volume terms (Sec. 2.3); C has a
       zero diagonal because H does.
 
 Array layouts: instance vectors are [n_nodes, 4, N] (u1, u2, u3, p; N instances contiguous).

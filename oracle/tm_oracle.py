@@ -14,7 +14,7 @@ rho_inf = 0 giving c1 = 1.5).  One time level's residual, with u, p and du/dt gi
     r^c_A   = int N_A div u + (1 / rho) grad N_A . tau_hat L
     L_i     = rho du_i/dt + rho u . grad u_i + dp/dx_i
 i.e. Eq. (NS-weak) with H u replaced by du/dt and without the least-squares H term (test functions do
-not depend on time).  Readings (also in the design notes):
+not depend on time).  Readings of what the paper leaves open (Sec. 3, Eq. tauhat, Sec. 2.3):
   R13 Generalized-alpha for first-order systems (Jansen, Whiting & Hulbert 2000): alpha_m =
       (3 - rho_inf) / (2 (1 + rho_inf)), alpha_f = 1 / (1 + rho_inf), gamma = 1/2 + alpha_m - alpha_f;
       the residual is taken at (u, p)_{n+alpha_f} and du/dt_{n+alpha_m} (the pressure at the same
