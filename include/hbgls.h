@@ -41,7 +41,8 @@ typedef enum {
     HB_ERR_OOM = 4,           /* device allocation failed */
     HB_ERR_NOT_CONVERGED = 5, /* solve stopped at its iteration limit; best state kept */
     HB_ERR_NAN = 6,           /* residual became NaN/Inf; last finite state kept */
-    HB_ERR_TIMEOUT = 7,       /* reserved: a bounded device wait gave up */
+    HB_ERR_TIMEOUT = 7,       /* a bounded device wait of the pipelined element pass gave up (reported by
+                                 the next call that synchronises: a host-buffer entry point or hb_solve) */
     HB_ERR_STATE = 8          /* call out of order (e.g. solve before any inflow is set) */
 } hb_status;
 
@@ -89,6 +90,17 @@ hb_status hb_set_outlet_pressure(hb_problem *p, int tag, const double *a, const 
 hb_status hb_set_outlet_resistance(hb_problem *p, int tag, double R, const double *a, const double *b);
 /* Backflow stabilisation coefficient beta in [0, 1] on every Neumann face (Sec. 2.3; default 0.2). */
 hb_status hb_set_backflow(hb_problem *p, double beta);
+
+/* Stabilisation variants of Sec. 2.2 (the remarks after Eq. tau).  variant 0: the GLS form of Eq. (NS-weak)
+ * as printed (default); variant 1: full RBVMS -- the subscale velocity u' = -tau L / rho is also added to
+ * the advecting velocity of the Galerkin convective term, which adds the cross stress
+ * int N_A rho u' . grad u_i and the Reynolds stress -int rho (u' . grad N_A) u'_i to the momentum rows of
+ * the residual and of the exact Jacobian (the paper's tangent keeps its GLS blocks).  ct_dt >= 0 adds
+ * ct_dt (1 / dt)^2 under the root of Eq. (tau) with the equivalent step dt = 2 pi / (N w) = T / N (0: Eq.
+ * tau as printed; 1: the remark's (1/dt)^2).  Applies to every later evaluation and solve of the problem
+ * (not to hb_march, which uses tau_hat of Eq. tauhat).  Synchronises the problem's stream; drops the last
+ * assembly of hb_assemble_dev.  Errors: INVALID_ARG for another variant or a negative / non-finite ct_dt. */
+hb_status hb_set_stabilization(hb_problem *p, int variant, double ct_dt);
 
 /* Initial state from harmonics ([n_nodes][4][2 n_h + 1]) or NULL for the default: Dirichlet values
  * built in (Sec. 2.3), zero interior velocity, pressure at the mean outlet level.  Dirichlet values
@@ -344,7 +356,12 @@ int64_t hb_launch_count(const hb_problem *p);
  * 0 = 256 threads per block, two instances per thread on paired FP32 instructions; 1 = 384 threads,
  * one instance per thread (the default); 2 = 512 threads, one instance per thread; 3 = 192 threads, one
  * instance per thread, four resident blocks per SM (pays with patches small enough for four blocks'
- * shared memory, see hb_tune_patches).  All give the same operator up to FP32 rounding.  hb_tune_patches also searches it for precision 1.  HB_ERR_INVALID_ARG
+ * shared memory, see hb_tune_patches); 4 = pipelined: one block per SM with a producer warp that copies
+ * the next patch's rows with bulk asynchronous copies into a second shared-memory stage while 20
+ * consumer warps compute (one instance per thread); 5 = the same with 15 consumer warps on instance pairs
+ * and paired FP32 instructions.  Variants 4 and 5 need N = 9, 13 or 21 and the node-level W pass of
+ * hb_jv_dev (elsewhere, e.g. in hb_jv_dev_noalloc and batches, they run variant 1).  All give the same
+ * operator up to FP32 rounding.  hb_tune_patches also searches it for precision 1.  HB_ERR_INVALID_ARG
  * for another value.  hb_get_launch_variant returns the current variant (-1 for a null problem). */
 hb_status hb_set_launch_variant(hb_problem *p, int variant);
 int hb_get_launch_variant(const hb_problem *p);

@@ -11,7 +11,7 @@ Everything follows the paper's Sec. 2 (arXiv 2411.14315):
   * Eqs. (splitK), (ptangent), (K_mat), (ctangent), (F_mat): the paper's tangent L~ = C + P;
   * Sec. 2.3 pseudo time stepping (c1 = 1.5), CFL rule, backflow stabilisation, Jacobi + GMRES.
 
-Readings of points the paper leaves open, each with the passage it interprets (the labels R1-R9 are
+Readings of points the paper leaves open, each with the passage it interprets (the labels R1-R9, R17 and R18 are
 the same in the library's headers and tests):
   R1  (Eq. NS-harm, Eqs. upghdft/upghharm) H is the real Fourier spectral differentiation matrix on
       t_n = n T / N (odd N):
@@ -32,6 +32,13 @@ the same in the library's headers and tests):
       paper leaves them out of scope (Sec. 3).
   R9  (Sec. 2.3) The Jacobi preconditioner is diag(P) + c1 rho/dt M_AA over the volume terms (Sec. 2.3); C has a
       zero diagonal because H does.
+  R17 (Sec. 2.2, remark 2 after Eq. tau) "Full RBVMS": the subscale velocity u' = -tau L / rho, which the
+      least-squares terms already place in the time coupling and the advected velocity, is also added to
+      the advecting velocity: cross stress int N_a rho u' . grad u_i and Reynolds stress
+      - int rho (u' . grad N_a) u'_i; no other term.  The paper's tangent keeps the GLS blocks; the exact
+      Jacobian includes the added terms.
+  R18 (Sec. 2.2, remark 4 after Eq. tau) The time-discretisation term of tau is ct_dt (1 / dt)^2 under the
+      root with the equivalent step dt = 2 pi / (N w) = T / N; ct_dt = 1 takes the remark's (1/dt)^2.
 
 Array layouts: instance vectors are [n_nodes, 4, N] (u1, u2, u3, p; N instances contiguous).
 """
@@ -164,6 +171,12 @@ class HBProblem:
         self.H = spectral_H(self.N, self.omega)
         self.beta_bf = float(beta_bf)
         self.convection = convection      # False only for the Stokes-mode check of the tests
+        # stabilisation variants of Sec. 2.2 (remarks after Eq. tau), readings R17 and R18:
+        #   stab = "gls": Eq. (NS-weak) as printed; "rbvms": the subscale velocity u' = -tau L / rho is added
+        #   to every velocity of the Galerkin convective term (cross- and Reynolds-stress terms);
+        #   ct_dt > 0: ct_dt (1 / dt)^2 under the root of Eq. (tau), dt = 2 pi / (N w) = T / N
+        self.stab = "gls"
+        self.ct_dt = 0.0
         self.n_nodes = self.xyz.shape[0]
         self.geo = Geometry(self.xyz, self.tets)
         self.inflow = {}
@@ -261,6 +274,13 @@ class HBProblem:
 # element terms of the residual (Eq. Rmc with readings R2-R4)
 
 
+def tau_dt_term(prob: HBProblem) -> float:
+    """ct_dt (1 / dt)^2 with the equivalent step dt = 2 pi / (N w) = T / N of the remark on the
+    time-discretisation term of tau (Sec. 2.2, reading R18); 0 for Eq. (tau) as printed."""
+    dt = prob.T / prob.N
+    return prob.ct_dt / (dt * dt)
+
+
 def _apply_H(prob: HBProblem, x: np.ndarray) -> np.ndarray:
     """Instance coupling of Eq. (NS-harm): (H x)[..., j] = sum_k H[j, k] x[..., k]."""
     return x @ prob.H.T
@@ -276,7 +296,7 @@ def _element_state(prob: HBProblem, y: np.ndarray, elems):
     gN = g.gradN[elems]
     V = g.V[elems]
     G = g.G[elems]
-    g2 = C_I * prob.nu ** 2 * g.GG[elems]
+    g2 = C_I * prob.nu ** 2 * g.GG[elems] + tau_dt_term(prob)
     Uq = np.einsum("qa,eain->eqin", NQ, U)
     if not prob.convection:
         Uq_tau = np.zeros_like(Uq)
@@ -310,11 +330,24 @@ def element_residual(prob: HBProblem, y: np.ndarray, elems=None):
           + np.einsum("e,eqan,eqin->eain", w, udN, tL)
           + mu * V[:, None, None, None] * np.einsum("eaj,eijn->eain", gN, s["gradU"])
           - V[:, None, None, None] * gN[:, :, :, None] * pbar[:, None, None, :])
+    if prob.stab == "rbvms":
+        # u' = -tau L / rho (so rho u' = -tau L): cross stress int N_a rho u' . grad u_i and Reynolds stress
+        # - int rho (u' . grad N_a) u'_i (reading R17)
+        Qm = Qm + _rbvms_terms(prob, w, gN, s["gradU"], tL)
     T = (rho * V[:, None, None, None] * np.einsum("ab,ebin->eain", MREF, U)
          - np.einsum("e,qa,eqin->eain", w, NQ, tL))
     Qc = (w[:, None, None] * div[:, None, :]
           + (1.0 / rho) * np.einsum("e,eai,eqin->ean", w, gN, tL))
     return s["t"], Qm, T, Qc
+
+
+def _rbvms_terms(prob: HBProblem, w, gN, gradU, tL):
+    """Cross- and Reynolds-stress terms of full RBVMS per element node (reading R17), with tL = tau L:
+    - sum_q w [N_a(q) (tL_q . grad) u_i + (1 / rho) (tL_q . grad N_a) tL_q,i]."""
+    cross = np.einsum("e,qa,eqjn,eijn->eain", w, NQ, tL, gradU)
+    tdN = np.einsum("eqjn,eaj->eqan", tL, gN)
+    reyn = np.einsum("e,eqan,eqin->eain", w, tdN, tL) / prob.rho
+    return -(cross + reyn)
 
 
 def _assemble(prob: HBProblem, t, Qm, T, Qc):
@@ -481,6 +514,14 @@ def jv_exact(prob: HBProblem, y: np.ndarray, v: np.ndarray, shift: float = 0.0) 
            + mu * Vb * np.einsum("eaj,eijn->eain", gN, gradV)
            - Vb * gN[:, :, :, None] * dP.mean(axis=1)[:, None, None, :]
            + shift * Vb * np.einsum("ab,ebin->eain", MREF, dU))
+    if prob.stab == "rbvms":
+        # derivative of the cross- and Reynolds-stress terms (reading R17)
+        tdN = np.einsum("eqjn,eaj->eqan", tL, gN)
+        dtdN = np.einsum("eqjn,eaj->eqan", dtL, gN)
+        dQm = dQm - (np.einsum("e,qa,eqjn,eijn->eain", w, NQ, dtL, gradU)
+                     + np.einsum("e,qa,eqjn,eijn->eain", w, NQ, tL, gradV)
+                     + (np.einsum("e,eqan,eqin->eain", w, dtdN, tL)
+                        + np.einsum("e,eqan,eqin->eain", w, tdN, dtL)) / rho)
     dT = rho * Vb * np.einsum("ab,ebin->eain", MREF, dU) - np.einsum("e,qa,eqin->eain", w, NQ, dtL)
     dQc = (w[:, None, None] * np.einsum("eiin->en", gradV)[:, None, :]
            + (1.0 / rho) * np.einsum("e,eai,eqin->ean", w, gN, dtL))

@@ -172,6 +172,9 @@ struct hb_problem {
     bool march_done = false;
     bool learned_dir = false;
     int jvp_variant = 1;                  // launch variant of the FP32 paper-tangent pass
+    DBuf<int> d_err;                      // status word of the pipelined element pass (0: no wait gave up)
+    int stab = 0;                         // 0: GLS as printed; 1: full RBVMS (hb_set_stabilization)
+    double ct_dt = 0;                     // coefficient of (1 / dt)^2 under the root of tau, dt = T / N
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev;
     size_t prof_used = 0;
 };
@@ -207,6 +210,19 @@ hb_status upload(hb_problem *p, DBuf<T> &b, const std::vector<T> &h) {
         HB_CUDA(cudaStreamSynchronize(p->stream));
     }
     return HB_OK;
+}
+
+// ct_dt (1 / dt)^2 with dt = 2 pi / (N w) = T / N, added under the root of Eq. (tau) (Sec. 2.2, remark 4)
+double tau_dt_term(const hb_problem *p) {
+    const double dt = p->T / double(p->N);
+    return p->ct_dt / (dt * dt);
+}
+
+// mean outlet pressure level over outlets and instances (0 without outlets)
+double p_level(const hb_problem *p) {
+    double pr = 0;
+    for (double v : p->level) pr += v / double(p->level.size());
+    return pr;
 }
 
 inline uint64_t spread3(uint64_t x) {  // 21 bits -> every third bit
@@ -370,6 +386,10 @@ hb_status make_patchset(hb_problem *p, PatchSetDev<T> &ps, const std::vector<int
     HB_TRY(dalloc(p, ps.geom, size_t(p->n_tets) * kGeomStride));
     launch_geom<T>(p->d_xyz.p, p->d_tets_ord.p, int(p->n_tets), p->mu / p->rho, ps.geom.p, p->stream);
     HB_LAUNCHED(p, 1);
+    if constexpr (sizeof(T) == 4) {
+        launch_pack_conn(ps.lconn.p, ps.geom.p, int(p->n_tets), p->stream);
+        HB_LAUNCHED(p, 1);
+    }
     HB_CUDA(cudaStreamSynchronize(p->stream));   // host vectors above are about to go out of scope
     return HB_OK;
 }
@@ -708,6 +728,7 @@ hb_status assemble_at(hb_problem *p, const T *y, cudaStream_t s) {
     a.mass = B::mass(A).p;
     a.rho = T(p->rho);
     a.mu = T(p->mu);
+    a.omega2 = T(p->omega2 + tau_dt_term(p));
     if (!B::mass_done(A)) {
         HB_CUDA(cudaMemsetAsync(a.mass, 0, size_t(A.nnz) * sizeof(T), s));
         launch_assemble_mass<T>(a, s);
@@ -784,9 +805,11 @@ hb_status apply_op(hb_problem *p, int mode, const T *y, const T *v, T *out, doub
     ea.mu = T(p->mu);
     ea.shift = T(shift);
     ea.shift_dev = shift_dev;
-    ea.omega2 = T(p->omega2);
+    ea.omega2 = T(p->omega2 + tau_dt_term(p));
     ea.ls_mass = p->ls_mass;
     ea.variant = p->jvp_variant;
+    ea.err = p->d_err.p;
+    ea.rbvms = p->stab;
     if (ps.P > 0 && mode != MODE_JVA) {
         if (mode == MODE_JVP) {
             // spectral pass over the nodes (each once): W = shift v + rho H v, gathered by the patches
@@ -833,6 +856,15 @@ hb_status apply_op(hb_problem *p, int mode, const T *y, const T *v, T *out, doub
     return HB_OK;
 }
 
+// Status word of the pipelined element pass, read back by the synchronising entry points: a bounded wait
+// inside the kernel that gave up (1: data of a patch, 2: a free stage, 3: copies in flight at exit) is
+// reported as HB_ERR_TIMEOUT once, and the word is cleared.
+hb_status dev_err_status(hb_problem *p, int err) {
+    if (err == 0) return HB_OK;
+    cudaMemsetAsync(p->d_err.p, 0, sizeof(int), p->stream);
+    return fail(HB_ERR_TIMEOUT, "a bounded wait of the pipelined element pass gave up (code " + std::to_string(err) + ")");
+}
+
 hb_status check_precision(int precision) {
     if (precision != 0 && precision != 1) return fail(HB_ERR_INVALID_ARG, "precision must be 0 (FP64) or 1 (FP32)");
     return HB_OK;
@@ -876,8 +908,10 @@ hb_status host_op(hb_problem *p, int mode, const double *y, const double *v, dou
         HB_LAUNCHED(p, 1);
     }
     HB_CUDA(cudaMemcpyAsync(out, p->w64b.p, nd * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+    int err = 0;
+    HB_CUDA(cudaMemcpyAsync(&err, p->d_err.p, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
     HB_CUDA(cudaStreamSynchronize(p->stream));
-    return HB_OK;
+    return dev_err_status(p, err);
 }
 
 hb_status dev_op(hb_problem *p, int mode, const void *y, const void *v, void *out, int precision, double shift,
@@ -903,10 +937,12 @@ hb_status dev_norm(hb_problem *p, const double *x, int64_t n, double &out) {
     launch_dot(x, x, n, p->scratch.p, p->small.p, p->stream);
     HB_LAUNCHED(p, 2);
     double v = 0;
+    int err = 0;
     HB_CUDA(cudaMemcpyAsync(&v, p->small.p, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+    HB_CUDA(cudaMemcpyAsync(&err, p->d_err.p, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
     HB_CUDA(cudaStreamSynchronize(p->stream));
     out = std::sqrt(v);
-    return HB_OK;
+    return dev_err_status(p, err);
 }
 
 hb_status dev_dot(hb_problem *p, const double *x, const double *y, int64_t n, double &out) {
@@ -1220,6 +1256,8 @@ hb_status apply_jv_noalloc(hb_problem *p, int mode, const T *y, const T *v, T *o
     ea.mu = T(p->mu);
     ea.shift = T(shift);
     ea.variant = p->jvp_variant;
+    ea.omega2 = T(tau_dt_term(p));
+    ea.rbvms = p->stab;
     if (ps.P > 0) {
         launch_elem<T>(mode, ea, ps.P, s);
         HB_LAUNCHED(p, 1);
@@ -1505,6 +1543,9 @@ hb_status hb_create(const hb_mesh *mesh, double rho, double mu, double period_T,
     }
     if ((st = dalloc(p, p->scratch, 300000)) != HB_OK) return bail(st);
     if ((st = dalloc(p, p->small, 512)) != HB_OK) return bail(st);
+    if ((st = dalloc(p, p->d_err, 1)) != HB_OK) return bail(st);
+    if (cudaMemsetAsync(p->d_err.p, 0, sizeof(int), p->stream) != cudaSuccess)
+        return bail(fail(HB_ERR_CUDA, "set-up failed"));
     if ((st = dalloc(p, p->y, size_t(p->n_nodes) * 4 * p->N)) != HB_OK) return bail(st);
     if (cudaStreamSynchronize(p->stream) != cudaSuccess) return bail(fail(HB_ERR_CUDA, "set-up failed"));
     *out = p;
@@ -1839,7 +1880,7 @@ static hb_status solve_impl(hb_problem *p, const hb_solve_opts &o, hb_report *re
         OpCtx c{newton ? MODE_JVE : MODE_JVP, shift, o.precision, p->shift_dev.p};
         // Jacobi diagonal of P (+ pseudo mass) and the frozen state in the kernels' precision
         if (o.precision == 1) {
-            launch_convert<double, float>(p->y.p, p->ky32.p, nd, p->stream);
+            launch_convert_state(p->y.p, p->ky32.p, nd, p->N, p_level(p), p->stream);
             HB_LAUNCHED(p, 1);
             HB_TRY(apply_op<float>(p, MODE_DIAG, p->ky32.p, nullptr, p->kdiag32.p, c.shift, p->stream, c.shift_dev));
             launch_convert<float, double>(p->kdiag32.p, p->kdiag.p, nd, p->stream);
@@ -2294,6 +2335,8 @@ hb_status batch_record(hb_batch *b) {
         ea.mu = T(p->mu);
         ea.shift = T(b->shift);
         ea.shift_dev = nullptr;
+        ea.omega2 = T(tau_dt_term(p));
+        ea.rbvms = p->stab;
         smem = std::max(smem, elem_smem_bytes(b->mode, p->N, ps.nl_max, ps.ep_max, sizeof(T), bstride));
     }
     DBuf<ElemArgs<T>> &dargs = [&]() -> DBuf<ElemArgs<T>> & {
@@ -2592,6 +2635,23 @@ hb_status hb_get_info(hb_problem *p, hb_info *info) {
 }
 
 int64_t hb_launch_count(const hb_problem *p) { return p ? p->launches : 0; }
+
+hb_status hb_set_stabilization(hb_problem *p, int variant, double ct_dt) {
+    if (!p) return fail(HB_ERR_INVALID_ARG, "null problem");
+    if (variant != 0 && variant != 1) return fail(HB_ERR_INVALID_ARG, "variant must be 0 (GLS) or 1 (full RBVMS)");
+    if (!(ct_dt >= 0) || !std::isfinite(ct_dt)) return fail(HB_ERR_INVALID_ARG, "ct_dt must be finite and >= 0");
+    cudaSetDevice(p->device);
+    if (p->stream) cudaStreamSynchronize(p->stream);
+    p->stab = variant;
+    p->ct_dt = ct_dt;
+    // captured GMRES cycles hold the old kernel arguments; assembled coefficients hold the old tau
+    for (auto &gc : p->cycle) {
+        if (gc.exec) cudaGraphExecDestroy(gc.exec);
+        gc = hb_problem::CycleGraph{};
+    }
+    p->as.ready32 = p->as.ready64 = false;
+    return HB_OK;
+}
 
 hb_status hb_set_launch_variant(hb_problem *p, int variant) {
     if (!p) return fail(HB_ERR_INVALID_ARG, "null problem");

@@ -52,7 +52,7 @@ __global__ void assemble_kernel(AsmArgs<T> a) {
     for (int k = 0; k < 4; ++k)
 #pragma unroll
         for (int j = 0; j < 3; ++j) gN[k][j] = g[3 * k + j];
-    const T V = g[12], g2 = g[13];
+    const T V = g[12], g2 = g[13] + a.omega2;
     const T w = V * T(0.25), rho = a.rho, mu = a.mu;
     T u[4][3];
 #pragma unroll

@@ -179,18 +179,29 @@ __device__ __forceinline__ L ldot3(const L *a, const L *b) {
 //   sum_q (u_q . grad v_i)           = (sum_a u_a) . grad v_i  (the 4 points average to the centroid)
 //   visc, pressure and Mx terms      = grad N_a . Z[:, i],   Z = w rho Mx + mu V (grad v)^T - V pbar I
 // with X_q = tau_q (u_q . grad v + grad q / rho) the strong residual of the direction over rho.
-template <typename T, typename L, int NT>
+//
+// PIPE (the pipelined pass, FP32): the packed local connectivity sits in slot 14 of the element's geometry
+// record instead of sConn, and the staged direction rows are the caller's unmodified values, so the
+// velocity of nodes with prescribed velocity is masked to 0 here, at load time.
+template <typename T, typename L, int NT, bool PIPE = false>
 __device__ __forceinline__ void jvp_lanes(int e, int n0, int d1, int Nrt, T rho, T mu, T omega2, T cs,
                                           const T *__restrict__ sGeom, const uint32_t *__restrict__ sConn,
                                           const T *__restrict__ sY, const T *__restrict__ sV,
                                           const T *__restrict__ sW, const int *__restrict__ sNode,
                                           T *__restrict__ gout) {
     const int N = NT > 0 ? NT : Nrt, N4 = 4 * N, WS = w_stride(N, int(sizeof(T)));
-    const uint32_t c = sConn[e];
+    uint32_t c;
+    if constexpr (PIPE) c = __float_as_uint(float(sGeom[e * kGeomStride + 14]));
+    else c = sConn[e];
     const int lo[4] = {int(c & 255u), int((c >> 8) & 255u), int((c >> 16) & 255u), int(c >> 24)};
     int rY[4];
 #pragma unroll
     for (int a = 0; a < 4; ++a) rY[a] = lo[a] * N4 + n0;
+    // velocity of the direction at the 4 nodes: 0 where the velocity is prescribed (PIPE only; the
+    // other passes zero those entries in shared memory after staging)
+    bool vfree[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) vfree[a] = !PIPE || sNode[lo[a]] >= 0;
     T gs[4][3], V, g2s;
     load_geom(sGeom + e * kGeomStride, gs, V, g2s);
     L gN[3][3];   // grad N_a of the vertices a = 1, 2, 3 (grad N_0 = -(sum of these))
@@ -208,7 +219,7 @@ __device__ __forceinline__ void jvp_lanes(int e, int n0, int d1, int Nrt, T rho,
     {
         L dv0[3];
 #pragma unroll
-        for (int i = 0; i < 3; ++i) dv0[i] = lload<L>(sV + rY[0] + i * N, d1);
+        for (int i = 0; i < 3; ++i) dv0[i] = vfree[0] ? lload<L>(sV + rY[0] + i * N, d1) : lsplat<L>(T(0));
         if constexpr (NT == 1) {
 #pragma unroll
             for (int i = 0; i < 3; ++i) vn[0][i] = dv0[i];
@@ -224,7 +235,7 @@ __device__ __forceinline__ void jvp_lanes(int e, int n0, int d1, int Nrt, T rho,
             for (int j = 0; j < 3; ++j) gVp[j] = a == 1 ? lmul(ddp, gN[0][j]) : lfma(ddp, gN[a - 1][j], gVp[j]);
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
-                const L va = lload<L>(sV + rY[a] + i * N, d1);
+                const L va = vfree[a] ? lload<L>(sV + rY[a] + i * N, d1) : lsplat<L>(T(0));
                 if constexpr (NT == 1) vn[a][i] = va;
                 const L dd = lsub(va, dv0[i]);
 #pragma unroll
@@ -331,14 +342,18 @@ __device__ __forceinline__ void jvp_lanes(int e, int n0, int d1, int Nrt, T rho,
             L val = a == 0 ? lsub(cW, gz0) : ladd(cW, gz[a - 1]);
             val = lfma(kd, ldot3(uq[a], gV[i]), val);
             val = lfma(m20, Wa[a], val);
-            if (sNode[lo[a]] >= 0) lred(go[a] + i * N, val, d1);   // prescribed velocity rows are set apart
+            // prescribed velocity rows are set apart
+            if (PIPE ? vfree[a] : sNode[lo[a]] >= 0) lred(go[a] + i * N, val, d1);
         }
     }
 }
 
 // NT > 0: the number of instances is the compile-time constant NT; NT = 0: runtime N
+// rbvms (RES, JVE): full RBVMS (Sec. 2.2, remark 2 after Eq. tau): with u' = -tau L / rho added to the
+// advecting velocity the momentum rows gain the cross stress - int N_a (tau L . grad) u_i and the Reynolds
+// stress - int (1 / rho) (tau L . grad N_a) (tau L)_i (and their derivatives in JVE).
 template <typename T, int MODE, int NT>
-__device__ __forceinline__ void element_instance(int e, int n, int Nrt, T rho, T mu, T shift, T omega2,
+__device__ __forceinline__ void element_instance(int e, int n, int Nrt, T rho, T mu, T shift, T omega2, int rbvms,
                                                  const T *__restrict__ sGeom,
                                                  const uint32_t *__restrict__ sConn,
                                                  const T *__restrict__ sY, const T *__restrict__ sV,
@@ -459,6 +474,18 @@ __device__ __forceinline__ void element_instance(int e, int n, int Nrt, T rho, T
             for (int a = 0; a < 4; ++a)
 #pragma unroll
                 for (int i = 0; i < 3; ++i) qm[a][i] += w * udN[a] * tL[i];
+            if (!TM && rbvms) {
+                T ctL[3], tdN[4];
+#pragma unroll
+                for (int i = 0; i < 3; ++i) ctL[i] = tL[0] * gU[i][0] + tL[1] * gU[i][1] + tL[2] * gU[i][2];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) tdN[a] = tL[0] * gN[a][0] + tL[1] * gN[a][1] + tL[2] * gN[a][2];
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int i = 0; i < 3; ++i)
+                        qm[a][i] -= w * ((a == q ? qb + qd : qb) * ctL[i] + tdN[a] * tL[i] / rho);
+            }
         }
         const T pbar = T(0.25) * (p[0] + p[1] + p[2] + p[3]);
         const T div = gU[0][0] + gU[1][1] + gU[2][2];
@@ -558,6 +585,23 @@ __device__ __forceinline__ void element_instance(int e, int n, int Nrt, T rho, T
             for (int a = 0; a < 4; ++a)
 #pragma unroll
                 for (int i = 0; i < 3; ++i) qm[a][i] += w * (dudN[a] * tL[i] + udN[a] * dtL[i]);
+            if (rbvms) {
+                T dc[3], tdN[4], dtdN[4];
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+                    dc[i] = dtL[0] * gU[i][0] + dtL[1] * gU[i][1] + dtL[2] * gU[i][2]
+                          + tL[0] * gV[i][0] + tL[1] * gV[i][1] + tL[2] * gV[i][2];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    tdN[a] = tL[0] * gN[a][0] + tL[1] * gN[a][1] + tL[2] * gN[a][2];
+                    dtdN[a] = dtL[0] * gN[a][0] + dtL[1] * gN[a][1] + dtL[2] * gN[a][2];
+                }
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int i = 0; i < 3; ++i)
+                        qm[a][i] -= w * ((a == q ? qb + qd : qb) * dc[i] + (dtdN[a] * tL[i] + tdN[a] * dtL[i]) / rho);
+            }
         }
         const T pbar = T(0.25) * (dvp[0] + dvp[1] + dvp[2] + dvp[3]);
         const T div = gV[0][0] + gV[1][1] + gV[2][2];
@@ -801,8 +845,8 @@ __device__ __forceinline__ void patch_pass(const ElemArgs<T> &a, const PatchSmem
     } else {
         for (int i = tid; i < ne * N; i += nt) {
             const int e = i / N, n = i - e * N;
-            element_instance<T, MODE, NT>(e, n, N, a.rho, a.mu, shift, a.omega2, sGeom, sConn, sY, sV, sHY, sHV,
-                                          sNode, a.out, sT);
+            element_instance<T, MODE, NT>(e, n, N, a.rho, a.mu, shift, a.omega2, a.rbvms, sGeom, sConn, sY, sV, sHY,
+                                          sHV, sNode, a.out, sT);
         }
     }
     __syncthreads();
@@ -856,6 +900,184 @@ __global__ void __launch_bounds__(ElemCfg<T, VAR>::block, ElemCfg<T, VAR>::minb)
         patch_pass<T, MODE, NT, typename ElemCfg<T, VAR>::lane>(a, sm, sm.slot(cur), shift, pf);
         cp_async_wait_all();
         __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------------------------------
+// Pipelined paper-tangent pass (FP32, fixed N, W given): one producer warp and C consumer warps per block,
+// one block per SM, two patch stages in shared memory.  The producer copies a patch's slot, element
+// geometry (with the packed local connectivity in slot 14) and node rows of y, v and W into a free stage
+// with 1-D bulk asynchronous copies (cp.async.bulk) that complete on the stage's "full" mbarrier; the
+// consumers wait on it, compute the patch's element-instances and release the stage on its "empty"
+// mbarrier.  No block-wide barrier sits in the patch loop: while the consumers work on one stage the
+// other is being filled, and consumer warps that finish a patch early go on to the next stage.
+//
+// Every wait is bounded (kPipeSpinLimit polls); a wait that gives up sets *err (1: a consumer's wait for
+// data, 2: the producer's wait for a free stage) and the block leaves the loop; before the producer
+// exits it waits, again bounded, until every copy it issued has landed.
+
+constexpr long long kPipeSpinLimit = 1ll << 26;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait for the phase of the given parity; false if it gave up
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    for (long long i = 0; i < kPipeSpinLimit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+// 1-D bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16) completing on bar
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// One stage of the pipelined pass: slot, geometry, y rows, v rows, W rows (each 16-byte aligned).
+struct PipeLayout {
+    size_t slot, geom, Y, V, W, stage;
+};
+__host__ __device__ inline PipeLayout pipe_layout(int N, int nl, int ep) {
+    PipeLayout L;
+    size_t o = 0;
+    L.slot = o; o += pad16(size_t(slot_ints(nl)) * 4);
+    L.geom = o; o += pad16(size_t(ep) * kGeomStride * 4);
+    L.Y = o;    o += pad16(size_t(nl) * 4 * N * 4);
+    L.V = o;    o += pad16(size_t(nl) * 4 * N * 4);
+    L.W = o;    o += pad16(size_t(nl) * w_stride(N, 4) * 4);
+    L.stage = o;
+    return L;
+}
+
+template <typename L, int NT, int C>
+__global__ void __launch_bounds__((C + 1) * 32, 1) jvp_pipe_kernel(ElemArgs<float> a, int *err) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t full[2], empty[2];
+    constexpr int N = NT, N4 = 4 * N, N3 = 3 * N, WS = w_stride(NT, 4);
+    constexpr int LW = int(sizeof(L) / sizeof(float));
+    constexpr int NP = (N + LW - 1) / LW;
+    const PipeLayout PL = pipe_layout(N, a.pv.nl_max, a.pv.ep_max);
+    const int P = a.pv.n_patches, stride = a.pv.slot_stride;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
+        mbar_init(&empty[0], C);
+        mbar_init(&empty[1], C);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    }
+    __syncthreads();
+    if (warp == C) {
+        // ---- producer warp.  The next patch's header and node ids are loaded into registers before the
+        // wait for a free stage, so their global-load latency overlaps the consumers' work.
+        constexpr int IDS = 8;                      // node ids per lane: patches of up to 256 nodes
+        int k = 0, issued = -1;
+        int p = int(blockIdx.x);
+        int e0 = 0, ne = 0, nl = 0, ids[IDS];
+        auto load_patch = [&](int q) {
+            const int *gs = a.pv.slots + size_t(q) * stride;
+            e0 = gs[0];
+            ne = gs[1];
+            nl = gs[2];
+#pragma unroll
+            for (int j = 0; j < IDS; ++j) {
+                const int l = lane + 32 * j;
+                ids[j] = l < a.pv.nl_max ? gs[4 + l] : 0;
+            }
+        };
+        if (p < P) load_patch(p);
+        for (; p < P; ++k, p += int(gridDim.x)) {
+            const int s = k & 1;
+            if (k >= 2 && !mbar_wait_bounded(&empty[s], uint32_t(((k >> 1) - 1) & 1))) {
+                if (lane == 0) atomicExch(err, 2);
+                break;
+            }
+            unsigned char *st = smem + size_t(s) * PL.stage;
+            const int *gslot = a.pv.slots + size_t(p) * stride;
+            const uint32_t bytes = uint32_t(stride) * 4 + uint32_t(ne) * kGeomStride * 4 +
+                                   uint32_t(nl) * uint32_t(2 * N4 + WS) * 4;
+            if (lane == 0) {
+                mbar_arrive_expect_tx(&full[s], bytes);
+                bulk_g2s(st + PL.slot, gslot, uint32_t(stride) * 4, &full[s]);
+                bulk_g2s(st + PL.geom, a.pv.geom + size_t(e0) * kGeomStride, uint32_t(ne) * kGeomStride * 4, &full[s]);
+            }
+            __syncwarp();
+#pragma unroll
+            for (int j = 0; j < IDS; ++j) {
+                const int l = lane + 32 * j;
+                if (l < nl) {
+                    const size_t node = size_t(uint32_t(ids[j]) & ~kDirBit);
+                    bulk_g2s(st + PL.Y + size_t(l) * N4 * 4, a.y + node * N4, N4 * 4, &full[s]);
+                    bulk_g2s(st + PL.V + size_t(l) * N4 * 4, a.v + node * N4, N4 * 4, &full[s]);
+                    bulk_g2s(st + PL.W + size_t(l) * WS * 4, a.W + node * WS, WS * 4, &full[s]);
+                }
+            }
+            issued = k;
+            if (p + int(gridDim.x) < P) load_patch(p + int(gridDim.x));
+        }
+        // every copy this warp issued has landed before the block may exit
+        for (int j = (issued >= 1 ? issued - 1 : 0); j <= issued; ++j)
+            if (!mbar_wait_bounded(&full[j & 1], uint32_t((j >> 1) & 1)) && lane == 0) atomicExch(err, 3);
+        return;
+    }
+    // ---- consumer warps
+    const int ct = threadIdx.x, nct = C * 32;
+    for (int k = 0;; ++k) {
+        const int p = int(blockIdx.x) + k * int(gridDim.x);
+        if (p >= P) break;
+        const int s = k & 1;
+        if (!mbar_wait_bounded(&full[s], uint32_t((k >> 1) & 1))) {
+            if (lane == 0) atomicExch(err, 1);
+            return;
+        }
+        const unsigned char *st = smem + size_t(s) * PL.stage;
+        const int *sSlot = reinterpret_cast<const int *>(st + PL.slot);
+        const float *sGeom = reinterpret_cast<const float *>(st + PL.geom);
+        const float *sY = reinterpret_cast<const float *>(st + PL.Y);
+        const float *sV = reinterpret_cast<const float *>(st + PL.V);
+        const float *sW = reinterpret_cast<const float *>(st + PL.W);
+        const int ne = sSlot[1], nl = sSlot[2], nd = sSlot[3];
+        const int *sNode = sSlot + 4;
+        // prescribed velocity rows of the output: v (identity rows); patches sharing a node store the
+        // same values
+        if (nd > 0) {
+            for (int i = ct; i < nl * N3; i += nct) {
+                const int l = i / N3;
+                if (sNode[l] >= 0) continue;
+                const int r = i - l * N3;
+                a.out[size_t(uint32_t(sNode[l]) & ~kDirBit) * N4 + r] = sV[l * N4 + r];
+            }
+        }
+        for (int i = ct; i < ne * NP; i += nct) {
+            const int e = i / NP, kk = i - e * NP;
+            const int d1 = (LW == 2 && kk + NP < N) ? NP : 0;
+            jvp_lanes<float, L, NT, true>(e, kk, d1, N, a.rho, a.mu, a.omega2, 0.f, sGeom, nullptr, sY, sV, sW,
+                                          sNode, a.out);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
     }
 }
 
@@ -970,6 +1192,11 @@ __global__ void geom_kernel(const double *__restrict__ xyz, const int *__restric
     g[15] = T(0);
 }
 
+__global__ void pack_conn_kernel(const uint32_t *__restrict__ lconn, float *__restrict__ geom, int n_tets) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n_tets) geom[size_t(e) * kGeomStride + 14] = __uint_as_float(lconn[e]);
+}
+
 inline int nblk(int64_t n, int b) { return int((n + b - 1) / b); }
 
 }  // namespace
@@ -988,10 +1215,34 @@ static void launch_elem_v(const ElemArgs<T> &a, int grid, cudaStream_t s) {
     if (grid > 0) kern<<<grid, ElemCfg<T, VAR>::block, smem, s>>>(a);
 }
 
+// Pipelined paper-tangent pass (variants 4 and 5): one block per SM; false if it cannot run (no W rows,
+// no status word, or two stages do not fit the opt-in shared memory), so the caller falls back.
+template <typename L, int NT, int C>
+static bool launch_pipe(const ElemArgs<float> &a, cudaStream_t s) {
+    if (!a.W || !a.err || a.pv.n_patches <= 0 || a.pv.nl_max > 256) return false;   // producer holds 256 ids
+    const size_t smem = 2 * pipe_layout(NT, a.pv.nl_max, a.pv.ep_max).stage;
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (smem + 64 > size_t(optin)) return false;
+    static LaunchCache cache;
+    auto kern = jvp_pipe_kernel<L, NT, C>;
+    const int per = cached_blocks_per_sm(cache, kern, (C + 1) * 32, smem);
+    const int grid = std::min(a.pv.n_patches, per * device_sms());
+    kern<<<grid, (C + 1) * 32, smem, s>>>(a, a.err);
+    return true;
+}
+
 template <typename T, int MODE, int NT>
 static void launch_elem_n(const ElemArgs<T> &a, int grid, cudaStream_t s) {
+    if constexpr (MODE == MODE_JVP && sizeof(T) == 4 && (NT == 9 || NT == 13 || NT == 21)) {
+        // 4: one instance per thread, 20 consumer warps; 5: instance pairs on paired FP32 instructions,
+        // 15 consumer warps.  Without the W rows (or if the stages do not fit) they run variant 1.
+        if (a.variant == 4 && launch_pipe<float, NT, 20>(a, s)) return;
+        if (a.variant == 5 && launch_pipe<float2, NT, 15>(a, s)) return;
+    }
     if constexpr (MODE == MODE_JVP && sizeof(T) == 4) {
-        if (a.variant == 1) {
+        if (a.variant == 1 || a.variant >= 4) {
             launch_elem_v<T, MODE, NT, 1>(a, grid, s);
             return;
         }
@@ -1050,7 +1301,7 @@ static void launch_batch_var(const BatchGroup<T> &g, size_t smem, int grid, cuda
 template <typename T, int MODE>
 static void launch_batch_mode(const BatchGroup<T> &g, size_t smem, int grid, cudaStream_t s) {
     if constexpr (MODE == MODE_JVP && sizeof(T) == 4) {
-        if (g.variant == 1) return launch_batch_var<T, MODE, 1>(g, smem, grid, s);
+        if (g.variant == 1 || g.variant >= 4) return launch_batch_var<T, MODE, 1>(g, smem, grid, s);
         if (g.variant == 2) return launch_batch_var<T, MODE, 2>(g, smem, grid, s);
         if (g.variant == 3) return launch_batch_var<T, MODE, 3>(g, smem, grid, s);
     }
@@ -1070,6 +1321,15 @@ void launch_batch_elem(int mode, const BatchGroup<T> &g, size_t smem, int grid, 
 template <typename T>
 void launch_geom(const double *xyz, const int *tets, int n_tets, double nu, T *geom, cudaStream_t s) {
     if (n_tets > 0) geom_kernel<T><<<nblk(n_tets, 128), 128, 0, s>>>(xyz, tets, n_tets, nu, geom);
+}
+
+void launch_pack_conn(const uint32_t *lconn, float *geom, int n_tets, cudaStream_t s) {
+    if (n_tets > 0) pack_conn_kernel<<<nblk(n_tets, 256), 256, 0, s>>>(lconn, geom, n_tets);
+}
+
+size_t pipe_smem_bytes(int N, int nl_max, int ep_max) {
+    if (N != 9 && N != 13 && N != 21) return 0;
+    return 2 * pipe_layout(N, nl_max, ep_max).stage;
 }
 
 template void launch_elem<float>(int, const ElemArgs<float> &, int, cudaStream_t);

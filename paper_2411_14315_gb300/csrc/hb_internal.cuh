@@ -75,7 +75,7 @@ enum Mode : int {
 
 constexpr int kGeomStride = 16;       // per element: grad N_a (4 x 3), V, C_I nu^2 G:G, 2 pad
 constexpr int kMaxN = 31;             // largest number of time instances supported
-constexpr int kJvpVariants = 4;       // launch variants of the FP32 paper-tangent element pass
+constexpr int kJvpVariants = 6;       // launch variants of the FP32 paper-tangent element pass
 constexpr double kCI = 3.0;           // Eq. (tau)
 // 4-point degree-2 Gauss rule on a tetrahedron (barycentric coordinates of the points)
 constexpr double kQA = 0.5854101966249685;
@@ -132,6 +132,10 @@ struct ElemArgs {
                                    // of the tangent (d(du/dt) = shift / rho d u); not its Jacobi diagonal
     const double *shift_dev = nullptr;   // if set, the shift is read from device memory instead
     int variant = 0;               // launch variant of the FP32 paper-tangent pass, [0, kJvpVariants)
+    int *err = nullptr;            // device status word of the pipelined pass: a bounded wait that gave up
+                                   // stores a nonzero code (left untouched otherwise)
+    int rbvms = 0;                 // residual and exact Jacobian: add the full-RBVMS cross- and
+                                   // Reynolds-stress terms of u' = -tau L / rho (Sec. 2.2, remark 2)
 };
 
 // Boundary (Neumann) faces.
@@ -160,6 +164,11 @@ void launch_elem(int mode, const ElemArgs<T> &a, int grid, cudaStream_t s);
 template <typename T>
 void launch_geom(const double *xyz, const int *tets_patch_order, int n_tets, double nu, T *geom,
                  cudaStream_t s);
+// FP32 geometry records carry the packed local connectivity of their patch in slot 14 (read by the
+// pipelined paper-tangent pass, which copies the geometry and nothing else per element)
+void launch_pack_conn(const uint32_t *lconn, float *geom, int n_tets, cudaStream_t s);
+// dynamic shared memory of the pipelined pass (two stages), 0 if it has no kernel for N
+size_t pipe_smem_bytes(int N, int nl_max, int ep_max);
 // persistent element pass over the patches of several problems that share one instance count N: args on
 // the device; batch slot i (bslot_stride ints at bslots + i * bslot_stride) = [problem index, 0, 0, 0,
 // that problem's slot of the patch]; the group's items are [item_begin, item_end); *counter must be 0 at
@@ -190,6 +199,10 @@ void launch_harmonics(const double *y, double *coef, int64_t rows, int N, int n_
 template <typename A, typename B>
 void launch_convert(const A *x, B *y, int64_t n, cudaStream_t s);
 void launch_axpy(double a, const double *x, double *y, int64_t n, cudaStream_t s);
+// FP32 copy of a state [n / (4 N)][4][N] with p_off subtracted from its pressure: the frozen state of the
+// mixed-precision operators, which use the pressure only through its gradient (exact Jacobian), so an
+// outlet pressure level far above the dynamic pressure does not cost FP32 digits
+void launch_convert_state(const double *y, float *y32, int64_t n, int N, double p_off, cudaStream_t s);
 void launch_scale_copy(double a, const double *x, double *y, int64_t n, cudaStream_t s);
 // z = x * dinv in z's precision (right Jacobi preconditioning); dinv = 1 / d
 template <typename T>
@@ -242,6 +255,7 @@ struct AsmArgs {
     T *coef;                       // [nnz][8][N], cleared before the assembly
     T *mass;                       // [nnz], cleared before the assembly
     T rho, mu;
+    T omega2 = 0;                  // constant added under the root of tau (time-discretisation term)
 };
 template <typename T>
 struct SpmvArgs {

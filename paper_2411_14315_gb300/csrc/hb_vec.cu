@@ -24,6 +24,15 @@ __global__ void convert_kernel(const A *__restrict__ x, B *__restrict__ y, int64
         y[i] = B(x[i]);
 }
 
+// FP32 copy of an FP64 state [node][4][N] with p_off subtracted from the pressure field
+__global__ void convert_state_kernel(const double *__restrict__ y, float *__restrict__ y32, int64_t n, int N,
+                                     double p_off) {
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+        const int f = int((i / N) & 3);
+        y32[i] = float(f == 3 ? y[i] - p_off : y[i]);
+    }
+}
+
 __global__ void axpy_kernel(double a, const double *__restrict__ x, double *__restrict__ y, int64_t n) {
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
         y[i] += a * x[i];
@@ -354,6 +363,10 @@ int multidot_dispatch(std::integer_sequence<int, Ks...>, int k, const double *V,
 template <typename A, typename B>
 void launch_convert(const A *x, B *y, int64_t n, cudaStream_t s) {
     if (n > 0) convert_kernel<A, B><<<stream_grid(n), kVB, 0, s>>>(x, y, n);
+}
+
+void launch_convert_state(const double *y, float *y32, int64_t n, int N, double p_off, cudaStream_t s) {
+    if (n > 0) convert_state_kernel<<<stream_grid(n), kVB, 0, s>>>(y, y32, n, N, p_off);
 }
 
 void launch_axpy(double a, const double *x, double *y, int64_t n, cudaStream_t s) {

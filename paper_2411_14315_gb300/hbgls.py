@@ -95,6 +95,7 @@ SIGNATURES = {
     "hb_set_inflow_harmonics": ([_P, C.c_int, _DP], C.c_int),
     "hb_set_outlet_resistance": ([_P, C.c_int, C.c_double, _DP, _DP], C.c_int),
     "hb_set_backflow": ([_P, C.c_double], C.c_int),
+    "hb_set_stabilization": ([_P, C.c_int, C.c_double], C.c_int),
     "hb_set_initial": ([_P, _DP], C.c_int),
     "hb_set_instances": ([_P, _DP], C.c_int),
     "hb_default_opts": ([C.POINTER(hb_solve_opts)], C.c_int),
@@ -281,6 +282,10 @@ class Problem:
 
     def set_backflow(self, beta: float):
         _check(lib().hb_set_backflow(self._h, beta))
+
+    def set_stabilization(self, variant: int = 0, ct_dt: float = 0.0):
+        """hb_set_stabilization: 0 = GLS as printed, 1 = full RBVMS; ct_dt (1/dt)^2 under the root of tau."""
+        _check(lib().hb_set_stabilization(self._h, int(variant), float(ct_dt)))
 
     def set_initial(self, harmonics=None):
         hm = None if harmonics is None else _f64(harmonics, (self.n_nodes, 4, 2 * self.n_h + 1))

@@ -122,3 +122,9 @@ def test_null_handles(lib):
     out = C.c_void_p()
     assert lib.hb_batch_create(None, 0, 1, C.byref(out)) == INVALID
     assert lib.hb_batch_destroy(None) == 0
+
+
+def test_set_stabilization_null_problem(lib):
+    """hb_set_stabilization checks its problem before anything else (no device work)."""
+    assert lib.hb_set_stabilization(None, 1, 0.0) == INVALID
+    assert lib.hb_last_error().decode()

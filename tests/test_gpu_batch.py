@@ -1,8 +1,10 @@
 """Batched operator application (one captured graph, one persistent element launch per instance count over
-many problems of different N) against per-problem calls, and patch autotuning."""
+many problems of different N) against the CPU oracle per member and per field, and against per-problem
+calls; patch autotuning."""
 import numpy as np
 import pytest
 
+from oracle import hb_oracle as O
 from paper_2411_14315_gb300 import inputs as I
 from tests import problems as P
 
@@ -14,6 +16,39 @@ def _problems():
              P.box_spec(seed=73, n_h=10, n=(7, 5, 4)), P.box_spec(seed=74, n_h=2, n=(4, 4, 4)),
              P.womersley_spec()]
     return specs, [P.gpu_problem(s) for s in specs]
+
+
+def _relerr_fields(a, b):
+    """max over the four fields of ||a_f - b_f|| / ||b_f||."""
+    return max(np.linalg.norm(a[:, f] - b[:, f]) / max(np.linalg.norm(b[:, f]), 1e-300) for f in range(4))
+
+
+@pytest.mark.parametrize("precision,kind", [(1, 0), (1, 1), (0, 0), (0, 1)])
+def test_batch_matches_oracle(precision, kind):
+    """Every member of a batch of five problems (N = 5, 9, 13, 21 and the Womersley pipe at 9; pressure,
+    resistance and traction-free outlets; prescribed velocities) against the oracle's paper tangent
+    (Eqs. ptangent, K_mat, ctangent, F_mat) or exact Jacobian, field by field: FP64 1e-12, FP32 1e-5."""
+    torch = pytest.importorskip("torch")
+    from paper_2411_14315_gb300 import hbgls
+    specs, probs = _problems()
+    dt = torch.float64 if precision == 0 else torch.float32
+    ys = [torch.tensor(I.random_state(s.mesh.n_nodes, s.N, 180 + k), dtype=dt, device="cuda") for k, s in enumerate(specs)]
+    vs = [torch.tensor(I.random_state(s.mesh.n_nodes, s.N, 190 + k), dtype=dt, device="cuda") for k, s in enumerate(specs)]
+    outs = [torch.empty_like(y) for y in ys]
+    shift = 0.6
+    b = hbgls.Batch(probs, precision)
+    st = torch.cuda.current_stream()
+    b.jv_dev(ys, vs, outs, kind, shift, stream=st)
+    st.synchronize()
+    tol = 1e-12 if precision == 0 else 1e-5
+    fn = O.jv_paper if kind == 0 else O.jv_exact
+    for s, y, v, o in zip(specs, ys, vs, outs):
+        ora = P.oracle_problem(s)
+        # the oracle sees exactly the values the kernels saw (FP32 inputs widened without rounding)
+        ref = fn(ora, y.double().cpu().numpy(), v.double().cpu().numpy(), shift=shift)
+        err = _relerr_fields(o.double().cpu().numpy(), ref)
+        assert err < tol, (s.N, err)
+    b.close()
 
 
 @pytest.mark.parametrize("precision,kind", [(1, 0), (1, 1), (0, 0)])

@@ -76,22 +76,42 @@ def test_residual_and_jv_across_instance_counts(n_h):
         assert relerr(gp.jv(y, v, 0, prec, 0.3), O.jv_paper(ora, y, v, shift=0.3)) < TOL[prec]
 
 
-@pytest.mark.parametrize("n_h", [0, 1, 4, 10, 15])
+@pytest.mark.parametrize("n_h", [0, 1, 4, 6, 10, 15])
 def test_paper_tangent_launch_variants(n_h):
     """Every launch variant of the FP32 paper-tangent pass (pairs of instances per thread, one instance
-    per thread at three block sizes) against the oracle, for compile-time and generic instance counts."""
+    per thread at three block sizes, and the two pipelined variants with a producer warp and bulk copies)
+    against the oracle, for compile-time and generic instance counts."""
     spec = P.box_spec(seed=70 + n_h, n_h=n_h, n=(6, 5, 4))
     ora = P.oracle_problem(spec)
     gp = P.gpu_problem(spec)
     y = I.random_state(spec.mesh.n_nodes, spec.N, 71)
     v = I.random_state(spec.mesh.n_nodes, spec.N, 72)
     ref = O.jv_paper(ora, y, v, shift=0.8)
-    for var in (0, 1, 2, 3):
+    for var in (0, 1, 2, 3, 4, 5):
         gp.set_launch_variant(var)
         assert gp.launch_variant() == var
         assert relerr(gp.jv(y, v, 0, 1, 0.8), ref) < TOL[1], var
     with pytest.raises(RuntimeError):
-        gp.set_launch_variant(4)
+        gp.set_launch_variant(6)
+
+
+def test_paper_tangent_variants_many_patches_per_block():
+    """The persistent and pipelined passes on a T-junction of ~120k tetrahedra (N = 21, several hundred
+    patches, so every block of the one-block-per-SM pipelined pass reuses both shared-memory stages
+    several times; prescribed velocities and resistance outlets) against the oracle's paper tangent."""
+    spec = P.glenn_spec(n_tets=120_000)
+    ora = P.oracle_problem(spec)
+    gp = P.gpu_problem(spec)
+    assert gp.info()["n_patches32"] > 4 * 152
+    y = I.random_state(spec.mesh.n_nodes, spec.N, 73)
+    v = I.random_state(spec.mesh.n_nodes, spec.N, 74)
+    y32 = y.astype(np.float32).astype(np.float64)
+    v32 = v.astype(np.float32).astype(np.float64)
+    ref = O.jv_paper(ora, y32, v32, shift=300.0)
+    for var in (0, 1, 4, 5):
+        gp.set_launch_variant(var)
+        assert relerr(gp.jv(y32, v32, 0, 1, 300.0), ref) < TOL[1], var
+    gp.close()
 
 
 def test_womersley_pipe_parabolic_profile_and_patches():
