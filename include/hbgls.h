@@ -365,6 +365,14 @@ int64_t hb_launch_count(const hb_problem *p);
  * for another value.  hb_get_launch_variant returns the current variant (-1 for a null problem). */
 hb_status hb_set_launch_variant(hb_problem *p, int variant);
 int hb_get_launch_variant(const hb_problem *p);
+/* Implementation of the node-level spectral pass W = shift v + rho H v (the F block of Eq. F_mat and the
+ * pseudo-time mass, a dense N x N product per node row) in FP32 at N = 9, 13, 21 (no counterpart in the
+ * paper; a tuning knob): 0 = tcgen05 tensor cores with the accumulator in tensor memory, 1 = warp-level
+ * mma.sync tensor cores, 2 = FP32 FMAs.  All are TF32 head/tail splits or FP32 and give the same W to FP32
+ * accuracy; FP64 and other N always use the FMA form.  HB_ERR_INVALID_ARG for another value;
+ * hb_get_spectral_path returns the current path (-1 for a null problem). */
+hb_status hb_set_spectral_path(hb_problem *p, int path);
+int hb_get_spectral_path(const hb_problem *p);
 /* Element-kernel timing: when enabled, every launch of the fused element kernel is bracketed by CUDA
  * events on the stream it is launched on.  hb_profile_read synchronises with those events, returns the
  * summed device time in milliseconds and the number of launches since the last read, and resets. */

@@ -174,6 +174,7 @@ struct hb_problem {
     int jvp_variant = 1;                  // launch variant of the FP32 paper-tangent pass
     DBuf<int> d_err;                      // status word of the pipelined element pass (0: no wait gave up)
     int stab = 0;                         // 0: GLS as printed; 1: full RBVMS (hb_set_stabilization)
+    int spectral_path = 1;                // FP32 W pass: 0 tcgen05, 1 mma.sync, 2 FMAs (hb_set_spectral_path)
     double ct_dt = 0;                     // coefficient of (1 / dt)^2 under the root of tau, dt = T / N
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev;
     size_t prof_used = 0;
@@ -772,7 +773,8 @@ hb_status apply_op(hb_problem *p, int mode, const T *y, const T *v, T *out, doub
         using B = AsmBufs<T>;
         if (!B::ready(A)) return fail(HB_ERR_STATE, "no assembled operator in this precision (hb_assemble_dev)");
         const int ws = w_stride(N, int(sizeof(T)));
-        launch_spectral_w<T>(v, Hmat<T>(p), p->d_flag.p, B::W(A).p, ws, p->n_nodes, N, T(p->rho), T(shift), shift_dev, s);
+        launch_spectral_w<T>(v, Hmat<T>(p), p->d_flag.p, B::W(A).p, ws, p->n_nodes, N, T(p->rho), T(shift), shift_dev, s,
+                             p->spectral_path, p->d_err.p);
         SpmvArgs<T> sa;
         sa.n_nodes = p->n_nodes;
         sa.N = N;
@@ -817,7 +819,8 @@ hb_status apply_op(hb_problem *p, int mode, const T *y, const T *v, T *out, doub
             DBuf<T> &W = B::W(p->as);
             const int ws = w_stride(N, int(sizeof(T)));
             HB_TRY(dalloc(p, W, size_t(p->n_nodes) * size_t(ws)));
-            launch_spectral_w<T>(v, Hmat<T>(p), p->d_flag.p, W.p, ws, p->n_nodes, N, T(p->rho), T(shift), shift_dev, s);
+            launch_spectral_w<T>(v, Hmat<T>(p), p->d_flag.p, W.p, ws, p->n_nodes, N, T(p->rho), T(shift), shift_dev, s,
+                                 p->spectral_path, p->d_err.p);
             HB_LAUNCHED(p, 1);
             ea.W = W.p;
         }
@@ -2652,6 +2655,19 @@ hb_status hb_set_stabilization(hb_problem *p, int variant, double ct_dt) {
     p->as.ready32 = p->as.ready64 = false;
     return HB_OK;
 }
+
+hb_status hb_set_spectral_path(hb_problem *p, int path) {
+    if (!p) return fail(HB_ERR_INVALID_ARG, "null problem");
+    if (path < 0 || path > 2) return fail(HB_ERR_INVALID_ARG, "path must be 0 (tcgen05), 1 (mma.sync) or 2 (FMA)");
+    p->spectral_path = path;
+    for (auto &gc : p->cycle) {                   // captured cycles hold the old launch
+        if (gc.exec) cudaGraphExecDestroy(gc.exec);
+        gc = hb_problem::CycleGraph{};
+    }
+    return HB_OK;
+}
+
+int hb_get_spectral_path(const hb_problem *p) { return p ? p->spectral_path : -1; }
 
 hb_status hb_set_launch_variant(hb_problem *p, int variant) {
     if (!p) return fail(HB_ERR_INVALID_ARG, "null problem");

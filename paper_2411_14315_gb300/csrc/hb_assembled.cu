@@ -454,11 +454,12 @@ void launch_assemble_mass(const AsmArgs<T> &a, cudaStream_t s) {
 
 template <typename T>
 void launch_spectral_w(const T *v, const T *H, const uint8_t *flag, T *W, int ws, int64_t n_nodes, int N, T rho,
-                       T shift, const double *shift_dev, cudaStream_t s) {
+                       T shift, const double *shift_dev, cudaStream_t s, int path, int *err) {
     if (n_nodes == 0) return;
     if constexpr (sizeof(T) == 4) {
-        // FP32 at the compile-time instance counts: the tensor-core form
-        switch (N) {
+        // FP32 at the compile-time instance counts: the tensor-core forms
+        if (path == 0 && launch_spectral_w_tc5(v, H, flag, W, n_nodes, N, rho, shift, shift_dev, err, s)) return;
+        if (path <= 1) switch (N) {
             case 9: launch_spectral_tc<9>(v, H, flag, W, n_nodes, rho, shift, shift_dev, s); return;
             case 13: launch_spectral_tc<13>(v, H, flag, W, n_nodes, rho, shift, shift_dev, s); return;
             case 21: launch_spectral_tc<21>(v, H, flag, W, n_nodes, rho, shift, shift_dev, s); return;
@@ -489,9 +490,9 @@ template void launch_assemble<double>(const AsmArgs<double> &, cudaStream_t);
 template void launch_assemble_mass<float>(const AsmArgs<float> &, cudaStream_t);
 template void launch_assemble_mass<double>(const AsmArgs<double> &, cudaStream_t);
 template void launch_spectral_w<float>(const float *, const float *, const uint8_t *, float *, int, int64_t, int, float,
-                                       float, const double *, cudaStream_t);
+                                       float, const double *, cudaStream_t, int, int *);
 template void launch_spectral_w<double>(const double *, const double *, const uint8_t *, double *, int, int64_t, int,
-                                        double, double, const double *, cudaStream_t);
+                                        double, double, const double *, cudaStream_t, int, int *);
 template void launch_spmv<float>(const SpmvArgs<float> &, cudaStream_t);
 template void launch_block_jacobi<float, float>(const float *, const float *, const int *, const uint8_t *,
                                                 const double *, float *, int64_t, int, double, const double *,

@@ -272,10 +272,15 @@ template <typename T>
 void launch_assemble(const AsmArgs<T> &a, cudaStream_t s);
 template <typename T>
 void launch_assemble_mass(const AsmArgs<T> &a, cudaStream_t s);
-// W = shift v + rho H v (velocity rows; H [N][N]; shift from shift_dev if set), rows of ws values
+// W = shift v + rho H v (velocity rows; H [N][N]; shift from shift_dev if set), rows of ws values.
+// FP32 at N = 9, 13, 21: path 0 = tcgen05 tensor cores with a TMEM accumulator (needs err, the status word
+// of its bounded waits), 1 = warp-level mma.sync, 2 = FP32 FMAs; FP64 and other N always take the FMAs.
 template <typename T>
 void launch_spectral_w(const T *v, const T *H, const uint8_t *flag, T *W, int ws, int64_t n_nodes, int N, T rho,
-                       T shift, const double *shift_dev, cudaStream_t s);
+                       T shift, const double *shift_dev, cudaStream_t s, int path = 1, int *err = nullptr);
+// the tcgen05 form (hb_spectral_tc5.cu); false if it has no kernel for N
+bool launch_spectral_w_tc5(const float *v, const float *H, const uint8_t *flag, float *W, int64_t n_nodes, int N,
+                           float rho, float shift, const double *shift_dev, int *err, cudaStream_t s);
 template <typename T>
 void launch_spmv(const SpmvArgs<T> &a, cudaStream_t s);
 // z = (node-block diagonal of the assembled tangent + shift M_AA)^-1 x per node and instance; dpos[A] is

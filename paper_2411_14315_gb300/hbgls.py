@@ -118,6 +118,8 @@ SIGNATURES = {
     "hb_launch_count": ([_P], C.c_int64),
     "hb_set_launch_variant": ([_P, C.c_int], C.c_int),
     "hb_get_launch_variant": ([_P], C.c_int),
+    "hb_set_spectral_path": ([_P, C.c_int], C.c_int),
+    "hb_get_spectral_path": ([_P], C.c_int),
     "hb_profile_elem": ([_P, C.c_int], C.c_int),
     "hb_profile_read": ([_P, C.POINTER(C.c_double), C.POINTER(C.c_int64)], C.c_int),
     "hb_jv_dev_noalloc": ([_P, _VP, _VP, _VP, C.c_int, C.c_int, C.c_double, _VP], C.c_int),
@@ -407,6 +409,13 @@ class Problem:
 
     def set_launch_variant(self, variant: int):
         _check(lib().hb_set_launch_variant(self._h, int(variant)))
+
+    def set_spectral_path(self, path: int):
+        """hb_set_spectral_path: 0 = tcgen05, 1 = mma.sync, 2 = FP32 FMAs (FP32, N = 9, 13, 21)."""
+        _check(lib().hb_set_spectral_path(self._h, int(path)))
+
+    def spectral_path(self) -> int:
+        return int(lib().hb_get_spectral_path(self._h))
 
     def launch_variant(self) -> int:
         return int(lib().hb_get_launch_variant(self._h))

@@ -241,3 +241,38 @@ def test_full_size_glenn_sampled_parity():
         got = run()[nodes]
         ref = _sampled_oracle(spec, y, vv, nodes, fn)
         assert relerr(got, ref) < 1e-5
+
+
+@pytest.mark.parametrize("n_h", [4, 6, 10])
+@pytest.mark.parametrize("path", [0, 1, 2])
+def test_spectral_pass_paths(n_h, path):
+    """The node-level W = shift v + rho H v pass on each implementation (tcgen05 with a TMEM accumulator,
+    warp-level mma.sync, FP32 FMAs) inside the paper-tangent Jv, fused and assembled, against the oracle
+    (N = 9, 13, 21; a ragged last 128-row tile)."""
+    spec = P.box_spec(seed=80 + n_h, n_h=n_h, n=(7, 5, 4))
+    ora = P.oracle_problem(spec)
+    gp = P.gpu_problem(spec)
+    gp.set_spectral_path(path)
+    assert gp.spectral_path() == path
+    y = I.random_state(spec.mesh.n_nodes, spec.N, 81)
+    v = I.random_state(spec.mesh.n_nodes, spec.N, 82)
+    ref = O.jv_paper(ora, y, v, shift=0.9)
+    assert relerr(gp.jv(y, v, 0, 1, 0.9), ref) < TOL[1]
+    assert relerr(gp.jv(y, v, 2, 1, 0.9), ref) < TOL[1]
+    gp.close()
+
+
+def test_spectral_tcgen05_many_tiles():
+    """tcgen05 spectral pass over ~65k velocity rows (hundreds of 128-row tiles, several per block, rows of a
+    node split across tiles) inside the FP32 paper-tangent Jv, against the oracle."""
+    spec = P.glenn_spec(n_tets=120_000)
+    ora = P.oracle_problem(spec)
+    gp = P.gpu_problem(spec)
+    gp.set_spectral_path(0)
+    y = I.random_state(spec.mesh.n_nodes, spec.N, 83).astype(np.float32).astype(np.float64)
+    v = I.random_state(spec.mesh.n_nodes, spec.N, 84).astype(np.float32).astype(np.float64)
+    ref = O.jv_paper(ora, y, v, shift=250.0)
+    assert relerr(gp.jv(y, v, 0, 1, 250.0), ref) < TOL[1]
+    with pytest.raises(RuntimeError):
+        gp.set_spectral_path(3)
+    gp.close()

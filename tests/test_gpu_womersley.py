@@ -2,7 +2,8 @@
 
 The pipe is driven by the exact inflow harmonics (general per-point Dirichlet data); the outlet is
 traction free.  Convection vanishes and the flow is band-limited in time, so the harmonic balance
-error is purely spatial: the velocity error must fall by about 4x per halving of the cell size (P1)."""
+error is purely spatial: the velocity error must fall at second order in the cell size (P1), fitted over
+three refinements."""
 import math
 
 import numpy as np
@@ -40,15 +41,19 @@ def test_harmonic_inflow_residual_matches_oracle():
 
 
 def test_womersley_second_order_convergence():
-    errs = []
-    for level in (1, 2):
+    """Three refinements of the pipe (~3k, ~24k, ~196k tetrahedra, each halving the cell size): the solved
+    velocity error against Womersley's solution fits an order >= 1.8 in h (P1 gives 2)."""
+    errs, hs = [], []
+    for level in (1, 2, 3):
         spec, exact = _spec(level)
         gp = P.gpu_problem(spec)
-        rep = gp.solve(precision=1, rtol=1e-10, max_steps=300)
+        rep = gp.solve(precision=1, rtol=1e-9, max_steps=400)
         assert rep["status"] == 0
         h = gp.harmonics()
         errs.append(float(np.linalg.norm(h[:, :3] - exact[:, :3]) / np.linalg.norm(exact[:, :3])))
+        hs.append(2.0 ** (1 - level))
         gp.close()
-    print("Womersley velocity errors by level:", errs)
+    order = np.polyfit(np.log(hs), np.log(errs), 1)[0]
+    print("Womersley velocity errors by level:", errs, "fitted order:", order)
     assert errs[0] < 0.08
-    assert errs[1] < errs[0] / 2.5
+    assert order >= 1.8
