@@ -68,6 +68,11 @@ def parse():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
     ap.add_argument("--extra", action="store_true", help="also time residual / exact Jv / FP64 rates")
+    ap.add_argument("--skip-variants", action="store_true", help="skip the per-launch-variant element timings")
+    ap.add_argument("--profile-small", type=int, default=0, metavar="TETS",
+                    help="run the small-case workload the ncu captures use (a Glenn-like T-junction of ~TETS tets at "
+                         "N = 21: FP32 paper-tangent Jv, the assembled tangent's product, one GMRES restart cycle, and "
+                         "a network prediction on a 30k-tet coronary-like tube) and exit")
     ap.add_argument("--march", action="store_true",
                     help="also time the conventional time-marching solver against the HB solve on the Womersley "
                          "pipe (~3,000 tets, N = 9)")
@@ -283,6 +288,61 @@ def time_solves():
         p.close()
     ref.close()
     return out
+
+
+def time_stab_variants():
+    """Sec. 2.2's stabilisation variants on the Womersley pipe (~3,000 tets, N = 9, mixed precision, to
+    1e-8): GLS as printed, full RBVMS, and the (1/dt)^2 term in tau (ct = 1): steps, GMRES iterations,
+    seconds, and the distance of each solution from the GLS one."""
+    from paper_2411_14315_gb300 import hbgls
+    from paper_2411_14315_gb300 import workloads as W
+    spec = W.womersley_spec()
+    out = {"workload": f"womersley pipe {spec.mesh.n_tets} tets N={spec.N}"}
+    ref = None
+    for name, var, ct in (("gls", 0, 0.0), ("rbvms", 1, 0.0), ("gls_dt_in_tau", 0, 1.0)):
+        p = hbgls.Problem.from_spec(spec)
+        p.set_stabilization(var, ct)
+        rep = p.solve(precision=1, rtol=1e-8, max_steps=300, check=False)
+        y = p.instances()
+        if ref is None:
+            ref = y
+        out[name] = {"status": rep["status"], "steps": rep["steps"], "gmres_iters": rep["gmres_iters"],
+                     "seconds": rep["seconds"],
+                     "rel_diff_vs_gls": float(np.linalg.norm(y - ref) / np.linalg.norm(ref))}
+        p.close()
+    return out
+
+
+def time_spectral_paths(prob, y32, v32, flush, stream, shift, reps: int = 20):
+    """The node-level W = shift v + rho H v pass on each implementation (tcgen05 with a TMEM accumulator,
+    warp-level mma.sync, FP32 FMAs), timed as a whole paper-tangent Jv with that path and as the same Jv
+    minus its element pass (the W pass plus the boundary kernels)."""
+    import torch
+
+    from paper_2411_14315_gb300 import hbgls
+    path0 = prob.spectral_path()
+    o = torch.empty_like(v32)
+    res = {}
+    for path in (0, 1, 2):
+        prob.set_spectral_path(path)
+        prob.jv_dev(y32, v32, o, hbgls.PAPER, hbgls.FP32, shift, stream=stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tot = 0.0
+        prob.profile_read()
+        prob.profile_elem(True)
+        for i in range(reps):
+            flush.fill_(float(i))
+            e0.record(stream)
+            prob.jv_dev(y32, v32, o, hbgls.PAPER, hbgls.FP32, shift, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+        prob.profile_elem(False)
+        ems, en = prob.profile_read()
+        res[["tcgen05", "mma_sync", "fma"][path]] = {"jv_ms": tot / reps, "jv_minus_elem_ms": tot / reps - ems / max(1, en)}
+    prob.set_spectral_path(path0)
+    return res
 
 
 def time_workloads(flush, stream, reps: int = 20):
@@ -550,6 +610,11 @@ def run_ours(args, dist: Dist, spec, config):
     except Exception as e:  # reported, not hidden
         result["assembled_jv"] = {"error": repr(e)}
 
+    try:
+        result["spectral_pass"] = time_spectral_paths(prob, y32, v32, flush, stream, shift)
+    except Exception as e:  # reported, not hidden
+        result["spectral_pass"] = {"error": repr(e)}
+
     # end to end through the C ABI with pinned host buffers
     if not args.skip_e2e:
         hy = torch.empty((n, 4, N), dtype=torch.float64, pin_memory=True).numpy()
@@ -566,9 +631,26 @@ def run_ours(args, dist: Dist, spec, config):
             prob.jv(hy, hv, kind=hbgls.PAPER, precision=hbgls.FP32, shift=shift, out=ho)
         e2e_rate, te = whole_job_rate(dist, units, (time.perf_counter() - t0) / ke)
         nb = n * 4 * N * 8
-        result["e2e"] = {"value": e2e_rate, "unit": UNIT, "h2d_bytes_per_step": 2 * nb,
-                         "d2h_bytes_per_step": nb, "ms_per_step": 1e3 * te,
-                         "path": "hb_jv (host float64 buffers, FP32 kernels)"}
+        e2e64 = {"value": e2e_rate, "unit": UNIT, "h2d_bytes_per_step": 2 * nb, "d2h_bytes_per_step": nb,
+                 "ms_per_step": 1e3 * te, "path": "hb_jv (host float64 buffers, FP32 kernels)"}
+        # the FP32 host-buffer entry point: the kernels compute in FP32 either way, half the bytes cross
+        hy32 = torch.empty((n, 4, N), dtype=torch.float32, pin_memory=True).numpy()
+        hv32 = torch.empty((n, 4, N), dtype=torch.float32, pin_memory=True).numpy()
+        ho32 = torch.empty((n, 4, N), dtype=torch.float32, pin_memory=True).numpy()
+        hy32[...] = y
+        hv32[...] = v
+        for _ in range(2):
+            prob.jv_f32(hy32, hv32, kind=hbgls.PAPER, shift=shift, out=ho32)
+        dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            prob.jv_f32(hy32, hv32, kind=hbgls.PAPER, shift=shift, out=ho32)
+        e2e32_rate, te32 = whole_job_rate(dist, units, (time.perf_counter() - t0) / ke)
+        nb32 = n * 4 * N * 4
+        result["e2e"] = {"value": e2e32_rate, "unit": UNIT, "h2d_bytes_per_step": 2 * nb32,
+                         "d2h_bytes_per_step": nb32, "ms_per_step": 1e3 * te32,
+                         "path": "hb_jv_f32 (host float32 buffers, FP32 kernels)"}
+        result["e2e_fp64_host"] = e2e64
 
     if args.extra:
         rates = {}
@@ -594,10 +676,11 @@ def run_ours(args, dist: Dist, spec, config):
                 tot += e0.elapsed_time(e1)
             rates[name] = units / (tot / reps / 1e3)
         result["other_rates"] = rates
+    if not args.skip_variants:
         # element-pass time of each launch variant of the FP32 paper-tangent pass
         var0 = prob.launch_variant()
         var_ms = {}
-        for var in range(4):
+        for var in range(7):
             prob.set_launch_variant(var)
             jv()
             torch.cuda.synchronize()
@@ -612,6 +695,7 @@ def run_ours(args, dist: Dist, spec, config):
             var_ms[str(var)] = t / max(1, c)
         prob.set_launch_variant(var0)
         result["jvp_variant_elem_ms"] = var_ms
+    if args.extra:
         result["other_workloads"] = time_workloads(flush, stream)
 
     if dist.rank == 0 and dist.world == 1:
@@ -625,6 +709,10 @@ def run_ours(args, dist: Dist, spec, config):
                 result["time_to_solve"] = time_solves()
             except Exception as e:  # reported, not hidden
                 result["time_to_solve"] = {"error": repr(e)}
+            try:
+                result["stabilisation_variants"] = time_stab_variants()
+            except Exception as e:  # reported, not hidden
+                result["stabilisation_variants"] = {"error": repr(e)}
         if not args.skip_cpu:
             result["cpu_baseline"] = cpu_baseline(spec)
     if args.march and dist.rank == 0:
@@ -644,8 +732,47 @@ def run_ours(args, dist: Dist, spec, config):
         print(json.dumps(result), flush=True)
 
 
+def profile_small(n_tets: int):
+    """The small case of the profile summaries (one capture per kernel, a few launches each)."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2411_14315_gb300 import hbgls
+    from paper_2411_14315_gb300 import inputs as I
+    from paper_2411_14315_gb300 import workloads as W
+    spec = W.glenn_spec(n_tets=n_tets)
+    s = torch.cuda.Stream()
+    torch.cuda.set_stream(s)
+    p = hbgls.Problem.from_spec(spec, stream=s)
+    n, N = spec.mesh.n_nodes, spec.N
+    y = torch.tensor(I.random_state(n, N, 81), dtype=torch.float32, device="cuda")
+    v = torch.tensor(I.random_state(n, N, 82), dtype=torch.float32, device="cuda")
+    o = torch.empty_like(y)
+    for _ in range(3):
+        p.jv_dev(y, v, o, hbgls.PAPER, hbgls.FP32, 300.0, stream=s)
+    p.assemble_dev(y, hbgls.FP32, stream=s)
+    for _ in range(3):
+        p.jv_dev(y, v, o, hbgls.ASSEMBLED, hbgls.FP32, 300.0, stream=s)
+    torch.cuda.synchronize()
+    rep = p.solve(precision=1, max_steps=1, gmres_restart=30, max_gmres=30, rtol=1e-12, gmres_rtol_pseudo=1e-12,
+                  check=False)
+    torch.cuda.synchronize()
+    cs = W.coronary_spec(n_tets=30_000, n_h=4)
+    cp = hbgls.Problem.from_spec(cs)
+    net = hbgls.MPNN(cs.n_h, seed=3)
+    for _ in range(2):
+        net.predict(cp)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_small": {"n_tets": spec.mesh.n_tets, "n_nodes": n, "patches": p.info()["n_patches32"],
+                                        "gmres_iters": rep["gmres_iters"]}}))
+
+
 def main():
     args = parse()
+    if args.profile_small:
+        profile_small(args.profile_small)
+        return
     dist = Dist()
     from paper_2411_14315_gb300 import workloads as W
     spec = W.glenn_spec(n_tets=args.tets, n_h=args.n_h)

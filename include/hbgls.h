@@ -140,8 +140,17 @@ typedef struct {
                                  (hb_assemble_dev) and let GMRES apply it as a sparse product          */
     int precond;              /* 0: Jacobi on diag(P) + shift M (Sec. 2.3); 1: node blocks (4 x 4 per
                                  node and instance) of the assembled paper tangent + shift M, inverted
-                                 through their pressure Schur complement (an extension; assembles the
-                                 tangent every outer step)                                            */
+                                 through their pressure Schur complement; 2: one V-cycle of aggregation
+                                 multigrid on the assembled paper tangent + shift M (greedy node
+                                 aggregates, Galerkin coarse operators, damped node-block Jacobi
+                                 smoothing); 1 and 2 are extensions that assemble the tangent every outer
+                                 step                                                                  */
+    int line_search;          /* 1 (default): after the switch, exact Newton without the pseudo shift and a
+                                 backtracking line search on ||r|| (step halved up to 4 times until
+                                 ||r|| falls by at least 1e-4 of the step fraction; if none does, the
+                                 step is retaken with the pseudo shift); 0: the pseudo shift stays in the
+                                 Newton phase until dt exceeds ser_max times the CFL step (an extension
+                                 either way; the paper stops at the switch criterion, Sec. 2.3)        */
 } hb_solve_opts;
 
 typedef struct {
@@ -175,6 +184,9 @@ hb_status hb_residual(hb_problem *p, const double *y, double *r, int precision);
  * Dirichlet velocity rows return v (identity); v's Dirichlet velocity entries are treated as 0. */
 hb_status hb_jv(hb_problem *p, const double *y, const double *v, double *jv, int kind, int precision,
                 double shift);
+/* The same product with FP32 host buffers (FP32 kernels): y, v, jv float [n_nodes][4][N].  Half the bytes
+ * of hb_jv's FP64 buffers cross the host link; otherwise identical to hb_jv with precision 1. */
+hb_status hb_jv_f32(hb_problem *p, const float *y, const float *v, float *jv, int kind, double shift);
 /* Jacobi diagonal: diag(P) + shift M_AA (Sec. 2.3); 1 on Dirichlet velocity rows. */
 hb_status hb_jacobi_diag(hb_problem *p, const double *y, double *d, int precision, double shift);
 
@@ -203,8 +215,9 @@ hb_status hb_jacobi_diag_dev(hb_problem *p, const void *y, void *d, int precisio
  *    flow rates of resistance outlets) is a file-scope device array of 4096 doubles that every GPU
  *    which loads the library holds until the process exits;
  *  - outlets x instances above 4096 is rejected with HB_ERR_INVALID_ARG;
- *  - the boundary data must already be prepared: after the last hb_set_* call, call hb_get_info (or any
- *    other entry point) once; otherwise HB_ERR_STATE;
+ *  - the boundary data must already be prepared: after the last hb_set_* boundary call (and after
+ *    hb_set_launch_variant or hb_tune_patches), call one of hb_get_info, hb_residual*, hb_jv*,
+ *    hb_jacobi_diag* or hb_solve once; otherwise HB_ERR_STATE;
  *  - the first call on a device looks up the scratch array's device address (cudaGetSymbolAddress, with
  *    that device current); make that first call before any stream capture;
  *  - all calls in the process share the one scratch array per device and it keeps the last call's
@@ -237,6 +250,10 @@ typedef struct {
 hb_status hb_mpnn_create(const hb_mpnn_config *cfg, int device, hb_mpnn **out);
 /* Free a network; NULL is accepted. */
 hb_status hb_mpnn_destroy(hb_mpnn *net);
+/* Forward MLP products on the tensor cores (default on; hidden 32 or 64): mma.sync TF32 with FP32
+ * accumulation, the FP32 activations split into a TF32 head and tail against the BF16 weights (exact in
+ * TF32), so the result keeps FP32 accuracy; 0 selects the FP32-FMA kernels.  INVALID_ARG for NULL. */
+hb_status hb_mpnn_set_tensor_cores(hb_mpnn *net, int enable);
 /* Number of FP32 parameters (the length of get/set and gradient arrays); 0 for NULL. */
 int64_t hb_mpnn_num_params(const hb_mpnn *net);
 hb_status hb_mpnn_get_params(hb_mpnn *net, float *params);          /* host [num_params] */
@@ -311,9 +328,11 @@ hb_status hb_get_march_samples(hb_problem *p, double *out);
 
 /* ---- batches of problems (many vessels of uneven size and N in one graph) ---------------------------
  * A batch applies the operator of every member problem in one captured CUDA graph: the output
- * clearing, one persistent element pass per distinct instance count N (specialised for that N) whose
- * work items (problem, patch) are taken from a global counter (so large and small problems share the
- * SMs; the FP32 paper-tangent pass takes the first problem's launch variant, see hb_set_launch_variant),
+ * clearing, for the paper's tangent each member's node-level W = shift v + rho H v pass (the graph runs them
+ * as parallel branches), one persistent element pass over every member (each member's patches run the pass
+ * specialised for its N) whose work items (problem, patch) are taken from a global counter (so large and
+ * small problems of any N share the SMs; the FP32 paper-tangent pass takes the first problem's launch
+ * variant, see hb_set_launch_variant),
  * then the boundary terms of each problem (prescribed velocity rows are written by the element pass).
  * All problems must live on one device; their boundary data are prepared at creation.  The graph is captured on first use and again whenever the
  * operands, kind or shift change.  Work is ordered after `stream` (NULL: the first problem's stream) and
@@ -356,12 +375,12 @@ int64_t hb_launch_count(const hb_problem *p);
  * 0 = 256 threads per block, two instances per thread on paired FP32 instructions; 1 = 384 threads,
  * one instance per thread (the default); 2 = 512 threads, one instance per thread; 3 = 192 threads, one
  * instance per thread, four resident blocks per SM (pays with patches small enough for four blocks'
- * shared memory, see hb_tune_patches); 4 = pipelined: one block per SM with a producer warp that copies
- * the next patch's rows with bulk asynchronous copies into a second shared-memory stage while 20
- * consumer warps compute (one instance per thread); 5 = the same with 15 consumer warps on instance pairs
- * and paired FP32 instructions.  Variants 4 and 5 need N = 9, 13 or 21 and the node-level W pass of
- * hb_jv_dev (elsewhere, e.g. in hb_jv_dev_noalloc and batches, they run variant 1).  All give the same
- * operator up to FP32 rounding.  hb_tune_patches also searches it for precision 1.  HB_ERR_INVALID_ARG
+ * shared memory, see hb_tune_patches); 4 = pipelined: one block per SM, 4 producer warps copy the next
+ * patch's rows into a second shared-memory stage (16-byte asynchronous copies completing on an mbarrier)
+ * while 20 consumer warps compute (one instance per thread); 5 = the same with 12 consumer warps on
+ * instance pairs and paired FP32 instructions; 6 = as 4 with one producer warp issuing 1-D bulk copies.
+ * Variants 4-6 need N = 9, 13 or 21 and the node-level W pass of hb_jv_dev (elsewhere, e.g. in
+ * hb_jv_dev_noalloc and batches, they run variant 1).  All give the same operator up to FP32 rounding.  hb_tune_patches also searches it for precision 1.  HB_ERR_INVALID_ARG
  * for another value.  hb_get_launch_variant returns the current variant (-1 for a null problem). */
 hb_status hb_set_launch_variant(hb_problem *p, int variant);
 int hb_get_launch_variant(const hb_problem *p);

@@ -12,7 +12,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libhbgls.so")
 SOURCES = ["hb_element.cu", "hb_boundary.cu", "hb_vec.cu", "hb_api.cu", "hb_mpnn.cu", "hb_assembled.cu",
-           "hb_spectral_tc5.cu"]
+           "hb_spectral_tc5.cu", "hb_amg.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
          "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "-I", os.path.join(ROOT, "include"), "-I", CSRC]

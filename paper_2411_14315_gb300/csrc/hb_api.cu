@@ -54,6 +54,20 @@ struct DBuf {
     DBuf() = default;
     DBuf(const DBuf &) = delete;
     DBuf &operator=(const DBuf &) = delete;
+    DBuf(DBuf &&o) noexcept : p(o.p), n(o.n) {
+        o.p = nullptr;
+        o.n = 0;
+    }
+    DBuf &operator=(DBuf &&o) noexcept {
+        if (this != &o) {
+            release();
+            p = o.p;
+            n = o.n;
+            o.p = nullptr;
+            o.n = 0;
+        }
+        return *this;
+    }
     ~DBuf() { release(); }
     void swap(DBuf &o) {
         std::swap(p, o.p);
@@ -156,6 +170,7 @@ struct hb_problem {
     // element-kernel timing
     bool prof_on = false;
     DBuf<double> ylearn, kd;              // learned prediction and the direction towards it (use_learned 2)
+    DBuf<double> yprev;                   // state before a Newton step (line search)
     // assembled paper tangent (Sec. 4's condensed storage): CSR of node pairs, element -> pair slots
     struct Assembled {
         int64_t nnz = 0;
@@ -164,7 +179,21 @@ struct hb_problem {
         DBuf<double> geom64, coef64, mass64, W64;
         bool ready32 = false, ready64 = false;   // coefficients assembled (at the last state given)
         bool mass32_done = false, mass64_done = false;
+        std::vector<int> h_rowptr, h_col;         // host copy of the pair structure (multigrid set-up)
     } as;
+    // aggregation multigrid on the assembled tangent (precond = 2): level 0 is `as`; levels 1.. are built
+    struct AmgLevel {
+        int64_t n = 0, nnz = 0;
+        DBuf<int> rowptr, col, dpos;              // levels >= 1
+        DBuf<uint8_t> flag;                       // levels >= 1 (bit 0: velocity prescribed)
+        DBuf<int> agg, aptr, aidx;                // to the next level: node -> aggregate, aggregate -> nodes
+        DBuf<int> cptr, cidx;                     // next level's pairs -> this level's pairs
+        DBuf<uint8_t> mmask;                      // this level's pairs whose two nodes are free
+        DBuf<float> coef32, mass32, x32, b32, r32, ax32, W32;
+        DBuf<double> coef64, mass64, x64, b64, r64, ax64, W64;
+    };
+    std::vector<AmgLevel> amg;
+    bool amg_mass32 = false, amg_mass64 = false;
     double omega2 = 0;                    // acceleration term of tau_hat in the element passes (time domain)
     int ls_mass = 0;                      // time domain: the shift enters the tangent's least-squares L too
     hb_problem *tm = nullptr;             // internal one-instance copy that runs the time-domain march
@@ -674,6 +703,8 @@ hb_status asm_structure(hb_problem *p) {
     HB_TRY(upload(p, A.dpos, dpos));
     HB_TRY(upload(p, A.rowptr, rowptr));
     HB_TRY(upload(p, A.col, col));
+    A.h_rowptr = rowptr;
+    A.h_col = col;
     HB_TRY(upload(p, A.tets, tets));
     HB_TRY(upload(p, A.epos, epos));
     A.nnz = int64_t(col.size());
@@ -957,13 +988,289 @@ hb_status dev_dot(hb_problem *p, const double *x, const double *y, int64_t n, do
     return HB_OK;
 }
 
+// pseudo shift of an operator application (value, or device word if set)
+struct OpCtxShift {
+    double shift;
+    const double *dev;
+};
+
+// ---------------------------------------------------------------------------------------------------
+// aggregation multigrid (precond = 2): hierarchy, coarse operators, V-cycle
+
+constexpr int kAmgCoarsest = 400;      // stop coarsening below this many nodes
+constexpr int kAmgMaxLevels = 8;
+constexpr double kAmgOmega = 0.7;      // damping of the node-block Jacobi smoother
+constexpr int kAmgPre = 2, kAmgPost = 2, kAmgCoarseSweeps = 8;
+
+// greedy aggregation of a node graph (CSR with the diagonal): roots whose neighbours are all unassigned
+// take them; remaining nodes join a neighbouring aggregate of the first pass; isolated leftovers are alone
+int aggregate(const std::vector<int> &rowptr, const std::vector<int> &col, int64_t n, std::vector<int> &agg) {
+    agg.assign(size_t(n), -1);
+    int nc = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (agg[size_t(i)] != -1) continue;
+        bool free = true;
+        for (int k = rowptr[size_t(i)]; k < rowptr[size_t(i) + 1] && free; ++k) free = agg[size_t(col[size_t(k)])] == -1;
+        if (!free) continue;
+        for (int k = rowptr[size_t(i)]; k < rowptr[size_t(i) + 1]; ++k) agg[size_t(col[size_t(k)])] = nc;
+        ++nc;
+    }
+    std::vector<int> tent(agg);
+    for (int64_t i = 0; i < n; ++i) {
+        if (agg[size_t(i)] != -1) continue;
+        for (int k = rowptr[size_t(i)]; k < rowptr[size_t(i) + 1]; ++k)
+            if (agg[size_t(col[size_t(k)])] != -1) {
+                tent[size_t(i)] = agg[size_t(col[size_t(k)])];
+                break;
+            }
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        if (tent[size_t(i)] == -1) tent[size_t(i)] = nc++;
+    }
+    agg.swap(tent);
+    return nc;
+}
+
+hb_status amg_build(hb_problem *p) {
+    if (!p->amg.empty()) return HB_OK;
+    hb_problem::Assembled &A = p->as;
+    std::vector<int> rowptr = A.h_rowptr, col = A.h_col;
+    std::vector<uint8_t> flag(static_cast<size_t>(p->n_nodes));
+    HB_CUDA(cudaMemcpy(flag.data(), p->d_flag.p, flag.size(), cudaMemcpyDeviceToHost));
+    int64_t n = p->n_nodes;
+    std::vector<hb_problem::AmgLevel> lv(1);
+    lv[0].n = n;
+    lv[0].nnz = A.nnz;
+    while (n > kAmgCoarsest && int(lv.size()) < kAmgMaxLevels) {
+        std::vector<int> agg;
+        const int nc = aggregate(rowptr, col, n, agg);
+        if (nc >= n * 9 / 10) break;                         // no useful coarsening left
+        // coarse pair structure and the fine pairs of each coarse pair
+        std::vector<std::vector<int>> crow(static_cast<size_t>(nc));
+        for (int64_t i = 0; i < n; ++i)
+            for (int k = rowptr[size_t(i)]; k < rowptr[size_t(i) + 1]; ++k)
+                crow[size_t(agg[size_t(i)])].push_back(agg[size_t(col[size_t(k)])]);
+        std::vector<int> crp(size_t(nc) + 1, 0), ccol;
+        for (int I = 0; I < nc; ++I) {
+            std::vector<int> &r = crow[size_t(I)];
+            std::sort(r.begin(), r.end());
+            r.erase(std::unique(r.begin(), r.end()), r.end());
+            ccol.insert(ccol.end(), r.begin(), r.end());
+            crp[size_t(I) + 1] = int(ccol.size());
+        }
+        const int64_t cnnz = int64_t(ccol.size());
+        const size_t fnnz = size_t(rowptr[size_t(n)]);
+        std::vector<int> owner(fnnz);                           // fine pair -> coarse pair
+        std::vector<uint8_t> mmask(owner.size());
+        for (int64_t i = 0; i < n; ++i)
+            for (int k = rowptr[size_t(i)]; k < rowptr[size_t(i) + 1]; ++k) {
+                const int I = agg[size_t(i)], J = agg[size_t(col[size_t(k)])];
+                owner[size_t(k)] = int(std::lower_bound(ccol.data() + crp[size_t(I)], ccol.data() + crp[size_t(I) + 1], J) -
+                                       ccol.data());
+                mmask[size_t(k)] = !(flag[size_t(i)] & 1) && !(flag[size_t(col[size_t(k)])] & 1);
+            }
+        std::vector<int> cptr(size_t(cnnz) + 1, 0), cidx(owner.size());
+        for (int o : owner) ++cptr[size_t(o) + 1];
+        for (int64_t q = 0; q < cnnz; ++q) cptr[size_t(q) + 1] += cptr[size_t(q)];
+        {
+            std::vector<int> fill(cptr.begin(), cptr.end() - 1);
+            for (size_t k = 0; k < owner.size(); ++k) cidx[size_t(fill[size_t(owner[k])]++)] = int(k);
+        }
+        std::vector<int> aptr(size_t(nc) + 1, 0), aidx(static_cast<size_t>(n));
+        for (int64_t i = 0; i < n; ++i) ++aptr[size_t(agg[size_t(i)]) + 1];
+        for (int I = 0; I < nc; ++I) aptr[size_t(I) + 1] += aptr[size_t(I)];
+        {
+            std::vector<int> fill(aptr.begin(), aptr.end() - 1);
+            for (int64_t i = 0; i < n; ++i) aidx[size_t(fill[size_t(agg[size_t(i)])]++)] = int(i);
+        }
+        std::vector<uint8_t> cflag(static_cast<size_t>(nc), 1);
+        for (int64_t i = 0; i < n; ++i)
+            if (!(flag[size_t(i)] & 1)) cflag[size_t(agg[size_t(i)])] = 0;
+        std::vector<int> cdpos(static_cast<size_t>(nc));
+        for (int I = 0; I < nc; ++I)
+            cdpos[size_t(I)] = int(std::lower_bound(ccol.data() + crp[size_t(I)], ccol.data() + crp[size_t(I) + 1], I) -
+                                   ccol.data());
+        hb_problem::AmgLevel &f = lv.back();
+        HB_TRY(upload(p, f.agg, agg));
+        HB_TRY(upload(p, f.aptr, aptr));
+        HB_TRY(upload(p, f.aidx, aidx));
+        HB_TRY(upload(p, f.cptr, cptr));
+        HB_TRY(upload(p, f.cidx, cidx));
+        HB_TRY(upload(p, f.mmask, mmask));
+        hb_problem::AmgLevel c;
+        c.n = nc;
+        c.nnz = cnnz;
+        HB_TRY(upload(p, c.rowptr, crp));
+        HB_TRY(upload(p, c.col, ccol));
+        HB_TRY(upload(p, c.dpos, cdpos));
+        HB_TRY(upload(p, c.flag, cflag));
+        lv.push_back(std::move(c));
+        rowptr.swap(crp);
+        col.swap(ccol);
+        flag.swap(cflag);
+        n = nc;
+    }
+    p->amg = std::move(lv);
+    return HB_OK;
+}
+
+template <typename T>
+struct AmgBufs;
+template <>
+struct AmgBufs<float> {
+    static DBuf<float> &coef(hb_problem::AmgLevel &l) { return l.coef32; }
+    static DBuf<float> &mass(hb_problem::AmgLevel &l) { return l.mass32; }
+    static DBuf<float> &x(hb_problem::AmgLevel &l) { return l.x32; }
+    static DBuf<float> &b(hb_problem::AmgLevel &l) { return l.b32; }
+    static DBuf<float> &r(hb_problem::AmgLevel &l) { return l.r32; }
+    static DBuf<float> &ax(hb_problem::AmgLevel &l) { return l.ax32; }
+    static DBuf<float> &W(hb_problem::AmgLevel &l) { return l.W32; }
+    static bool &mass_done(hb_problem *p) { return p->amg_mass32; }
+};
+template <>
+struct AmgBufs<double> {
+    static DBuf<double> &coef(hb_problem::AmgLevel &l) { return l.coef64; }
+    static DBuf<double> &mass(hb_problem::AmgLevel &l) { return l.mass64; }
+    static DBuf<double> &x(hb_problem::AmgLevel &l) { return l.x64; }
+    static DBuf<double> &b(hb_problem::AmgLevel &l) { return l.b64; }
+    static DBuf<double> &r(hb_problem::AmgLevel &l) { return l.r64; }
+    static DBuf<double> &ax(hb_problem::AmgLevel &l) { return l.ax64; }
+    static DBuf<double> &W(hb_problem::AmgLevel &l) { return l.W64; }
+    static bool &mass_done(hb_problem *p) { return p->amg_mass64; }
+};
+
+// level operator views (level 0 is the assembled tangent itself)
+template <typename T>
+struct AmgOp {
+    int64_t n, nnz;
+    const int *rowptr, *col, *dpos;
+    const uint8_t *flag;
+    const T *coef, *mass;
+};
+template <typename T>
+AmgOp<T> amg_op(hb_problem *p, size_t l) {
+    hb_problem::AmgLevel &L = p->amg[l];
+    if (l == 0) {
+        hb_problem::Assembled &A = p->as;
+        return AmgOp<T>{L.n, L.nnz, A.rowptr.p, A.col.p, A.dpos.p, p->d_flag.p, AsmBufs<T>::coef(A).p,
+                        AsmBufs<T>::mass(A).p};
+    }
+    return AmgOp<T>{L.n, L.nnz, L.rowptr.p, L.col.p, L.dpos.p, L.flag.p, AmgBufs<T>::coef(L).p, AmgBufs<T>::mass(L).p};
+}
+
+// coarse operators from the last assembly (after assemble_at<T>); allocates every level's work vectors
+template <typename T>
+hb_status amg_values(hb_problem *p, cudaStream_t s) {
+    HB_TRY(amg_build(p));
+    const int N = p->N, ws = w_stride(N, int(sizeof(T)));
+    const bool mass = !AmgBufs<T>::mass_done(p);
+    for (size_t l = 0; l < p->amg.size(); ++l) {
+        hb_problem::AmgLevel &L = p->amg[l];
+        const size_t nv = size_t(L.n) * 4 * size_t(N);
+        HB_TRY(dalloc(p, AmgBufs<T>::x(L), nv));
+        HB_TRY(dalloc(p, AmgBufs<T>::b(L), nv));
+        HB_TRY(dalloc(p, AmgBufs<T>::r(L), nv));
+        HB_TRY(dalloc(p, AmgBufs<T>::ax(L), nv));
+        HB_TRY(dalloc(p, AmgBufs<T>::W(L), size_t(L.n) * size_t(ws)));
+        if (l > 0) {
+            HB_TRY(dalloc(p, AmgBufs<T>::coef(L), size_t(L.nnz) * 8 * size_t(N)));
+            HB_TRY(dalloc(p, AmgBufs<T>::mass(L), size_t(L.nnz)));
+        }
+    }
+    for (size_t l = 0; l + 1 < p->amg.size(); ++l) {
+        const AmgOp<T> f = amg_op<T>(p, l);
+        hb_problem::AmgLevel &F = p->amg[l], &C = p->amg[l + 1];
+        launch_amg_coarse<T>(F.cptr.p, F.cidx.p, F.mmask.p, f.coef, f.mass, AmgBufs<T>::coef(C).p,
+                             AmgBufs<T>::mass(C).p, C.nnz, N, mass, s);
+        HB_LAUNCHED(p, mass ? 2 : 1);
+    }
+    AmgBufs<T>::mass_done(p) = true;
+    return HB_OK;
+}
+
+// ax = A_l x on level l (W = shift x + rho H x per node, then the row-wise sparse product)
+template <typename T>
+void amg_matvec(hb_problem *p, size_t l, const OpCtxShift &sh, const T *x, T *ax, cudaStream_t s) {
+    const AmgOp<T> op = amg_op<T>(p, l);
+    hb_problem::AmgLevel &L = p->amg[l];
+    const int N = p->N, ws = w_stride(N, int(sizeof(T)));
+    launch_spectral_w<T>(x, Hmat<T>(p), op.flag, AmgBufs<T>::W(L).p, ws, op.n, N, T(p->rho), T(sh.shift), sh.dev, s,
+                         p->spectral_path, p->d_err.p);
+    SpmvArgs<T> a;
+    a.n_nodes = op.n;
+    a.N = N;
+    a.w_stride = ws;
+    a.rowptr = op.rowptr;
+    a.col = op.col;
+    a.coef = op.coef;
+    a.mass = op.mass;
+    a.v = x;
+    a.W = AmgBufs<T>::W(L).p;
+    a.out = ax;
+    a.flag = op.flag;
+    launch_spmv<T>(a, s);
+    p->launches += 2;
+}
+
+// x_l ~= A_l^-1 b_l by one V-cycle from x_l = 0
+template <typename T>
+void amg_vcycle(hb_problem *p, size_t l, const OpCtxShift &sh, cudaStream_t s) {
+    const AmgOp<T> op = amg_op<T>(p, l);
+    hb_problem::AmgLevel &L = p->amg[l];
+    const int N = p->N;
+    T *x = AmgBufs<T>::x(L).p, *b = AmgBufs<T>::b(L).p, *r = AmgBufs<T>::r(L).p, *ax = AmgBufs<T>::ax(L).p;
+    const int64_t nv = op.n * 4 * N;
+    auto sweep = [&](bool first) {
+        if (first) {
+            launch_amg_smooth<T>(op.coef, op.mass, op.dpos, op.flag, b, x, op.n, N, kAmgOmega, sh.shift, sh.dev, 0, s);
+            p->launches += 1;
+            return;
+        }
+        amg_matvec<T>(p, l, sh, x, ax, s);
+        launch_amg_sub<T>(b, ax, r, nv, s);
+        launch_amg_smooth<T>(op.coef, op.mass, op.dpos, op.flag, r, x, op.n, N, kAmgOmega, sh.shift, sh.dev, 1, s);
+        p->launches += 2;
+    };
+    const bool coarsest = l + 1 == p->amg.size();
+    const int pre = coarsest ? kAmgCoarseSweeps : kAmgPre;
+    for (int k = 0; k < pre; ++k) sweep(k == 0);
+    if (coarsest) return;
+    amg_matvec<T>(p, l, sh, x, ax, s);
+    launch_amg_sub<T>(b, ax, r, nv, s);
+    hb_problem::AmgLevel &C = p->amg[l + 1];
+    launch_amg_restrict<T>(L.aptr.p, L.aidx.p, op.flag, r, AmgBufs<T>::b(C).p, C.n, N, s);
+    p->launches += 2;
+    amg_vcycle<T>(p, l + 1, sh, s);
+    launch_amg_prolong<T>(L.agg.p, op.flag, AmgBufs<T>::x(C).p, x, op.n, N, s);
+    p->launches += 1;
+    for (int k = 0; k < kAmgPost; ++k) sweep(false);
+}
+
+// z = V-cycle(x): x the FP64 Krylov vector, the cycle in the precision of the assembly T, z in Z
+template <typename T, typename Z>
+hb_status amg_apply(hb_problem *p, const OpCtxShift &sh, const double *x, Z *z, cudaStream_t s) {
+    if (p->amg.empty()) return fail(HB_ERR_STATE, "multigrid preconditioner not set up");
+    hb_problem::AmgLevel &L0 = p->amg[0];
+    const int64_t nv = L0.n * 4 * p->N;
+    launch_convert<double, T>(x, AmgBufs<T>::b(L0).p, nv, s);
+    HB_LAUNCHED(p, 1);
+    amg_vcycle<T>(p, 0, sh, s);
+    if constexpr (std::is_same<T, Z>::value) {
+        HB_CUDA(cudaMemcpyAsync(z, AmgBufs<T>::x(L0).p, size_t(nv) * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    } else {
+        launch_convert<T, Z>(AmgBufs<T>::x(L0).p, z, nv, s);
+        HB_LAUNCHED(p, 1);
+    }
+    return HB_OK;
+}
+
 struct OpCtx {
     int mode;
     double shift;
     int precision;
     const double *shift_dev = nullptr;   // pseudo shift read from device memory (graph-stable)
     int precond = 0;                     // 0: Jacobi (inverse diagonal in kdiag); 1: node blocks of the
-                                         // assembled tangent
+                                         // assembled tangent; 2: aggregation multigrid V-cycle on it
 };
 
 // z = M^-1 x for the preconditioner of c (x: FP64 Krylov vector); Z = float writes the mixed path's
@@ -971,6 +1278,12 @@ struct OpCtx {
 template <typename Z>
 hb_status apply_precond(hb_problem *p, const OpCtx &c, const double *x, Z *z, cudaStream_t s) {
     const int64_t nd = p->n_nodes * 4 * p->N;
+    if (c.precond == 2) {
+        const OpCtxShift sh{c.shift, c.shift_dev};
+        if (c.precision == 1) return amg_apply<float, Z>(p, sh, x, z, s);
+        if constexpr (sizeof(Z) == 8) return amg_apply<double, double>(p, sh, x, z, s);
+        return fail(HB_ERR_STATE, "FP32 preconditioner output requested in the FP64 path");
+    }
     if (c.precond == 1) {
         const hb_problem::Assembled &A = p->as;
         if (c.precision == 1) {      // coefficients assembled in FP32
@@ -1224,20 +1537,27 @@ double h_char(const hb_problem *p) { return std::cbrt(6.0 * std::sqrt(2.0) * p->
 constexpr int kNoAllocScratch = 4096;   // doubles: n_out x N must not exceed this
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratch];
 constexpr int kMaxDevices = 64;
-static void *g_noalloc_ptr[kMaxDevices] = {nullptr};
+static std::atomic<void *> g_noalloc_ptr[kMaxDevices];   // per device; set once, guarded by g_noalloc_mutex
+static std::mutex g_noalloc_mutex;
 
 hb_status noalloc_scratch(int device, void **ptr) {
     if (device < 0 || device >= kMaxDevices) return fail(HB_ERR_INVALID_ARG, "device index too large for the no-alloc scratch table");
-    if (!g_noalloc_ptr[device]) {   // first call on this device, which is current here
-        void *q = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&q, g_noalloc_scratch);
-        if (e != cudaSuccess || !q) {
-            cudaGetLastError();
-            return fail(HB_ERR_CUDA, std::string("cudaGetSymbolAddress(no-alloc scratch): ") + cudaGetErrorString(e));
+    void *have = g_noalloc_ptr[device].load(std::memory_order_acquire);
+    if (!have) {   // first call on this device, which is current here; host threads serialise the lookup
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        have = g_noalloc_ptr[device].load(std::memory_order_relaxed);
+        if (!have) {
+            void *q = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&q, g_noalloc_scratch);
+            if (e != cudaSuccess || !q) {
+                cudaGetLastError();
+                return fail(HB_ERR_CUDA, std::string("cudaGetSymbolAddress(no-alloc scratch): ") + cudaGetErrorString(e));
+            }
+            g_noalloc_ptr[device].store(q, std::memory_order_release);
+            have = q;
         }
-        g_noalloc_ptr[device] = q;
     }
-    *ptr = g_noalloc_ptr[device];
+    *ptr = have;
     return HB_OK;
 }
 
@@ -1725,6 +2045,27 @@ hb_status hb_jv(hb_problem *p, const double *y, const double *v, double *jv, int
     return host_op(p, jv_mode(kind), y, v, jv, precision, shift);
 }
 
+hb_status hb_jv_f32(hb_problem *p, const float *y, const float *v, float *jv, int kind, double shift) {
+    if (!p || !y || !v || !jv) return fail(HB_ERR_INVALID_ARG, "null argument");
+    if (kind < 0 || kind > 2)
+        return fail(HB_ERR_INVALID_ARG, "kind must be 0 (paper tangent), 1 (exact) or 2 (assembled paper tangent)");
+    const int mode = jv_mode(kind);
+    const size_t nd = size_t(p->n_nodes) * 4 * p->N;
+    HB_CUDA(cudaSetDevice(p->device));
+    HB_TRY(dalloc(p, p->w32a, nd));
+    HB_TRY(dalloc(p, p->w32b, nd));
+    HB_TRY(dalloc(p, p->w32c, nd));
+    HB_CUDA(cudaMemcpyAsync(p->w32a.p, y, nd * sizeof(float), cudaMemcpyHostToDevice, p->stream));
+    HB_CUDA(cudaMemcpyAsync(p->w32c.p, v, nd * sizeof(float), cudaMemcpyHostToDevice, p->stream));
+    if (mode == MODE_JVA) HB_TRY(assemble_at<float>(p, p->w32a.p, p->stream));
+    HB_TRY(apply_op<float>(p, mode, p->w32a.p, p->w32c.p, p->w32b.p, shift, p->stream));
+    HB_CUDA(cudaMemcpyAsync(jv, p->w32b.p, nd * sizeof(float), cudaMemcpyDeviceToHost, p->stream));
+    int err = 0;
+    HB_CUDA(cudaMemcpyAsync(&err, p->d_err.p, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+    HB_CUDA(cudaStreamSynchronize(p->stream));
+    return dev_err_status(p, err);
+}
+
 hb_status hb_jacobi_diag(hb_problem *p, const double *y, double *d, int precision, double shift) {
     return host_op(p, MODE_DIAG, y, nullptr, d, precision, shift);
 }
@@ -1772,6 +2113,7 @@ hb_status hb_default_opts(hb_solve_opts *o) {
     o->r_ref = 0.0;
     o->assembled = 0;
     o->precond = 0;
+    o->line_search = 1;
     return HB_OK;
 }
 
@@ -1790,7 +2132,8 @@ hb_status hb_solve(hb_problem *p, const hb_solve_opts *opts, hb_report *rep) {
     if (opts) o = *opts;
     HB_TRY(check_precision(o.precision));
     if (o.gmres_restart < 1 || o.gmres_restart > 200) return fail(HB_ERR_INVALID_ARG, "gmres_restart must be in [1, 200]");
-    if (o.precond != 0 && o.precond != 1) return fail(HB_ERR_INVALID_ARG, "precond must be 0 (Jacobi) or 1 (node blocks)");
+    if (o.precond < 0 || o.precond > 2)
+        return fail(HB_ERR_INVALID_ARG, "precond must be 0 (Jacobi), 1 (node blocks) or 2 (aggregation multigrid)");
     HB_CUDA(cudaSetDevice(p->device));
     if (o.use_learned < 0 || o.use_learned > 2) return fail(HB_ERR_INVALID_ARG, "use_learned must be 0, 1 or 2");
     p->learned_dir = false;
@@ -1861,6 +2204,7 @@ static hb_status solve_impl(hb_problem *p, const hb_solve_opts &o, hb_report *re
     double dxn = INFINITY;
     double eta = 0.1, rn_prev = rn;   // Eisenstat-Walker forcing term of the Newton phase
     double dtk = dt;                  // current pseudo step (adaptive when o.ser)
+    bool ls_fallback = false;         // the last Newton step found no decrease: retake it with the shift
     for (int step = 0; step < o.max_steps; ++step) {
         if (!std::isfinite(rn)) {
             result = fail(HB_ERR_NAN, "residual is not finite");
@@ -1877,7 +2221,8 @@ static hb_status solve_impl(hb_problem *p, const hb_solve_opts &o, hb_report *re
         // paper's tangent after the switch, and the shift is dropped once dt exceeds ser_max x the CFL step.
         double shift = 0.0;
         if (!o.ser) shift = newton ? 0.0 : shift0;
-        else if (std::isfinite(dtk) && dtk < dt * o.ser_max) shift = kC1 * p->rho / dtk;
+        else if (std::isfinite(dtk) && dtk < dt * o.ser_max && !(newton && o.line_search && !ls_fallback))
+            shift = kC1 * p->rho / dtk;
         p->shift_host = shift;
         HB_CUDA(cudaMemcpyAsync(p->shift_dev.p, &p->shift_host, sizeof(double), cudaMemcpyHostToDevice, p->stream));
         OpCtx c{newton ? MODE_JVE : MODE_JVP, shift, o.precision, p->shift_dev.p};
@@ -1893,11 +2238,16 @@ static hb_status solve_impl(hb_problem *p, const hb_solve_opts &o, hb_report *re
         }
         launch_reciprocal(p->kdiag.p, p->kdiag.p, nd, p->stream);   // kdiag holds the inverse diagonal
         HB_LAUNCHED(p, 1);
-        if ((o.assembled && c.mode == MODE_JVP) || o.precond == 1) {
+        if ((o.assembled && c.mode == MODE_JVP) || o.precond >= 1) {
             // the paper's tangent assembled once for this step: GMRES applies it as a sparse product
-            // (assembled, paper-tangent phase) and / or takes its node blocks as the preconditioner
+            // (assembled, paper-tangent phase) and / or builds the preconditioner from it (node blocks, or
+            // the multigrid hierarchy's coarse operators)
             if (o.precision == 1) HB_TRY(assemble_at<float>(p, p->ky32.p, p->stream));
             else HB_TRY(assemble_at<double>(p, p->y.p, p->stream));
+            if (o.precond == 2) {
+                if (o.precision == 1) HB_TRY(amg_values<float>(p, p->stream));
+                else HB_TRY(amg_values<double>(p, p->stream));
+            }
             if (o.assembled && c.mode == MODE_JVP) c.mode = MODE_JVA;
             c.precond = o.precond;
         }
@@ -1952,14 +2302,49 @@ static hb_status solve_impl(hb_problem *p, const hb_solve_opts &o, hb_report *re
         }
         R.gmres_iters += its;
         R.jv_calls += jvc;
+        const bool search = newton && o.line_search && shift == 0.0;
+        if (search) {
+            HB_TRY(dalloc(p, p->yprev, size_t(nd)));
+            HB_CUDA(cudaMemcpyAsync(p->yprev.p, p->y.p, size_t(nd) * sizeof(double), cudaMemcpyDeviceToDevice,
+                                    p->stream));
+        }
         launch_axpy(1.0, p->kdx.p, p->y.p, nd, p->stream);
         HB_LAUNCHED(p, 1);
         HB_TRY(apply_op<double>(p, MODE_RES, p->y.p, nullptr, r, 0.0, p->stream));
         R.residual_calls++;
         double yn = 0;
+        HB_TRY(dev_norm(p, r, nd, rn));
+        if (search) {
+            // backtracking on ||r||: y = y_prev + lambda dx, lambda = 1, 1/2, ..., 1/16
+            double lam = 1.0;
+            for (int b = 0; b < 4 && !(rn <= (1.0 - 1e-4 * lam) * rn_before); ++b) {
+                lam *= 0.5;
+                launch_scale_copy(1.0, p->yprev.p, p->y.p, nd, p->stream);
+                launch_axpy(lam, p->kdx.p, p->y.p, nd, p->stream);
+                HB_LAUNCHED(p, 2);
+                HB_TRY(apply_op<double>(p, MODE_RES, p->y.p, nullptr, r, 0.0, p->stream));
+                R.residual_calls++;
+                HB_TRY(dev_norm(p, r, nd, rn));
+            }
+            ls_fallback = !(rn < rn_before);
+            if (ls_fallback) {            // no decrease: take the step back and retake it with the shift
+                launch_scale_copy(1.0, p->yprev.p, p->y.p, nd, p->stream);
+                HB_LAUNCHED(p, 1);
+                HB_TRY(apply_op<double>(p, MODE_RES, p->y.p, nullptr, r, 0.0, p->stream));
+                R.residual_calls++;
+                HB_TRY(dev_norm(p, r, nd, rn));
+            }
+            if (ls_fallback) {
+                dtk = std::max(dt, 0.1 * dtk);        // the retaken step gets a noticeable shift
+            } else if (lam != 1.0) {
+                launch_scale_copy(lam, p->kdx.p, p->kdx.p, nd, p->stream);
+                HB_LAUNCHED(p, 1);
+            }
+        } else {
+            ls_fallback = false;
+        }
         HB_TRY(dev_norm(p, p->kdx.p, nd, dxn));
         HB_TRY(dev_norm(p, p->y.p, nd, yn));
-        HB_TRY(dev_norm(p, r, nd, rn));
         R.steps++;
         if (newton) R.newton_steps++;
         if (o.ser) {
@@ -2303,6 +2688,8 @@ struct hb_batch {
     std::vector<const void *> y, v;
     std::vector<void *> out;
     int64_t launches_per_replay = 0, launches = 0;
+    static constexpr int kSide = 4;       // side streams of the captured graph's parallel W passes
+    cudaStream_t side[kSide] = {};
 };
 
 namespace {
@@ -2340,6 +2727,13 @@ hb_status batch_record(hb_batch *b) {
         ea.shift_dev = nullptr;
         ea.omega2 = T(tau_dt_term(p));
         ea.rbvms = p->stab;
+        if (b->mode == MODE_JVP) {
+            // the member's node-level W = shift v + rho H v pass runs inside the graph (parallel branches);
+            // the batched element pass gathers its rows as the single-problem pass does
+            DBuf<T> &W = AsmBufs<T>::W(p->as);
+            HB_TRY(dalloc(p, W, size_t(p->n_nodes) * size_t(w_stride(p->N, int(sizeof(T))))));
+            ea.W = W.p;
+        }
         smem = std::max(smem, elem_smem_bytes(b->mode, p->N, ps.nl_max, ps.ep_max, sizeof(T), bstride));
     }
     DBuf<ElemArgs<T>> &dargs = [&]() -> DBuf<ElemArgs<T>> & {
@@ -2370,21 +2764,20 @@ hb_status batch_record(hb_batch *b) {
         }
         HB_CUDA(cudaStreamSynchronize(s));
     }
+    // one persistent launch over every member's patches (N = -1: the kernel dispatches on each member's
+    // instance count), so members of different N share the SMs and the launch's tail
     std::vector<BatchGroup<T>> groups;
-    for (size_t r0 = 0; r0 < np;) {
-        size_t r1 = r0 + 1;
-        while (r1 < np && args[r1].N == args[r0].N) ++r1;
+    {
         BatchGroup<T> g;
         g.args = dargs.p;
         g.bslots = b->bslots.p;
         g.bslot_stride = bstride;
-        g.N = args[r0].N;
-        g.item_begin = first[r0];
-        g.item_end = first[r1];
+        g.N = -1;
+        g.item_begin = 0;
+        g.item_end = b->n_items;
         g.variant = p0->jvp_variant;
-        g.counter = b->counter.p + groups.size();
-        groups.push_back(g);
-        r0 = r1;
+        g.counter = b->counter.p;
+        if (b->n_items > 0) groups.push_back(g);
     }
     int max_blocks = 1;
     if (smem <= 113 * 1024 && sizeof(T) == 4) max_blocks = 2;
@@ -2400,6 +2793,35 @@ hb_status batch_record(hb_batch *b) {
     }
     if (st == HB_OK && cudaMemsetAsync(b->counter.p, 0, groups.size() * sizeof(int), s) != cudaSuccess)
         st = fail(HB_ERR_CUDA, "memset in batch capture");
+    std::vector<cudaEvent_t> evs;
+    if (st == HB_OK && b->mode == MODE_JVP) {
+        // fork: the members' W passes on kSide branches, joined before the element pass
+        cudaEvent_t fork = nullptr;
+        if (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess) st = fail(HB_ERR_CUDA, "event");
+        else {
+            evs.push_back(fork);
+            cudaEventRecord(fork, s);
+            for (int k = 0; k < hb_batch::kSide; ++k) cudaStreamWaitEvent(b->side[k], fork, 0);
+            for (size_t q = 0; q < b->probs.size(); ++q) {
+                hb_problem *p = b->probs[q];
+                cudaStream_t ss = b->side[q % hb_batch::kSide];
+                launch_spectral_w<T>(static_cast<const T *>(b->v[q]), Hmat<T>(p), p->d_flag.p, AsmBufs<T>::W(p->as).p,
+                                     w_stride(p->N, int(sizeof(T))), p->n_nodes, p->N, T(p->rho), T(b->shift), nullptr,
+                                     ss, p->spectral_path, p->d_err.p);
+                p0->launches += 1;
+            }
+            for (int k = 0; k < hb_batch::kSide; ++k) {
+                cudaEvent_t join = nullptr;
+                if (cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess) {
+                    st = fail(HB_ERR_CUDA, "event");
+                    break;
+                }
+                evs.push_back(join);
+                cudaEventRecord(join, b->side[k]);
+                cudaStreamWaitEvent(s, join, 0);
+            }
+        }
+    }
     for (size_t k = 0; k < groups.size() && st == HB_OK; ++k) {
         const BatchGroup<T> &g = groups[k];
         launch_batch_elem<T>(b->mode, g, smem, std::min(b->grid, g.item_end - g.item_begin), s);
@@ -2441,6 +2863,7 @@ hb_status batch_record(hb_batch *b) {
     }
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(s, &graph);
+    for (cudaEvent_t ev : evs) cudaEventDestroy(ev);
     if (st != HB_OK) {
         if (graph) cudaGraphDestroy(graph);
         return st;
@@ -2486,6 +2909,11 @@ hb_status hb_batch_create(hb_problem *const *problems, int count, int precision,
         delete b;
         return fail(HB_ERR_CUDA, "cudaStreamCreate failed");
     }
+    for (int k = 0; k < hb_batch::kSide; ++k)
+        if (cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking) != cudaSuccess) {
+            hb_batch_destroy(b);
+            return fail(HB_ERR_CUDA, "cudaStreamCreate failed");
+        }
     hb_status st = dalloc(p0, b->counter, size_t(count));
     if (st != HB_OK) {
         cudaStreamDestroy(b->stream);
@@ -2502,8 +2930,10 @@ hb_status hb_batch_destroy(hb_batch *b) {
     cudaStreamSynchronize(b->stream);
     if (b->exec) cudaGraphExecDestroy(b->exec);
     cudaStream_t s = b->stream;
+    for (int k = 0; k < hb_batch::kSide; ++k)
+        if (b->side[k]) cudaStreamDestroy(b->side[k]);
     delete b;
-    cudaStreamDestroy(s);
+    if (s) cudaStreamDestroy(s);
     return HB_OK;
 }
 

@@ -970,8 +970,13 @@ __host__ __device__ inline PipeLayout pipe_layout(int N, int nl, int ep) {
     return L;
 }
 
-template <typename L, int NT, int C>
-__global__ void __launch_bounds__((C + 1) * 32, 1) jvp_pipe_kernel(ElemArgs<float> a, int *err) {
+// PW producer warps: 1 = one warp issuing 1-D bulk copies (cp.async.bulk, completion counted in bytes);
+// PW > 1 = PW warps issuing 16-byte cp.async copies spread over all their lanes, each lane signalling the
+// stage's barrier once its own copies have landed (cp.async.mbarrier.arrive.noinc).  The bulk form moves a
+// patch with ~3 copies per node, which the bulk-copy engine serves at a lower rate than the LSU serves many
+// 16-byte copies from 128 lanes.
+template <typename L, int NT, int C, int PW>
+__global__ void __launch_bounds__((C + PW) * 32, 1) jvp_pipe_kernel(ElemArgs<float> a, int *err) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t full[2], empty[2];
     constexpr int N = NT, N4 = 4 * N, N3 = 3 * N, WS = w_stride(NT, 4);
@@ -981,15 +986,47 @@ __global__ void __launch_bounds__((C + 1) * 32, 1) jvp_pipe_kernel(ElemArgs<floa
     const int P = a.pv.n_patches, stride = a.pv.slot_stride;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
-        mbar_init(&full[0], 1);
-        mbar_init(&full[1], 1);
+        mbar_init(&full[0], PW == 1 ? 1 : PW * 32);
+        mbar_init(&full[1], PW == 1 ? 1 : PW * 32);
         mbar_init(&empty[0], C);
         mbar_init(&empty[1], C);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     }
     __syncthreads();
-    if (warp == C) {
+    if (PW > 1 && warp >= C) {
+        // ---- producer warps (16-byte copies)
+        const int pt = int(threadIdx.x) - C * 32;
+        constexpr int NPT = PW * 32, CPR = N4 / 4, WPR = WS / 4, RPN = 2 * CPR + WPR;
+        int issued = -1, k = 0;
+        for (int p = int(blockIdx.x); p < P; ++k, p += int(gridDim.x)) {
+            const int s = k & 1;
+            if (k >= 2 && !mbar_wait_bounded(&empty[s], uint32_t(((k >> 1) - 1) & 1))) {
+                if (pt == 0) atomicExch(err, 2);
+                break;
+            }
+            unsigned char *st = smem + size_t(s) * PL.stage;
+            const int *gslot = a.pv.slots + size_t(p) * stride;
+            const int e0 = gslot[0], ne = gslot[1], nl = gslot[2];
+            for (int i = pt; i < stride / 4; i += NPT) cp_async16(st + PL.slot + 16 * size_t(i), gslot + 4 * i);
+            const float *gg = a.pv.geom + size_t(e0) * kGeomStride;
+            for (int i = pt; i < ne * (kGeomStride / 4); i += NPT) cp_async16(st + PL.geom + 16 * size_t(i), gg + 4 * i);
+            for (int i = pt; i < nl * RPN; i += NPT) {
+                const int l = i / RPN, c = i - l * RPN;
+                const size_t node = size_t(uint32_t(__ldg(gslot + 4 + l)) & ~kDirBit);
+                if (c < CPR) cp_async16(st + PL.Y + (size_t(l) * CPR + c) * 16, a.y + node * N4 + 4 * c);
+                else if (c < 2 * CPR)
+                    cp_async16(st + PL.V + (size_t(l) * CPR + c - CPR) * 16, a.v + node * N4 + 4 * (c - CPR));
+                else cp_async16(st + PL.W + (size_t(l) * WPR + c - 2 * CPR) * 16, a.W + node * WS + 4 * (c - 2 * CPR));
+            }
+            asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(smem_u32(&full[s])) : "memory");
+            issued = k;
+        }
+        cp_async_wait_all();                        // no copy of this thread is in flight at exit
+        (void)issued;
+        return;
+    }
+    if (PW == 1 && warp == C) {
         // ---- producer warp.  The next patch's header and node ids are loaded into registers before the
         // wait for a free stage, so their global-load latency overlaps the consumers' work.
         constexpr int IDS = 8;                      // node ids per lane: patches of up to 256 nodes
@@ -1098,6 +1135,23 @@ struct BatchPrefetch {
     }
 };
 
+// NT = -1: one launch for members of any instance count; each problem switch dispatches to the pass
+// specialised for its N (9, 13, 21) or the generic one.
+template <typename T, int MODE, int NT, typename L, typename Prefetch>
+__device__ __forceinline__ void batch_patch(const ElemArgs<T> &a, const PatchSmem<T> &sm, const int *slot, T shift,
+                                            Prefetch pf) {
+    if constexpr (NT >= 0) {
+        patch_pass<T, MODE, NT, L>(a, sm, slot, shift, pf);
+    } else {
+        switch (a.N) {
+            case 9: patch_pass<T, MODE, 9, L>(a, sm, slot, shift, pf); break;
+            case 13: patch_pass<T, MODE, 13, L>(a, sm, slot, shift, pf); break;
+            case 21: patch_pass<T, MODE, 21, L>(a, sm, slot, shift, pf); break;
+            default: patch_pass<T, MODE, 0, L>(a, sm, slot, shift, pf); break;
+        }
+    }
+}
+
 template <typename T, int MODE, int NT, int VAR>
 __global__ void __launch_bounds__(ElemCfg<T, VAR>::block, ElemCfg<T, VAR>::minb)
     batch_elem_kernel(const ElemArgs<T> *__restrict__ args, const int *__restrict__ bslots, int bslot_stride,
@@ -1123,13 +1177,16 @@ __global__ void __launch_bounds__(ElemCfg<T, VAR>::block, ElemCfg<T, VAR>::minb)
         const int N = NT > 0 ? NT : a.N;
         const PatchSmem<T> sm = patch_smem<T, MODE>(smem, N, a.pv.nl_max, a.pv.ep_max, bslot_stride);
         if (q != last) {
-            stage_H<T, NT>(a, sm.H, N);
+            // fixed N (also inside the all-N launch): the first column of the circulant H; generic: all of H
+            const bool fixedN = NT > 0 || (NT < 0 && (N == 9 || N == 13 || N == 21));
+            if (fixedN) stage_H<T, 1>(a, sm.H, N);
+            else stage_H<T, 0>(a, sm.H, N);
             __syncthreads();
         }
         const T shift = a.shift_dev ? T(*a.shift_dev) : a.shift;
         const BatchPrefetch pf{bslots, bslot_stride, item_begin, item_end, counter, &s_item[cur ^ 1],
                                slot0 + (cur ^ 1) * bslot_stride};
-        patch_pass<T, MODE, NT, typename ElemCfg<T, VAR>::lane>(a, sm, bslot + 4, shift, pf);
+        batch_patch<T, MODE, NT, typename ElemCfg<T, VAR>::lane>(a, sm, bslot + 4, shift, pf);
         cp_async_wait_all();
         __syncthreads();
         last = q;
@@ -1217,7 +1274,7 @@ static void launch_elem_v(const ElemArgs<T> &a, int grid, cudaStream_t s) {
 
 // Pipelined paper-tangent pass (variants 4 and 5): one block per SM; false if it cannot run (no W rows,
 // no status word, or two stages do not fit the opt-in shared memory), so the caller falls back.
-template <typename L, int NT, int C>
+template <typename L, int NT, int C, int PW>
 static bool launch_pipe(const ElemArgs<float> &a, cudaStream_t s) {
     if (!a.W || !a.err || a.pv.n_patches <= 0 || a.pv.nl_max > 256) return false;   // producer holds 256 ids
     const size_t smem = 2 * pipe_layout(NT, a.pv.nl_max, a.pv.ep_max).stage;
@@ -1226,20 +1283,22 @@ static bool launch_pipe(const ElemArgs<float> &a, cudaStream_t s) {
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (smem + 64 > size_t(optin)) return false;
     static LaunchCache cache;
-    auto kern = jvp_pipe_kernel<L, NT, C>;
-    const int per = cached_blocks_per_sm(cache, kern, (C + 1) * 32, smem);
+    auto kern = jvp_pipe_kernel<L, NT, C, PW>;
+    const int per = cached_blocks_per_sm(cache, kern, (C + PW) * 32, smem);
     const int grid = std::min(a.pv.n_patches, per * device_sms());
-    kern<<<grid, (C + 1) * 32, smem, s>>>(a, a.err);
+    kern<<<grid, (C + PW) * 32, smem, s>>>(a, a.err);
     return true;
 }
 
 template <typename T, int MODE, int NT>
 static void launch_elem_n(const ElemArgs<T> &a, int grid, cudaStream_t s) {
     if constexpr (MODE == MODE_JVP && sizeof(T) == 4 && (NT == 9 || NT == 13 || NT == 21)) {
-        // 4: one instance per thread, 20 consumer warps; 5: instance pairs on paired FP32 instructions,
-        // 15 consumer warps.  Without the W rows (or if the stages do not fit) they run variant 1.
-        if (a.variant == 4 && launch_pipe<float, NT, 20>(a, s)) return;
-        if (a.variant == 5 && launch_pipe<float2, NT, 15>(a, s)) return;
+        // 4: one instance per thread, 20 consumer warps and 4 producer warps (16-byte copies); 5: instance
+        // pairs on paired FP32 instructions, 12 consumer warps; 6: as 4 with one producer warp issuing bulk
+        // copies.  Without the W rows (or if the stages do not fit) they run variant 1.
+        if (a.variant == 4 && launch_pipe<float, NT, 20, 4>(a, s)) return;
+        if (a.variant == 5 && launch_pipe<float2, NT, 12, 4>(a, s)) return;
+        if (a.variant == 6 && launch_pipe<float, NT, 20, 1>(a, s)) return;
     }
     if constexpr (MODE == MODE_JVP && sizeof(T) == 4) {
         if (a.variant == 1 || a.variant >= 4) {
@@ -1290,6 +1349,7 @@ static void launch_batch_var(const BatchGroup<T> &g, size_t smem, int grid, cuda
                                                          g.counter);
     };
     switch (g.N) {
+        case -1: go(batch_elem_kernel<T, MODE, -1, VAR>); break;     // every member in one launch
         case 9: go(batch_elem_kernel<T, MODE, 9, VAR>); break;
         case 13: go(batch_elem_kernel<T, MODE, 13, VAR>); break;
         case 21: go(batch_elem_kernel<T, MODE, 21, VAR>); break;

@@ -75,7 +75,7 @@ enum Mode : int {
 
 constexpr int kGeomStride = 16;       // per element: grad N_a (4 x 3), V, C_I nu^2 G:G, 2 pad
 constexpr int kMaxN = 31;             // largest number of time instances supported
-constexpr int kJvpVariants = 6;       // launch variants of the FP32 paper-tangent element pass
+constexpr int kJvpVariants = 7;       // launch variants of the FP32 paper-tangent element pass
 constexpr double kCI = 3.0;           // Eq. (tau)
 // 4-point degree-2 Gauss rule on a tetrahedron (barycentric coordinates of the points)
 constexpr double kQA = 0.5854101966249685;
@@ -288,6 +288,23 @@ void launch_spmv(const SpmvArgs<T> &a, cudaStream_t s);
 template <typename T, typename Z>
 void launch_block_jacobi(const T *coef, const T *mass, const int *dpos, const uint8_t *flag, const double *x, Z *z,
                          int64_t n_nodes, int N, double shift, const double *shift_dev, cudaStream_t s);
+
+// Aggregation multigrid on the assembled tangent (hb_amg.cu)
+template <typename T>
+void launch_amg_restrict(const int *aptr, const int *aidx, const uint8_t *flag_f, const T *r_f, T *b_c, int64_t n_c,
+                         int N, cudaStream_t s);
+template <typename T>
+void launch_amg_prolong(const int *agg, const uint8_t *flag_f, const T *x_c, T *x_f, int64_t n_f, int N,
+                        cudaStream_t s);
+template <typename T>
+void launch_amg_coarse(const int *cptr, const int *cidx, const uint8_t *mmask, const T *coef_f, const T *mass_f,
+                       T *coef_c, T *mass_c, int64_t nnz_c, int N, bool with_mass, cudaStream_t s);
+template <typename T>
+void launch_amg_smooth(const T *coef, const T *mass, const int *dpos, const uint8_t *flag, const T *r, T *x,
+                       int64_t n_nodes, int N, double omega, double shift, const double *shift_dev, int accumulate,
+                       cudaStream_t s);
+template <typename T>
+void launch_amg_sub(const T *b, const T *ax, T *r, int64_t n, cudaStream_t s);
 
 // Inputs of the learned warm start taken from a problem (host copies).
 constexpr int kLearnedFeatures = 32;  // per-node input features of the network

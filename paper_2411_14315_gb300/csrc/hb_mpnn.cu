@@ -212,6 +212,163 @@ __global__ void __launch_bounds__(256) wgrad_kernel(Segs U, int rows, const floa
     }
 }
 
+// Tensor-core form of mlp_fwd_kernel: a warp takes 16 rows; both layers are mma.sync m16n8k8 TF32 products
+// with FP32 accumulation.  The BF16 weights are exact in TF32; the FP32 activations are split into a TF32
+// head and tail (x = hi + lo), so X W = Xhi W + Xlo W keeps FP32 accuracy (the tail's own TF32 rounding is
+// ~2^-22 relative).  Shared memory: W1 as [KP1][HS] (bias row kin, zero rows up to KP1), W2 as [KP2][OS]
+// (bias row hid), and per warp the 16 input rows [16][XS] and hidden rows [16][AS] (a column of ones at
+// kin / hid).  Strides are padded so that the fragment loads of a warp hit 32 distinct banks.
+constexpr int kTcWarps = 8;
+
+__device__ __forceinline__ uint32_t tf32_of(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void mma_m16n8k8_tf32(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+                 "{%8, %9}, {%0, %1, %2, %3};"
+                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+struct TcDims {
+    int kin, hid, kout, KP1, KP2, HS, OS, XS, AS;
+};
+__host__ __device__ inline TcDims tc_dims(int kin, int hid, int kout) {
+    TcDims d;
+    d.kin = kin;
+    d.hid = hid;
+    d.kout = kout;
+    d.KP1 = (kin + 1 + 7) / 8 * 8;            // K of layer 1 (inputs + bias), padded to the MMA's K
+    d.KP2 = (hid + 1 + 7) / 8 * 8;
+    d.HS = (hid + 31) / 32 * 32 + 8;          // row stride of W1 (words): 8 mod 32 spreads k rows over banks
+    d.OS = (kout + 31) / 32 * 32 + 8;         // row stride of W2, same
+    d.XS = d.KP1 + 4;                         // row stride of the staged inputs: 4 mod 8 words
+    d.AS = d.KP2 + 4;
+    return d;
+}
+__host__ __device__ inline size_t tc_smem_floats(const TcDims &d) {
+    return size_t(d.KP1) * d.HS + size_t(d.KP2) * d.OS + size_t(kTcWarps) * 16 * (d.XS + d.AS);
+}
+
+template <int NT1>
+__global__ void __launch_bounds__(32 * kTcWarps) mlp_fwd_tc_kernel(Segs in, const __nv_bfloat16 *__restrict__ w,
+                                                                   int hid, int kout, int rows,
+                                                                   float *__restrict__ A_save, float *__restrict__ Y,
+                                                                   int ymode, const int *__restrict__ ydst) {
+    extern __shared__ float sm[];
+    const TcDims d = tc_dims(in.total, hid, kout);
+    const int kin = d.kin;
+    float *sW1 = sm, *sW2 = sW1 + size_t(d.KP1) * d.HS;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+    float *sX = sW2 + size_t(d.KP2) * d.OS + size_t(warp) * 16 * (d.XS + d.AS);
+    float *sA = sX + 16 * d.XS;
+    // weights (the parameter block: W1 [kin][hid], b1 [hid], W2 [hid][kout], b2 [kout])
+    for (int i = threadIdx.x; i < d.KP1 * hid; i += blockDim.x) {
+        const int k = i / hid, j = i - k * hid;
+        sW1[k * d.HS + j] = k <= kin ? __bfloat162float(w[k * hid + j]) : 0.f;
+    }
+    const __nv_bfloat16 *w2 = w + (kin + 1) * hid;
+    const int kop = (kout + 7) / 8 * 8;
+    for (int i = threadIdx.x; i < d.KP2 * kop; i += blockDim.x) {
+        const int k = i / kop, o = i - k * kop;
+        sW2[k * d.OS + o] = (k <= hid && o < kout) ? __bfloat162float(w2[k * kout + o]) : 0.f;
+    }
+    __syncthreads();
+    for (int r0 = (blockIdx.x * kTcWarps + warp) * 16; r0 < rows; r0 += gridDim.x * kTcWarps * 16) {
+        // stage the 16 input rows (segments gathered; bias column of ones; zero padding)
+        for (int i = lane; i < 16 * d.KP1; i += 32) {
+            const int rr = i / d.KP1, k = i - rr * d.KP1, r = r0 + rr;
+            float x = 0.f;
+            if (r < rows) x = k < kin ? seg_value(in, r, k) : (k == kin ? 1.f : 0.f);
+            sX[rr * d.XS + k] = x;
+        }
+        __syncwarp();
+        // layer 1: Z = [X, 1] [W1; b1], NT1 tiles of 8 hidden units
+        float acc[NT1][4];
+#pragma unroll
+        for (int t = 0; t < NT1; ++t) acc[t][0] = acc[t][1] = acc[t][2] = acc[t][3] = 0.f;
+        for (int k0 = 0; k0 < d.KP1; k0 += 8) {
+            const float av[4] = {sX[g * d.XS + k0 + q], sX[(g + 8) * d.XS + k0 + q], sX[g * d.XS + k0 + q + 4],
+                                 sX[(g + 8) * d.XS + k0 + q + 4]};
+            uint32_t ah[4], al[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                ah[i] = tf32_of(av[i]);
+                al[i] = tf32_of(av[i] - __uint_as_float(ah[i]));
+            }
+#pragma unroll
+            for (int t = 0; t < NT1; ++t) {
+                const uint32_t b0 = __float_as_uint(sW1[(k0 + q) * d.HS + 8 * t + g]);
+                const uint32_t b1 = __float_as_uint(sW1[(k0 + q + 4) * d.HS + 8 * t + g]);
+                mma_m16n8k8_tf32(acc[t], al, b0, b1);
+                mma_m16n8k8_tf32(acc[t], ah, b0, b1);
+            }
+        }
+        // relu, save, stage [A, 1]
+#pragma unroll
+        for (int t = 0; t < NT1; ++t)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int rr = g + 8 * h, r = r0 + rr;
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const int j = 8 * t + 2 * q + c;
+                    const float z = fmaxf(acc[t][2 * h + c], 0.f);
+                    sA[rr * d.AS + j] = z;
+                    if (A_save && r < rows && j < hid) A_save[size_t(r) * hid + j] = z;
+                }
+            }
+        for (int i = lane; i < 16 * (d.KP2 - hid); i += 32) {
+            const int rr = i / (d.KP2 - hid), k = hid + (i - rr * (d.KP2 - hid));
+            sA[rr * d.AS + k] = k == hid ? 1.f : 0.f;
+        }
+        __syncwarp();
+        // layer 2: Y = [A, 1] [W2; b2], NT2 tiles of 8 outputs
+        constexpr int NT2 = 12;                   // outputs <= 96
+        float out[NT2][4];
+#pragma unroll
+        for (int t = 0; t < NT2; ++t) out[t][0] = out[t][1] = out[t][2] = out[t][3] = 0.f;
+        for (int k0 = 0; k0 < d.KP2; k0 += 8) {
+            const float av[4] = {sA[g * d.AS + k0 + q], sA[(g + 8) * d.AS + k0 + q], sA[g * d.AS + k0 + q + 4],
+                                 sA[(g + 8) * d.AS + k0 + q + 4]};
+            uint32_t ah[4], al[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                ah[i] = tf32_of(av[i]);
+                al[i] = tf32_of(av[i] - __uint_as_float(ah[i]));
+            }
+#pragma unroll
+            for (int t = 0; t < NT2; ++t) {
+                if (8 * t >= kout) break;
+                const uint32_t b0 = __float_as_uint(sW2[(k0 + q) * d.OS + 8 * t + g]);
+                const uint32_t b1 = __float_as_uint(sW2[(k0 + q + 4) * d.OS + 8 * t + g]);
+                mma_m16n8k8_tf32(out[t], al, b0, b1);
+                mma_m16n8k8_tf32(out[t], ah, b0, b1);
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < NT2; ++t)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int r = r0 + g + 8 * h;
+                if (r >= rows) continue;
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const int o = 8 * t + 2 * q + c;
+                    if (o >= kout) continue;
+                    const float y = out[t][2 * h + c];
+                    if (ymode == 0) Y[size_t(r) * kout + o] = y;
+                    else if (ymode == 1) Y[size_t(r) * kout + o] += y;
+                    else atomicAdd(Y + size_t(ydst[r]) * kout + o, y);
+                }
+            }
+        __syncwarp();
+    }
+}
+
 // loss += sum (out - target)^2 / count; dout = 2 (out - target) / count
 __global__ void mse_kernel(const float *__restrict__ out, const float *__restrict__ tgt, int64_t count,
                            float *__restrict__ dout, float *__restrict__ loss) {
@@ -310,6 +467,7 @@ struct hb_mpnn {
     int64_t step = 0;
     cudaStream_t stream = nullptr;
     std::unordered_map<uint64_t, Graph> graphs;   // keyed by the problem's unique id
+    bool tensor_cores = true;                     // forward MLPs on mma.sync TF32 (hidden 32 or 64)
 };
 
 namespace {
@@ -354,6 +512,21 @@ DSegs dsegs(std::initializer_list<DSeg> l) {
 hb_status run_fwd(hb_mpnn *net, int which, const Segs &in, int rows, float *A_save, float *Y, int ymode,
                   const int *ydst) {
     const int kin = net->kin[size_t(which)], kout = net->kout[size_t(which)], H = net->hidden;
+    if (net->tensor_cores && (H == 32 || H == 64) && kout <= 96 && rows > 0) {
+        const size_t sm = tc_smem_floats(tc_dims(kin, H, kout)) * sizeof(float);
+        const int grid = grid_for(rows, kTcWarps * 16, 2 * 152);
+        if (H == 64) {
+            MP_CUDA(cudaFuncSetAttribute(mlp_fwd_tc_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
+            mlp_fwd_tc_kernel<8><<<grid, 32 * kTcWarps, sm, net->stream>>>(
+                in, net->P16.p + net->off[size_t(which)], H, kout, rows, A_save, Y, ymode, ydst);
+        } else {
+            MP_CUDA(cudaFuncSetAttribute(mlp_fwd_tc_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
+            mlp_fwd_tc_kernel<4><<<grid, 32 * kTcWarps, sm, net->stream>>>(
+                in, net->P16.p + net->off[size_t(which)], H, kout, rows, A_save, Y, ymode, ydst);
+        }
+        MP_CUDA(cudaGetLastError());
+        return HB_OK;
+    }
     const size_t sm = fwd_smem(kin, H, kout);
     MP_CUDA(cudaFuncSetAttribute(mlp_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
     mlp_fwd_kernel<<<grid_for(rows, kWarps), 32 * kWarps, sm, net->stream>>>(
@@ -636,6 +809,12 @@ hb_status hb_mpnn_create(const hb_mpnn_config *cfg, int device, hb_mpnn **out) {
     }
     *out = net;
     return hb_mpnn_set_params(net, p.data());
+}
+
+hb_status hb_mpnn_set_tensor_cores(hb_mpnn *net, int enable) {
+    if (!net) return set_error(HB_ERR_INVALID_ARG, "null network");
+    net->tensor_cores = enable != 0;
+    return HB_OK;
 }
 
 hb_status hb_mpnn_destroy(hb_mpnn *net) {

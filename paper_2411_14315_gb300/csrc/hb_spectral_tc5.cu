@@ -150,10 +150,10 @@ __global__ void __launch_bounds__(128) spectral_tc5_kernel(const float *__restri
         *reinterpret_cast<uint32_t *>(sBh + canon<NT>(m, k)) = hi;
         *reinterpret_cast<uint32_t *>(sBl + canon<NT>(m, k)) = tf32_rna(b - __uint_as_float(hi));
     }
-    // X rows past the tile's 3 NPT rows and the zero columns k in [NT, K) never change
+    // X rows past the tile's 3 NPT rows and the zero columns k in [4 ceil(NT / 4), K) never change
     for (int i = tid; i < kTc5Rows * K; i += 128) {
         const int m = i / K, k = i - m * K;
-        if (m >= 3 * NPT || k >= NT) {
+        if (m >= 3 * NPT || k >= 4 * ((NT + 3) / 4)) {
             *reinterpret_cast<uint32_t *>(sAh + canon<NT>(m, k)) = 0u;
             *reinterpret_cast<uint32_t *>(sAl + canon<NT>(m, k)) = 0u;
         }
@@ -174,28 +174,45 @@ __global__ void __launch_bounds__(128) spectral_tc5_kernel(const float *__restri
     const uint32_t tmem = tmem_slot;
     constexpr uint32_t idesc = idesc_tf32<NC>();
     uint32_t phase = 0;
+    // work item (velocity row m of the tile, K chunk c of 4 instances): row m is (node m / 3, field m % 3);
+    // CH chunks per row carry real instances (the rest of K is zero padding written once above); LPT
+    // items per thread, loaded one tile ahead into registers
+    constexpr int CH = (NT + 3) / 4, ITEMS = 3 * NPT * CH, LPT = (ITEMS + 127) / 128;
+    float pre[LPT][4];
+    auto fetch = [&](int64_t tile) {
+        const int64_t b0 = tile * NPT;
+        const int nb = int(n_nodes - b0 < NPT ? n_nodes - b0 : NPT);
+#pragma unroll
+        for (int u = 0; u < LPT; ++u) {
+            const int i = tid + 128 * u, m = i / CH, c = i - m * CH, l = m / 3;
+            const float *row = v + (b0 + l) * N4 + (m - 3 * l) * NT + 4 * c;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) pre[u][q] = (i < ITEMS && l < nb && 4 * c + q < NT) ? row[q] : 0.f;
+        }
+    };
+    fetch(blockIdx.x);
     for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
         const int64_t n0 = t * NPT;
         const int nn = int(n_nodes - n0 < NPT ? n_nodes - n0 : NPT);
-        // X tile: the velocity rows (node l, field f) of the tile's nodes, read as whole node rows of 4 N
-        // values with 16-byte loads (the pressure values are dropped); rows of missing nodes are 0
-        const float4 *src = reinterpret_cast<const float4 *>(v + n0 * N4);
-        for (int i = tid; i < NPT * N4 / 4; i += 128) {
-            const int l = (4 * i) / N4;
-            float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (l < nn) q = src[i];
-            const float e[4] = {q.x, q.y, q.z, q.w};
+        // X tile from the prefetched rows: TF32 head and tail, one 16-byte store each per chunk (a chunk is
+        // one row of a core matrix in the canonical layout)
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const int pos = 4 * i + c - l * N4, f = pos / NT;
-                if (f < 3) {
-                    const int m = 3 * l + f, k = pos - f * NT;
-                    const uint32_t hi = tf32_rna(e[c]);
-                    *reinterpret_cast<uint32_t *>(sAh + canon<NT>(m, k)) = hi;
-                    *reinterpret_cast<uint32_t *>(sAl + canon<NT>(m, k)) = tf32_rna(e[c] - __uint_as_float(hi));
-                }
+        for (int u = 0; u < LPT; ++u) {
+            const int i = tid + 128 * u;
+            if (i >= ITEMS) continue;
+            const int m = i / CH, c = i - m * CH;
+            uint4 hv, lv;
+            uint32_t *h = &hv.x, *lo = &lv.x;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                h[q] = tf32_rna(pre[u][q]);
+                lo[q] = tf32_rna(pre[u][q] - __uint_as_float(h[q]));
             }
+            *reinterpret_cast<uint4 *>(sAh + canon<NT>(m, 4 * c)) = hv;
+            *reinterpret_cast<uint4 *>(sAl + canon<NT>(m, 4 * c)) = lv;
         }
+        // the next tile's rows are in flight while this one is multiplied and written back
+        if (t + gridDim.x < n_tiles) fetch(t + gridDim.x);
         // generic-proxy writes of the operands -> visible to the tensor core (async proxy)
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -257,11 +274,11 @@ __global__ void __launch_bounds__(128) spectral_tc5_kernel(const float *__restri
 template <int NT>
 void launch_tc5(const float *v, const float *H, const uint8_t *flag, float *W, int64_t n_nodes, float rho, float shift,
                 const double *shift_dev, int *err, cudaStream_t s) {
-    static LaunchCache cache;
     auto kern = spectral_tc5_kernel<NT>;
     const size_t smem = Tc5<NT>::SMEM;
-    // at most 8 blocks per SM: 8 x 32 = 256 of the 512 TMEM columns, so an allocation never waits
-    const int per = std::min(8, cached_blocks_per_sm(cache, kern, 128, smem));
+    // 4 blocks per SM (4 x ~42 KB of shared memory; 4 x 32 = 128 of the 512 TMEM columns, so an allocation
+    // never waits); the loop is persistent over the tiles
+    const int per = 4;
     const int64_t tiles = (n_nodes + Tc5<NT>::NPT - 1) / Tc5<NT>::NPT;
     const int grid = int(std::min<int64_t>(tiles, int64_t(per) * device_sms()));
     kern<<<grid, 128, smem, s>>>(v, H, flag, W, n_nodes, rho, shift, shift_dev, err);

@@ -469,6 +469,8 @@ void launch_vel_norm2(const double *x, int64_t n, double *partials, double *resu
 
 template void launch_convert<double, float>(const double *, float *, int64_t, cudaStream_t);
 template void launch_convert<float, double>(const float *, double *, int64_t, cudaStream_t);
+template void launch_convert<double, double>(const double *, double *, int64_t, cudaStream_t);
+template void launch_convert<float, float>(const float *, float *, int64_t, cudaStream_t);
 template void launch_precond<float>(const double *, const double *, float *, int64_t, cudaStream_t);
 template void launch_precond<double>(const double *, const double *, double *, int64_t, cudaStream_t);
 

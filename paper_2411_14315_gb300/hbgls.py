@@ -40,7 +40,7 @@ class hb_solve_opts(C.Structure):
                 ("gmres_restart", C.c_int), ("max_gmres", C.c_int), ("max_steps", C.c_int),
                 ("dt_pseudo", C.c_double), ("cfl", C.c_double), ("use_learned", C.c_int),
                 ("verbose", C.c_int), ("ser", C.c_int), ("ser_max", C.c_double), ("r_ref", C.c_double),
-                ("assembled", C.c_int), ("precond", C.c_int)]
+                ("assembled", C.c_int), ("precond", C.c_int), ("line_search", C.c_int)]
 
 
 class hb_report(C.Structure):
@@ -111,6 +111,8 @@ SIGNATURES = {
     "hb_residual": ([_P, _DP, _DP, C.c_int], C.c_int),
     "hb_jv": ([_P, _DP, _DP, _DP, C.c_int, C.c_int, C.c_double], C.c_int),
     "hb_jacobi_diag": ([_P, _DP, _DP, C.c_int, C.c_double], C.c_int),
+    "hb_jv_f32": ([_P, C.POINTER(C.c_float), C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_int, C.c_double],
+                  C.c_int),
     "hb_residual_dev": ([_P, _VP, _VP, C.c_int, _VP], C.c_int),
     "hb_jv_dev": ([_P, _VP, _VP, _VP, C.c_int, C.c_int, C.c_double, _VP], C.c_int),
     "hb_jacobi_diag_dev": ([_P, _VP, _VP, C.c_int, C.c_double, _VP], C.c_int),
@@ -125,6 +127,7 @@ SIGNATURES = {
     "hb_jv_dev_noalloc": ([_P, _VP, _VP, _VP, C.c_int, C.c_int, C.c_double, _VP], C.c_int),
     "hb_mpnn_create": ([C.c_void_p, C.c_int, C.POINTER(_P)], C.c_int),
     "hb_mpnn_destroy": ([_P], C.c_int),
+    "hb_mpnn_set_tensor_cores": ([_P, C.c_int], C.c_int),
     "hb_mpnn_num_params": ([_P], C.c_int64),
     "hb_mpnn_get_params": ([_P, C.POINTER(C.c_float)], C.c_int),
     "hb_mpnn_set_params": ([_P, C.POINTER(C.c_float)], C.c_int),
@@ -311,6 +314,16 @@ class Problem:
         _check(lib().hb_jv(self._h, _dptr(y), _dptr(v), _dptr(r), kind, precision, shift))
         return r
 
+    def jv_f32(self, y, v, kind: int = PAPER, shift: float = 0.0, out=None):
+        """hb_jv_f32: FP32 host buffers in and out (FP32 kernels)."""
+        y = np.ascontiguousarray(y, dtype=np.float32).reshape(self.shape)
+        v = np.ascontiguousarray(v, dtype=np.float32).reshape(self.shape)
+        r = np.empty(self.shape, dtype=np.float32) if out is None else out
+        fp = C.POINTER(C.c_float)
+        _check(lib().hb_jv_f32(self._h, y.ctypes.data_as(fp), v.ctypes.data_as(fp), r.ctypes.data_as(fp), kind,
+                               shift))
+        return r
+
     def jacobi_diag(self, y, precision: int = FP64, shift: float = 0.0):
         y = _f64(y, self.shape)
         d = np.empty(self.shape)
@@ -463,6 +476,10 @@ class MPNN:
             self.close()
         except Exception:
             pass
+
+    def set_tensor_cores(self, enable: bool):
+        """hb_mpnn_set_tensor_cores: forward MLPs on the tensor cores (True) or on FP32 FMAs (False)."""
+        _check(lib().hb_mpnn_set_tensor_cores(self._h, int(bool(enable))))
 
     @property
     def num_params(self) -> int:

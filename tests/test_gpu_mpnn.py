@@ -63,11 +63,15 @@ def test_graph_inputs_match_oracle_definition():
         assert np.allclose(lib[(int(so[k]), int(do[k]))], eo[k], atol=2e-6)
 
 
-def test_loss_and_gradient_match_oracle():
+@pytest.mark.parametrize("tensor_cores", [True, False])
+def test_loss_and_gradient_match_oracle(tensor_cores):
+    """Loss and parameter gradient against the FP64 oracle with BF16-exact weights, with the forward MLPs on
+    the tensor cores (TF32 head/tail split, FP32 accumulation) and on FP32 FMAs."""
     from paper_2411_14315_gb300 import hbgls
     spec = _spec()
     gp = P.gpu_problem(spec)
     net = hbgls.MPNN(spec.n_h, seed=5)
+    net.set_tensor_cores(tensor_cores)
     M = 2 * spec.n_h + 1
     shapes = MO.layer_shapes(MO.F_IN, MO.F_E, 4 * M, hidden=64, layers=3)
     rng = np.random.default_rng(6)
@@ -108,3 +112,22 @@ def test_training_reduces_loss_and_warm_start_sets_state():
     ora = P.oracle_problem(spec)
     mask, g = ora.dirichlet()
     assert np.allclose(y[mask, :3], g[mask], atol=1e-12)
+
+
+def test_tensor_core_forward_matches_fma_forward():
+    """The prediction with tensor-core MLPs equals the FP32-FMA prediction to FP32 accuracy (hidden 32 and
+    64, output widths of N = 7 and N = 21)."""
+    from paper_2411_14315_gb300 import hbgls
+    for n_h, hidden in ((3, 64), (10, 64), (3, 32)):
+        spec = _spec(n_h=n_h)
+        gp = P.gpu_problem(spec)
+        net = hbgls.MPNN(n_h, hidden=hidden, seed=9)
+        p = net.get_params()
+        net.set_params(p + np.random.default_rng(3).normal(0, 0.05, p.shape).astype(np.float32))
+        net.set_tensor_cores(False)
+        a = net.predict(gp)
+        net.set_tensor_cores(True)
+        b = net.predict(gp)
+        assert np.linalg.norm(b - a) <= 2e-5 * np.linalg.norm(a), (n_h, hidden)
+        net.close()
+        gp.close()

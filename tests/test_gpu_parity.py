@@ -87,12 +87,12 @@ def test_paper_tangent_launch_variants(n_h):
     y = I.random_state(spec.mesh.n_nodes, spec.N, 71)
     v = I.random_state(spec.mesh.n_nodes, spec.N, 72)
     ref = O.jv_paper(ora, y, v, shift=0.8)
-    for var in (0, 1, 2, 3, 4, 5):
+    for var in range(7):
         gp.set_launch_variant(var)
         assert gp.launch_variant() == var
         assert relerr(gp.jv(y, v, 0, 1, 0.8), ref) < TOL[1], var
     with pytest.raises(RuntimeError):
-        gp.set_launch_variant(6)
+        gp.set_launch_variant(7)
 
 
 def test_paper_tangent_variants_many_patches_per_block():
@@ -108,7 +108,7 @@ def test_paper_tangent_variants_many_patches_per_block():
     y32 = y.astype(np.float32).astype(np.float64)
     v32 = v.astype(np.float32).astype(np.float64)
     ref = O.jv_paper(ora, y32, v32, shift=300.0)
-    for var in (0, 1, 4, 5):
+    for var in (0, 1, 4, 5, 6):
         gp.set_launch_variant(var)
         assert relerr(gp.jv(y32, v32, 0, 1, 300.0), ref) < TOL[1], var
     gp.close()
@@ -276,3 +276,15 @@ def test_spectral_tcgen05_many_tiles():
     with pytest.raises(RuntimeError):
         gp.set_spectral_path(3)
     gp.close()
+
+
+@pytest.mark.parametrize("kind", [0, 1, 2])
+def test_fp32_host_buffer_entry_point(box, kind):
+    """hb_jv_f32 (FP32 host buffers) against the oracle at the FP32-rounded state and direction."""
+    spec, ora, gp = box
+    y = I.random_state(spec.mesh.n_nodes, spec.N, 35).astype(np.float32)
+    v = I.random_state(spec.mesh.n_nodes, spec.N, 36).astype(np.float32)
+    ref = (O.jv_exact if kind == 1 else O.jv_paper)(ora, y.astype(np.float64), v.astype(np.float64), shift=1.1)
+    got = gp.jv_f32(y, v, kind=kind, shift=1.1)
+    assert got.dtype == np.float32
+    assert relerr(got.astype(np.float64), ref) < TOL[1]

@@ -29,9 +29,10 @@ def channel_root():
     return spec, ora, y
 
 
-@pytest.mark.parametrize("precision,precond", [(0, 0), (1, 0), (0, 1), (1, 1)])
+@pytest.mark.parametrize("precision,precond", [(0, 0), (1, 0), (0, 1), (1, 1), (0, 2), (1, 2)])
 def test_solution_matches_oracle_root(channel_root, precision, precond):
-    """Plain Jacobi (the paper's) and node-block preconditioning reach the same root."""
+    """Plain Jacobi (the paper's), node-block and aggregation-multigrid preconditioning reach the same
+    root."""
     spec, ora, y_ref = channel_root
     gp = P.gpu_problem(spec)
     rep = gp.solve(precision=precision, rtol=1e-12, precond=precond)
@@ -42,3 +43,23 @@ def test_solution_matches_oracle_root(channel_root, precision, precond):
     r = O.residual(ora, y)
     assert np.linalg.norm(r) <= 1e-9 * np.linalg.norm(O.residual(ora, ora.initial_state()))
     gp.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_multigrid_preconditioner_on_the_pipe(precision):
+    """On the Womersley pipe (~3,000 tets, N = 9; the multigrid hierarchy has a coarse level) the solve with
+    the multigrid preconditioner ends at the state of the Jacobi-preconditioned solve (1e-8) with fewer
+    GMRES iterations."""
+    spec = P.womersley_spec()
+    ref = P.gpu_problem(spec)
+    r0 = ref.solve(precision=0, rtol=1e-12, max_steps=300)
+    assert r0["status"] == 0
+    yref = ref.instances()
+    gp = P.gpu_problem(spec)
+    rep = gp.solve(precision=precision, rtol=1e-11, max_steps=300, precond=2)
+    assert rep["status"] == 0
+    assert relerr(gp.instances(), yref) < 1e-8
+    print("GMRES iterations: jacobi", r0["gmres_iters"], "multigrid", rep["gmres_iters"])
+    assert rep["gmres_iters"] < r0["gmres_iters"]
+    gp.close()
+    ref.close()

@@ -20,12 +20,14 @@ pytestmark = pytest.mark.gpu
 TOL = {0: 1e-12, 1: 1e-5}
 
 
+@pytest.mark.parametrize("n_h", [3, 10])
 @pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("kind", [0, 1])
-def test_noalloc_jv_matches_allocating_jv_twice(precision, kind):
+def test_noalloc_jv_matches_allocating_jv_twice(precision, kind, n_h):
+    """N = 7 (generic in-patch H) and N = 21 (the circulant kernel in registers)."""
     torch = pytest.importorskip("torch")
     from paper_2411_14315_gb300 import hbgls
-    spec = P.box_spec(seed=77, n=(6, 4, 4), n_h=3, resistance=True)
+    spec = P.box_spec(seed=77, n=(6, 4, 4), n_h=n_h, resistance=True)
     gp = P.gpu_problem(spec)
     gp.info()                                   # prepares the boundary data (allocates, once)
     dt = torch.float64 if precision == 0 else torch.float32
@@ -49,6 +51,28 @@ def test_noalloc_jv_matches_allocating_jv_twice(precision, kind):
         assert np.linalg.norm(o - r) / np.linalg.norm(r) < TOL[precision]
     gp.close()
     assert hbgls.HB_OK == 0
+
+
+def test_noalloc_jv_every_fp32_launch_variant():
+    """The FP32 paper-tangent product through hb_jv_dev_noalloc under every launch variant (the pipelined
+    variants need the allocating W pass and run variant 1 here) against hb_jv_dev, N = 21."""
+    torch = pytest.importorskip("torch")
+    spec = P.box_spec(seed=79, n=(6, 4, 4), n_h=10, resistance=True)
+    gp = P.gpu_problem(spec)
+    y = torch.tensor(I.random_state(spec.mesh.n_nodes, spec.N, 93), dtype=torch.float32, device="cuda")
+    v = torch.tensor(I.random_state(spec.mesh.n_nodes, spec.N, 94), dtype=torch.float32, device="cuda")
+    ref = torch.empty_like(y)
+    out = torch.empty_like(y)
+    s = torch.cuda.current_stream()
+    for var in range(7):
+        gp.set_launch_variant(var)
+        gp.info()                               # the variant change asks for prepared data again
+        gp.jv_dev(y, v, ref, 0, 1, 0.4, stream=s)
+        gp.jv_dev_noalloc(y, v, out, 0, 1, 0.4, stream=s)
+        s.synchronize()
+        r = ref.double().cpu().numpy()
+        assert np.linalg.norm(out.double().cpu().numpy() - r) / np.linalg.norm(r) < TOL[1], var
+    gp.close()
 
 
 def test_noalloc_jv_requires_prepared_boundary_data():
