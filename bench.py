@@ -71,8 +71,9 @@ def parse():
     ap.add_argument("--skip-variants", action="store_true", help="skip the per-launch-variant element timings")
     ap.add_argument("--profile-small", type=int, default=0, metavar="TETS",
                     help="run the small-case workload the ncu captures use (a Glenn-like T-junction of ~TETS tets at "
-                         "N = 21: FP32 paper-tangent Jv, the assembled tangent's product, one GMRES restart cycle, and "
-                         "a network prediction on a 30k-tet coronary-like tube) and exit")
+                         "N = 21: FP32 paper-tangent Jv with both tensor-core spectral passes, the assembled tangent's "
+                         "product, one GMRES restart cycle, and a network prediction on a 30k-tet coronary-like tube) "
+                         "and exit")
     ap.add_argument("--march", action="store_true",
                     help="also time the conventional time-marching solver against the HB solve on the Womersley "
                          "pipe (~3,000 tets, N = 9)")
@@ -751,6 +752,10 @@ def profile_small(n_tets: int):
     o = torch.empty_like(y)
     for _ in range(3):
         p.jv_dev(y, v, o, hbgls.PAPER, hbgls.FP32, 300.0, stream=s)
+    p.set_spectral_path(0)                       # the tcgen05 form of the spectral pass
+    for _ in range(2):
+        p.jv_dev(y, v, o, hbgls.PAPER, hbgls.FP32, 300.0, stream=s)
+    p.set_spectral_path(1)
     p.assemble_dev(y, hbgls.FP32, stream=s)
     for _ in range(3):
         p.jv_dev(y, v, o, hbgls.ASSEMBLED, hbgls.FP32, 300.0, stream=s)

@@ -47,7 +47,7 @@ def test_womersley_second_order_convergence():
     for level in (1, 2, 3):
         spec, exact = _spec(level)
         gp = P.gpu_problem(spec)
-        rep = gp.solve(precision=1, rtol=1e-9, max_steps=400)
+        rep = gp.solve(precision=1, rtol=1e-9, max_steps=400, precond=2)
         assert rep["status"] == 0
         h = gp.harmonics()
         errs.append(float(np.linalg.norm(h[:, :3] - exact[:, :3]) / np.linalg.norm(exact[:, :3])))
