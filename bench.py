@@ -69,6 +69,9 @@ def parse():
     ap.add_argument("--skip-batch", action="store_true")
     ap.add_argument("--extra", action="store_true", help="also time residual / exact Jv / FP64 rates")
     ap.add_argument("--skip-variants", action="store_true", help="skip the per-launch-variant element timings")
+    ap.add_argument("--learned", action="store_true",
+                    help="also train the learned warm start on coronary-like tubes (~30k tets, N = 21) from the method's "
+                         "own solves and time cold vs warm solves of held-out tubes (a few minutes)")
     ap.add_argument("--profile-small", type=int, default=0, metavar="TETS",
                     help="run the small-case workload the ncu captures use (a Glenn-like T-junction of ~TETS tets at "
                          "N = 21: FP32 paper-tangent Jv with both tensor-core spectral passes, the assembled tangent's "
@@ -270,24 +273,56 @@ def traffic_from_profile(n_tets: int, n_nodes: int):
 
 
 def time_solves():
-    """Time to solve the Womersley pipe (~3,000 tets, N = 9) to 1e-8 of a tight FP64 solution."""
+    """Time to solve (M2): the mixed-precision solve (FP32 operator, FP64 Arnoldi, residual and update)
+    against the plain FP64 GPU solve, each to 1e-10 of its initial residual, with the error of each
+    against a tight FP64 reference:
+      * the Womersley pipe (~3,000 tets, N = 9) with the paper's Jacobi preconditioner (and the assembled
+        tangent), reference to 1e-13;
+      * the Womersley pipe refined twice (~196k tets) with the multigrid preconditioner, reference to 1e-13;
+      * the coronary-like tube at SURVEY's C4 size (~300k tets, N = 21) with the multigrid
+        preconditioner; reference: the plain FP64 solve itself (a tighter FP64 solve stagnates near 1e-12
+        and takes minutes), and the mixed solve with the paper's Jacobi preconditioner for contrast (its
+        steps capped at 60)."""
     from paper_2411_14315_gb300 import hbgls
     from paper_2411_14315_gb300 import workloads as W
+    out = {}
+
+    def leg(name, spec, runs, ref_opts):
+        res = {"n_tets": spec.mesh.n_tets, "N": spec.N}
+        yref = None
+        if ref_opts is not None:
+            ref = hbgls.Problem.from_spec(spec)
+            rep = ref.solve(check=False, **ref_opts)
+            yref = ref.instances()
+            res["reference"] = {"status": rep["status"], "res_rel": rep["res_final"] / max(rep["res0"], 1e-300),
+                                "seconds": rep["seconds"], "opts": ref_opts}
+            ref.close()
+        for tag, opts in runs:
+            p = hbgls.Problem.from_spec(spec)
+            rep = p.solve(check=False, **opts)
+            y = p.instances()
+            if yref is None:
+                yref = y
+            res[tag] = {"seconds": rep["seconds"], "status": rep["status"], "steps": rep["steps"],
+                        "gmres_iters": rep["gmres_iters"], "jv_calls": rep["jv_calls"],
+                        "res_rel": rep["res_final"] / max(rep["res0"], 1e-300),
+                        "rel_err_vs_fp64_ref": float(np.linalg.norm(y - yref) / np.linalg.norm(yref))}
+            p.close()
+        out[name] = res
+
     spec = W.womersley_spec()
-    out = {"workload": "womersley pipe ~3,000 tets N=9"}
-    ref = hbgls.Problem.from_spec(spec)
-    rep = ref.solve(precision=0, rtol=1e-13, check=False)
-    yref = ref.instances()
-    out["reference"] = {"status": rep["status"], "res_rel": rep["res_final"] / max(rep["res0"], 1e-300)}
-    for name, prec, asm in (("mixed", 1, 0), ("mixed_assembled", 1, 1), ("fp64", 0, 0)):
-        p = hbgls.Problem.from_spec(spec)
-        rep = p.solve(precision=prec, rtol=1e-10, assembled=asm, check=False)
-        y = p.instances()
-        err = float(np.linalg.norm(y - yref) / np.linalg.norm(yref))
-        out[name] = {"seconds": rep["seconds"], "rel_err_vs_fp64_ref": err, "status": rep["status"],
-                     "steps": rep["steps"], "gmres_iters": rep["gmres_iters"], "jv_calls": rep["jv_calls"]}
-        p.close()
-    ref.close()
+    leg(f"womersley_pipe_{spec.mesh.n_tets}_N{spec.N}", spec,
+        [("mixed", dict(precision=1, rtol=1e-10)), ("mixed_assembled", dict(precision=1, rtol=1e-10, assembled=1)),
+         ("fp64", dict(precision=0, rtol=1e-10))], dict(precision=0, rtol=1e-13))
+    spec = W.womersley_spec(level=3)
+    leg(f"womersley_pipe_{spec.mesh.n_tets}_N{spec.N}", spec,
+        [("mixed_multigrid", dict(precision=1, rtol=1e-10, precond=2)),
+         ("fp64_multigrid", dict(precision=0, rtol=1e-10, precond=2))], dict(precision=0, rtol=1e-13, precond=2))
+    spec = W.coronary_spec()
+    leg(f"coronary_like_{spec.mesh.n_tets}_N{spec.N}", spec,
+        [("fp64_multigrid", dict(precision=0, rtol=1e-10, precond=2, max_steps=200)),
+         ("mixed_multigrid", dict(precision=1, rtol=1e-10, precond=2, max_steps=200)),
+         ("mixed_jacobi_60_steps", dict(precision=1, rtol=1e-10, precond=0, max_steps=60))], None)
     return out
 
 
@@ -344,6 +379,35 @@ def time_spectral_paths(prob, y32, v32, flush, stream, shift, reps: int = 20):
         res[["tcgen05", "mma_sync", "fma"][path]] = {"jv_ms": tot / reps, "jv_minus_elem_ms": tot / reps - ems / max(1, en)}
     prob.set_spectral_path(path0)
     return res
+
+
+def time_learned(n_train: int = 32, n_test: int = 8, steps: int = 6000):
+    """The learned warm start on the coronary-like family (30k tets, N = 21): training data from the method's
+    own multigrid-preconditioned mixed solves, training with the project's kernels, then each held-out tube
+    solved cold (default state) and warm (network prediction) to the same absolute residual."""
+    from paper_2411_14315_gb300 import hbgls
+    from paper_2411_14315_gb300 import learned as LR
+    t0 = time.perf_counter()
+    data, rejected = LR.generate(LR.coronary_family(range(7000, 7000 + n_train)), precond=2, rtol=1e-8,
+                                 max_steps=200)
+    t_gen = time.perf_counter() - t0
+    net = hbgls.MPNN(10, seed=1, p_scale=LR.pressure_scale(data))
+    t0 = time.perf_counter()
+    losses = LR.train(net, data, steps=steps, lr=3e-3, lr_final=3e-5)
+    t_train = time.perf_counter() - t0
+    ev = LR.evaluate(net, LR.coronary_family(range(8000, 8000 + n_test)), precond=2, rtol=1e-8, max_steps=200)
+    out = {"family": "coronary-like tubes, ~30k tets, N = 21, multigrid-preconditioned mixed solves to 1e-8",
+           "train_solves": len(data), "rejected": rejected, "generate_s": t_gen, "train_s": t_train,
+           "train_steps": steps, "loss_first": losses[0], "loss_last100": float(np.mean(losses[-100:]))}
+    for key in ("cold", "warm"):
+        out[key] = {"steps": sum(e[key]["steps"] for e in ev), "gmres_iters": sum(e[key]["gmres_iters"] for e in ev),
+                    "seconds": sum(e["t_" + key] for e in ev), "converged": sum(e[key]["status"] == 0 for e in ev)}
+    out["pred_rel_err_median"] = float(np.median([e["pred_rel_err"] for e in ev]))
+    out["warm_vs_cold_max"] = float(max(e["warm_vs_cold"] for e in ev))
+    net.close()
+    for p, _, _ in data:
+        p.close()
+    return out
 
 
 def time_workloads(flush, stream, reps: int = 20):
@@ -716,6 +780,11 @@ def run_ours(args, dist: Dist, spec, config):
                 result["stabilisation_variants"] = {"error": repr(e)}
         if not args.skip_cpu:
             result["cpu_baseline"] = cpu_baseline(spec)
+    if args.learned and dist.rank == 0:
+        try:
+            result["learned_warm_start"] = time_learned()
+        except Exception as e:  # reported, not hidden
+            result["learned_warm_start"] = {"error": repr(e)}
     if args.march and dist.rank == 0:
         try:
             result["time_marching_vs_hb"] = time_march()

@@ -143,8 +143,9 @@ typedef struct {
                                  through their pressure Schur complement; 2: one V-cycle of aggregation
                                  multigrid on the assembled paper tangent + shift M (greedy node
                                  aggregates, Galerkin coarse operators, damped node-block Jacobi
-                                 smoothing); 1 and 2 are extensions that assemble the tangent every outer
-                                 step                                                                  */
+                                 smoothing; after two consecutive linear solves that stop at max_gmres
+                                 above their tolerance the solve continues with 0); 1 and 2 are
+                                 extensions that assemble the tangent every outer step                 */
     int line_search;          /* 1 (default): after the switch, exact Newton without the pseudo shift and a
                                  backtracking line search on ||r|| (step halved up to 4 times until
                                  ||r|| falls by at least 1e-4 of the step fraction; if none does, the

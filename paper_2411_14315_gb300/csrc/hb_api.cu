@@ -2205,6 +2205,8 @@ static hb_status solve_impl(hb_problem *p, const hb_solve_opts &o, hb_report *re
     double eta = 0.1, rn_prev = rn;   // Eisenstat-Walker forcing term of the Newton phase
     double dtk = dt;                  // current pseudo step (adaptive when o.ser)
     bool ls_fallback = false;         // the last Newton step found no decrease: retake it with the shift
+    int pc = o.precond;               // preconditioner in use: multigrid falls back to Jacobi after two
+    int pc_misses = 0;                // consecutive linear solves that miss their tolerance at the cap
     for (int step = 0; step < o.max_steps; ++step) {
         if (!std::isfinite(rn)) {
             result = fail(HB_ERR_NAN, "residual is not finite");
@@ -2238,18 +2240,18 @@ static hb_status solve_impl(hb_problem *p, const hb_solve_opts &o, hb_report *re
         }
         launch_reciprocal(p->kdiag.p, p->kdiag.p, nd, p->stream);   // kdiag holds the inverse diagonal
         HB_LAUNCHED(p, 1);
-        if ((o.assembled && c.mode == MODE_JVP) || o.precond >= 1) {
+        if ((o.assembled && c.mode == MODE_JVP) || pc >= 1) {
             // the paper's tangent assembled once for this step: GMRES applies it as a sparse product
             // (assembled, paper-tangent phase) and / or builds the preconditioner from it (node blocks, or
             // the multigrid hierarchy's coarse operators)
             if (o.precision == 1) HB_TRY(assemble_at<float>(p, p->ky32.p, p->stream));
             else HB_TRY(assemble_at<double>(p, p->y.p, p->stream));
-            if (o.precond == 2) {
+            if (pc == 2) {
                 if (o.precision == 1) HB_TRY(amg_values<float>(p, p->stream));
                 else HB_TRY(amg_values<double>(p, p->stream));
             }
             if (o.assembled && c.mode == MODE_JVP) c.mode = MODE_JVA;
-            c.precond = o.precond;
+            c.precond = pc;
         }
         launch_scale_copy(-1.0, r, b, nd, p->stream);
         HB_LAUNCHED(p, 1);
@@ -2302,6 +2304,10 @@ static hb_status solve_impl(hb_problem *p, const hb_solve_opts &o, hb_report *re
         }
         R.gmres_iters += its;
         R.jv_calls += jvc;
+        if (pc == 2) {
+            pc_misses = (its >= o.max_gmres && relres > tol * 1.0001) ? pc_misses + 1 : 0;
+            if (pc_misses >= 2) pc = 0;
+        }
         const bool search = newton && o.line_search && shift == 0.0;
         if (search) {
             HB_TRY(dalloc(p, p->yprev, size_t(nd)));

