@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--tets", type=int, default=1_000_000)
     ap.add_argument("--n-h", type=int, default=10)
     ap.add_argument("--skip-solve", action="store_true")
+    ap.add_argument("--solve-large", action="store_true",
+                    help="add the time-to-solve leg on the ~300k-tet coronary-like tube (N = 21; minutes)")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
@@ -272,17 +274,17 @@ def traffic_from_profile(n_tets: int, n_nodes: int):
         return None
 
 
-def time_solves():
+def time_solves(large: bool = False):
     """Time to solve (M2): the mixed-precision solve (FP32 operator, FP64 Arnoldi, residual and update)
     against the plain FP64 GPU solve, each to 1e-10 of its initial residual, with the error of each
     against a tight FP64 reference:
       * the Womersley pipe (~3,000 tets, N = 9) with the paper's Jacobi preconditioner (and the assembled
         tangent), reference to 1e-13;
       * the Womersley pipe refined twice (~196k tets) with the multigrid preconditioner, reference to 1e-13;
-      * the coronary-like tube at SURVEY's C4 size (~300k tets, N = 21) with the multigrid
+      * with large: the stenosed coronary-like tube (~300k tets, N = 21) with the multigrid
         preconditioner; reference: the plain FP64 solve itself (a tighter FP64 solve stagnates near 1e-12
         and takes minutes), and the mixed solve with the paper's Jacobi preconditioner for contrast (its
-        steps capped at 60)."""
+        steps capped at 60); a few minutes."""
     from paper_2411_14315_gb300 import hbgls
     from paper_2411_14315_gb300 import workloads as W
     out = {}
@@ -318,6 +320,8 @@ def time_solves():
     leg(f"womersley_pipe_{spec.mesh.n_tets}_N{spec.N}", spec,
         [("mixed_multigrid", dict(precision=1, rtol=1e-10, precond=2)),
          ("fp64_multigrid", dict(precision=0, rtol=1e-10, precond=2))], dict(precision=0, rtol=1e-13, precond=2))
+    if not large:
+        return out
     spec = W.coronary_spec()
     leg(f"coronary_like_{spec.mesh.n_tets}_N{spec.N}", spec,
         [("fp64_multigrid", dict(precision=0, rtol=1e-10, precond=2, max_steps=200)),
@@ -500,6 +504,49 @@ def time_assembled(prob, y32, v32, out32, flush, stream, shift, units, hbm_peak,
 prob_jv_ms_cache = {}
 
 
+def time_scatter(prob, y32, v32, out32, flush, stream, shift, units, reps: int = 20):
+    """The FP32 paper-tangent product and the FP64 residual with atomic and with deterministic
+    summation (hb_set_scatter): mean time per call (CUDA events, L2 flushed) and, over five repeated
+    calls on equal inputs, how many output entries differ from the first call's."""
+    import torch
+    from paper_2411_14315_gb300 import hbgls
+    y64, v64 = y32.double(), v32.double()
+    o64 = torch.empty_like(y64)
+    cases = {"jv_paper_fp32": (lambda: prob.jv_dev(y32, v32, out32, hbgls.PAPER, hbgls.FP32, shift, stream=stream),
+                               out32, reps),
+             "residual_fp64": (lambda: prob.residual_dev(y64, o64, hbgls.FP64, stream=stream), o64, 5)}
+    out = {}
+    for mode, label in ((1, "atomic"), (0, "deterministic")):
+        prob.set_scatter(mode)
+        for name, (fn, dst, r) in cases.items():
+            fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            tot = 0.0
+            for i in range(r):
+                flush.fill_(float(i))
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                tot += e0.elapsed_time(e1)
+            first = None
+            mismatch = 0
+            for _ in range(5):
+                fn()
+                torch.cuda.synchronize()
+                if first is None:
+                    first = dst.clone()
+                else:
+                    mismatch = max(mismatch, int((dst != first).sum().item()))
+            ms = tot / r
+            out[f"{name}_{label}"] = {"ms": ms, "rate": units / (ms / 1e3), "repeat_mismatch_entries": mismatch,
+                                      "entries": int(dst.numel())}
+    prob.set_scatter(1)
+    out["unit"] = UNIT
+    return out
+
+
 def time_march(spp: int = 1008, periods: int = 4):
     """The paper's comparison (Sec. 3) on one GPU: the HB solve against the conventional time-marching
     GLS solver (tau_hat, generalized-alpha, GMRES 0.03, Newton 1e-3 per step) marched from rest for
@@ -680,6 +727,11 @@ def run_ours(args, dist: Dist, spec, config):
     except Exception as e:  # reported, not hidden
         result["spectral_pass"] = {"error": repr(e)}
 
+    try:
+        result["scatter"] = time_scatter(prob, y32, v32, out32, flush, stream, shift, units)
+    except Exception as e:  # reported, not hidden
+        result["scatter"] = {"error": repr(e)}
+
     # end to end through the C ABI with pinned host buffers
     if not args.skip_e2e:
         hy = torch.empty((n, 4, N), dtype=torch.float64, pin_memory=True).numpy()
@@ -771,7 +823,7 @@ def run_ours(args, dist: Dist, spec, config):
                 result["batch"] = {"error": repr(e)}
         if not args.skip_solve:
             try:
-                result["time_to_solve"] = time_solves()
+                result["time_to_solve"] = time_solves(large=args.solve_large)
             except Exception as e:  # reported, not hidden
                 result["time_to_solve"] = {"error": repr(e)}
             try:

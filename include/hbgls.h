@@ -102,6 +102,25 @@ hb_status hb_set_backflow(hb_problem *p, double beta);
  * assembly of hb_assemble_dev.  Errors: INVALID_ARG for another variant or a negative / non-finite ct_dt. */
 hb_status hb_set_stabilization(hb_problem *p, int variant, double ct_dt);
 
+/* Element-to-node summation of every later evaluation (residual, Jv of kinds 0-2, Jacobi diagonal,
+ * assembly) and solve of the problem.  The element integrals of Eq. (Rmc) and of the tangent blocks
+ * (Eqs. K_mat, ctangent, F_mat) are summed into each node's rows:
+ *   1 (default): with floating-point atomics from the element and face kernels; the order of the
+ *      additions, and so the last bits of the result, can change from run to run;
+ *   0: deterministic.  Each element stores its contributions in its own slot
+ *      ([element][4 nodes][4 or 7 fields][N]) and each Neumann face in its own
+ *      ([face][3 nodes][3 fields][N]); one gather kernel per call sums every node's slots in a fixed
+ *      order (elements in patch order, then faces), and the row-wise assembly adds a node's element
+ *      blocks in element order.  Resistance-outlet flow rates are summed in face order by one warp per
+ *      outlet and instance.  No floating-point atomics run, so equal inputs give bitwise equal outputs.
+ *      Device memory: about 64 N (FP32) or 128 N (FP64) bytes per element for the paper tangent, 112 N
+ *      or 224 N for the residual and the exact Jacobian, allocated on first use.
+ * hb_jv_dev_noalloc and batches keep the atomic summation.  Synchronises the problem's stream; drops
+ * the last assembly.  INVALID_ARG for another value; hb_get_scatter returns the current setting (-1 for
+ * a null problem). */
+hb_status hb_set_scatter(hb_problem *p, int scatter);
+int hb_get_scatter(const hb_problem *p);
+
 /* Initial state from harmonics ([n_nodes][4][2 n_h + 1]) or NULL for the default: Dirichlet values
  * built in (Sec. 2.3), zero interior velocity, pressure at the mean outlet level.  Dirichlet values
  * always overwrite the velocity of Dirichlet nodes. */
@@ -144,7 +163,8 @@ typedef struct {
                                  multigrid on the assembled paper tangent + shift M (greedy node
                                  aggregates, Galerkin coarse operators, damped node-block Jacobi
                                  smoothing; after two consecutive linear solves that stop at max_gmres
-                                 above their tolerance the solve continues with 0); 1 and 2 are
+                                 with more than half of their right-hand side left the solve
+                                 continues with 0); 1 and 2 are
                                  extensions that assemble the tangent every outer step                 */
     int line_search;          /* 1 (default): after the switch, exact Newton without the pseudo shift and a
                                  backtracking line search on ||r|| (step halved up to 4 times until
@@ -152,6 +172,10 @@ typedef struct {
                                  step is retaken with the pseudo shift); 0: the pseudo shift stays in the
                                  Newton phase until dt exceeds ser_max times the CFL step (an extension
                                  either way; the paper stops at the switch criterion, Sec. 2.3)        */
+    int scatter;              /* element-to-node summation (Sec. 2.2's assembly of the element
+                                 integrals): 1 (default) floating-point atomics; 0 deterministic (the
+                                 colour-free equivalent of a colour-class scatter, see hb_set_scatter).
+                                 hb_solve applies it to the problem (it stays set afterwards)          */
 } hb_solve_opts;
 
 typedef struct {
@@ -223,7 +247,9 @@ hb_status hb_jacobi_diag_dev(hb_problem *p, const void *y, void *d, int precisio
  *    that device current); make that first call before any stream capture;
  *  - all calls in the process share the one scratch array per device and it keeps the last call's
  *    contents (the call clears the part it uses before use): calls that overlap in time on the GPU,
- *    from any problem or stream, race on it and must be serialised by the caller. */
+ *    from any problem or stream, race on it and must be serialised by the caller;
+ *  - it sums with atomics whatever hb_set_scatter says (the deterministic summation needs per-element
+ *    slot buffers). */
 hb_status hb_jv_dev_noalloc(hb_problem *p, const void *y, const void *v, void *jv, int kind, int precision,
                             double shift, void *stream);
 
@@ -335,6 +361,7 @@ hb_status hb_get_march_samples(hb_problem *p, double *out);
  * small problems of any N share the SMs; the FP32 paper-tangent pass takes the first problem's launch
  * variant, see hb_set_launch_variant),
  * then the boundary terms of each problem (prescribed velocity rows are written by the element pass).
+ * A batch sums with atomics whatever hb_set_scatter says of its problems.
  * All problems must live on one device; their boundary data are prepared at creation.  The graph is captured on first use and again whenever the
  * operands, kind or shift change.  Work is ordered after `stream` (NULL: the first problem's stream) and
  * `stream` waits for it. */

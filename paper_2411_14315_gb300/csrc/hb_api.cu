@@ -87,6 +87,7 @@ struct PatchSetDev {
     DBuf<uint32_t> lconn;
     DBuf<T> geom;
     std::vector<int> h_eptr, h_nptr, h_nodes;   // host copies, to rebuild the slots' Dirichlet bits
+    DBuf<int> det_ptr, det_slot;        // deterministic scatter: node -> (element in patch order x 4 + a)
     PatchView<T> view() const {
         return PatchView<T>{P, nl_max, ep_max, slot_ints(nl_max), slots.p, lconn.p, geom.p};
     }
@@ -180,6 +181,7 @@ struct hb_problem {
         bool ready32 = false, ready64 = false;   // coefficients assembled (at the last state given)
         bool mass32_done = false, mass64_done = false;
         std::vector<int> h_rowptr, h_col;         // host copy of the pair structure (multigrid set-up)
+        DBuf<int> det_ptr, det_slot;              // deterministic assembly: row node -> (element x 4 + a)
     } as;
     // aggregation multigrid on the assembled tangent (precond = 2): level 0 is `as`; levels 1.. are built
     struct AmgLevel {
@@ -204,6 +206,11 @@ struct hb_problem {
     DBuf<int> d_err;                      // status word of the pipelined element pass (0: no wait gave up)
     int stab = 0;                         // 0: GLS as printed; 1: full RBVMS (hb_set_stabilization)
     int spectral_path = 1;                // FP32 W pass: 0 tcgen05, 1 mma.sync, 2 FMAs (hb_set_spectral_path)
+    int scatter = 1;                      // 0: deterministic (slots + fixed-order gather), 1: atomic (hb_set_scatter)
+    DBuf<int> det_fptr, det_fslot;        // node -> Neumann-face slots (face x 3 + b)
+    DBuf<int> det_optr, det_oface;        // resistance outlet o -> its Neumann faces, in face order
+    DBuf<float> det_c32, det_t32, det_f32;     // element slots, T sums, face slots (FP32)
+    DBuf<double> det_c64, det_t64, det_f64;    // (FP64)
     double ct_dt = 0;                     // coefficient of (1 / dt)^2 under the root of tau, dt = T / N
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev;
     size_t prof_used = 0;
@@ -393,6 +400,20 @@ hb_status upload_slots(hb_problem *p, PatchSetDev<T> &ps, const std::vector<uint
     return upload(p, ps.slots, sl);
 }
 
+// Lists of the deterministic scatter: node -> the slots whose node is it, in increasing slot order
+// (counting sort of node_of_slot; entries < 0 are skipped).
+void node_slot_lists(const std::vector<int> &node_of_slot, int64_t n_nodes, std::vector<int> &ptr,
+                     std::vector<int> &list) {
+    ptr.assign(size_t(n_nodes) + 1, 0);
+    for (int nd : node_of_slot)
+        if (nd >= 0) ++ptr[size_t(nd) + 1];
+    for (int64_t i = 0; i < n_nodes; ++i) ptr[size_t(i) + 1] += ptr[size_t(i)];
+    list.assign(size_t(ptr[size_t(n_nodes)]), 0);
+    std::vector<int> fill(ptr.begin(), ptr.end() - 1);
+    for (size_t k = 0; k < node_of_slot.size(); ++k)
+        if (node_of_slot[k] >= 0) list[size_t(fill[size_t(node_of_slot[k])]++)] = int(k);
+}
+
 // Patches sized so that `size_mode`'s shared-memory layout fits `budget` (two blocks per SM for FP32,
 // one for FP64), unless nl_override gives the node cap.
 template <typename T>
@@ -413,6 +434,12 @@ hb_status make_patchset(hb_problem *p, PatchSetDev<T> &ps, const std::vector<int
     for (int64_t k = 0; k < p->n_tets; ++k)
         for (int a = 0; a < 4; ++a) tets_p[size_t(4 * k + a)] = tets_ord[size_t(4 * hp.perm[size_t(k)] + a)];
     HB_TRY(upload(p, p->d_tets_ord, tets_p));
+    {
+        std::vector<int> ptr, list;
+        node_slot_lists(tets_p, p->n_nodes, ptr, list);
+        HB_TRY(upload(p, ps.det_ptr, ptr));
+        HB_TRY(upload(p, ps.det_slot, list));
+    }
     HB_TRY(dalloc(p, ps.geom, size_t(p->n_tets) * kGeomStride));
     launch_geom<T>(p->d_xyz.p, p->d_tets_ord.p, int(p->n_tets), p->mu / p->rho, ps.geom.p, p->stream);
     HB_LAUNCHED(p, 1);
@@ -601,6 +628,15 @@ hb_status prepare_bc(hb_problem *p) {
     HB_LAUNCHED(p, p->n_dir > 0 ? 1 : 0);
     HB_TRY(upload(p, p->d_nf_nodes, nf_nodes));
     HB_TRY(upload(p, p->d_nf_out, nf_out));
+    {
+        std::vector<int> ptr, list;
+        node_slot_lists(nf_nodes, n, ptr, list);
+        HB_TRY(upload(p, p->det_fptr, ptr));
+        HB_TRY(upload(p, p->det_fslot, list));
+        node_slot_lists(nf_out, int64_t(p->outlets.size()), ptr, list);
+        HB_TRY(upload(p, p->det_optr, ptr));
+        HB_TRY(upload(p, p->det_oface, list));
+    }
     HB_TRY(upload(p, p->d_nf_geo64, nf_geo));
     std::vector<float> nf_geo32(nf_geo.begin(), nf_geo.end());
     HB_TRY(upload(p, p->d_nf_geo32, nf_geo32));
@@ -707,6 +743,12 @@ hb_status asm_structure(hb_problem *p) {
     A.h_col = col;
     HB_TRY(upload(p, A.tets, tets));
     HB_TRY(upload(p, A.epos, epos));
+    {
+        std::vector<int> ptr, list;
+        node_slot_lists(tets, n, ptr, list);
+        HB_TRY(upload(p, A.det_ptr, ptr));
+        HB_TRY(upload(p, A.det_slot, list));
+    }
     A.nnz = int64_t(col.size());
     return HB_OK;
 }
@@ -761,6 +803,11 @@ hb_status assemble_at(hb_problem *p, const T *y, cudaStream_t s) {
     a.rho = T(p->rho);
     a.mu = T(p->mu);
     a.omega2 = T(p->omega2 + tau_dt_term(p));
+    if (p->scatter == 0) {          // deterministic: rows in list order
+        a.n_nodes = p->n_nodes;
+        a.rptr = A.det_ptr.p;
+        a.rslot = A.det_slot.p;
+    }
     if (!B::mass_done(A)) {
         HB_CUDA(cudaMemsetAsync(a.mass, 0, size_t(A.nnz) * sizeof(T), s));
         launch_assemble_mass<T>(a, s);
@@ -778,10 +825,26 @@ hb_status assemble_at(hb_problem *p, const T *y, cudaStream_t s) {
 // operators
 
 template <typename T>
+struct DetBufs;
+template <>
+struct DetBufs<float> {
+    static DBuf<float> &c(hb_problem *p) { return p->det_c32; }
+    static DBuf<float> &t(hb_problem *p) { return p->det_t32; }
+    static DBuf<float> &f(hb_problem *p) { return p->det_f32; }
+};
+template <>
+struct DetBufs<double> {
+    static DBuf<double> &c(hb_problem *p) { return p->det_c64; }
+    static DBuf<double> &t(hb_problem *p) { return p->det_t64; }
+    static DBuf<double> &f(hb_problem *p) { return p->det_f64; }
+};
+
+template <typename T>
 hb_status apply_op(hb_problem *p, int mode, const T *y, const T *v, T *out, double shift, cudaStream_t s,
                    const double *shift_dev = nullptr) {
     HB_TRY(prepare_bc(p));
     const int N = p->N;
+    const bool det = p->scatter == 0;      // element and face slots, then one fixed-order gather
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     auto prof_begin = [&]() -> hb_status {
         if (p->prof_on) {
@@ -825,7 +888,7 @@ hb_status apply_op(hb_problem *p, int mode, const T *y, const T *v, T *out, doub
     }
     const int fmode = mode == MODE_JVA ? MODE_JVP : mode;     // boundary terms of the paper tangent
     PatchSetDev<T> &ps = patches<T>(p, fmode);
-    if (mode != MODE_JVA) HB_CUDA(cudaMemsetAsync(out, 0, size_t(p->n_nodes) * 4 * N * sizeof(T), s));
+    if (mode != MODE_JVA && !det) HB_CUDA(cudaMemsetAsync(out, 0, size_t(p->n_nodes) * 4 * N * sizeof(T), s));
     ElemArgs<T> ea;
     ea.pv = ps.view();
     ea.y = y;
@@ -843,6 +906,11 @@ hb_status apply_op(hb_problem *p, int mode, const T *y, const T *v, T *out, doub
     ea.variant = p->jvp_variant;
     ea.err = p->d_err.p;
     ea.rbvms = p->stab;
+    if (det && ps.P > 0 && mode != MODE_JVA) {
+        DBuf<T> &cb = DetBufs<T>::c(p);
+        HB_TRY(dalloc(p, cb, size_t(p->n_tets) * size_t(det_slot_values(mode)) * size_t(N)));
+        ea.cbuf = cb.p;
+    }
     if (ps.P > 0 && mode != MODE_JVA) {
         if (mode == MODE_JVP) {
             // spectral pass over the nodes (each once): W = shift v + rho H v, gathered by the patches
@@ -883,9 +951,55 @@ hb_status apply_op(hb_problem *p, int mode, const T *y, const T *v, T *out, doub
             fa.R = p->d_R64.p;
             fa.Q = p->d_Q64.p;
         }
-        if (p->has_res) HB_CUDA(cudaMemsetAsync(fa.Q, 0, size_t(p->n_out) * N * sizeof(T), s));
+        if (det) {
+            DBuf<T> &fb = DetBufs<T>::f(p);
+            HB_TRY(dalloc(p, fb, size_t(p->n_nf) * 9 * size_t(N)));
+            fa.fbuf = fb.p;
+            fa.optr = p->det_optr.p;
+            fa.oface = p->det_oface.p;
+        } else if (p->has_res) {
+            HB_CUDA(cudaMemsetAsync(fa.Q, 0, size_t(p->n_out) * N * sizeof(T), s));
+        }
         launch_faces<T>(fmode, fa, p->has_res, p->n_out, s);
         HB_LAUNCHED(p, p->has_res ? 2 : 1);
+    }
+    if (det) {
+        DetGatherArgs<T> g;
+        g.n_nodes = p->n_nodes;
+        g.N = N;
+        g.flag = p->d_flag.p;
+        g.v = v;
+        g.H = Hmat<T>(p);
+        g.out = out;
+        g.eptr = g.eslot = g.fptr = g.fslot = nullptr;
+        g.cbuf = g.fbuf = g.tbuf = nullptr;
+        g.presc = 0;
+        const bool faces = mode != MODE_DIAG && p->n_nf > 0;
+        if (faces) {
+            g.fptr = p->det_fptr.p;
+            g.fslot = p->det_fslot.p;
+            g.fbuf = DetBufs<T>::f(p).p;
+        }
+        if (mode == MODE_JVA) {            // faces only, added to the sparse product
+            g.F = 3;
+            if (faces) {
+                launch_det_gather<T>(g, s);
+                HB_LAUNCHED(p, 1);
+            }
+        } else {
+            g.F = det_slot_values(mode) / 4;
+            g.presc = mode == MODE_DIAG ? 1 : (mode == MODE_RES || mode == MODE_TRES) ? 0 : 2;
+            g.eptr = ps.det_ptr.p;
+            g.eslot = ps.det_slot.p;
+            g.cbuf = DetBufs<T>::c(p).p;
+            if (g.F == 7) {
+                DBuf<T> &tb = DetBufs<T>::t(p);
+                HB_TRY(dalloc(p, tb, size_t(p->n_nodes) * 3 * size_t(N)));
+                g.tbuf = tb.p;
+            }
+            launch_det_gather<T>(g, s);
+            HB_LAUNCHED(p, g.F == 7 ? 2 : 1);
+        }
     }
     return HB_OK;
 }
@@ -2114,6 +2228,7 @@ hb_status hb_default_opts(hb_solve_opts *o) {
     o->assembled = 0;
     o->precond = 0;
     o->line_search = 1;
+    o->scatter = 1;
     return HB_OK;
 }
 
@@ -2135,6 +2250,7 @@ hb_status hb_solve(hb_problem *p, const hb_solve_opts *opts, hb_report *rep) {
     if (o.precond < 0 || o.precond > 2)
         return fail(HB_ERR_INVALID_ARG, "precond must be 0 (Jacobi), 1 (node blocks) or 2 (aggregation multigrid)");
     HB_CUDA(cudaSetDevice(p->device));
+    if (o.scatter != p->scatter) HB_TRY(hb_set_scatter(p, o.scatter));
     if (o.use_learned < 0 || o.use_learned > 2) return fail(HB_ERR_INVALID_ARG, "use_learned must be 0, 1 or 2");
     p->learned_dir = false;
     if (o.use_learned) {
@@ -2206,7 +2322,7 @@ static hb_status solve_impl(hb_problem *p, const hb_solve_opts &o, hb_report *re
     double dtk = dt;                  // current pseudo step (adaptive when o.ser)
     bool ls_fallback = false;         // the last Newton step found no decrease: retake it with the shift
     int pc = o.precond;               // preconditioner in use: multigrid falls back to Jacobi after two
-    int pc_misses = 0;                // consecutive linear solves that miss their tolerance at the cap
+    int pc_misses = 0;                // consecutive linear solves that stall at the cap
     for (int step = 0; step < o.max_steps; ++step) {
         if (!std::isfinite(rn)) {
             result = fail(HB_ERR_NAN, "residual is not finite");
@@ -2304,8 +2420,8 @@ static hb_status solve_impl(hb_problem *p, const hb_solve_opts &o, hb_report *re
         }
         R.gmres_iters += its;
         R.jv_calls += jvc;
-        if (pc == 2) {
-            pc_misses = (its >= o.max_gmres && relres > tol * 1.0001) ? pc_misses + 1 : 0;
+        if (pc == 2) {   // a stalled multigrid solve: at the cap with less than half the residual removed
+            pc_misses = (its >= o.max_gmres && relres > 0.5) ? pc_misses + 1 : 0;
             if (pc_misses >= 2) pc = 0;
         }
         const bool search = newton && o.line_search && shift == 0.0;
@@ -2694,7 +2810,7 @@ struct hb_batch {
     std::vector<const void *> y, v;
     std::vector<void *> out;
     int64_t launches_per_replay = 0, launches = 0;
-    static constexpr int kSide = 4;       // side streams of the captured graph's parallel W passes
+    static constexpr int kSide = 8;       // side streams of the captured graph's parallel branches
     cudaStream_t side[kSide] = {};
 };
 
@@ -2792,49 +2908,60 @@ hb_status batch_record(hb_batch *b) {
     const int64_t l0 = p0->launches;
     HB_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
     hb_status st = HB_OK;
+    std::vector<cudaEvent_t> evs;
+    // fork s into the kSide branches (member q on branch q mod kSide), and join them back into s
+    auto fork = [&]() {
+        cudaEvent_t ev = nullptr;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+            st = fail(HB_ERR_CUDA, "event");
+            return;
+        }
+        evs.push_back(ev);
+        cudaEventRecord(ev, s);
+        for (int k = 0; k < hb_batch::kSide; ++k) cudaStreamWaitEvent(b->side[k], ev, 0);
+    };
+    auto join = [&]() {
+        for (int k = 0; k < hb_batch::kSide && st == HB_OK; ++k) {
+            cudaEvent_t ev = nullptr;
+            if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+                st = fail(HB_ERR_CUDA, "event");
+                return;
+            }
+            evs.push_back(ev);
+            cudaEventRecord(ev, b->side[k]);
+            cudaStreamWaitEvent(s, ev, 0);
+        }
+    };
+    if (cudaMemsetAsync(b->counter.p, 0, groups.size() * sizeof(int), s) != cudaSuccess)
+        st = fail(HB_ERR_CUDA, "memset in batch capture");
+    // branches before the element pass: each member's output cleared, then (paper tangent) its node-level
+    // W = shift v + rho H v pass, whose rows the batched element pass gathers
+    if (st == HB_OK) fork();
     for (size_t q = 0; q < b->probs.size() && st == HB_OK; ++q) {
         hb_problem *p = b->probs[q];
-        if (cudaMemsetAsync(b->out[q], 0, size_t(p->n_nodes) * 4 * p->N * sizeof(T), s) != cudaSuccess)
+        cudaStream_t ss = b->side[q % hb_batch::kSide];
+        if (cudaMemsetAsync(b->out[q], 0, size_t(p->n_nodes) * 4 * p->N * sizeof(T), ss) != cudaSuccess) {
             st = fail(HB_ERR_CUDA, "memset in batch capture");
-    }
-    if (st == HB_OK && cudaMemsetAsync(b->counter.p, 0, groups.size() * sizeof(int), s) != cudaSuccess)
-        st = fail(HB_ERR_CUDA, "memset in batch capture");
-    std::vector<cudaEvent_t> evs;
-    if (st == HB_OK && b->mode == MODE_JVP) {
-        // fork: the members' W passes on kSide branches, joined before the element pass
-        cudaEvent_t fork = nullptr;
-        if (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess) st = fail(HB_ERR_CUDA, "event");
-        else {
-            evs.push_back(fork);
-            cudaEventRecord(fork, s);
-            for (int k = 0; k < hb_batch::kSide; ++k) cudaStreamWaitEvent(b->side[k], fork, 0);
-            for (size_t q = 0; q < b->probs.size(); ++q) {
-                hb_problem *p = b->probs[q];
-                cudaStream_t ss = b->side[q % hb_batch::kSide];
-                launch_spectral_w<T>(static_cast<const T *>(b->v[q]), Hmat<T>(p), p->d_flag.p, AsmBufs<T>::W(p->as).p,
-                                     w_stride(p->N, int(sizeof(T))), p->n_nodes, p->N, T(p->rho), T(b->shift), nullptr,
-                                     ss, p->spectral_path, p->d_err.p);
-                p0->launches += 1;
-            }
-            for (int k = 0; k < hb_batch::kSide; ++k) {
-                cudaEvent_t join = nullptr;
-                if (cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess) {
-                    st = fail(HB_ERR_CUDA, "event");
-                    break;
-                }
-                evs.push_back(join);
-                cudaEventRecord(join, b->side[k]);
-                cudaStreamWaitEvent(s, join, 0);
-            }
+            break;
+        }
+        if (b->mode == MODE_JVP) {
+            launch_spectral_w<T>(static_cast<const T *>(b->v[q]), Hmat<T>(p), p->d_flag.p, AsmBufs<T>::W(p->as).p,
+                                 w_stride(p->N, int(sizeof(T))), p->n_nodes, p->N, T(p->rho), T(b->shift), nullptr,
+                                 ss, p->spectral_path, p->d_err.p);
+            p0->launches += 1;
         }
     }
+    if (st == HB_OK) join();
     for (size_t k = 0; k < groups.size() && st == HB_OK; ++k) {
         const BatchGroup<T> &g = groups[k];
         launch_batch_elem<T>(b->mode, g, smem, std::min(b->grid, g.item_end - g.item_begin), s);
         p0->launches += 1;
     }
+    // branches after it: each member's boundary terms
+    if (st == HB_OK) fork();
     for (size_t q = 0; q < b->probs.size() && st == HB_OK; ++q) {
         hb_problem *p = b->probs[q];
+        cudaStream_t ss = b->side[q % hb_batch::kSide];
         const T *y = static_cast<const T *>(b->y[q]);
         const T *v = static_cast<const T *>(b->v[q]);
         T *out = static_cast<T *>(b->out[q]);
@@ -2861,12 +2988,13 @@ hb_status batch_record(hb_batch *b) {
                 fa.R = p->d_R64.p;
                 fa.Q = p->d_Q64.p;
             }
-            if (p->has_res && cudaMemsetAsync(fa.Q, 0, size_t(p->n_out) * p->N * sizeof(T), s) != cudaSuccess)
+            if (p->has_res && cudaMemsetAsync(fa.Q, 0, size_t(p->n_out) * p->N * sizeof(T), ss) != cudaSuccess)
                 st = fail(HB_ERR_CUDA, "memset in batch capture");
-            launch_faces<T>(b->mode, fa, p->has_res, p->n_out, s);
+            launch_faces<T>(b->mode, fa, p->has_res, p->n_out, ss);
             p0->launches += p->has_res ? 2 : 1;
         }
     }
+    if (st == HB_OK) join();
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(s, &graph);
     for (cudaEvent_t ev : evs) cudaEventDestroy(ev);
@@ -3091,6 +3219,26 @@ hb_status hb_set_stabilization(hb_problem *p, int variant, double ct_dt) {
     p->as.ready32 = p->as.ready64 = false;
     return HB_OK;
 }
+
+hb_status hb_set_scatter(hb_problem *p, int scatter) {
+    if (!p) return fail(HB_ERR_INVALID_ARG, "null problem");
+    if (scatter != 0 && scatter != 1) return fail(HB_ERR_INVALID_ARG, "scatter must be 0 (deterministic) or 1 (atomic)");
+    if (scatter == p->scatter) return HB_OK;
+    cudaSetDevice(p->device);
+    if (p->stream) cudaStreamSynchronize(p->stream);
+    p->scatter = scatter;
+    for (auto &gc : p->cycle) {                   // captured cycles hold the old launches
+        if (gc.exec) cudaGraphExecDestroy(gc.exec);
+        gc = hb_problem::CycleGraph{};
+    }
+    // assembled values (and the multigrid levels' mass) were summed in the other order
+    p->as.ready32 = p->as.ready64 = false;
+    p->as.mass32_done = p->as.mass64_done = false;
+    p->amg_mass32 = p->amg_mass64 = false;
+    return HB_OK;
+}
+
+int hb_get_scatter(const hb_problem *p) { return p ? p->scatter : -1; }
 
 hb_status hb_set_spectral_path(hb_problem *p, int path) {
     if (!p) return fail(HB_ERR_INVALID_ARG, "null problem");

@@ -29,6 +29,81 @@ __device__ __forceinline__ float rsqrt_a<float>(float x) { return rsqrtf(x); }
 template <>
 __device__ __forceinline__ double rsqrt_a<double>(double x) { return rsqrt(x); }
 
+// One element at one instance: node ids, prescribed flags, shape gradients and the quadrature values
+// u_q . grad N_b and tau_q of the frozen state.
+template <typename T>
+struct AsmElem {
+    bool dir[4];
+    T gN[4][3], V, w;
+    T udN[4][4], tau[4];           // udN[q][b] = u_q . grad N_b
+};
+
+template <typename T>
+__device__ __forceinline__ void asm_elem_load(const AsmArgs<T> &a, int64_t e, int n, AsmElem<T> &s) {
+    const int N = a.N, N4 = 4 * N;
+    int nd[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        nd[k] = a.tets[4 * e + k];
+        s.dir[k] = a.flag[nd[k]] & 1;
+    }
+    const T *g = a.geom + e * kGeomStride;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) s.gN[k][j] = g[3 * k + j];
+    s.V = g[12];
+    s.w = s.V * T(0.25);
+    const T g2 = g[13] + a.omega2;
+    T u[4][3];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) u[k][j] = a.y[int64_t(nd[k]) * N4 + j * N + n];
+    const T qa = T(kQA), qb = T(kQB);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        T uq[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) uq[j] = qb * (u[0][j] + u[1][j] + u[2][j] + u[3][j]) + (qa - qb) * u[q][j];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) s.udN[q][b] = uq[0] * s.gN[b][0] + uq[1] * s.gN[b][1] + uq[2] * s.gN[b][2];
+        s.tau[q] = rsqrt_a<T>(s.udN[q][1] * s.udN[q][1] + s.udN[q][2] * s.udN[q][2] + s.udN[q][3] * s.udN[q][3] + g2);
+    }
+}
+
+// The (ra, cb) block of one element at one instance added into the pair slot c (stride N between the
+// 8 values): global reductions, or plain read-modify-write where the calling thread owns the row.
+template <typename T, bool OWN>
+__device__ __forceinline__ void asm_pair(const AsmElem<T> &s, int ra, int cb, T rho, T mu, T *c, int N) {
+    const T qa = T(kQA), qb = T(kQB), w = s.w;
+    T kgal = 0, ksupg = 0, gs = 0, ds = 0, lt = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const T Na = (q == ra) ? qa : qb;
+        kgal += Na * s.udN[q][cb];
+        ksupg += s.tau[q] * s.udN[q][ra] * s.udN[q][cb];
+        gs += s.tau[q] * s.udN[q][ra];             // times dN_B/dx_i
+        ds += s.tau[q] * s.udN[q][cb];             // times dN_A/dx_j
+        lt += s.tau[q];
+    }
+    const T gg = s.gN[ra][0] * s.gN[cb][0] + s.gN[ra][1] * s.gN[cb][1] + s.gN[ra][2] * s.gN[cb][2];
+    auto add = [&](T *p, T v) {
+        if constexpr (OWN) *p += v;
+        else atomicAdd(p, v);
+    };
+    if (!s.dir[ra]) {
+        if (!s.dir[cb]) add(c, w * rho * kgal + mu * s.V * gg + w * rho * ksupg);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) add(c + (1 + j) * N, -w * s.gN[ra][j] + w * gs * s.gN[cb][j]);
+    }
+    if (!s.dir[cb]) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) add(c + (4 + j) * N, w * s.gN[cb][j] + w * ds * s.gN[ra][j]);
+    }
+    add(c + 7 * N, (w / rho) * lt * gg);
+}
+
 // One thread per (element, instance): the element's 16 (a, b) blocks at instance n, reduced into the
 // pair slots epos[e][4 a + b] (coalesced over n).
 template <typename T>
@@ -38,66 +113,35 @@ __global__ void assemble_kernel(AsmArgs<T> a) {
     if (i >= a.n_tets * int64_t(N)) return;
     const int64_t e = i / N;
     const int n = int(i - e * N);
-    const int N4 = 4 * N;
-    int nd[4];
-    bool dir[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        nd[k] = a.tets[4 * e + k];
-        dir[k] = a.flag[nd[k]] & 1;
-    }
-    const T *g = a.geom + e * kGeomStride;
-    T gN[4][3];
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) gN[k][j] = g[3 * k + j];
-    const T V = g[12], g2 = g[13] + a.omega2;
-    const T w = V * T(0.25), rho = a.rho, mu = a.mu;
-    T u[4][3];
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) u[k][j] = a.y[int64_t(nd[k]) * N4 + j * N + n];
-    const T qa = T(kQA), qb = T(kQB);
-    T udN[4][4], tau[4];               // udN[q][b] = u_q . grad N_b
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        T uq[3];
-#pragma unroll
-        for (int j = 0; j < 3; ++j) uq[j] = qb * (u[0][j] + u[1][j] + u[2][j] + u[3][j]) + (qa - qb) * u[q][j];
-#pragma unroll
-        for (int b = 0; b < 4; ++b) udN[q][b] = uq[0] * gN[b][0] + uq[1] * gN[b][1] + uq[2] * gN[b][2];
-        tau[q] = rsqrt_a<T>(udN[q][1] * udN[q][1] + udN[q][2] * udN[q][2] + udN[q][3] * udN[q][3] + g2);
-    }
+    AsmElem<T> s;
+    asm_elem_load(a, e, n, s);
     const int *pos = a.epos + e * 16;
 #pragma unroll
-    for (int ra = 0; ra < 4; ++ra) {
+    for (int ra = 0; ra < 4; ++ra)
 #pragma unroll
-        for (int cb = 0; cb < 4; ++cb) {
-            T kgal = 0, ksupg = 0, gs = 0, ds = 0, lt = 0;
+        for (int cb = 0; cb < 4; ++cb)
+            asm_pair<T, false>(s, ra, cb, a.rho, a.mu, a.coef + int64_t(pos[4 * ra + cb]) * 8 * N + n, N);
+}
+
+// Deterministic assembly: one thread per (row node A, instance) owns row A at that instance and adds the
+// row-A blocks of A's elements in the fixed order of the list rslot[rptr[A] .. rptr[A + 1]) (entries
+// element x 4 + local index of A); no two threads write one value.
+template <typename T>
+__global__ void assemble_rows_kernel(AsmArgs<T> a) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int N = a.N;
+    if (i >= a.n_nodes * int64_t(N)) return;
+    const int64_t A = i / N;
+    const int n = int(i - A * N);
+    for (int k = a.rptr[A]; k < a.rptr[A + 1]; ++k) {
+        const int64_t e = a.rslot[k] >> 2;
+        const int ra = a.rslot[k] & 3;
+        AsmElem<T> s;
+        asm_elem_load(a, e, n, s);
+        const int *pos = a.epos + e * 16 + 4 * ra;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const T Na = (q == ra) ? qa : qb;
-                kgal += Na * udN[q][cb];
-                ksupg += tau[q] * udN[q][ra] * udN[q][cb];
-                gs += tau[q] * udN[q][ra];             // times dN_B/dx_i
-                ds += tau[q] * udN[q][cb];             // times dN_A/dx_j
-                lt += tau[q];
-            }
-            const T gg = gN[ra][0] * gN[cb][0] + gN[ra][1] * gN[cb][1] + gN[ra][2] * gN[cb][2];
-            T *c = a.coef + int64_t(pos[4 * ra + cb]) * 8 * N + n;
-            if (!dir[ra]) {
-                if (!dir[cb]) atomicAdd(c, w * rho * kgal + mu * V * gg + w * rho * ksupg);
-#pragma unroll
-                for (int j = 0; j < 3; ++j) atomicAdd(c + (1 + j) * N, -w * gN[ra][j] + w * gs * gN[cb][j]);
-            }
-            if (!dir[cb]) {
-#pragma unroll
-                for (int j = 0; j < 3; ++j) atomicAdd(c + (4 + j) * N, w * gN[cb][j] + w * ds * gN[ra][j]);
-            }
-            atomicAdd(c + 7 * N, (w / rho) * lt * gg);
-        }
+        for (int cb = 0; cb < 4; ++cb)
+            asm_pair<T, true>(s, ra, cb, a.rho, a.mu, a.coef + int64_t(pos[cb]) * 8 * N + n, N);
     }
 }
 
@@ -110,6 +154,19 @@ __global__ void assemble_mass_kernel(AsmArgs<T> a) {
     for (int ra = 0; ra < 4; ++ra) {
         if (a.flag[a.tets[4 * e + ra]] & 1) continue;
         for (int cb = 0; cb < 4; ++cb) atomicAdd(a.mass + a.epos[e * 16 + 4 * ra + cb], V * T(ra == cb ? 0.1 : 0.05));
+    }
+}
+
+// The same by rows in list order (deterministic)
+template <typename T>
+__global__ void assemble_mass_rows_kernel(AsmArgs<T> a) {
+    const int64_t A = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (A >= a.n_nodes || (a.flag[A] & 1)) return;
+    for (int k = a.rptr[A]; k < a.rptr[A + 1]; ++k) {
+        const int64_t e = a.rslot[k] >> 2;
+        const int ra = a.rslot[k] & 3;
+        const T V = a.geom[e * kGeomStride + 12];
+        for (int cb = 0; cb < 4; ++cb) a.mass[a.epos[e * 16 + 4 * ra + cb]] += V * T(ra == cb ? 0.1 : 0.05);
     }
 }
 
@@ -443,12 +500,21 @@ void launch_block_jacobi(const T *coef, const T *mass, const int *dpos, const ui
 
 template <typename T>
 void launch_assemble(const AsmArgs<T> &a, cudaStream_t s) {
+    if (a.rptr) {
+        const int64_t n = a.n_nodes * int64_t(a.N);
+        if (n > 0) assemble_rows_kernel<T><<<nblk(n, 128), 128, 0, s>>>(a);
+        return;
+    }
     const int64_t n = a.n_tets * int64_t(a.N);
     if (n > 0) assemble_kernel<T><<<nblk(n, 128), 128, 0, s>>>(a);
 }
 
 template <typename T>
 void launch_assemble_mass(const AsmArgs<T> &a, cudaStream_t s) {
+    if (a.rptr) {
+        if (a.n_nodes > 0) assemble_mass_rows_kernel<T><<<nblk(a.n_nodes, 128), 128, 0, s>>>(a);
+        return;
+    }
     if (a.n_tets > 0) assemble_mass_kernel<T><<<nblk(a.n_tets, 128), 128, 0, s>>>(a);
 }
 

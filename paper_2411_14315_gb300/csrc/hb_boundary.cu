@@ -53,6 +53,30 @@ __global__ void outlet_flux_kernel(FaceArgs<T> a, int n_out) {
     }
 }
 
+// Deterministic flow rates: one warp per (outlet, instance) sums the outlet's faces in list order (lane j
+// takes faces j, j + 32, ...) and a fixed butterfly combines the lanes; Q is written, not accumulated.
+template <typename T, int MODE>
+__global__ void outlet_flux_det_kernel(FaceArgs<T> a) {
+    const int o = blockIdx.x, n = blockIdx.y, lane = threadIdx.x, N4 = 4 * a.N;
+    const T *x = (MODE == MODE_RES) ? a.y : a.v;
+    T s = 0;
+    for (int j = a.optr[o] + lane; j < a.optr[o + 1]; j += 32) {
+        const int f = a.oface[j];
+        const T nx = a.fgeo[4 * f], ny = a.fgeo[4 * f + 1], nz = a.fgeo[4 * f + 2], S = a.fgeo[4 * f + 3];
+        T sf = 0;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const int nd = a.fnodes[3 * f + b];
+            if (MODE != MODE_RES && (a.flag[nd] & 1)) continue;
+            const T *r = x + size_t(nd) * N4 + n;
+            sf += r[0] * nx + r[a.N] * ny + r[2 * a.N] * nz;
+        }
+        s += sf * (S / T(3));
+    }
+    for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+    if (lane == 0) a.Q[o * a.N + n] = s;
+}
+
 template <typename T, int MODE>
 __global__ void face_kernel(FaceArgs<T> a) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -114,12 +138,65 @@ __global__ void face_kernel(FaceArgs<T> a) {
             c[e1[m]][k] += cb * term[k];
         }
     }
+    if (a.fbuf) {                              // deterministic scatter: the face's own slots
+        T *fs = a.fbuf + size_t(f) * 9 * N + n;
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) fs[(3 * b + k) * N] = c[b][k];
+        return;
+    }
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
         if (a.flag[nd[b]] & 1) continue;       // prescribed velocity rows are set by the element pass
 #pragma unroll
         for (int k = 0; k < 3; ++k) atomicAdd(a.out + size_t(nd[b]) * N4 + k * N + n, c[b][k]);
     }
+}
+
+// Deterministic gather of the element and face slots, one thread per (node, field, instance): fields
+// 0-3 go to out (prescribed velocity rows: a.presc), fields 4-6 (F = 7) sum T into tbuf; F = 3 adds the
+// face slots alone to the velocity rows of out.
+template <typename T>
+__global__ void det_gather_kernel(DetGatherArgs<T> a) {
+    const int N = a.N, F = a.F;
+    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t >= a.n_nodes * F * N) return;
+    const int64_t A = t / (int64_t(F) * N);
+    const int r = int(t - A * F * N), f = r / N, n = r - f * N;
+    if (F == 3) {                  // faces only, added to a product written before (assembled operator)
+        if (a.flag[A] & 1) return;
+        T s = 0;
+        for (int k = a.fptr[A]; k < a.fptr[A + 1]; ++k) s += a.fbuf[(size_t(a.fslot[k]) * 3 + f) * N + n];
+        a.out[A * 4 * N + r] += s;
+        return;
+    }
+    const bool presc = (a.flag[A] & 1) && (f < 3 || f >= 4);
+    T s = 0;
+    if (presc) {
+        if (f < 3) s = a.presc == 2 ? a.v[A * 4 * N + r] : T(a.presc == 1 ? 1 : 0);
+    } else {
+        for (int k = a.eptr[A]; k < a.eptr[A + 1]; ++k) s += a.cbuf[(size_t(a.eslot[k]) * F + f) * N + n];
+        if (a.fptr && f < 3)
+            for (int k = a.fptr[A]; k < a.fptr[A + 1]; ++k) s += a.fbuf[(size_t(a.fslot[k]) * 3 + f) * N + n];
+    }
+    if (f < 4) a.out[A * 4 * N + r] = s;
+    else a.tbuf[(A * 3 + (f - 4)) * N + n] = s;
+}
+
+// out[A][i][n] += sum_k H[n][k] tbuf[A][i][k] on free velocity rows (F = 7)
+template <typename T>
+__global__ void det_apply_h_kernel(DetGatherArgs<T> a) {
+    const int N = a.N;
+    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t >= a.n_nodes * 3 * N) return;
+    const int64_t A = t / (3 * N);
+    if (a.flag[A] & 1) return;
+    const int r = int(t - A * 3 * N), i = r / N, n = r - i * N;
+    const T *h = a.H + size_t(n) * N, *x = a.tbuf + (A * 3 + i) * N;
+    T s = 0;
+    for (int k = 0; k < N; ++k) s += h[k] * x[k];
+    a.out[A * 4 * N + i * N + n] += s;
 }
 
 // ---------------------------------------------------------------------------------------------------
@@ -207,6 +284,20 @@ void launch_faces(int mode, const FaceArgs<T> &a, bool has_resistance, int n_out
     const int64_t n = int64_t(a.n_faces) * a.N;
     if (n == 0 || mode == MODE_DIAG) return;
     const int g = nblk(n, 128);
+    if (a.fbuf) {                                  // deterministic scatter
+        const dim3 fg(unsigned(n_out), unsigned(a.N));
+        if (mode == MODE_RES || mode == MODE_TRES) {
+            if (has_resistance && n_out > 0) outlet_flux_det_kernel<T, MODE_RES><<<fg, 32, 0, s>>>(a);
+            face_kernel<T, MODE_RES><<<g, 128, 0, s>>>(a);
+        } else if (mode == MODE_JVP) {
+            if (has_resistance && n_out > 0) outlet_flux_det_kernel<T, MODE_JVP><<<fg, 32, 0, s>>>(a);
+            face_kernel<T, MODE_JVP><<<g, 128, 0, s>>>(a);
+        } else {
+            if (has_resistance && n_out > 0) outlet_flux_det_kernel<T, MODE_JVE><<<fg, 32, 0, s>>>(a);
+            face_kernel<T, MODE_JVE><<<g, 128, 0, s>>>(a);
+        }
+        return;
+    }
     if (mode == MODE_RES || mode == MODE_TRES) {   // a time level's residual has the same boundary terms
         if (has_resistance) outlet_flux_kernel<T, MODE_RES><<<dim3(nblk(a.n_faces, 256), a.N), 256, 0, s>>>(a, n_out);
         face_kernel<T, MODE_RES><<<g, 128, 0, s>>>(a);
@@ -241,6 +332,15 @@ void launch_harmonics(const double *in, double *out, int64_t rows, int N, int n_
         synthesis_kernel<<<nblk(rows * N, 256), 256, 0, s>>>(in, out, rows, N, n_h);
 }
 
+template <typename T>
+void launch_det_gather(const DetGatherArgs<T> &a, cudaStream_t s) {
+    if (a.n_nodes <= 0) return;
+    det_gather_kernel<T><<<nblk(a.n_nodes * a.F * a.N, 256), 256, 0, s>>>(a);
+    if (a.F == 7) det_apply_h_kernel<T><<<nblk(a.n_nodes * 3 * a.N, 256), 256, 0, s>>>(a);
+}
+
+template void launch_det_gather<float>(const DetGatherArgs<float> &, cudaStream_t);
+template void launch_det_gather<double>(const DetGatherArgs<double> &, cudaStream_t);
 template void launch_faces<float>(int, const FaceArgs<float> &, bool, int, cudaStream_t);
 template void launch_faces<double>(int, const FaceArgs<double> &, bool, int, cudaStream_t);
 

@@ -183,12 +183,25 @@ __device__ __forceinline__ L ldot3(const L *a, const L *b) {
 // PIPE (the pipelined pass, FP32): the packed local connectivity sits in slot 14 of the element's geometry
 // record instead of sConn, and the staged direction rows are the caller's unmodified values, so the
 // velocity of nodes with prescribed velocity is masked to 0 here, at load time.
-template <typename T, typename L, int NT, bool PIPE = false>
+//
+// DET (deterministic scatter): instead of reductions into gout, the element stores its 16 contributions
+// (node a, field f) at cslot[(4 a + f) N + n]; a node-level gather sums them in a fixed order.
+template <typename L, typename T>
+__device__ __forceinline__ void lstore(T *p, L v, int d1) {
+    if constexpr (sizeof(L) == 2 * sizeof(T)) {
+        p[0] = v.x;
+        if (d1) p[d1] = v.y;
+    } else {
+        p[0] = v;
+    }
+}
+
+template <typename T, typename L, int NT, bool PIPE = false, bool DET = false>
 __device__ __forceinline__ void jvp_lanes(int e, int n0, int d1, int Nrt, T rho, T mu, T omega2, T cs,
                                           const T *__restrict__ sGeom, const uint32_t *__restrict__ sConn,
                                           const T *__restrict__ sY, const T *__restrict__ sV,
                                           const T *__restrict__ sW, const int *__restrict__ sNode,
-                                          T *__restrict__ gout) {
+                                          T *__restrict__ gout, T *__restrict__ cslot = nullptr) {
     const int N = NT > 0 ? NT : Nrt, N4 = 4 * N, WS = w_stride(N, int(sizeof(T)));
     uint32_t c;
     if constexpr (PIPE) c = __float_as_uint(float(sGeom[e * kGeomStride + 14]));
@@ -307,9 +320,15 @@ __device__ __forceinline__ void jvp_lanes(int e, int n0, int d1, int Nrt, T rho,
         L gS[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) gS[a] = ldot3(gN[a], Sw);
-        lred(go[0] + 3 * N, lsub(wdiv, ladd(gS[0], ladd(gS[1], gS[2]))), d1);
+        if constexpr (DET) {
+            lstore(cslot + 3 * N + n0, lsub(wdiv, ladd(gS[0], ladd(gS[1], gS[2]))), d1);
 #pragma unroll
-        for (int a = 0; a < 3; ++a) lred(go[a + 1] + 3 * N, ladd(wdiv, gS[a]), d1);
+            for (int a = 0; a < 3; ++a) lstore(cslot + (4 * (a + 1) + 3) * N + n0, ladd(wdiv, gS[a]), d1);
+        } else {
+            lred(go[0] + 3 * N, lsub(wdiv, ladd(gS[0], ladd(gS[1], gS[2]))), d1);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) lred(go[a + 1] + 3 * N, ladd(wdiv, gS[a]), d1);
+        }
     }
     // Z[j][i] = w rho Mx[j][i] + mu V d_j v_i - V pbar delta_ij
     {
@@ -342,8 +361,9 @@ __device__ __forceinline__ void jvp_lanes(int e, int n0, int d1, int Nrt, T rho,
             L val = a == 0 ? lsub(cW, gz0) : ladd(cW, gz[a - 1]);
             val = lfma(kd, ldot3(uq[a], gV[i]), val);
             val = lfma(m20, Wa[a], val);
-            // prescribed velocity rows are set apart
-            if (PIPE ? vfree[a] : sNode[lo[a]] >= 0) lred(go[a] + i * N, val, d1);
+            // prescribed velocity rows are set apart (the deterministic gather skips them)
+            if constexpr (DET) lstore(cslot + (4 * a + i) * N + n0, val, d1);
+            else if (PIPE ? vfree[a] : sNode[lo[a]] >= 0) lred(go[a] + i * N, val, d1);
         }
     }
 }
@@ -352,14 +372,14 @@ __device__ __forceinline__ void jvp_lanes(int e, int n0, int d1, int Nrt, T rho,
 // rbvms (RES, JVE): full RBVMS (Sec. 2.2, remark 2 after Eq. tau): with u' = -tau L / rho added to the
 // advecting velocity the momentum rows gain the cross stress - int N_a (tau L . grad) u_i and the Reynolds
 // stress - int (1 / rho) (tau L . grad N_a) (tau L)_i (and their derivatives in JVE).
-template <typename T, int MODE, int NT>
+template <typename T, int MODE, int NT, bool DET = false>
 __device__ __forceinline__ void element_instance(int e, int n, int Nrt, T rho, T mu, T shift, T omega2, int rbvms,
                                                  const T *__restrict__ sGeom,
                                                  const uint32_t *__restrict__ sConn,
                                                  const T *__restrict__ sY, const T *__restrict__ sV,
                                                  const T *__restrict__ sHY, const T *__restrict__ sHV,
                                                  const int *__restrict__ sNode, T *__restrict__ gout,
-                                                 T *sT) {
+                                                 T *sT, T *__restrict__ cslot = nullptr) {
     const int N = NT > 0 ? NT : Nrt;
     const int N4 = 4 * N, N3 = 3 * N;
     const uint32_t c = sConn[e];
@@ -412,6 +432,12 @@ __device__ __forceinline__ void element_instance(int e, int n, int Nrt, T rho, T
             const T gg = gN[a][0] * gN[a][0] + gN[a][1] * gN[a][1] + gN[a][2] * gN[a][2];
             const T dv = dvel[a] + w * rho * qb * udNs[a] + mu * V * gg + shift * V * T(0.1);
             const T dp = (w / rho) * taus * gg;
+            if constexpr (DET) {
+                T *cs = cslot + 4 * a * N + n;
+                cs[0] = cs[N] = cs[2 * N] = dv;
+                cs[3 * N] = dp;
+                continue;
+            }
             if (sNode[lo[a]] >= 0) {            // prescribed velocity rows are set apart
                 atomicAdd(go[a], dv);
                 atomicAdd(go[a] + N, dv);
@@ -495,6 +521,15 @@ __device__ __forceinline__ void element_instance(int e, int n, int Nrt, T rho, T
             for (int i = 0; i < 3; ++i) {
                 const T visc = gN[a][0] * gU[i][0] + gN[a][1] * gU[i][1] + gN[a][2] * gU[i][2];
                 T vq = qm[a][i] + w * rho * qb * convs[i] + mu * V * visc - V * gN[a][i] * pbar;
+                if constexpr (DET) {
+                    if constexpr (TM) {
+                        cslot[(4 * a + i) * N + n] = vq + rho * m20 * (husum[i] + hu[a][i]);
+                    } else {
+                        cslot[(7 * a + i) * N + n] = vq;
+                        cslot[(7 * a + 4 + i) * N + n] = tt[a][i] + rho * m20 * (usum[i] + u[a][i]) - w * qb * S[i];
+                    }
+                    continue;
+                }
                 if (sNode[lo[a]] >= 0) {        // prescribed velocity rows are set apart
                     if constexpr (TM) {
                         vq += rho * m20 * (husum[i] + hu[a][i]);
@@ -507,7 +542,8 @@ __device__ __forceinline__ void element_instance(int e, int n, int Nrt, T rho, T
                 }
             }
             const T qc = w * div + (w / rho) * (gN[a][0] * S[0] + gN[a][1] * S[1] + gN[a][2] * S[2]);
-            atomicAdd(go[a] + 3 * N, qc);
+            if constexpr (DET) cslot[((TM ? 4 : 7) * a + 3) * N + n] = qc;
+            else atomicAdd(go[a] + 3 * N, qc);
         }
         return;
     } else {  // MODE_JVE (MODE_JVP runs jvp_lanes)
@@ -613,13 +649,19 @@ __device__ __forceinline__ void element_instance(int e, int n, int Nrt, T rho, T
                 const T mv = m20 * (dvsum[i] + dv[a][i]);
                 const T vq = qm[a][i] + w * rho * qb * dconvs[i] + mu * V * visc - V * gN[a][i] * pbar + shift * mv;
                 const T vt = tt[a][i] + rho * mv - w * qb * S[i];
+                if constexpr (DET) {
+                    cslot[(7 * a + i) * N + n] = vq;
+                    cslot[(7 * a + 4 + i) * N + n] = vt;
+                    continue;
+                }
                 if (sNode[lo[a]] >= 0) {        // prescribed velocity rows are set apart
                     atomicAdd(go[a] + i * N, vq);
                     atomicAdd(sT + lo[a] * N3 + i * N + n, vt);
                 }
             }
             const T qc = w * div + (w / rho) * (gN[a][0] * S[0] + gN[a][1] * S[1] + gN[a][2] * S[2]);
-            atomicAdd(go[a] + 3 * N, qc);
+            if constexpr (DET) cslot[(7 * a + 3) * N + n] = qc;
+            else atomicAdd(go[a] + 3 * N, qc);
         }
         return;
     }
@@ -719,7 +761,7 @@ __device__ __forceinline__ void stage_H(const ElemArgs<T> &a, T *sH, int N) {
 // element-instance work, H T flush.  `prefetch` runs on every thread once the staged rows are no longer
 // being written (the caller uses it to stage the next patch's slot).  Ends with a block barrier, so
 // shared memory can be reused by the next patch.
-template <typename T, int MODE, int NT, typename L, typename Prefetch>
+template <typename T, int MODE, int NT, typename L, typename Prefetch, bool DET = false>
 __device__ __forceinline__ void patch_pass(const ElemArgs<T> &a, const PatchSmem<T> &sm, const int *sSlot, T shift,
                                            Prefetch prefetch) {
     const int N = NT > 0 ? NT : a.N, N4 = 4 * N, N3 = 3 * N;
@@ -728,7 +770,7 @@ __device__ __forceinline__ void patch_pass(const ElemArgs<T> &a, const PatchSmem
     const int tid = threadIdx.x, nt = blockDim.x;
     const int e0 = sSlot[0], ne = sSlot[1], nl = sSlot[2], nd = sSlot[3];
     const int *sNode = sSlot + 4;           // global node ids, kDirBit on prescribed velocities
-    if constexpr (MODE == MODE_RES || MODE == MODE_JVE)
+    if constexpr ((MODE == MODE_RES || MODE == MODE_JVE) && !DET)
         for (int i = tid; i < nl * N3; i += nt) sT[i] = T(0);
 
     // asynchronous copies of the patch's element data and node rows (4 N values per node), so every
@@ -822,7 +864,7 @@ __device__ __forceinline__ void patch_pass(const ElemArgs<T> &a, const PatchSmem
     // prescribed velocity rows of the output (no element or face term reaches them): 0 for the
     // residual (left from the clearing), 1 for the Jacobi diagonal, v (identity) for Jacobian products;
     // patches sharing a node store the same values
-    if constexpr (MODE != MODE_RES && MODE != MODE_TRES) {
+    if constexpr (MODE != MODE_RES && MODE != MODE_TRES && !DET) {
         if (nd > 0) {
             for (int i = tid; i < nl * N3; i += nt) {
                 const int l = i / N3;
@@ -839,20 +881,23 @@ __device__ __forceinline__ void patch_pass(const ElemArgs<T> &a, const PatchSmem
         for (int i = tid; i < ne * NP; i += nt) {
             const int e = i / NP, k = i - e * NP;
             const int d1 = (LW == 2 && k + NP < N) ? NP : 0;
-            jvp_lanes<T, L, NT>(e, k, d1, N, a.rho, a.mu, a.omega2, a.ls_mass ? shift / a.rho : T(0), sGeom, sConn,
-                                sY, sV, sHV, sNode, a.out);
+            jvp_lanes<T, L, NT, false, DET>(e, k, d1, N, a.rho, a.mu, a.omega2, a.ls_mass ? shift / a.rho : T(0), sGeom,
+                                            sConn, sY, sV, sHV, sNode, a.out,
+                                            DET ? a.cbuf + (size_t(e0) + size_t(e)) * 16 * size_t(N) : nullptr);
         }
     } else {
         for (int i = tid; i < ne * N; i += nt) {
             const int e = i / N, n = i - e * N;
-            element_instance<T, MODE, NT>(e, n, N, a.rho, a.mu, shift, a.omega2, a.rbvms, sGeom, sConn, sY, sV, sHY,
-                                          sHV, sNode, a.out, sT);
+            element_instance<T, MODE, NT, DET>(e, n, N, a.rho, a.mu, shift, a.omega2, a.rbvms, sGeom, sConn, sY, sV,
+                                               sHY, sHV, sNode, a.out, sT,
+                                               DET ? a.cbuf + (size_t(e0) + size_t(e)) * size_t(det_slot_values(MODE)) * N
+                                                   : nullptr);
         }
     }
     __syncthreads();
 
     // H T on the patch-assembled T rows (fixed N: in place, one row per thread)
-    if constexpr ((MODE == MODE_RES || MODE == MODE_JVE) && NT > 0) {
+    if constexpr ((MODE == MODE_RES || MODE == MODE_JVE) && NT > 0 && !DET) {
         for (int r = tid; r < nl * 3; r += nt) {
             T *row = sT + (r / 3) * N3 + (r % 3) * N;
             circulant_row<T, NT>(sH, row, row);
@@ -861,7 +906,7 @@ __device__ __forceinline__ void patch_pass(const ElemArgs<T> &a, const PatchSmem
     }
 
     // flush: out += H T on the velocity rows, once per local node
-    if constexpr (MODE == MODE_RES || MODE == MODE_JVE) {
+    if constexpr ((MODE == MODE_RES || MODE == MODE_JVE) && !DET) {
         for (int i = tid; i < nl * N3; i += nt) {
             const int l = i / N3, r = i - l * N3;
             T val;
@@ -882,7 +927,7 @@ __device__ __forceinline__ void patch_pass(const ElemArgs<T> &a, const PatchSmem
 
 // Persistent element pass: block b takes patches b, b + G, b + 2G, ... (G = gridDim.x) and stages each
 // next patch's slot while the current one computes.
-template <typename T, int MODE, int NT, int VAR>
+template <typename T, int MODE, int NT, int VAR, bool DET = false>
 __global__ void __launch_bounds__(ElemCfg<T, VAR>::block, ElemCfg<T, VAR>::minb) elem_kernel(ElemArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int N = NT > 0 ? NT : a.N;
@@ -897,7 +942,7 @@ __global__ void __launch_bounds__(ElemCfg<T, VAR>::block, ElemCfg<T, VAR>::minb)
     __syncthreads();
     for (int cur = 0; p < P; p += gridDim.x, cur ^= 1) {
         const SlotPrefetch pf{a.pv.slots, a.pv.slot_stride, p + int(gridDim.x), P, sm.slot(cur ^ 1)};
-        patch_pass<T, MODE, NT, typename ElemCfg<T, VAR>::lane>(a, sm, sm.slot(cur), shift, pf);
+        patch_pass<T, MODE, NT, typename ElemCfg<T, VAR>::lane, SlotPrefetch, DET>(a, sm, sm.slot(cur), shift, pf);
         cp_async_wait_all();
         __syncthreads();
     }
@@ -1263,11 +1308,11 @@ size_t elem_smem_bytes(int mode, int N, int nl_max, int ep_max, size_t tsize, in
 }
 
 // grid: upper bound on the blocks (the patch count); the persistent kernel runs at most one wave
-template <typename T, int MODE, int NT, int VAR>
+template <typename T, int MODE, int NT, int VAR, bool DET = false>
 static void launch_elem_v(const ElemArgs<T> &a, int grid, cudaStream_t s) {
     const size_t smem = elem_smem_bytes(MODE, a.N, a.pv.nl_max, a.pv.ep_max, sizeof(T));
     static LaunchCache cache;
-    auto kern = elem_kernel<T, MODE, NT, VAR>;
+    auto kern = elem_kernel<T, MODE, NT, VAR, DET>;
     grid = std::min(grid, cached_blocks_per_sm(cache, kern, ElemCfg<T, VAR>::block, smem) * device_sms());
     if (grid > 0) kern<<<grid, ElemCfg<T, VAR>::block, smem, s>>>(a);
 }
@@ -1292,6 +1337,10 @@ static bool launch_pipe(const ElemArgs<float> &a, cudaStream_t s) {
 
 template <typename T, int MODE, int NT>
 static void launch_elem_n(const ElemArgs<T> &a, int grid, cudaStream_t s) {
+    if (a.cbuf) {          // deterministic scatter: FP32 paper tangent one instance per thread (variant 1)
+        launch_elem_v<T, MODE, NT, (MODE == MODE_JVP && sizeof(T) == 4) ? 1 : 0, true>(a, grid, s);
+        return;
+    }
     if constexpr (MODE == MODE_JVP && sizeof(T) == 4 && (NT == 9 || NT == 13 || NT == 21)) {
         // 4: one instance per thread, 20 consumer warps and 4 producer warps (16-byte copies); 5: instance
         // pairs on paired FP32 instructions, 12 consumer warps; 6: as 4 with one producer warp issuing bulk

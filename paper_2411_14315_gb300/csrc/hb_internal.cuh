@@ -136,7 +136,35 @@ struct ElemArgs {
                                    // stores a nonzero code (left untouched otherwise)
     int rbvms = 0;                 // residual and exact Jacobian: add the full-RBVMS cross- and
                                    // Reynolds-stress terms of u' = -tau L / rho (Sec. 2.2, remark 2)
+    T *cbuf = nullptr;             // JVP, deterministic scatter: per-element contribution slots
+                                   // [E (patch order)][4 nodes][4 fields][N], gathered per node afterwards
 };
+
+// Deterministic scatter (no floating-point atomics): the element pass stores each element's contributions
+// in its own slot of cbuf, [element in patch order][4 nodes][F fields][N], F = 7 for the residual and the
+// exact Jacobian (4 direct rows, then the 3 rows of T that go through H) and 4 otherwise; Neumann faces
+// store theirs in fbuf, [face][3 nodes][3 fields][N].  The gather sums, per node, field and instance, its
+// element slots (eslot = element x 4 + local node) and face slots (fslot = face x 3 + local node) in the
+// fixed order of the lists, and then out += H T on the velocity rows; prescribed velocity rows get
+// presc (0: 0, 1: 1, 2: v).
+__host__ __device__ constexpr int det_slot_values(int mode) { return (mode == MODE_RES || mode == MODE_JVE) ? 28 : 16; }
+
+template <typename T>
+struct DetGatherArgs {
+    int64_t n_nodes;
+    int N, F, presc;
+    const int *eptr, *eslot;       // node -> element slots, CSR over nodes
+    const T *cbuf;
+    const int *fptr, *fslot;       // node -> face slots (null: no faces)
+    const T *fbuf;
+    const uint8_t *flag;
+    const T *v;                    // presc 2
+    const T *H;                    // F = 7: the N x N operator H
+    T *tbuf;                       // F = 7: [n_nodes][3][N] scratch (sum of T)
+    T *out;
+};
+template <typename T>
+void launch_det_gather(const DetGatherArgs<T> &a, cudaStream_t s);
 
 // Boundary (Neumann) faces.
 template <typename T>
@@ -154,6 +182,9 @@ struct FaceArgs {
     T *out;
     int N;
     T rho, beta;
+    T *fbuf = nullptr;             // deterministic scatter: per-face slots [F][3 nodes][3 fields][N]
+    const int *optr = nullptr;     // and the outlet flow rates summed in a fixed order: faces of outlet o
+    const int *oface = nullptr;    // are oface[optr[o] .. optr[o + 1])
 };
 
 // shared memory of one element-pass block; slot_cap = 0: the patch set's own slot size
@@ -256,6 +287,10 @@ struct AsmArgs {
     T *mass;                       // [nnz], cleared before the assembly
     T rho, mu;
     T omega2 = 0;                  // constant added under the root of tau (time-discretisation term)
+    // deterministic assembly (set: one thread per row and instance adds the row's element blocks in
+    // list order): node A's (element x 4 + local index) entries are rslot[rptr[A] .. rptr[A + 1])
+    int64_t n_nodes = 0;
+    const int *rptr = nullptr, *rslot = nullptr;
 };
 template <typename T>
 struct SpmvArgs {

@@ -40,7 +40,8 @@ class hb_solve_opts(C.Structure):
                 ("gmres_restart", C.c_int), ("max_gmres", C.c_int), ("max_steps", C.c_int),
                 ("dt_pseudo", C.c_double), ("cfl", C.c_double), ("use_learned", C.c_int),
                 ("verbose", C.c_int), ("ser", C.c_int), ("ser_max", C.c_double), ("r_ref", C.c_double),
-                ("assembled", C.c_int), ("precond", C.c_int), ("line_search", C.c_int)]
+                ("assembled", C.c_int), ("precond", C.c_int), ("line_search", C.c_int),
+                ("scatter", C.c_int)]
 
 
 class hb_report(C.Structure):
@@ -122,6 +123,8 @@ SIGNATURES = {
     "hb_get_launch_variant": ([_P], C.c_int),
     "hb_set_spectral_path": ([_P, C.c_int], C.c_int),
     "hb_get_spectral_path": ([_P], C.c_int),
+    "hb_set_scatter": ([_P, C.c_int], C.c_int),
+    "hb_get_scatter": ([_P], C.c_int),
     "hb_profile_elem": ([_P, C.c_int], C.c_int),
     "hb_profile_read": ([_P, C.POINTER(C.c_double), C.POINTER(C.c_int64)], C.c_int),
     "hb_jv_dev_noalloc": ([_P, _VP, _VP, _VP, C.c_int, C.c_int, C.c_double, _VP], C.c_int),
@@ -429,6 +432,13 @@ class Problem:
 
     def spectral_path(self) -> int:
         return int(lib().hb_get_spectral_path(self._h))
+
+    def set_scatter(self, scatter: int):
+        """hb_set_scatter: 0 = deterministic (per-element slots, fixed-order gather), 1 = atomic."""
+        _check(lib().hb_set_scatter(self._h, int(scatter)))
+
+    def scatter(self) -> int:
+        return int(lib().hb_get_scatter(self._h))
 
     def launch_variant(self) -> int:
         return int(lib().hb_get_launch_variant(self._h))

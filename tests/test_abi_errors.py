@@ -128,3 +128,9 @@ def test_set_stabilization_null_problem(lib):
     """hb_set_stabilization checks its problem before anything else (no device work)."""
     assert lib.hb_set_stabilization(None, 1, 0.0) == INVALID
     assert lib.hb_last_error().decode()
+
+
+def test_scatter_setting_null_problem(lib):
+    """hb_set_scatter / hb_get_scatter check their problem before anything else (no device work)."""
+    assert lib.hb_set_scatter(None, 0) == INVALID
+    assert lib.hb_get_scatter(None) == -1
