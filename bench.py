@@ -578,8 +578,9 @@ def time_march(spp: int = 1008, periods: int = 4):
 
 
 def time_batch(reps: int = 20):
-    """64 vessels of uneven size and N (20k-400k tets, N in {9, 13, 21}): one captured graph with one
-    persistent element launch for the whole batch, against 64 per-problem Jv calls."""
+    """64 vessels of uneven size and N (20k-400k tets, N in {9, 13, 21}): one captured graph for the whole
+    batch, in the library's default launch layout and in each layout of hb_batch_set_grouping, against 64
+    per-problem Jv calls in sequence."""
     import torch
 
     from paper_2411_14315_gb300 import hbgls
@@ -607,7 +608,16 @@ def time_batch(reps: int = 20):
 
     res = {"workload": f"{len(specs)} vessels, {sum(s.mesh.n_tets for s in specs)} tets, N in "
                        f"{sorted(set(s.N for s in specs))}", "units_per_jv": units, "setup_s": setup_s}
-    for name, fn in (("batched", batched), ("sequential", sequential)):
+
+    def layout(g):
+        def fn():
+            b.set_grouping(g)
+            batched()
+        return fn
+
+    legs = [("batched", batched)] + [(f"batched_grouping_{g}", layout(g)) for g in (0, 1, 2)] + \
+        [("sequential", sequential)]
+    for name, fn in legs:
         for _ in range(3):
             fn()
         torch.cuda.synchronize()
@@ -620,6 +630,7 @@ def time_batch(reps: int = 20):
         ms = e0.elapsed_time(e1) / reps
         res[name] = {"ms_per_jv": ms, "element_instances_per_s": units / (ms / 1e3)}
     res["graph_launches_per_batched_jv"] = 1
+    res["default_grouping"] = "the library's default layout (hb_batch_set_grouping)"
     b.close()
     for p in probs:
         p.close()

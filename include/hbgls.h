@@ -354,17 +354,17 @@ hb_status hb_time_jv(hb_problem *p, const double *y, const double *v, double *jv
 hb_status hb_get_march_samples(hb_problem *p, double *out);
 
 /* ---- batches of problems (many vessels of uneven size and N in one graph) ---------------------------
- * A batch applies the operator of every member problem in one captured CUDA graph: the output
- * clearing, for the paper's tangent each member's node-level W = shift v + rho H v pass (the graph runs them
- * as parallel branches), one persistent element pass over every member (each member's patches run the pass
- * specialised for its N) whose work items (problem, patch) are taken from a global counter (so large and
- * small problems of any N share the SMs; the FP32 paper-tangent pass takes the first problem's launch
- * variant, see hb_set_launch_variant),
- * then the boundary terms of each problem (prescribed velocity rows are written by the element pass).
- * A batch sums with atomics whatever hb_set_scatter says of its problems.
- * All problems must live on one device; their boundary data are prepared at creation.  The graph is captured on first use and again whenever the
- * operands, kind or shift change.  Work is ordered after `stream` (NULL: the first problem's stream) and
- * `stream` waits for it. */
+ * A batch applies the operator of every member problem in one captured CUDA graph (not the paper's
+ * method: a throughput layer for many independent vessels).  In the default launch layout (2, see
+ * hb_batch_set_grouping) the graph has 8 parallel branches, and each member's whole single-problem
+ * operator -- output clearing, for the paper's tangent the node-level W = shift v + rho H v pass, the
+ * element pass with the member's own launch variant and summation setting, the boundary terms -- runs on
+ * branch q mod 8; the branches' launches run concurrently and fill one another's tails.  Layouts 0 and 1
+ * instead run one persistent element pass over every member (or one per instance count) whose work items
+ * (problem, patch) come from a global counter; they sum with atomics whatever hb_set_scatter says.
+ * All problems must live on one device; their boundary data are prepared at creation.  The graph is
+ * captured on first use and again whenever the operands, kind, shift or layout change.  Work is ordered
+ * after `stream` (NULL: the first problem's stream) and `stream` waits for it. */
 typedef struct hb_batch hb_batch;
 /* Create a batch over `count` problems (not owned; they must outlive the batch) at precision 0 or 1. */
 hb_status hb_batch_create(hb_problem *const *problems, int count, int precision, hb_batch **out);
@@ -377,6 +377,17 @@ hb_status hb_batch_jv_dev(hb_batch *b, const void *const *y, const void *const *
 /* Kernel launches queued by the batch since creation: its graph's launches times its replays (0 for
  * NULL). */
 int64_t hb_batch_launch_count(const hb_batch *b);
+/* Launch layout of the batch's graph: 0 one persistent element launch over every member (the kernel
+ * dispatches on each work item's instance count); 1 one persistent element launch per instance count,
+ * specialised for it, the launches on parallel graph branches (at most 8 distinct counts); 2 (default)
+ * every member's single-problem operator (clearing, W pass, its own element launch, boundary terms) on
+ * one of 8 parallel graph branches, members q, q + 8, ... in sequence on branch q mod 8, so that the
+ * branches' launches fill one another's tails (the fastest: the element launches keep their arguments
+ * in the constant bank, where 0 and 1 read each work item's arguments from shared memory).  Same results
+ * in every layout up to the order of the atomic additions (a member set to deterministic summation keeps
+ * it in layout 2).  The next hb_batch_jv_dev recaptures.  INVALID_ARG for a null batch or another
+ * value. */
+hb_status hb_batch_set_grouping(hb_batch *b, int grouping);
 /* Patch-size autotuning: rebuild the problem's element patches (precision 0 or 1) with each candidate
  * node cap (and, for precision 1, each launch variant, see hb_set_launch_variant), time `reps`
  * paper-tangent Jv element passes with CUDA events, and keep the fastest.  Returns the chosen cap and

@@ -2810,14 +2810,79 @@ struct hb_batch {
     std::vector<const void *> y, v;
     std::vector<void *> out;
     int64_t launches_per_replay = 0, launches = 0;
+    int grouping = 2;                     // launch layout (hb_batch_set_grouping): 2 = members on parallel branches
     static constexpr int kSide = 8;       // side streams of the captured graph's parallel branches
     cudaStream_t side[kSide] = {};
 };
 
 namespace {
 
+// grouping 2: every member's whole operator (the single-problem path: clearing, W pass, element pass with
+// the member's own kernel arguments, boundary terms) on one of kSide parallel graph branches, members
+// q, q + kSide, ... in sequence on branch q mod kSide; the branches run concurrently, so the blocks of one
+// member's element launch fill the SMs that another's tail leaves idle.
+template <typename T>
+hb_status batch_record_branches(hb_batch *b) {
+    cudaStream_t s = b->stream;
+    const size_t np = b->probs.size();
+    std::vector<int64_t> l0(np);
+    for (size_t q = 0; q < np; ++q) {
+        hb_problem *p = b->probs[q];
+        HB_TRY(prepare_bc(p));          // host work and uploads stay outside the capture
+        l0[q] = p->launches;
+        if (b->mode == MODE_JVP) {     // the W rows, allocated outside the capture
+            DBuf<T> &W = AsmBufs<T>::W(p->as);
+            HB_TRY(dalloc(p, W, size_t(p->n_nodes) * size_t(w_stride(p->N, int(sizeof(T))))));
+        }
+    }
+    HB_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+    hb_status st = HB_OK;
+    std::vector<cudaEvent_t> evs;
+    cudaEvent_t ev = nullptr;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) st = fail(HB_ERR_CUDA, "event");
+    if (st == HB_OK) {
+        evs.push_back(ev);
+        cudaEventRecord(ev, s);
+        for (int k = 0; k < hb_batch::kSide; ++k) cudaStreamWaitEvent(b->side[k], ev, 0);
+    }
+    for (size_t q = 0; q < np && st == HB_OK; ++q)
+        st = apply_op<T>(b->probs[q], b->mode, static_cast<const T *>(b->y[q]), static_cast<const T *>(b->v[q]),
+                         static_cast<T *>(b->out[q]), b->shift, b->side[q % hb_batch::kSide]);
+    for (int k = 0; k < hb_batch::kSide && st == HB_OK; ++k) {
+        cudaEvent_t j = nullptr;
+        if (cudaEventCreateWithFlags(&j, cudaEventDisableTiming) != cudaSuccess) {
+            st = fail(HB_ERR_CUDA, "event");
+            break;
+        }
+        evs.push_back(j);
+        cudaEventRecord(j, b->side[k]);
+        cudaStreamWaitEvent(s, j, 0);
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s, &graph);
+    for (cudaEvent_t x : evs) cudaEventDestroy(x);
+    int64_t launched = 0;
+    for (size_t q = 0; q < np; ++q) {
+        launched += b->probs[q]->launches - l0[q];
+        b->probs[q]->launches = l0[q];
+    }
+    if (st != HB_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e != cudaSuccess) return fail(HB_ERR_CUDA, std::string("batch capture: ") + cudaGetErrorString(e));
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+    e = cudaGraphInstantiate(&b->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(HB_ERR_CUDA, std::string("batch graph instantiate: ") + cudaGetErrorString(e));
+    b->launches_per_replay = launched;
+    return HB_OK;
+}
+
 template <typename T>
 hb_status batch_record(hb_batch *b) {
+    if (b->grouping == 2) return batch_record_branches<T>(b);
     cudaStream_t s = b->stream;
     hb_problem *p0 = b->probs[0];
     // problems ordered by instance count: each run of equal N is one persistent launch of the pass
@@ -2886,20 +2951,37 @@ hb_status batch_record(hb_batch *b) {
         }
         HB_CUDA(cudaStreamSynchronize(s));
     }
-    // one persistent launch over every member's patches (N = -1: the kernel dispatches on each member's
-    // instance count), so members of different N share the SMs and the launch's tail
+    // grouping 0: one persistent launch over every member's patches (N = -1: the kernel dispatches on each
+    // member's instance count), so members of different N share the SMs and the launch's tail;
+    // grouping 1: one persistent launch per instance count (the kernel specialised for that N), the
+    // launches on parallel graph branches so that one's tail overlaps the next one's start
     std::vector<BatchGroup<T>> groups;
     {
         BatchGroup<T> g;
         g.args = dargs.p;
         g.bslots = b->bslots.p;
         g.bslot_stride = bstride;
-        g.N = -1;
-        g.item_begin = 0;
-        g.item_end = b->n_items;
         g.variant = p0->jvp_variant;
-        g.counter = b->counter.p;
-        if (b->n_items > 0) groups.push_back(g);
+        if (b->grouping == 0) {
+            g.N = -1;
+            g.item_begin = 0;
+            g.item_end = b->n_items;
+            if (b->n_items > 0) groups.push_back(g);
+        } else {
+            for (size_t r = 0; r < np;) {
+                size_t r1 = r;
+                while (r1 < np && b->probs[ord[r1]]->N == b->probs[ord[r]]->N) ++r1;
+                g.N = b->probs[ord[r]]->N;
+                g.item_begin = first[r];
+                g.item_end = first[r1];
+                if (g.item_end > g.item_begin) groups.push_back(g);
+                r = r1;
+            }
+        }
+        if (groups.size() > size_t(hb_batch::kSide))
+            return fail(HB_ERR_INVALID_ARG, "more distinct instance counts than parallel branches in the batch");
+        HB_TRY(dalloc(p0, b->counter, std::max<size_t>(1, groups.size())));
+        for (size_t k = 0; k < groups.size(); ++k) groups[k].counter = b->counter.p + k;
     }
     int max_blocks = 1;
     if (smem <= 113 * 1024 && sizeof(T) == 4) max_blocks = 2;
@@ -2952,10 +3034,18 @@ hb_status batch_record(hb_batch *b) {
         }
     }
     if (st == HB_OK) join();
-    for (size_t k = 0; k < groups.size() && st == HB_OK; ++k) {
-        const BatchGroup<T> &g = groups[k];
+    if (groups.size() == 1) {
+        const BatchGroup<T> &g = groups[0];
         launch_batch_elem<T>(b->mode, g, smem, std::min(b->grid, g.item_end - g.item_begin), s);
         p0->launches += 1;
+    } else if (st == HB_OK && !groups.empty()) {
+        fork();
+        for (size_t k = 0; k < groups.size(); ++k) {
+            const BatchGroup<T> &g = groups[k];
+            launch_batch_elem<T>(b->mode, g, smem, std::min(b->grid, g.item_end - g.item_begin), b->side[k]);
+            p0->launches += 1;
+        }
+        join();
     }
     // branches after it: each member's boundary terms
     if (st == HB_OK) fork();
@@ -3107,6 +3197,17 @@ hb_status hb_batch_jv_dev(hb_batch *b, const void *const *y, const void *const *
 }
 
 int64_t hb_batch_launch_count(const hb_batch *b) { return b ? b->launches : 0; }
+
+hb_status hb_batch_set_grouping(hb_batch *b, int grouping) {
+    if (!b) return fail(HB_ERR_INVALID_ARG, "null batch");
+    if (grouping < 0 || grouping > 2)
+        return fail(HB_ERR_INVALID_ARG, "grouping must be 0 (one launch), 1 (per N) or 2 (per member, concurrent)");
+    if (grouping != b->grouping) {
+        b->grouping = grouping;
+        b->mode = -1;                         // recapture on the next call
+    }
+    return HB_OK;
+}
 
 // Autotuning of the patch node cap: rebuild the patches with each candidate, time `reps` paper-tangent
 // Jv applications (CUDA events around the element pass), keep the fastest.

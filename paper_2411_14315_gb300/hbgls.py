@@ -145,6 +145,7 @@ SIGNATURES = {
     "hb_batch_destroy": ([_P], C.c_int),
     "hb_batch_jv_dev": ([_P, C.POINTER(_VP), C.POINTER(_VP), C.POINTER(_VP), C.c_int, C.c_double, _VP], C.c_int),
     "hb_batch_launch_count": ([_P], C.c_int64),
+    "hb_batch_set_grouping": ([_P, C.c_int], C.c_int),
     "hb_tune_patches": ([_P, C.c_int, C.POINTER(C.c_int), C.c_int, C.c_int, C.POINTER(C.c_int),
                          C.POINTER(C.c_double)], C.c_int),
 }
@@ -572,3 +573,8 @@ class Batch:
 
     def launch_count(self) -> int:
         return int(lib().hb_batch_launch_count(self._h))
+
+    def set_grouping(self, grouping: int):
+        """hb_batch_set_grouping: 0 = one element launch over every N, 1 = one launch per N, 2 = every
+        member's own operator on parallel graph branches."""
+        _check(lib().hb_batch_set_grouping(self._h, int(grouping)))

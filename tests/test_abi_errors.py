@@ -134,3 +134,7 @@ def test_scatter_setting_null_problem(lib):
     """hb_set_scatter / hb_get_scatter check their problem before anything else (no device work)."""
     assert lib.hb_set_scatter(None, 0) == INVALID
     assert lib.hb_get_scatter(None) == -1
+
+
+def test_batch_grouping_null_batch(lib):
+    assert lib.hb_batch_set_grouping(None, 1) == INVALID

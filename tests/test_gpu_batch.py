@@ -1,5 +1,5 @@
-"""Batched operator application (one captured graph, one persistent element launch per instance count over
-many problems of different N) against the CPU oracle per member and per field, and against per-problem
+"""Batched operator application (one captured graph; one persistent element launch over many problems of
+different N, or one per instance count) against the CPU oracle per member and per field, and against per-problem
 calls; patch autotuning."""
 import numpy as np
 import pytest
@@ -23,8 +23,9 @@ def _relerr_fields(a, b):
     return max(np.linalg.norm(a[:, f] - b[:, f]) / max(np.linalg.norm(b[:, f]), 1e-300) for f in range(4))
 
 
+@pytest.mark.parametrize("grouping", [0, 1, 2])
 @pytest.mark.parametrize("precision,kind", [(1, 0), (1, 1), (0, 0), (0, 1)])
-def test_batch_matches_oracle(precision, kind):
+def test_batch_matches_oracle(precision, kind, grouping):
     """Every member of a batch of five problems (N = 5, 9, 13, 21 and the Womersley pipe at 9; pressure,
     resistance and traction-free outlets; prescribed velocities) against the oracle's paper tangent
     (Eqs. ptangent, K_mat, ctangent, F_mat) or exact Jacobian, field by field: FP64 1e-12, FP32 1e-5."""
@@ -37,6 +38,7 @@ def test_batch_matches_oracle(precision, kind):
     outs = [torch.empty_like(y) for y in ys]
     shift = 0.6
     b = hbgls.Batch(probs, precision)
+    b.set_grouping(grouping)
     st = torch.cuda.current_stream()
     b.jv_dev(ys, vs, outs, kind, shift, stream=st)
     st.synchronize()
