@@ -76,8 +76,9 @@ def parse():
                          "own solves and time cold vs warm solves of held-out tubes (a few minutes)")
     ap.add_argument("--profile-small", type=int, default=0, metavar="TETS",
                     help="run the small-case workload the ncu captures use (a Glenn-like T-junction of ~TETS tets at "
-                         "N = 21: FP32 paper-tangent Jv with both tensor-core spectral passes, the assembled tangent's "
-                         "product, one GMRES restart cycle, and a network prediction on a 30k-tet coronary-like tube) "
+                         "N = 21: FP32 paper-tangent Jv with both tensor-core spectral passes and with deterministic "
+                         "summation, the assembled tangent's product, one GMRES restart cycle, and network "
+                         "predictions and training steps on a 30k-tet coronary-like tube) "
                          "and exit")
     ap.add_argument("--march", action="store_true",
                     help="also time the conventional time-marching solver against the HB solve on the Womersley "
@@ -888,6 +889,10 @@ def profile_small(n_tets: int):
     for _ in range(2):
         p.jv_dev(y, v, o, hbgls.PAPER, hbgls.FP32, 300.0, stream=s)
     p.set_spectral_path(1)
+    p.set_scatter(0)                             # deterministic summation: slot-writing pass and gather
+    for _ in range(2):
+        p.jv_dev(y, v, o, hbgls.PAPER, hbgls.FP32, 300.0, stream=s)
+    p.set_scatter(1)
     p.assemble_dev(y, hbgls.FP32, stream=s)
     for _ in range(3):
         p.jv_dev(y, v, o, hbgls.ASSEMBLED, hbgls.FP32, 300.0, stream=s)
@@ -898,8 +903,11 @@ def profile_small(n_tets: int):
     cs = W.coronary_spec(n_tets=30_000, n_h=4)
     cp = hbgls.Problem.from_spec(cs)
     net = hbgls.MPNN(cs.n_h, seed=3)
+    pred = None
     for _ in range(2):
-        net.predict(cp)
+        pred = net.predict(cp)
+    for _ in range(2):                           # training steps (backward, weight gradients, Adam) towards a
+        net.train_step(cp, 0.5 * pred, 1e-3)     # stand-in target: the kernels' work does not depend on it
     torch.cuda.synchronize()
     print(json.dumps({"profile_small": {"n_tets": spec.mesh.n_tets, "n_nodes": n, "patches": p.info()["n_patches32"],
                                         "gmres_iters": rep["gmres_iters"]}}))
