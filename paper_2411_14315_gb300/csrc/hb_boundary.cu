@@ -176,17 +176,21 @@ __global__ void det_gather_kernel(DetGatherArgs<T> a) {
     if (presc) {
         if (f < 3) s = a.presc == 2 ? a.v[A * 4 * N + r] : T(a.presc == 1 ? 1 : 0);
     } else {
-        // four slot loads in flight at a time; the additions keep the list order
+        // sixteen slot indices, then sixteen slot values in flight at a time (a node has ~20 element slots);
+        // the additions keep the list order
+        constexpr int U = 16;
         const int k0 = a.eptr[A], k1 = a.eptr[A + 1];
-        int k = k0;
-        for (; k + 4 <= k1; k += 4) {
-            T x[4];
+        for (int k = k0; k < k1; k += U) {
+            int e[U];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) x[j] = a.cbuf[(size_t(a.eslot[k + j]) * F + f) * N + n];
+            for (int j = 0; j < U; ++j) e[j] = k + j < k1 ? __ldg(a.eslot + k + j) : -1;
+            T x[U];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) s += x[j];
+            for (int j = 0; j < U; ++j) x[j] = e[j] >= 0 ? __ldg(a.cbuf + (size_t(e[j]) * F + f) * N + n) : T(0);
+#pragma unroll
+            for (int j = 0; j < U; ++j)
+                if (k + j < k1) s += x[j];
         }
-        for (; k < k1; ++k) s += a.cbuf[(size_t(a.eslot[k]) * F + f) * N + n];
         if (a.fptr && f < 3)
             for (int k = a.fptr[A]; k < a.fptr[A + 1]; ++k) s += a.fbuf[(size_t(a.fslot[k]) * 3 + f) * N + n];
     }
