@@ -839,6 +839,58 @@ struct DetBufs<double> {
     static DBuf<double> &f(hb_problem *p) { return p->det_f64; }
 };
 
+// Kernel arguments of the element pass over patch set ps and of the boundary-face kernels, from the
+// problem's current settings (one place for every caller: operators, the no-allocation product, batches)
+template <typename T>
+ElemArgs<T> elem_args(hb_problem *p, PatchSetDev<T> &ps, const T *y, const T *v, T *out, double shift,
+                      const double *shift_dev) {
+    ElemArgs<T> ea;
+    ea.pv = ps.view();
+    ea.y = y;
+    ea.v = v;
+    ea.out = out;
+    ea.H = Hmat<T>(p);
+    ea.flag = p->d_flag.p;
+    ea.N = p->N;
+    ea.rho = T(p->rho);
+    ea.mu = T(p->mu);
+    ea.shift = T(shift);
+    ea.shift_dev = shift_dev;
+    ea.omega2 = T(p->omega2 + tau_dt_term(p));
+    ea.ls_mass = p->ls_mass;
+    ea.variant = p->jvp_variant;
+    ea.err = p->d_err.p;
+    ea.rbvms = p->stab;
+    return ea;
+}
+
+template <typename T>
+FaceArgs<T> face_args(hb_problem *p, const T *y, const T *v, T *out) {
+    FaceArgs<T> fa;
+    fa.n_faces = p->n_nf;
+    fa.fnodes = p->d_nf_nodes.p;
+    fa.foutlet = p->d_nf_out.p;
+    fa.flag = p->d_flag.p;
+    fa.y = y;
+    fa.v = v;
+    fa.out = out;
+    fa.N = p->N;
+    fa.rho = T(p->rho);
+    fa.beta = T(p->beta);
+    if constexpr (sizeof(T) == 4) {
+        fa.fgeo = p->d_nf_geo32.p;
+        fa.hbase = p->d_hbase32.p;
+        fa.R = p->d_R32.p;
+        fa.Q = p->d_Q32.p;
+    } else {
+        fa.fgeo = p->d_nf_geo64.p;
+        fa.hbase = p->d_hbase64.p;
+        fa.R = p->d_R64.p;
+        fa.Q = p->d_Q64.p;
+    }
+    return fa;
+}
+
 template <typename T>
 hb_status apply_op(hb_problem *p, int mode, const T *y, const T *v, T *out, double shift, cudaStream_t s,
                    const double *shift_dev = nullptr) {
@@ -889,23 +941,7 @@ hb_status apply_op(hb_problem *p, int mode, const T *y, const T *v, T *out, doub
     const int fmode = mode == MODE_JVA ? MODE_JVP : mode;     // boundary terms of the paper tangent
     PatchSetDev<T> &ps = patches<T>(p, fmode);
     if (mode != MODE_JVA && !det) HB_CUDA(cudaMemsetAsync(out, 0, size_t(p->n_nodes) * 4 * N * sizeof(T), s));
-    ElemArgs<T> ea;
-    ea.pv = ps.view();
-    ea.y = y;
-    ea.v = v;
-    ea.out = out;
-    ea.H = Hmat<T>(p);
-    ea.flag = p->d_flag.p;
-    ea.N = N;
-    ea.rho = T(p->rho);
-    ea.mu = T(p->mu);
-    ea.shift = T(shift);
-    ea.shift_dev = shift_dev;
-    ea.omega2 = T(p->omega2 + tau_dt_term(p));
-    ea.ls_mass = p->ls_mass;
-    ea.variant = p->jvp_variant;
-    ea.err = p->d_err.p;
-    ea.rbvms = p->stab;
+    ElemArgs<T> ea = elem_args<T>(p, ps, y, v, out, shift, shift_dev);
     if (det && ps.P > 0 && mode != MODE_JVA) {
         DBuf<T> &cb = DetBufs<T>::c(p);
         HB_TRY(dalloc(p, cb, size_t(p->n_tets) * size_t(det_slot_values(mode)) * size_t(N)));
@@ -929,28 +965,7 @@ hb_status apply_op(hb_problem *p, int mode, const T *y, const T *v, T *out, doub
         if (p->prof_on) HB_CUDA(cudaEventRecord(e1, s));
     }
     if (mode != MODE_DIAG && p->n_nf > 0) {
-        FaceArgs<T> fa;
-        fa.n_faces = p->n_nf;
-        fa.fnodes = p->d_nf_nodes.p;
-        fa.foutlet = p->d_nf_out.p;
-        fa.flag = p->d_flag.p;
-        fa.y = y;
-        fa.v = v;
-        fa.out = out;
-        fa.N = N;
-        fa.rho = T(p->rho);
-        fa.beta = T(p->beta);
-        if constexpr (sizeof(T) == 4) {
-            fa.fgeo = p->d_nf_geo32.p;
-            fa.hbase = p->d_hbase32.p;
-            fa.R = p->d_R32.p;
-            fa.Q = p->d_Q32.p;
-        } else {
-            fa.fgeo = p->d_nf_geo64.p;
-            fa.hbase = p->d_hbase64.p;
-            fa.R = p->d_R64.p;
-            fa.Q = p->d_Q64.p;
-        }
+        FaceArgs<T> fa = face_args<T>(p, y, v, out);
         if (det) {
             DBuf<T> &fb = DetBufs<T>::f(p);
             HB_TRY(dalloc(p, fb, size_t(p->n_nf) * 9 * size_t(N)));
@@ -1679,49 +1694,17 @@ template <typename T>
 hb_status apply_jv_noalloc(hb_problem *p, int mode, const T *y, const T *v, T *out, double shift, cudaStream_t s,
                            T *qscratch) {
     PatchSetDev<T> &ps = patches<T>(p, mode);
-    const int N = p->N;
-    HB_CUDA(cudaMemsetAsync(out, 0, size_t(p->n_nodes) * 4 * N * sizeof(T), s));
-    ElemArgs<T> ea;
-    ea.pv = ps.view();
-    ea.y = y;
-    ea.v = v;
-    ea.out = out;
-    ea.H = Hmat<T>(p);
-    ea.flag = p->d_flag.p;
-    ea.N = N;
-    ea.rho = T(p->rho);
-    ea.mu = T(p->mu);
-    ea.shift = T(shift);
-    ea.variant = p->jvp_variant;
-    ea.omega2 = T(tau_dt_term(p));
-    ea.rbvms = p->stab;
+    HB_CUDA(cudaMemsetAsync(out, 0, size_t(p->n_nodes) * 4 * p->N * sizeof(T), s));
+    // no W rows (the in-patch H product) and no device-side shift: the same arguments as every other pass
+    const ElemArgs<T> ea = elem_args<T>(p, ps, y, v, out, shift, nullptr);
     if (ps.P > 0) {
         launch_elem<T>(mode, ea, ps.P, s);
         HB_LAUNCHED(p, 1);
     }
     if (p->n_nf > 0) {
-        FaceArgs<T> fa;
-        fa.n_faces = p->n_nf;
-        fa.fnodes = p->d_nf_nodes.p;
-        fa.foutlet = p->d_nf_out.p;
-        fa.flag = p->d_flag.p;
-        fa.y = y;
-        fa.v = v;
-        fa.out = out;
-        fa.N = N;
-        fa.rho = T(p->rho);
-        fa.beta = T(p->beta);
-        if constexpr (sizeof(T) == 4) {
-            fa.fgeo = p->d_nf_geo32.p;
-            fa.hbase = p->d_hbase32.p;
-            fa.R = p->d_R32.p;
-        } else {
-            fa.fgeo = p->d_nf_geo64.p;
-            fa.hbase = p->d_hbase64.p;
-            fa.R = p->d_R64.p;
-        }
+        FaceArgs<T> fa = face_args<T>(p, y, v, out);
         fa.Q = qscratch;   // the shared array keeps the last call's values: clear it first
-        if (p->has_res) HB_CUDA(cudaMemsetAsync(qscratch, 0, size_t(p->n_out) * N * sizeof(T), s));
+        if (p->has_res) HB_CUDA(cudaMemsetAsync(qscratch, 0, size_t(p->n_out) * p->N * sizeof(T), s));
         launch_faces<T>(mode, fa, p->has_res, p->n_out, s);
         HB_LAUNCHED(p, p->has_res ? 2 : 1);
     }
@@ -2901,19 +2884,8 @@ hb_status batch_record(hb_batch *b) {
         hb_problem *p = b->probs[q];
         PatchSetDev<T> &ps = patches<T>(p, b->mode);
         ElemArgs<T> &ea = args[r];
-        ea.pv = ps.view();
-        ea.y = static_cast<const T *>(b->y[q]);
-        ea.v = static_cast<const T *>(b->v[q]);
-        ea.out = static_cast<T *>(b->out[q]);
-        ea.H = Hmat<T>(p);
-        ea.flag = p->d_flag.p;
-        ea.N = p->N;
-        ea.rho = T(p->rho);
-        ea.mu = T(p->mu);
-        ea.shift = T(b->shift);
-        ea.shift_dev = nullptr;
-        ea.omega2 = T(tau_dt_term(p));
-        ea.rbvms = p->stab;
+        ea = elem_args<T>(p, ps, static_cast<const T *>(b->y[q]), static_cast<const T *>(b->v[q]),
+                          static_cast<T *>(b->out[q]), b->shift, nullptr);
         if (b->mode == MODE_JVP) {
             // the member's node-level W = shift v + rho H v pass runs inside the graph (parallel branches);
             // the batched element pass gathers its rows as the single-problem pass does
@@ -3056,28 +3028,7 @@ hb_status batch_record(hb_batch *b) {
         const T *v = static_cast<const T *>(b->v[q]);
         T *out = static_cast<T *>(b->out[q]);
         if (b->mode != MODE_DIAG && p->n_nf > 0) {
-            FaceArgs<T> fa;
-            fa.n_faces = p->n_nf;
-            fa.fnodes = p->d_nf_nodes.p;
-            fa.foutlet = p->d_nf_out.p;
-            fa.flag = p->d_flag.p;
-            fa.y = y;
-            fa.v = v;
-            fa.out = out;
-            fa.N = p->N;
-            fa.rho = T(p->rho);
-            fa.beta = T(p->beta);
-            if constexpr (sizeof(T) == 4) {
-                fa.fgeo = p->d_nf_geo32.p;
-                fa.hbase = p->d_hbase32.p;
-                fa.R = p->d_R32.p;
-                fa.Q = p->d_Q32.p;
-            } else {
-                fa.fgeo = p->d_nf_geo64.p;
-                fa.hbase = p->d_hbase64.p;
-                fa.R = p->d_R64.p;
-                fa.Q = p->d_Q64.p;
-            }
+            FaceArgs<T> fa = face_args<T>(p, y, v, out);
             if (p->has_res && cudaMemsetAsync(fa.Q, 0, size_t(p->n_out) * p->N * sizeof(T), ss) != cudaSuccess)
                 st = fail(HB_ERR_CUDA, "memset in batch capture");
             launch_faces<T>(b->mode, fa, p->has_res, p->n_out, ss);

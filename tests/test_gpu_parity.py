@@ -241,6 +241,12 @@ def test_full_size_glenn_sampled_parity():
         got = run()[nodes]
         ref = _sampled_oracle(spec, y, vv, nodes, fn)
         assert relerr(got, ref) < 1e-5
+    # the deterministic summation at full size: bitwise equal on repeat, same sampled values
+    gp.set_scatter(0)
+    first = gp.jv(y, v, 0, 1, 0.0)
+    assert np.array_equal(first, gp.jv(y, v, 0, 1, 0.0))
+    assert relerr(first[nodes], _sampled_oracle(spec, y, v, nodes, lambda pr, yy, vv: O.jv_paper(pr, yy, vv))) < 1e-5
+    gp.close()
 
 
 @pytest.mark.parametrize("n_h", [4, 6, 10])
