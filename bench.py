@@ -73,7 +73,7 @@ def parse():
     ap.add_argument("--skip-variants", action="store_true", help="skip the per-launch-variant element timings")
     ap.add_argument("--learned", action="store_true",
                     help="also train the learned warm start on coronary-like tubes (~30k tets, N = 21) from the method's "
-                         "own solves and time cold vs warm solves of held-out tubes (a few minutes)")
+                         "own solves and time cold, warm and learned-correction solves of held-out tubes (minutes)")
     ap.add_argument("--profile-small", type=int, default=0, metavar="TETS",
                     help="run the small-case workload the ncu captures use (a Glenn-like T-junction of ~TETS tets at "
                          "N = 21: FP32 paper-tangent Jv with both tensor-core spectral passes and with deterministic "
@@ -386,10 +386,11 @@ def time_spectral_paths(prob, y32, v32, flush, stream, shift, reps: int = 20):
     return res
 
 
-def time_learned(n_train: int = 32, n_test: int = 8, steps: int = 6000):
+def time_learned(n_train: int = 64, n_test: int = 8, steps: int = 12000):
     """The learned warm start on the coronary-like family (30k tets, N = 21): training data from the method's
     own multigrid-preconditioned mixed solves, training with the project's kernels, then each held-out tube
-    solved cold (default state) and warm (network prediction) to the same absolute residual."""
+    solved cold (default state), warm (network prediction) and with learned correction steps, to the same
+    absolute residual."""
     from paper_2411_14315_gb300 import hbgls
     from paper_2411_14315_gb300 import learned as LR
     t0 = time.perf_counter()
@@ -400,15 +401,19 @@ def time_learned(n_train: int = 32, n_test: int = 8, steps: int = 6000):
     t0 = time.perf_counter()
     losses = LR.train(net, data, steps=steps, lr=3e-3, lr_final=3e-5)
     t_train = time.perf_counter() - t0
-    ev = LR.evaluate(net, LR.coronary_family(range(8000, 8000 + n_test)), precond=2, rtol=1e-8, max_steps=200)
+    ev = LR.evaluate(net, LR.coronary_family(range(8000, 8000 + n_test)), correction=True, precond=2, rtol=1e-8,
+                     max_steps=200)
     out = {"family": "coronary-like tubes, ~30k tets, N = 21, multigrid-preconditioned mixed solves to 1e-8",
            "train_solves": len(data), "rejected": rejected, "generate_s": t_gen, "train_s": t_train,
            "train_steps": steps, "loss_first": losses[0], "loss_last100": float(np.mean(losses[-100:]))}
-    for key in ("cold", "warm"):
+    for key in ("cold", "warm", "correction"):
         out[key] = {"steps": sum(e[key]["steps"] for e in ev), "gmres_iters": sum(e[key]["gmres_iters"] for e in ev),
                     "seconds": sum(e["t_" + key] for e in ev), "converged": sum(e[key]["status"] == 0 for e in ev)}
+    out["per_case"] = [{k: {"steps": e[k]["steps"], "gmres_iters": e[k]["gmres_iters"], "seconds": e["t_" + k]}
+                        for k in ("cold", "warm", "correction")} for e in ev]
     out["pred_rel_err_median"] = float(np.median([e["pred_rel_err"] for e in ev]))
     out["warm_vs_cold_max"] = float(max(e["warm_vs_cold"] for e in ev))
+    out["correction_vs_cold_max"] = float(max(e["correction_vs_cold"] for e in ev))
     net.close()
     for p, _, _ in data:
         p.close()
