@@ -88,3 +88,30 @@ def test_patch_autotuning_keeps_results():
     assert best in (16, 32, 48, 64, 96) and ms > 0
     after = gp.jv(y, v, 1, 1, 0.2)
     assert np.linalg.norm(after - before) <= 2e-6 * np.linalg.norm(before)
+
+
+def test_batch_member_with_deterministic_summation():
+    """In the default layout each member runs its own operator, so a member set to deterministic
+    summation (hb_set_scatter(0)) keeps it inside the batch: bitwise equal on a second replay and equal to
+    its own per-problem call."""
+    torch = pytest.importorskip("torch")
+    from paper_2411_14315_gb300 import hbgls
+    specs, probs = _problems()
+    probs[2].set_scatter(0)
+    ys = [torch.tensor(I.random_state(s.mesh.n_nodes, s.N, 280 + k), dtype=torch.float32, device="cuda")
+          for k, s in enumerate(specs)]
+    vs = [torch.tensor(I.random_state(s.mesh.n_nodes, s.N, 290 + k), dtype=torch.float32, device="cuda")
+          for k, s in enumerate(specs)]
+    outs = [torch.empty_like(y) for y in ys]
+    st = torch.cuda.current_stream()
+    b = hbgls.Batch(probs, 1)
+    b.jv_dev(ys, vs, outs, 0, 0.6, stream=st)
+    st.synchronize()
+    first = outs[2].clone()
+    b.jv_dev(ys, vs, outs, 0, 0.6, stream=st)
+    ref = torch.empty_like(ys[2])
+    probs[2].jv_dev(ys[2], vs[2], ref, 0, 1, 0.6, stream=st)
+    st.synchronize()
+    assert torch.equal(first, outs[2])
+    assert torch.equal(first, ref)
+    b.close()
