@@ -53,14 +53,17 @@ __global__ void outlet_flux_kernel(FaceArgs<T> a, int n_out) {
     }
 }
 
-// Deterministic flow rates: one warp per (outlet, instance) sums the outlet's faces in list order (lane j
-// takes faces j, j + 32, ...) and a fixed butterfly combines the lanes; Q is written, not accumulated.
+// Deterministic flow rates: one block of kFluxThreads per (outlet, instance); thread j sums the outlet's
+// faces j, j + kFluxThreads, ... in list order and a fixed tree combines the threads; Q is written, not
+// accumulated.
+constexpr int kFluxThreads = 256;
 template <typename T, int MODE>
-__global__ void outlet_flux_det_kernel(FaceArgs<T> a) {
+__global__ void __launch_bounds__(kFluxThreads) outlet_flux_det_kernel(FaceArgs<T> a) {
+    __shared__ T red[kFluxThreads];
     const int o = blockIdx.x, n = blockIdx.y, lane = threadIdx.x, N4 = 4 * a.N;
     const T *x = (MODE == MODE_RES) ? a.y : a.v;
     T s = 0;
-    for (int j = a.optr[o] + lane; j < a.optr[o + 1]; j += 32) {
+    for (int j = a.optr[o] + lane; j < a.optr[o + 1]; j += kFluxThreads) {
         const int f = a.oface[j];
         const T nx = a.fgeo[4 * f], ny = a.fgeo[4 * f + 1], nz = a.fgeo[4 * f + 2], S = a.fgeo[4 * f + 3];
         T sf = 0;
@@ -73,8 +76,13 @@ __global__ void outlet_flux_det_kernel(FaceArgs<T> a) {
         }
         s += sf * (S / T(3));
     }
-    for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
-    if (lane == 0) a.Q[o * a.N + n] = s;
+    red[lane] = s;
+    __syncthreads();
+    for (int w = kFluxThreads / 2; w > 0; w >>= 1) {
+        if (lane < w) red[lane] += red[lane + w];
+        __syncthreads();
+    }
+    if (lane == 0) a.Q[o * a.N + n] = red[0];
 }
 
 template <typename T, int MODE>
@@ -176,9 +184,8 @@ __global__ void det_gather_kernel(DetGatherArgs<T> a) {
     if (presc) {
         if (f < 3) s = a.presc == 2 ? a.v[A * 4 * N + r] : T(a.presc == 1 ? 1 : 0);
     } else {
-        // sixteen slot indices, then sixteen slot values in flight at a time (a node has ~20 element slots);
-        // the additions keep the list order
-        constexpr int U = 16;
+        // eight slot indices, then eight slot values in flight at a time; the additions keep the list order
+        constexpr int U = 8;
         const int k0 = a.eptr[A], k1 = a.eptr[A + 1];
         for (int k = k0; k < k1; k += U) {
             int e[U];
@@ -301,13 +308,13 @@ void launch_faces(int mode, const FaceArgs<T> &a, bool has_resistance, int n_out
     if (a.fbuf) {                                  // deterministic scatter
         const dim3 fg(unsigned(n_out), unsigned(a.N));
         if (mode == MODE_RES || mode == MODE_TRES) {
-            if (has_resistance && n_out > 0) outlet_flux_det_kernel<T, MODE_RES><<<fg, 32, 0, s>>>(a);
+            if (has_resistance && n_out > 0) outlet_flux_det_kernel<T, MODE_RES><<<fg, kFluxThreads, 0, s>>>(a);
             face_kernel<T, MODE_RES><<<g, 128, 0, s>>>(a);
         } else if (mode == MODE_JVP) {
-            if (has_resistance && n_out > 0) outlet_flux_det_kernel<T, MODE_JVP><<<fg, 32, 0, s>>>(a);
+            if (has_resistance && n_out > 0) outlet_flux_det_kernel<T, MODE_JVP><<<fg, kFluxThreads, 0, s>>>(a);
             face_kernel<T, MODE_JVP><<<g, 128, 0, s>>>(a);
         } else {
-            if (has_resistance && n_out > 0) outlet_flux_det_kernel<T, MODE_JVE><<<fg, 32, 0, s>>>(a);
+            if (has_resistance && n_out > 0) outlet_flux_det_kernel<T, MODE_JVE><<<fg, kFluxThreads, 0, s>>>(a);
             face_kernel<T, MODE_JVE><<<g, 128, 0, s>>>(a);
         }
         return;
