@@ -111,13 +111,13 @@ hb_status hb_set_stabilization(hb_problem *p, int variant, double ct_dt);
  *      ([element][4 nodes][4 or 7 fields][N]) and each Neumann face in its own
  *      ([face][3 nodes][3 fields][N]); one gather kernel per call sums every node's slots in a fixed
  *      order (elements in patch order, then faces), and the row-wise assembly adds a node's element
- *      blocks in element order.  Resistance-outlet flow rates are summed in face order by one warp per
+ *      blocks in element order.  Resistance-outlet flow rates are summed in face order by one block per
  *      outlet and instance.  No floating-point atomics run, so equal inputs give bitwise equal outputs.
  *      Device memory: about 64 N (FP32) or 128 N (FP64) bytes per element for the paper tangent, 112 N
  *      or 224 N for the residual and the exact Jacobian, allocated on first use.
- * hb_jv_dev_noalloc and batches keep the atomic summation.  Synchronises the problem's stream; drops
- * the last assembly.  INVALID_ARG for another value; hb_get_scatter returns the current setting (-1 for
- * a null problem). */
+ * hb_jv_dev_noalloc and batch layouts 0 and 1 keep the atomic summation (hb_batch_set_grouping).
+ * Synchronises the problem's stream; drops the last assembly.  INVALID_ARG for another value;
+ * hb_get_scatter returns the current setting (-1 for a null problem). */
 hb_status hb_set_scatter(hb_problem *p, int scatter);
 int hb_get_scatter(const hb_problem *p);
 
