@@ -363,7 +363,9 @@ hb_status hb_get_march_samples(hb_problem *p, double *out);
  * instead run one persistent element pass over every member (or one per instance count) whose work items
  * (problem, patch) come from a global counter; they sum with atomics whatever hb_set_scatter says.
  * All problems must live on one device; their boundary data are prepared at creation.  The graph is
- * captured on first use and again whenever the operands, kind, shift or layout change.  Work is ordered
+ * captured on first use and again whenever the operands, kind, shift or layout change, or a member's
+ * boundary data or settings (backflow, stabilisation, summation, spectral path, launch variant,
+ * patches) changed since the capture.  Work is ordered
  * after `stream` (NULL: the first problem's stream) and `stream` waits for it. */
 typedef struct hb_batch hb_batch;
 /* Create a batch over `count` problems (not owned; they must outlive the batch) at precision 0 or 1. */

@@ -163,7 +163,12 @@ struct hb_problem {
         int m = 0, precision = -1, precond = -1;
         double shift = 0;
         int64_t launches = 0;
+        uint64_t gen = 0;              // the problem's settings generation it was captured at
     } cycle[3];                        // paper tangent, exact Jacobian, assembled paper tangent
+    // settings generation: bumped by every change that captured launches depend on (kernel arguments
+    // taken by value, buffers that can be reallocated): boundary data, patches, backflow, stabilisation,
+    // summation mode, spectral path, launch variant.  Captured graphs are replayed only at their own.
+    uint64_t gen = 0;
     DBuf<double> gm;
     DBuf<int> gate;
     DBuf<double> shift_dev;
@@ -419,6 +424,7 @@ void node_slot_lists(const std::vector<int> &node_of_slot, int64_t n_nodes, std:
 template <typename T>
 hb_status make_patchset(hb_problem *p, PatchSetDev<T> &ps, const std::vector<int32_t> &tets_ord, size_t budget,
                         int nl_override = 0, int size_mode = MODE_JVP) {
+    ++p->gen;                                     // new patch buffers
     const int NL = nl_override > 0 ? std::min(nl_override, 255) : choose_nl(p->N, sizeof(T), budget, size_mode);
     const int EP = 3 * NL;
     HostPatches hp = build_patches(tets_ord, p->n_tets, p->n_nodes, NL, EP, std::max(1, 31 / p->N));
@@ -695,6 +701,7 @@ hb_status prepare_bc(hb_problem *p) {
     }
     HB_CUDA(cudaStreamSynchronize(p->stream));
     p->bc_dirty = false;
+    ++p->gen;
     return HB_OK;
 }
 
@@ -1507,7 +1514,9 @@ hb_status cycle_graph(hb_problem *p, const OpCtx &c, int m, hb_problem::CycleGra
     hb_problem::CycleGraph &gc = p->cycle[c.mode == MODE_JVE ? 1 : c.mode == MODE_JVA ? 2 : 0];
     out = &gc;
     const double key = c.shift_dev ? -1.0 : c.shift;
-    if (gc.exec && gc.m == m && gc.precision == c.precision && gc.shift == key && gc.precond == c.precond) return HB_OK;
+    if (gc.exec && gc.m == m && gc.precision == c.precision && gc.shift == key && gc.precond == c.precond &&
+        gc.gen == p->gen)
+        return HB_OK;
     if (gc.exec) {
         cudaGraphExecDestroy(gc.exec);
         gc.exec = nullptr;
@@ -1532,6 +1541,7 @@ hb_status cycle_graph(hb_problem *p, const OpCtx &c, int m, hb_problem::CycleGra
     gc.precision = c.precision;
     gc.precond = c.precond;
     gc.shift = key;
+    gc.gen = p->gen;
     gc.launches = p->launches - l0;
     p->launches = l0;
     return HB_OK;
@@ -2070,6 +2080,7 @@ hb_status hb_set_backflow(hb_problem *p, double beta) {
     if (!p) return fail(HB_ERR_INVALID_ARG, "null problem");
     if (!(beta >= 0 && beta <= 1)) return fail(HB_ERR_INVALID_ARG, "beta must be in [0, 1]");
     p->beta = beta;
+    ++p->gen;                                     // face kernels take beta by value
     return HB_OK;
 }
 
@@ -2794,6 +2805,7 @@ struct hb_batch {
     std::vector<void *> out;
     int64_t launches_per_replay = 0, launches = 0;
     int grouping = 2;                     // launch layout (hb_batch_set_grouping): 2 = members on parallel branches
+    std::vector<uint64_t> gens;           // the members' settings generations at the last capture
     static constexpr int kSide = 8;       // side streams of the captured graph's parallel branches
     cudaStream_t side[kSide] = {};
 };
@@ -3119,8 +3131,10 @@ hb_status hb_batch_jv_dev(hb_batch *b, const void *const *y, const void *const *
     HB_CUDA(cudaSetDevice(b->device));
     const size_t n = b->probs.size();
     const int mode = kind == 0 ? MODE_JVP : MODE_JVE;
-    bool same = b->exec && b->mode == mode && b->shift == shift && b->y.size() == n;
-    for (size_t q = 0; same && q < n; ++q) same = (b->y[q] == y[q] && b->v[q] == v[q] && b->out[q] == jv[q]);
+    for (size_t q = 0; q < n; ++q) HB_TRY(prepare_bc(b->probs[q]));   // boundary data changed since the capture
+    bool same = b->exec && b->mode == mode && b->shift == shift && b->y.size() == n && b->gens.size() == n;
+    for (size_t q = 0; same && q < n; ++q)
+        same = (b->y[q] == y[q] && b->v[q] == v[q] && b->out[q] == jv[q] && b->gens[q] == b->probs[q]->gen);
     for (size_t q = 0; q < n; ++q)
         if (!y[q] || !v[q] || !jv[q] || jv[q] == y[q] || jv[q] == v[q])
             return fail(HB_ERR_INVALID_ARG, "null or aliased operand in batch");
@@ -3130,8 +3144,15 @@ hb_status hb_batch_jv_dev(hb_batch *b, const void *const *y, const void *const *
         b->y.assign(y, y + n);
         b->v.assign(v, v + n);
         b->out.assign(jv, jv + n);
-        if (b->precision == 0) HB_TRY(batch_record<double>(b));
-        else HB_TRY(batch_record<float>(b));
+        const hb_status st = b->precision == 0 ? batch_record<double>(b) : batch_record<float>(b);
+        if (st != HB_OK) {                        // no graph of other operands may be replayed later
+            if (b->exec) cudaGraphExecDestroy(b->exec);
+            b->exec = nullptr;
+            b->mode = -1;
+            return st;
+        }
+        b->gens.resize(n);
+        for (size_t q = 0; q < n; ++q) b->gens[q] = b->probs[q]->gen;
     }
     cudaStream_t user = stream ? static_cast<cudaStream_t>(stream) : b->probs[0]->stream;
     cudaEvent_t ev;
@@ -3263,6 +3284,7 @@ hb_status hb_set_stabilization(hb_problem *p, int variant, double ct_dt) {
     if (p->stream) cudaStreamSynchronize(p->stream);
     p->stab = variant;
     p->ct_dt = ct_dt;
+    ++p->gen;
     // captured GMRES cycles hold the old kernel arguments; assembled coefficients hold the old tau
     for (auto &gc : p->cycle) {
         if (gc.exec) cudaGraphExecDestroy(gc.exec);
@@ -3279,6 +3301,7 @@ hb_status hb_set_scatter(hb_problem *p, int scatter) {
     cudaSetDevice(p->device);
     if (p->stream) cudaStreamSynchronize(p->stream);
     p->scatter = scatter;
+    ++p->gen;
     for (auto &gc : p->cycle) {                   // captured cycles hold the old launches
         if (gc.exec) cudaGraphExecDestroy(gc.exec);
         gc = hb_problem::CycleGraph{};
@@ -3295,6 +3318,7 @@ int hb_get_scatter(const hb_problem *p) { return p ? p->scatter : -1; }
 hb_status hb_set_spectral_path(hb_problem *p, int path) {
     if (!p) return fail(HB_ERR_INVALID_ARG, "null problem");
     if (path < 0 || path > 2) return fail(HB_ERR_INVALID_ARG, "path must be 0 (tcgen05), 1 (mma.sync) or 2 (FMA)");
+    if (path != p->spectral_path) ++p->gen;
     p->spectral_path = path;
     for (auto &gc : p->cycle) {                   // captured cycles hold the old launch
         if (gc.exec) cudaGraphExecDestroy(gc.exec);
@@ -3308,6 +3332,7 @@ int hb_get_spectral_path(const hb_problem *p) { return p ? p->spectral_path : -1
 hb_status hb_set_launch_variant(hb_problem *p, int variant) {
     if (!p) return fail(HB_ERR_INVALID_ARG, "null problem");
     if (variant < 0 || variant >= kJvpVariants) return fail(HB_ERR_INVALID_ARG, "unknown launch variant");
+    if (variant != p->jvp_variant) ++p->gen;
     p->jvp_variant = variant;
     return HB_OK;
 }

@@ -115,3 +115,34 @@ def test_batch_member_with_deterministic_summation():
     assert torch.equal(first, outs[2])
     assert torch.equal(first, ref)
     b.close()
+
+
+def test_batch_recaptures_after_a_member_setting_changes():
+    """A member switched to full RBVMS after the batch's first use (same operands, kind and shift) is
+    applied with the new setting on the next batched call: its exact-Jacobian product then equals its own
+    per-problem call and differs from the one before."""
+    torch = pytest.importorskip("torch")
+    from paper_2411_14315_gb300 import hbgls
+    specs, probs = _problems()
+    ys = [torch.tensor(I.random_state(s.mesh.n_nodes, s.N, 380 + k), dtype=torch.float32, device="cuda")
+          for k, s in enumerate(specs)]
+    vs = [torch.tensor(I.random_state(s.mesh.n_nodes, s.N, 390 + k), dtype=torch.float32, device="cuda")
+          for k, s in enumerate(specs)]
+    outs = [torch.empty_like(y) for y in ys]
+    st = torch.cuda.current_stream()
+    for grouping in (2, 0):
+        probs[2].set_stabilization(0, 0.0)
+        b = hbgls.Batch(probs, 1)
+        b.set_grouping(grouping)
+        b.jv_dev(ys, vs, outs, 1, 0.6, stream=st)
+        st.synchronize()
+        before = outs[2].double().cpu().numpy()
+        probs[2].set_stabilization(1, 0.0)
+        b.jv_dev(ys, vs, outs, 1, 0.6, stream=st)
+        ref = torch.empty_like(ys[2])
+        probs[2].jv_dev(ys[2], vs[2], ref, 1, 1, 0.6, stream=st)
+        st.synchronize()
+        after, ref = outs[2].double().cpu().numpy(), ref.double().cpu().numpy()
+        assert np.linalg.norm(after - ref) <= 2e-6 * np.linalg.norm(ref), grouping
+        assert np.linalg.norm(after - before) > 1e-4 * np.linalg.norm(ref), grouping
+        b.close()
