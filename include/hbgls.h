@@ -176,6 +176,9 @@ typedef struct {
                                  integrals): 1 (default) floating-point atomics; 0 deterministic (the
                                  colour-free equivalent of a colour-class scatter, see hb_set_scatter).
                                  hb_solve applies it to the problem (it stays set afterwards)          */
+    double backflow_beta;     /* >= 0: backflow stabilisation coefficient beta in [0, 1] (Sec. 2.3),
+                                 applied to the problem as hb_set_backflow would (it stays set); < 0
+                                 (default): keep the problem's value                                   */
 } hb_solve_opts;
 
 typedef struct {

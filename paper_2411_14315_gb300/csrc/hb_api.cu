@@ -2223,6 +2223,7 @@ hb_status hb_default_opts(hb_solve_opts *o) {
     o->precond = 0;
     o->line_search = 1;
     o->scatter = 1;
+    o->backflow_beta = -1.0;
     return HB_OK;
 }
 
@@ -2245,6 +2246,7 @@ hb_status hb_solve(hb_problem *p, const hb_solve_opts *opts, hb_report *rep) {
         return fail(HB_ERR_INVALID_ARG, "precond must be 0 (Jacobi), 1 (node blocks) or 2 (aggregation multigrid)");
     HB_CUDA(cudaSetDevice(p->device));
     if (o.scatter != p->scatter) HB_TRY(hb_set_scatter(p, o.scatter));
+    if (o.backflow_beta >= 0 && o.backflow_beta != p->beta) HB_TRY(hb_set_backflow(p, o.backflow_beta));
     if (o.use_learned < 0 || o.use_learned > 2) return fail(HB_ERR_INVALID_ARG, "use_learned must be 0, 1 or 2");
     p->learned_dir = false;
     if (o.use_learned) {

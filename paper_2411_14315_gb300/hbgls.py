@@ -41,7 +41,7 @@ class hb_solve_opts(C.Structure):
                 ("dt_pseudo", C.c_double), ("cfl", C.c_double), ("use_learned", C.c_int),
                 ("verbose", C.c_int), ("ser", C.c_int), ("ser_max", C.c_double), ("r_ref", C.c_double),
                 ("assembled", C.c_int), ("precond", C.c_int), ("line_search", C.c_int),
-                ("scatter", C.c_int)]
+                ("scatter", C.c_int), ("backflow_beta", C.c_double)]
 
 
 class hb_report(C.Structure):
