@@ -103,6 +103,9 @@ def test_defaults_are_filled(lib):
     o = hbgls.hb_solve_opts()
     assert lib.hb_default_opts(C.byref(o)) == 0
     assert o.precision == 1 and 1 <= o.gmres_restart <= 200 and o.rtol > 0 and o.max_steps > 0
+    # the paper's settings of Sec. 2.3 where it states them; the extensions default to "unchanged"
+    assert o.gmres_rtol_pseudo == 0.03 and o.switch_rtol == 1e-3
+    assert o.scatter == 1 and o.backflow_beta < 0 and o.precond == 0 and o.line_search == 1
     mo = hbgls.hb_march_opts()
     assert lib.hb_default_march_opts(C.byref(mo)) == 0
     assert mo.gmres_rtol == 0.03 and mo.newton_rtol == 1e-3 and mo.periods == 4 and mo.rho_inf == 0.5
